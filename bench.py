@@ -1,0 +1,367 @@
+"""Benchmark: SIDWT-domain multiresolution correlation throughput on GB300.
+
+Workload (one "step" = one pass of the whole path over one batch):
+  4096 received complex64 pulses, N = 8192, J = 5; pulses 0-2047 echo an LFM
+  chirp (TB = 256), pulses 2048-4095 a Barker-13 code (16 samples / chip),
+  seeded delays, SNR uniform in 0-20 dB.  Per step:
+    * the two stored references' SIDWT trees for LeGall 5/3, CDF 9/7 and the
+      reversible integer 5/3 (reference store, 6 trees);
+    * all-lag, all-scale correlation + peaks of every pulse against its
+      reference with 5/3 and with 9/7 (8192 pairs);
+    * the int16 I/Q reversible integer 5/3 analysis of the 4096 pulses.
+  Metric: GSamples/s = pairs x N / step time (all N lags at all J+1 scales).
+
+`python bench.py --gpus N --steps K --warmup W` prints one JSON line.
+`--impl reference` times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "SIDWT-correlation GSamples/s (all lags, all scales)"
+UNIT = "GSamples/s"
+WORKLOAD = "two-reference batch: 4096 complex64 pulses x N=8192, J=5, LeGall 5/3 + CDF 9/7 (+ int16 reversible 5/3 analysis)"
+B, N, J = 4096, 8192, 5
+FILTER_IDS = {"legall53": 1, "cdf97": 2}
+
+
+def flops_per_pair(N: int, J: int) -> float:
+    """Algorithmic flops of one pair: 8 real flops per complex MAC, N lags,
+    sum over scales of the correlated coefficient count N (2 - 2^-J)."""
+    return 8.0 * N * N * (2.0 - 2.0 ** (-J))
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            out = ROOT / "gpurun_out"
+            out.mkdir(exist_ok=True)
+            self.path = out / f"clocks_{os.getpid()}.csv"
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={CLOCK_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.path.read_text().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# roofline helpers
+# --------------------------------------------------------------------------
+def measured_peaks() -> dict:
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        return json.loads(p.read_text())
+    return {}
+
+
+def source_sha(path: Path) -> str:
+    return hashlib.sha256(path.read_bytes()).hexdigest()[:16]
+
+
+def committed_traffic(kernel: str, src: Path) -> float | None:
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source."""
+    p = ROOT / "profiles" / "traffic.json"
+    if not p.exists():
+        return None
+    d = json.loads(p.read_text()).get(kernel)
+    if not d or d.get("source_sha") != source_sha(src):
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+# --------------------------------------------------------------------------
+# CPU oracle baseline
+# --------------------------------------------------------------------------
+def cpu_oracle_sample(w, seconds: float = 12.0, max_pairs: int = 4096):
+    """Time the FP64 oracle on whole pairs of the same workload until about
+    `seconds` of wall time have been spent (at least one batch)."""
+    from oracle import oracle as O
+    O.lib()
+    cores = os.cpu_count() or 1
+    pairs = 0
+    t0 = time.perf_counter()
+    used = 1
+    batch_i = 0
+    while True:
+        idx = (np.arange(cores) * 37 + batch_i * cores * 37 + 11) % B
+        X = w["refs"][w["ref_ids"][idx]].astype(np.complex128)
+        Y = w["y"][idx].astype(np.complex128)
+        fid = FILTER_IDS["legall53"] if batch_i % 2 == 0 else FILTER_IDS["cdf97"]
+        _, _, _, _, used = O.correlate_batch(fid, X, Y, J, form=1, want_r=False, nthreads=cores)
+        pairs += len(idx)
+        batch_i += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or pairs >= max_pairs:
+            break
+    return {"pairs": pairs, "seconds": el, "cores": used, "value": pairs * N / el / 1e9}
+
+
+def run_reference(args):
+    from paper_cs_0607001_gb300 import inputs
+    from paper_cs_0607001_gb300 import multigpu as M
+    rank, world, _ = M.dist_env()
+    if rank != 0:
+        return 0
+    w = inputs.two_ref_batch(B=B, N=N, J=J)
+    cores = os.cpu_count() or 1
+    step_seconds = min(10.0, max(2.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, seconds=step_seconds / 4)
+    vals, pairs, secs, used = [], 0, 0.0, cores
+    for _ in range(args.steps):
+        r = cpu_oracle_sample(w, seconds=step_seconds)
+        vals.append(r["value"])
+        pairs += r["pairs"]
+        secs += r["seconds"]
+        used = r["cores"]
+    value = pairs * N / secs / 1e9
+    sample = f"{pairs} of the workload's 8192 (pulse, filter) pairs over {args.steps} steps, N={N}, J={J}, 5/3 and 9/7 alternating"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pairs_per_step_full": 2 * B, "N": N, "J": J},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_cs_0607001_gb300 import inputs
+    from paper_cs_0607001_gb300 import multigpu as M
+    from paper_cs_0607001_gb300 import sidwt as S
+
+    rank, world, local = M.init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    S.lib()
+    w = inputs.two_ref_batch(B=B, N=N, J=J)
+    refs_c = torch.from_numpy(w["refs"]).to(dev)
+    y_c = torch.from_numpy(w["y"]).to(dev)
+    ids = torch.from_numpy(w["ref_ids"]).to(dev)
+    y_i16_host = inputs.to_iq16(w["y"].astype(np.complex128))
+    refs_i16 = torch.from_numpy(inputs.to_iq16(w["refs"].astype(np.complex128))).to(dev)
+    y_i16 = torch.from_numpy(y_i16_host).to(dev)
+
+    prec = args.precision
+    plans = {"legall53": S.Plan("legall53", N, J), "cdf97": S.Plan("cdf97", N, J)}
+    pint = S.Plan("legall53_int", N, J)
+    for p in list(plans.values()) + [pint]:
+        p.reserve(2, B)
+    outs = {k: (torch.empty((B, J + 1), dtype=torch.int32, device=dev),
+                torch.empty((B, J + 1), dtype=torch.float32, device=dev),
+                torch.empty((B, J + 1), dtype=torch.float64, device=dev)) for k in plans}
+    int_en = torch.empty((B, J + 1), dtype=torch.float64, device=dev)
+
+    def step():
+        for p in plans.values():
+            p.reset_references()
+            p.store_reference(refs_c[0])
+            p.store_reference(refs_c[1])
+        pint.reset_references()
+        pint.store_reference(refs_i16[0])
+        pint.store_reference(refs_i16[1])
+        for k, p in plans.items():
+            p.correlate(ids, y_c, precision=prec)
+            p.peaks_into(B, *outs[k])
+        pint.analyze_into(y_i16, None, int_en)
+
+    # warm-up (also checks the peaks land on the injected delays at scale 0)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    lag0 = outs["cdf97"][0][:, 0].cpu().numpy()
+    hit = float(np.mean(lag0 == w["delays"]))
+
+    for p in plans.values():
+        p.read_timing(reset=True)
+        p.set_timing(True)
+    pint.set_timing(True)
+    pint.read_timing(reset=True)
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    M.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    M.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = M.max_over_ranks(ms)
+    tims = {k: p.read_timing(reset=True) for k, p in plans.items()}
+    ti = pint.read_timing(reset=True)
+    for p in list(plans.values()) + [pint]:
+        p.set_timing(False)
+    launches = sum(t["launches"] for t in tims.values()) + ti["launches"]
+
+    pairs = 2 * B
+    value = world * pairs * N / (ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (the correlation)
+    corr_ms = sum(t["correlate_ms"] for t in tims.values()) / sum(t["correlate_calls"] for t in tims.values())
+    flops_launch = flops_per_pair(N, J) * B
+    achieved = flops_launch / (corr_ms * 1e-3) / 1e12
+    peaks = measured_peaks()
+    if prec == "fp32":
+        # FP32 CUDA-core peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz
+        peak = 152 * 128 * 2 * 2.070e9 / 1e12
+        bound, peak_src = "alu", "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz"
+    else:
+        peak = peaks.get("bf16_tflops_sustained", 1705.3) / 3.0
+        bound, peak_src = "tensor", "measured bf16 dense (sustained) / 3 products"
+    src = ROOT / "paper_cs_0607001_gb300" / "csrc" / ("corr_simt.cu" if prec == "fp32" else "corr_tc.cu")
+    kname = "corr_simt_kernel" if prec == "fp32" else "corr_tc_kernel"
+    traffic = committed_traffic(kname, src)
+    stage = {k: {s: round(t[s] / max(1, t["correlate_calls"]), 4) for s in
+                 ("group_ms", "analyze_ms", "correlate_ms", "peaks_ms")} for k, t in tims.items()}
+    stage["store_ms_per_step"] = round(sum(t["store_ms"] for t in tims.values()) / args.steps + ti["store_ms"] /
+                                       args.steps, 4)
+    stage["int53_analyze_ms"] = round(ti["analyze_ms"] / args.steps, 4)
+
+    # end to end through the host-buffer C-ABI call: pinned y in, peaks out
+    e2e = None
+    if not args.no_e2e:
+        y_pin = torch.from_numpy(w["y"]).pin_memory()
+        ids_pin = torch.from_numpy(w["ref_ids"]).pin_memory()
+        hout = {k: (torch.empty((B, J + 1), dtype=torch.int32).pin_memory(),
+                    torch.empty((B, J + 1), dtype=torch.float32).pin_memory(),
+                    torch.empty((B, J + 1), dtype=torch.float64).pin_memory()) for k in plans}
+
+        def e2e_step():
+            for k, p in plans.items():
+                p.correlate_host(ids_pin, y_pin, precision=prec, lag=hout[k][0], mag=hout[k][1], norm=hout[k][2])
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        M.barrier()
+        t0 = time.perf_counter()
+        k_e2e = max(1, args.steps)
+        for _ in range(k_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = M.max_over_ranks((time.perf_counter() - t0) / k_e2e)
+        h2d = 2 * (y_pin.numel() * 8 + ids_pin.numel() * 4)
+        d2h = 2 * B * (J + 1) * (4 + 4 + 8)
+        e2e = {"value": world * pairs * N / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": el * 1e3,
+               "path": "sidwt_correlate_host per filter (pinned host y -> device, peaks -> host)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        r = cpu_oracle_sample(w, seconds=args.cpu_seconds)
+        cpu = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+               "sample": f"{r['pairs']} whole (pulse, filter) pairs of this workload (N={N}, J={J}, all lags and "
+                         f"scales, peaks), {r['seconds']:.1f} s wall"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "bf16x3", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pulses": B, "N": N, "J": J, "pairs_per_step": pairs,
+                   "precision": prec, "l2": "inputs larger than L2 (268 MB complex64 + 134 MB int16 per step)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": kname,
+                     "flops_per_launch": flops_launch, "launch_ms": corr_ms, "peak_source": peak_src},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "stages_ms_per_call": stage,
+        "peak_at_injected_delay_scale0": hit,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    for p in list(plans.values()) + [pint]:
+        p.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,199 @@
+/*
+ * sidwt.h -- C ABI of libsidwt, the GB300 (sm_103a) library for
+ * multiresolution correlation of complex signals in the shift-invariant DWT
+ * (SIDWT) domain by lifting (Bhattacharya & Mahapatra, "A Novel Application of
+ * Lifting Scheme for Multiresolution Correlation of Complex Radar Signals").
+ *
+ * Problem (Sec. II, eq. 5-6; Sec. IV, eq. 20-20a).  A stored matching signal
+ * x and received signals y, each N complex samples, are compared at every
+ * circular lag D in [0, N) and at every dyadic scale j = 0..J:
+ *
+ *     r_j[D] = sum_k conj(X_{j,D}[k]) * Y_j[k]
+ *
+ * where X_{j,D} is the level-j primal (x-side) analysis of x delayed by D and
+ * Y_j the level-j dual (y-side) analysis of y (scale 0: the signals
+ * themselves).  The library evaluates the paper's DWT-domain form: for j < J
+ * the level-(j+1) approximation and detail bands of the stored signal's SIDWT
+ * tree (the shift-circulant block matrices of eq. 6 / 20) against the
+ * received pulse's level-(j+1) bands; for j = J the level-J approximations
+ * only (eq. 20a).  Real lifting steps act on Re and Im separately (eq. 19).
+ *
+ * Filters and sides (Sec. III):
+ *   SIDWT_D4           causal Daubechies-4 lifting, eq. 17, on both sides;
+ *                      polyphase pair (v[2n], v[2n-1]).
+ *   SIDWT_LEGALL53     LeGall 5/3: x side P~(z^-1) and y side P^T(z^-1) of
+ *                      Sec. III-C Case I; pair (v[2n], v[2n+1]).
+ *   SIDWT_CDF97        CDF 9/7 with the rational Table I constants: x side
+ *                      P~(z^-1), y side P^T(z^-1) of Sec. III-C Case II.
+ *   SIDWT_LEGALL53_INT reversible integer 5/3 (Sec. I, V-B): floor-rounded
+ *                      steps, diagonal scalings dropped; inputs int16 I/Q,
+ *                      coefficients int32, bit-exact.
+ * Boundary handling is periodic at every level.
+ *
+ * Conventions shared by every entry point:
+ *   - Complex data is interleaved (re, im) float32 ("complex64").  Integer
+ *     plans take int16 (I, Q) pairs and produce int32 (re, im) pairs.
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller and
+ *     must stay valid until the stream work that uses them has finished.
+ *     Pointers named *_host are host pointers read or written before the call
+ *     returns.
+ *   - Calls enqueue work on `stream` (0 = the legacy default stream) and
+ *     return without synchronising unless stated.  Errors detectable on the
+ *     host return at once with a status; asynchronous device errors surface
+ *     as SIDWT_ECUDA from a later call.  sidwt_last_error() describes the
+ *     last failure of the calling thread.  No C++ exception crosses the ABI.
+ *   - A plan is not thread-safe: serialise calls on one plan.
+ */
+#ifndef SIDWT_H
+#define SIDWT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st *sidwt_stream; /* same type as cudaStream_t */
+
+typedef enum {
+    SIDWT_D4 = 0,
+    SIDWT_LEGALL53 = 1,
+    SIDWT_CDF97 = 2,
+    SIDWT_LEGALL53_INT = 3
+} sidwt_filter;
+
+typedef enum {
+    SIDWT_PREC_FP32 = 0,  /* plain FP32 CUDA-core path ("plain")                      */
+    SIDWT_PREC_BF16X3 = 1, /* tcgen05 tensor cores, bf16 hi+lo split, FP32 accumulate */
+    SIDWT_PREC_TF32X3 = 2  /* reserved: 3xTF32 split (returns SIDWT_EUNSUPPORTED)     */
+} sidwt_precision;
+
+typedef enum {
+    SIDWT_OK = 0,
+    SIDWT_EINVAL = 1,      /* bad argument                                 */
+    SIDWT_ENOMEM = 2,      /* device or host allocation failed             */
+    SIDWT_ECUDA = 3,       /* a CUDA call failed (message has the detail)  */
+    SIDWT_ETIMEOUT = 4,    /* a bounded wait ran out                       */
+    SIDWT_EBUSY = 5,       /* resource in use                              */
+    SIDWT_EUNSUPPORTED = 6 /* valid request this build does not implement  */
+} sidwt_status;
+
+typedef struct sidwt_plan sidwt_plan; /* opaque; owns the reference store and workspaces */
+
+/* Library version string, e.g. "libsidwt 0.1 sm_103a". */
+const char *sidwt_version(void);
+
+/* Thread-local description of the last failure ("" if none). */
+const char *sidwt_last_error(void);
+
+/* Create a plan for pulses of N complex samples analysed to J dyadic levels
+ * with filter f (Sec. II: L = 2^J samples; multiples of 2^J are accepted).
+ * EINVAL unless 1 <= J <= 15, N % 2^J == 0, N >= 2^J and N <= 2^26.
+ * *out receives the plan; destroy it with sidwt_plan_destroy. */
+sidwt_status sidwt_plan_create(sidwt_filter f, int64_t N, int J, sidwt_plan **out);
+
+/* Release the plan, its reference store and workspaces.  Synchronises the
+ * device first.  NULL is accepted. */
+sidwt_status sidwt_plan_destroy(sidwt_plan *p);
+
+/* Pre-size the reference store for max_refs references and the workspaces
+ * for batches of up to max_batch pulses, so that later calls allocate
+ * nothing (needed before stream capture). */
+sidwt_status sidwt_plan_reserve(sidwt_plan *p, int32_t max_refs, int64_t max_batch);
+
+/* Number of stored references. */
+int32_t sidwt_plan_num_refs(const sidwt_plan *p);
+
+/* Store a matching signal x (Sec. II eq. 5, Fig. 1 and 5): computes its SIDWT
+ * tree -- for every level l = 1..J and variant v < 2^l, the level-l
+ * approximation A and detail B of x delayed by v -- and the FP64 energies
+ * ||X_{l,v}||^2 (eq. 1), and keeps them on the device.
+ * x_dev: complex64[N] (float plans) or int16[N][2] (integer plan), 8- resp.
+ * 4-byte aligned.  *ref_id_out receives the new reference's id (0, 1, ...).
+ * The store may grow (a device allocation) unless reserved. */
+sidwt_status sidwt_store_reference(sidwt_plan *p, const void *x_dev, int32_t *ref_id_out,
+                                   sidwt_stream stream);
+
+/* Copy reference ref_id's SIDWT tree and energies to caller buffers (either
+ * may be NULL).  tree_dev layout: level l = 1..J at element offset 2N(l-1):
+ * A[2^l][N >> l] then B[2^l][N >> l]; complex64 for float plans, int32 pairs
+ * for the integer plan.  energies_dev: double[2^(J+1) - 1], level l variant v
+ * at 2^l - 1 + v (level 0 is x itself). */
+sidwt_status sidwt_reference_tree(sidwt_plan *p, int32_t ref_id, void *tree_dev, double *energies_dev,
+                                  sidwt_stream stream);
+
+/* Dual-basis analysis of B received pulses (Sec. III, Fig. 3(b) / 4(b)):
+ * all J levels in one pass.  y_dev: [B][N] complex64 (float plans) or
+ * int16[B][N][2] (integer plan).  Results stay in the plan's workspace; if
+ * pyr_dev is not NULL they are also copied there as [B][2N - 2(N >> J)]
+ * elements (complex64 or int32 pairs), level l at offset 2N - 4(N >> l):
+ * c_l[N >> l] then d_l[N >> l].  energies_dev (optional): double[B][J+1],
+ * ||c_j||^2 with c_0 = y. */
+sidwt_status sidwt_analyze(sidwt_plan *p, const void *y_dev, int64_t B, void *pyr_dev, double *energies_dev,
+                           sidwt_stream stream);
+
+/* Correlate B received pulses, pulse b against stored reference
+ * ref_ids_dev[b], at all N lags and all J+1 scales (eq. 20 / 20a), and
+ * locate the peak of every (pulse, scale).  Runs the received analysis, the
+ * correlation and the peak epilogue; results are read with sidwt_peaks.
+ * ref_ids_dev: int32[B]; an id outside [0, num_refs) marks that pulse
+ *   invalid (its peaks read lag -1) and is reported by sidwt_check.
+ * y_dev: as for sidwt_analyze.
+ * prec: SIDWT_PREC_FP32 or SIDWT_PREC_BF16X3.
+ * r_dev: optional complex64[B][J+1][N], r_j[D] at [b][j][D]; NULL skips it
+ *   (the full output is large: B (J+1) N 8 bytes). */
+sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const void *y_dev, int64_t B,
+                             sidwt_precision prec, void *r_dev, sidwt_stream stream);
+
+/* Peaks of the last sidwt_correlate on this plan (B must match it), per
+ * pulse b and scale j at [b][j]: lag_dev int32 (delay D of the stored signal
+ * with the largest |r_j[D]|, smallest D on ties; -1 for an invalid pulse),
+ * mag_dev float |r_j[lag]|, norm_dev double |r_j[lag]| /
+ * sqrt(E_x[j][lag mod 2^j] E_y[j]) with the FP64 energies of eq. 1.  Any of
+ * the three may be NULL. */
+sidwt_status sidwt_peaks(sidwt_plan *p, int64_t B, int32_t *lag_dev, float *mag_dev, double *norm_dev,
+                         sidwt_stream stream);
+
+/* End-to-end call on host buffers: copies ref_ids_host and y_host to the
+ * device (through pinned staging owned by the plan), correlates, and copies
+ * the peaks back; returns after the stream has finished.  Any output pointer
+ * may be NULL.  Same layouts as sidwt_correlate / sidwt_peaks. */
+sidwt_status sidwt_correlate_host(sidwt_plan *p, const int32_t *ref_ids_host, const void *y_host, int64_t B,
+                                  sidwt_precision prec, int32_t *lag_host, float *mag_host, double *norm_host,
+                                  sidwt_stream stream);
+
+/* Forget every stored reference (ids restart at 0); the store's capacity is
+ * kept, so storing again allocates nothing. */
+sidwt_status sidwt_reset_references(sidwt_plan *p);
+
+/* Per-stage GPU time of this plan's calls, measured with CUDA events that the
+ * library records on the call's stream around each stage while timing is
+ * enabled.  Milliseconds summed over the calls since the last reset;
+ * `launches` counts the library's kernel launches in those calls. */
+typedef struct {
+    double store_ms;     /* SIDWT tree of stored references                 */
+    double group_ms;     /* grouping a batch by reference                   */
+    double analyze_ms;   /* received dual-basis analysis                    */
+    double correlate_ms; /* all-lag, all-scale correlation                  */
+    double peaks_ms;     /* peak epilogue                                   */
+    int64_t correlate_calls;
+    int64_t launches;
+} sidwt_timing;
+
+/* Enable (1) or disable (0) stage timing on this plan. */
+sidwt_status sidwt_set_timing(sidwt_plan *p, int enable);
+
+/* Synchronise the recorded events and return the sums; reset != 0 clears
+ * them afterwards. */
+sidwt_status sidwt_read_timing(sidwt_plan *p, sidwt_timing *out, int reset);
+
+/* Synchronise `stream` and report device-side argument errors recorded by
+ * earlier calls on this plan (an out-of-range reference id): SIDWT_OK or
+ * SIDWT_EINVAL; the record is cleared. */
+sidwt_status sidwt_check(sidwt_plan *p, sidwt_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIDWT_H */

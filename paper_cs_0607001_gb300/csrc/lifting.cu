@@ -1,0 +1,544 @@
+// Lifting kernels: the received (dual-basis) analysis of a batch of pulses,
+// all J levels in one pass through shared memory, and the stored signal's
+// SIDWT tree (even and odd children at every level).
+//
+// Received analysis (Sec. III, Fig. 3(b) / 4(b); eq. 17 for D4): one CTA per
+// pulse.  The pulse is read once with 128-bit loads straight into its two
+// polyphase phases (the split is fused into the load), each lifting step runs
+// over the level in shared memory, and the scaled outputs go to HBM while the
+// approximation is written, already split into the next level's phases, into
+// the other half of a 1.5 N ping-pong buffer.  Levels ping-pong between the
+// regions [0, N) and [N, 1.5 N).
+//
+// SIDWT tree (Sec. II, Fig. 1 and 5): level j -> j+1 for all 2^j variants and
+// both children at once; every thread recomputes one output pair from an
+// 11-sample window of its input (the lifting steps have support <= 9), so a
+// level is one fully parallel launch.  The same window kernel is the
+// received-side path for pulses too long for shared memory.
+#include <cmath>
+
+#include "sidwt_internal.cuh"
+
+namespace sidwt {
+
+LiftCoef lift_coef(int filter, int side) {
+    LiftCoef c{};
+    if (filter == SIDWT_LEGALL53 || filter == SIDWT_LEGALL53_INT) {
+        if (side == SIDE_X) {  // P~(z^-1) = diag(1, 1/2) U((1+z^-1)/4) P(-(1+z)/2)
+            c.c0[0] = c.c1[0] = -0.5f;
+            c.c0[1] = c.c1[1] = 0.25f;
+            c.ce = 1.0f;
+            c.co = 0.5f;
+        } else {  // P^T(z^-1) = diag(1, 2) P(-(1+z)/4) U((1+z^-1)/2)
+            c.c0[0] = c.c1[0] = 0.5f;
+            c.c0[1] = c.c1[1] = -0.25f;
+            c.ce = 1.0f;
+            c.co = 2.0f;
+        }
+    } else if (filter == SIDWT_CDF97) {  // Table I, t = 5/4
+        const double a = -1.5, b = -1.0 / 16.0, g = 4.0 / 5.0, d = 15.0 / 32.0;
+        const double x = 4.0 * std::sqrt(2.0) / 5.0;
+        const double st[4] = {a, b, g, d};
+        for (int s = 0; s < 4; ++s) {
+            double v = (side == SIDE_X) ? st[s] : -st[s];
+            c.c0[s] = c.c1[s] = (float)v;
+        }
+        c.ce = (float)((side == SIDE_X) ? x : 1.0 / x);
+        c.co = (float)((side == SIDE_X) ? 1.0 / x : x);
+    } else {  // causal D4, eq. 17
+        const double s3 = std::sqrt(3.0), s2 = std::sqrt(2.0);
+        c.c0[0] = (float)(-s3);
+        c.c1[0] = 0.0f;
+        c.c0[1] = (float)(s3 / 4.0);
+        c.c1[1] = (float)((s3 - 2.0) / 4.0);
+        c.ce = (float)((s3 + 1.0) / s2);
+        c.co = (float)((s3 - 1.0) / s2);
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 axpy2(float2 x, float c0, float2 y0, float c1, float2 y1) {
+    x.x = fmaf(c1, y1.x, fmaf(c0, y0.x, x.x));
+    x.y = fmaf(c1, y1.y, fmaf(c0, y0.y, x.y));
+    return x;
+}
+__device__ __forceinline__ float2 scale2(float s, float2 v) { return make_float2(s * v.x, s * v.y); }
+__device__ __forceinline__ int wrapi(int64_t i, int64_t m) {
+    int64_t r = i % m;
+    return (int)(r < 0 ? r + m : r);
+}
+
+template <typename T>
+__device__ __forceinline__ float2 to_f2(T v);
+template <>
+__device__ __forceinline__ float2 to_f2<float2>(float2 v) { return v; }
+template <>
+__device__ __forceinline__ float2 to_f2<int2>(int2 v) { return make_float2((float)v.x, (float)v.y); }
+
+template <typename T>
+__device__ __forceinline__ int2 to_i2(T v);
+template <>
+__device__ __forceinline__ int2 to_i2<short2>(short2 v) { return make_int2(v.x, v.y); }
+template <>
+__device__ __forceinline__ int2 to_i2<int2>(int2 v) { return v; }
+
+__device__ __forceinline__ double norm2d(float2 v) { return (double)v.x * v.x + (double)v.y * v.y; }
+__device__ __forceinline__ double norm2d(int2 v) { return (double)v.x * v.x + (double)v.y * v.y; }
+
+// Deterministic block sum of one double per thread (blockDim.x multiple of 32).
+__device__ double block_sum(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; ++i) t += red[i];
+    return t;  // valid in thread 0
+}
+
+// ---------------------------------------------------------------------------
+// Integer 5/3 steps (floor division by arithmetic shift; Sec. I / V-B).
+// x side: O -= (E[n] + E[n+1]) >> 1;  E += (O[n-1] + O[n] + 2) >> 2.
+// y side: E += (O[n] + O[n-1] + 1) >> 1;  O -= (E[n] + E[n+1] + 2) >> 2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int2 isub_shr(int2 x, int2 a, int2 b, int add, int sh) {
+    return make_int2(x.x - ((a.x + b.x + add) >> sh), x.y - ((a.y + b.y + add) >> sh));
+}
+__device__ __forceinline__ int2 iadd_shr(int2 x, int2 a, int2 b, int add, int sh) {
+    return make_int2(x.x + ((a.x + b.x + add) >> sh), x.y + ((a.y + b.y + add) >> sh));
+}
+
+// ---------------------------------------------------------------------------
+// Window lifting (register arrays, one output pair per thread).
+// E[i], O[i] hold the phases at n - R + i.  After the steps the centre R is
+// exact (each step consumes at most one neighbour on one side).
+// ---------------------------------------------------------------------------
+template <int F, int S, int R>
+__device__ __forceinline__ void lift_window(float2 (&E)[2 * R + 1], float2 (&O)[2 * R + 1], const LiftCoef &c) {
+    using Sh = LiftShape<F, S>;
+#pragma unroll
+    for (int s = 0; s < Sh::nsteps; ++s) {
+        const float c0 = c.c0[s], c1 = c.c1[s];
+        if (Sh::target(s) == 1) {
+            if (Sh::nb(s) > 0) {
+#pragma unroll
+                for (int i = 0; i < 2 * R; ++i) O[i] = axpy2(O[i], c0, E[i], c1, E[i + 1]);
+            } else {
+#pragma unroll
+                for (int i = 2 * R; i >= 1; --i) O[i] = axpy2(O[i], c0, E[i], c1, E[i - 1]);
+            }
+        } else {
+            if (Sh::nb(s) > 0) {
+#pragma unroll
+                for (int i = 0; i < 2 * R; ++i) E[i] = axpy2(E[i], c0, O[i], c1, O[i + 1]);
+            } else {
+#pragma unroll
+                for (int i = 2 * R; i >= 1; --i) E[i] = axpy2(E[i], c0, O[i], c1, O[i - 1]);
+            }
+        }
+    }
+}
+
+template <int S, int R>
+__device__ __forceinline__ void int53_window(int2 (&E)[2 * R + 1], int2 (&O)[2 * R + 1]) {
+    if (S == SIDE_X) {
+#pragma unroll
+        for (int i = 0; i < 2 * R; ++i) O[i] = isub_shr(O[i], E[i], E[i + 1], 0, 1);
+#pragma unroll
+        for (int i = 2 * R; i >= 1; --i) E[i] = iadd_shr(E[i], O[i - 1], O[i], 2, 2);
+    } else {
+#pragma unroll
+        for (int i = 2 * R; i >= 1; --i) E[i] = iadd_shr(E[i], O[i], O[i - 1], 1, 1);
+#pragma unroll
+        for (int i = 0; i < 2 * R; ++i) O[i] = isub_shr(O[i], E[i], E[i + 1], 2, 2);
+    }
+}
+
+constexpr int WR = 5;  // window radius
+
+// One analysis level over many rows by per-output recomputation.
+// Row r (of nrows) of `in` has K samples at in + r * in_stride; child 1 reads
+// the row delayed by one sample.  Output row (r + child * nrows) of length
+// K/2 goes to lo/hi at row stride out_stride.
+template <int F, int S, typename TIn>
+__global__ void level_window_f(const TIn *__restrict__ in, int64_t in_stride, int nrows, int nchild, int64_t K,
+                               float2 *__restrict__ lo, float2 *__restrict__ hi, int64_t out_stride, LiftCoef c) {
+    const int64_t H = K / 2;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= H) return;
+    const int rc = blockIdx.y;
+    const int row = rc % nrows, child = rc / nrows;
+    if (child >= nchild) return;
+    const TIn *v = in + (int64_t)row * in_stride;
+    using Sh = LiftShape<F, S>;
+    float2 E[2 * WR + 1], O[2 * WR + 1];
+#pragma unroll
+    for (int i = 0; i <= 2 * WR; ++i) {
+        const int64_t m = n - WR + i;
+        E[i] = to_f2(v[wrapi(2 * m - child, K)]);
+        O[i] = to_f2(v[wrapi(Sh::d4 ? 2 * m - 1 - child : 2 * m + 1 - child, K)]);
+    }
+    lift_window<F, S, WR>(E, O, c);
+    const float2 l = scale2(c.ce, E[WR]);
+    float2 h;
+    if (Sh::d4) h = scale2(c.co, make_float2(E[WR].x + O[WR - 1].x, E[WR].y + O[WR - 1].y));
+    else h = scale2(c.co, O[WR]);
+    const int64_t orow = (int64_t)(row + child * nrows) * out_stride;
+    lo[orow + n] = l;
+    hi[orow + n] = h;
+}
+
+template <int S, typename TIn>
+__global__ void level_window_i(const TIn *__restrict__ in, int64_t in_stride, int nrows, int nchild, int64_t K,
+                               int2 *__restrict__ lo, int2 *__restrict__ hi, int64_t out_stride,
+                               float2 *__restrict__ lo_f, float2 *__restrict__ hi_f) {
+    const int64_t H = K / 2;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= H) return;
+    const int rc = blockIdx.y;
+    const int row = rc % nrows, child = rc / nrows;
+    if (child >= nchild) return;
+    const TIn *v = in + (int64_t)row * in_stride;
+    int2 E[2 * WR + 1], O[2 * WR + 1];
+#pragma unroll
+    for (int i = 0; i <= 2 * WR; ++i) {
+        const int64_t m = n - WR + i;
+        E[i] = to_i2(v[wrapi(2 * m - child, K)]);
+        O[i] = to_i2(v[wrapi(2 * m + 1 - child, K)]);
+    }
+    int53_window<S, WR>(E, O);
+    const int64_t o = (int64_t)(row + child * nrows) * out_stride + n;
+    lo[o] = E[WR];
+    hi[o] = O[WR];
+    if (lo_f) {
+        lo_f[o] = to_f2(E[WR]);
+        hi_f[o] = to_f2(O[WR]);
+    }
+}
+
+// Energies ||X_{l,v}||^2 of one reference: block b -> (level l, variant v)
+// with b = 2^l - 1 + v.  Level 0 reads x, level l >= 1 the stored A band.
+template <typename TIn, typename TTree>
+__global__ void ref_energy_kernel(const TIn *__restrict__ x, const TTree *__restrict__ tree, int64_t N,
+                                  double *__restrict__ out) {
+    __shared__ double red[32];
+    const int b = blockIdx.x;
+    int l = 0;
+    while ((2 << l) - 1 <= b) ++l;
+    const int v = b - ((1 << l) - 1);
+    const int64_t K = N >> l;
+    double s = 0.0;
+    if (l == 0) {
+        for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
+            TIn t = x[k];
+            s += (double)t.x * t.x + (double)t.y * t.y;
+        }
+    } else {
+        const TTree *A = tree + 2 * N * (int64_t)(l - 1) + (int64_t)v * K;
+        for (int64_t k = threadIdx.x; k < K; k += blockDim.x) s += norm2d(A[k]);
+    }
+    double t = block_sum(s, red);
+    if (threadIdx.x == 0) out[b] = t;
+}
+
+// ---------------------------------------------------------------------------
+// Received analysis, all levels in one pass through shared memory.
+// ---------------------------------------------------------------------------
+template <int F>
+__device__ __forceinline__ void smem_steps_f(float2 *E, float2 *O, int H, const LiftCoef &c) {
+    using Sh = LiftShape<F, SIDE_Y>;
+#pragma unroll
+    for (int s = 0; s < Sh::nsteps; ++s) {
+        float2 *X = Sh::target(s) ? O : E;
+        const float2 *Y = Sh::target(s) ? E : O;
+        const int nb = Sh::nb(s);
+        const float c0 = c.c0[s], c1 = c.c1[s];
+        for (int n = threadIdx.x; n < H; n += blockDim.x) {
+            int m = n + nb;
+            m = m < 0 ? m + H : (m >= H ? m - H : m);
+            X[n] = axpy2(X[n], c0, Y[n], c1, Y[m]);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void smem_steps_i(int2 *E, int2 *O, int H) {
+    // y side of the reversible 5/3
+    for (int n = threadIdx.x; n < H; n += blockDim.x) {
+        const int m = n == 0 ? H - 1 : n - 1;
+        E[n] = iadd_shr(E[n], O[n], O[m], 1, 1);
+    }
+    __syncthreads();
+    for (int n = threadIdx.x; n < H; n += blockDim.x) {
+        const int m = n + 1 == H ? 0 : n + 1;
+        O[n] = isub_shr(O[n], E[n], E[m], 2, 2);
+    }
+    __syncthreads();
+}
+
+// One CTA per pulse.  Shared memory: 1.5 N elements of T.
+template <int F, typename T>
+__global__ void __launch_bounds__(256) analyze_smem_kernel(const void *__restrict__ y_in, int64_t N, int J,
+                                                           float2 *__restrict__ pyr_f, int2 *__restrict__ pyr_i,
+                                                           int64_t pyr_elems, double *__restrict__ yen,
+                                                           LiftCoef c) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sm = reinterpret_cast<T *>(smraw);
+    __shared__ double red[32];
+    constexpr bool INT = (F == SIDWT_LEGALL53_INT);
+    constexpr bool D4 = (F == SIDWT_D4);
+    const int64_t b = blockIdx.x;
+    const int H1 = (int)(N / 2);
+    double en = 0.0;
+
+    // level-1 load with the polyphase split fused in: element pairs
+    // (y[2n], y[2n+1]) arrive in one 128-bit (float) or 64-bit (int16) load
+    T *E = sm, *O = sm + H1;
+    if constexpr (INT) {
+        const short4 *y4 = reinterpret_cast<const short4 *>(y_in) + b * H1;
+        for (int n = threadIdx.x; n < H1; n += blockDim.x) {
+            short4 v = y4[n];
+            int2 e = make_int2(v.x, v.y), o = make_int2(v.z, v.w);
+            E[n] = e;
+            O[n] = o;
+            en += norm2d(e) + norm2d(o);
+        }
+    } else {
+        const float4 *y4 = reinterpret_cast<const float4 *>(y_in) + b * H1;
+        for (int n = threadIdx.x; n < H1; n += blockDim.x) {
+            float4 v = y4[n];
+            float2 e = make_float2(v.x, v.y), o = make_float2(v.z, v.w);
+            E[n] = e;
+            if (D4) O[n + 1 == H1 ? 0 : n + 1] = o;  // odd phase of D4 is y[2n-1]
+            else O[n] = o;
+            en += norm2d(e) + norm2d(o);
+        }
+    }
+    {
+        double t = block_sum(en, red);
+        if (threadIdx.x == 0) yen[b * (J + 1)] = t;
+    }
+    __syncthreads();
+
+    for (int l = 1; l <= J; ++l) {
+        const int H = (int)(N >> l);
+        // steps
+        if constexpr (INT) smem_steps_i(reinterpret_cast<int2 *>(E), reinterpret_cast<int2 *>(O), H);
+        else smem_steps_f<F>(reinterpret_cast<float2 *>(E), reinterpret_cast<float2 *>(O), H, c);
+        // outputs: c_l, d_l to HBM; c_l split into the next level's phases
+        const int64_t off = b * pyr_elems + 2 * N - 4 * (int64_t)H;
+        const bool more = l < J;
+        const int Hn = H / 2;
+        T *En = sm + ((l + 1) % 2 == 0 ? N : 0);
+        T *On = En + Hn;
+        en = 0.0;
+        for (int n = threadIdx.x; n < H; n += blockDim.x) {
+            T lo, hi;
+            if constexpr (INT) {
+                lo = E[n];
+                hi = O[n];
+                pyr_i[off + n] = lo;
+                pyr_i[off + H + n] = hi;
+                pyr_f[off + n] = to_f2(lo);
+                pyr_f[off + H + n] = to_f2(hi);
+            } else {
+                const float2 e = E[n];
+                lo = scale2(c.ce, e);
+                if (D4) {
+                    const float2 om = O[n == 0 ? H - 1 : n - 1];
+                    hi = scale2(c.co, make_float2(e.x + om.x, e.y + om.y));
+                } else {
+                    hi = scale2(c.co, O[n]);
+                }
+                pyr_f[off + n] = lo;
+                pyr_f[off + H + n] = hi;
+            }
+            en += norm2d(lo);
+            if (more) {
+                if ((n & 1) == 0) En[n >> 1] = lo;
+                else if (D4) On[((n + 1) >> 1) == Hn ? 0 : ((n + 1) >> 1)] = lo;
+                else On[n >> 1] = lo;
+            }
+        }
+        double t = block_sum(en, red);
+        if (threadIdx.x == 0) yen[b * (J + 1) + l] = t;
+        __syncthreads();
+        E = En;
+        O = On;
+    }
+}
+
+// Energies of the received pyramid for the window path (c_l read back).
+__global__ void pyr_energy_kernel(const float2 *__restrict__ y, const float2 *__restrict__ pyr_f,
+                                  const int2 *__restrict__ pyr_i, const short2 *__restrict__ y_i, int64_t N, int J,
+                                  int64_t pyr_elems, double *__restrict__ yen) {
+    __shared__ double red[32];
+    const int64_t b = blockIdx.x;
+    const int l = blockIdx.y;
+    const int64_t K = N >> l;
+    double s = 0.0;
+    if (l == 0) {
+        if (y_i) {
+            for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
+                short2 t = y_i[b * N + k];
+                s += (double)t.x * t.x + (double)t.y * t.y;
+            }
+        } else {
+            for (int64_t k = threadIdx.x; k < K; k += blockDim.x) s += norm2d(y[b * N + k]);
+        }
+    } else {
+        const int64_t off = b * pyr_elems + 2 * N - 4 * K;
+        if (pyr_i) {
+            for (int64_t k = threadIdx.x; k < K; k += blockDim.x) s += norm2d(pyr_i[off + k]);
+        } else {
+            for (int64_t k = threadIdx.x; k < K; k += blockDim.x) s += norm2d(pyr_f[off + k]);
+        }
+    }
+    double t = block_sum(s, red);
+    if (threadIdx.x == 0) yen[b * (J + 1) + l] = t;
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+static constexpr int kSmemLimit = 227 * 1024;
+
+template <int F, typename TIn>
+static void launch_level_f(int side, const TIn *in, int64_t in_stride, int nrows, int nchild, int64_t K,
+                           float2 *lo, float2 *hi, int64_t out_stride, const LiftCoef &c, cudaStream_t s) {
+    const int64_t H = K / 2;
+    dim3 grid((unsigned)((H + 127) / 128), (unsigned)(nrows * nchild));
+    if (side == SIDE_X)
+        level_window_f<F, SIDE_X, TIn><<<grid, 128, 0, s>>>(in, in_stride, nrows, nchild, K, lo, hi, out_stride, c);
+    else
+        level_window_f<F, SIDE_Y, TIn><<<grid, 128, 0, s>>>(in, in_stride, nrows, nchild, K, lo, hi, out_stride, c);
+}
+
+template <typename TIn>
+static void launch_level_any(int filter, int side, const TIn *in, int64_t in_stride, int nrows, int nchild,
+                             int64_t K, float2 *lo, float2 *hi, int64_t out_stride, const LiftCoef &c,
+                             cudaStream_t s) {
+    switch (filter) {
+    case SIDWT_D4: launch_level_f<SIDWT_D4>(side, in, in_stride, nrows, nchild, K, lo, hi, out_stride, c, s); break;
+    case SIDWT_LEGALL53:
+        launch_level_f<SIDWT_LEGALL53>(side, in, in_stride, nrows, nchild, K, lo, hi, out_stride, c, s);
+        break;
+    default: launch_level_f<SIDWT_CDF97>(side, in, in_stride, nrows, nchild, K, lo, hi, out_stride, c, s); break;
+    }
+}
+
+template <typename TIn>
+static void launch_level_int(int side, const TIn *in, int64_t in_stride, int nrows, int nchild, int64_t K, int2 *lo,
+                             int2 *hi, int64_t out_stride, float2 *lo_f, float2 *hi_f, cudaStream_t s) {
+    const int64_t H = K / 2;
+    dim3 grid((unsigned)((H + 127) / 128), (unsigned)(nrows * nchild));
+    if (side == SIDE_X)
+        level_window_i<SIDE_X, TIn><<<grid, 128, 0, s>>>(in, in_stride, nrows, nchild, K, lo, hi, out_stride, lo_f, hi_f);
+    else
+        level_window_i<SIDE_Y, TIn><<<grid, 128, 0, s>>>(in, in_stride, nrows, nchild, K, lo, hi, out_stride, lo_f, hi_f);
+}
+
+sidwt_status build_reference_tree(sidwt_plan *p, const void *x_dev, int32_t ref, cudaStream_t s) {
+    const int64_t N = p->N;
+    const int J = p->J;
+    const LiftCoef c = lift_coef(p->filter, SIDE_X);
+    float2 *tf = p->tree_f + (int64_t)ref * p->tree_elems;
+    double *xe = p->xen + (int64_t)ref * p->xen_len;
+    if (!p->is_int) {
+        for (int j = 0; j < J; ++j) {
+            const int64_t K = N >> j;
+            const int nv = 1 << j;
+            float2 *A = tf + 2 * N * (int64_t)j;  // level j+1 block
+            float2 *B = A + N;
+            if (j == 0)
+                launch_level_any(p->filter, SIDE_X, reinterpret_cast<const float2 *>(x_dev), 0, 1, 2, K, A, B, K / 2, c,
+                                 s);
+            else
+                launch_level_any(p->filter, SIDE_X, tf + 2 * N * (int64_t)(j - 1), K, nv, 2, K, A, B, K / 2, c, s);
+        }
+        ref_energy_kernel<float2, float2><<<(1 << (J + 1)) - 1, 256, 0, s>>>(
+            reinterpret_cast<const float2 *>(x_dev), tf, N, xe);
+    } else {
+        int2 *ti = p->tree_i + (int64_t)ref * p->tree_elems;
+        for (int j = 0; j < J; ++j) {
+            const int64_t K = N >> j;
+            const int nv = 1 << j;
+            int2 *A = ti + 2 * N * (int64_t)j;
+            int2 *B = A + N;
+            float2 *Af = tf + 2 * N * (int64_t)j;
+            float2 *Bf = Af + N;
+            if (j == 0)
+                launch_level_int(SIDE_X, reinterpret_cast<const short2 *>(x_dev), 0, 1, 2, K, A, B, K / 2, Af, Bf, s);
+            else
+                launch_level_int(SIDE_X, ti + 2 * N * (int64_t)(j - 1), K, nv, 2, K, A, B, K / 2, Af, Bf, s);
+        }
+        ref_energy_kernel<short2, int2><<<(1 << (J + 1)) - 1, 256, 0, s>>>(
+            reinterpret_cast<const short2 *>(x_dev), ti, N, xe);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "reference tree launch");
+}
+
+template <int F, typename T>
+static cudaError_t launch_smem(sidwt_plan *p, const void *y, int64_t B, cudaStream_t s, const LiftCoef &c) {
+    const size_t smem = (size_t)(p->N + p->N / 2) * sizeof(T);
+    auto k = analyze_smem_kernel<F, T>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<(unsigned)B, 256, smem, s>>>(y, p->N, p->J, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c);
+    return cudaGetLastError();
+}
+
+int analyze_launch_count(const sidwt_plan *p) {
+    const size_t smem = (size_t)(p->N + p->N / 2) * 8;
+    return smem <= (size_t)kSmemLimit ? 1 : p->J + 1;
+}
+
+sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStream_t s) {
+    if (B == 0) return SIDWT_OK;
+    const int64_t N = p->N;
+    const int J = p->J;
+    const LiftCoef c = lift_coef(p->filter, SIDE_Y);
+    const size_t smem = (size_t)(N + N / 2) * 8;
+    cudaError_t e = cudaSuccess;
+    if (smem <= (size_t)kSmemLimit && B <= 0x7fffffff) {
+        switch (p->filter) {
+        case SIDWT_D4: e = launch_smem<SIDWT_D4, float2>(p, y_dev, B, s, c); break;
+        case SIDWT_LEGALL53: e = launch_smem<SIDWT_LEGALL53, float2>(p, y_dev, B, s, c); break;
+        case SIDWT_CDF97: e = launch_smem<SIDWT_CDF97, float2>(p, y_dev, B, s, c); break;
+        default: e = launch_smem<SIDWT_LEGALL53_INT, int2>(p, y_dev, B, s, c); break;
+        }
+        return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "analysis launch");
+    }
+    // long pulses: one launch per level through HBM
+    for (int l = 1; l <= J; ++l) {
+        const int64_t K = N >> (l - 1);
+        const int64_t off = 2 * N - 4 * (N >> l);
+        const int64_t prev = 2 * N - 4 * K;  // c_{l-1} offset (l >= 2)
+        if (!p->is_int) {
+            const float2 *in = (l == 1) ? reinterpret_cast<const float2 *>(y_dev) : p->pyr_f + prev;
+            launch_level_any(p->filter, SIDE_Y, in, l == 1 ? N : p->pyr_elems, (int)B, 1, K, p->pyr_f + off,
+                             p->pyr_f + off + (N >> l), p->pyr_elems, c, s);
+        } else if (l == 1) {
+            launch_level_int(SIDE_Y, reinterpret_cast<const short2 *>(y_dev), N, (int)B, 1, K, p->pyr_i + off,
+                             p->pyr_i + off + (N >> l), p->pyr_elems, p->pyr_f + off, p->pyr_f + off + (N >> l), s);
+        } else {
+            launch_level_int(SIDE_Y, p->pyr_i + prev, p->pyr_elems, (int)B, 1, K, p->pyr_i + off,
+                             p->pyr_i + off + (N >> l), p->pyr_elems, p->pyr_f + off, p->pyr_f + off + (N >> l), s);
+        }
+    }
+    dim3 g((unsigned)B, (unsigned)(J + 1));
+    pyr_energy_kernel<<<g, 256, 0, s>>>(p->is_int ? nullptr : reinterpret_cast<const float2 *>(y_dev), p->pyr_f,
+                                        p->is_int ? p->pyr_i : nullptr,
+                                        p->is_int ? reinterpret_cast<const short2 *>(y_dev) : nullptr, N, J,
+                                        p->pyr_elems, p->yen);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "analysis (window path) launch");
+}
+
+}  // namespace sidwt

@@ -1,0 +1,173 @@
+// Internal declarations of libsidwt: lifting programs, plan state and the
+// kernel launchers shared between translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "sidwt.h"
+
+namespace sidwt {
+
+enum Side { SIDE_X = 0, SIDE_Y = 1 };  // x: primal analysis P~(z^-1); y: dual P^T(z^-1)
+
+// ---------------------------------------------------------------------------
+// Lifting programs.  One analysis level of a periodic phase pair (E, O):
+// steps X[n] += c0[s] * Y[n] + c1[s] * Y[n + nb[s]] with X = O (target 1) or
+// E (target 0) and Y the other phase, then lo = ce E[n] and hi = co O[n]
+// (D4: hi = co (E[n] + O[n-1])).  The structure is compile-time
+// (LiftShape); the coefficients are computed on the host in double precision
+// (LiftCoef) and passed by value.
+//   LeGall 5/3, Sec. III-C Case I:  x: O -= (E[n]+E[n+1])/2, E += (O[n]+O[n-1])/4,
+//     scale (1, 1/2);  y: E += (O[n]+O[n-1])/2, O -= (E[n]+E[n+1])/4, scale (1, 2).
+//   CDF 9/7, Sec. III-C Case II with Table I: four steps a, b, g, d and the
+//     scaling x (x side) or their negations in reverse roles (y side).
+//   Causal D4, eq. 17 (both sides): O -= sqrt3 E; E += (sqrt3/4) O[n] +
+//     ((sqrt3-2)/4) O[n-1]; lo = K1 E, hi = K2 (E[n] + O[n-1]); the odd phase is
+//     v[2n-1].
+// ---------------------------------------------------------------------------
+struct LiftCoef {
+    float c0[4], c1[4];
+    float ce, co;
+};
+
+template <int F, int S>
+struct LiftShape;
+
+// target(s): 1 if step s updates the odd phase, 0 if the even phase.
+// nb(s): offset of the second neighbour in the other phase (+1 or -1).
+template <>
+struct LiftShape<SIDWT_LEGALL53, SIDE_X> {
+    static constexpr int nsteps = 2;
+    __host__ __device__ static constexpr int target(int s) { return s == 0 ? 1 : 0; }
+    __host__ __device__ static constexpr int nb(int s) { return s == 0 ? +1 : -1; }
+    static constexpr bool d4 = false;
+};
+template <>
+struct LiftShape<SIDWT_LEGALL53, SIDE_Y> {
+    static constexpr int nsteps = 2;
+    __host__ __device__ static constexpr int target(int s) { return s == 0 ? 0 : 1; }
+    __host__ __device__ static constexpr int nb(int s) { return s == 0 ? -1 : +1; }
+    static constexpr bool d4 = false;
+};
+template <>
+struct LiftShape<SIDWT_CDF97, SIDE_X> {
+    static constexpr int nsteps = 4;
+    __host__ __device__ static constexpr int target(int s) { return (s & 1) ? 0 : 1; }
+    __host__ __device__ static constexpr int nb(int s) { return (s & 1) ? -1 : +1; }
+    static constexpr bool d4 = false;
+};
+template <>
+struct LiftShape<SIDWT_CDF97, SIDE_Y> {
+    static constexpr int nsteps = 4;
+    __host__ __device__ static constexpr int target(int s) { return (s & 1) ? 1 : 0; }
+    __host__ __device__ static constexpr int nb(int s) { return (s & 1) ? +1 : -1; }
+    static constexpr bool d4 = false;
+};
+template <int S>
+struct LiftShape<SIDWT_D4, S> {
+    static constexpr int nsteps = 2;
+    __host__ __device__ static constexpr int target(int s) { return s == 0 ? 1 : 0; }
+    __host__ __device__ static constexpr int nb(int s) { return s == 0 ? +1 : -1; }
+    static constexpr bool d4 = true;
+};
+
+// Host-side coefficient tables (double math, rounded once to float).
+LiftCoef lift_coef(int filter, int side);
+
+// ---------------------------------------------------------------------------
+// Plan state.
+// ---------------------------------------------------------------------------
+struct TileList {  // per correlate: pulse tiles grouped by reference
+    int32_t *perm = nullptr;        // [B] pulse indices grouped by reference
+    int32_t *tile_ref = nullptr;    // [max_tiles]
+    int32_t *tile_start = nullptr;  // [max_tiles] offset into perm
+    int32_t *tile_count = nullptr;  // [max_tiles]
+    int32_t *ntiles = nullptr;      // [1]
+    int32_t *cursor = nullptr;      // [cap_refs] scratch
+    int64_t max_tiles = 0;
+};
+
+}  // namespace sidwt
+
+struct sidwt_plan {
+    int filter = 0;
+    int64_t N = 0;
+    int J = 0;
+    bool is_int = false;
+
+    // reference store
+    int32_t nrefs = 0, cap_refs = 0;
+    int64_t tree_elems = 0;        // 2 J N elements per reference
+    float2 *tree_f = nullptr;      // [cap][tree_elems] (float view; integer plan: converted copy)
+    int2 *tree_i = nullptr;        // [cap][tree_elems] integer plan only
+    double *xen = nullptr;         // [cap][2^(J+1) - 1]
+    int64_t xen_len = 0;
+
+    // workspaces (sized for cap_batch pulses)
+    int64_t cap_batch = 0;
+    int64_t pyr_elems = 0;         // 2N - 2(N >> J) elements per pulse
+    float2 *pyr_f = nullptr;       // [cap_batch][pyr_elems]
+    int2 *pyr_i = nullptr;         // integer plan only
+    double *yen = nullptr;         // [cap_batch][J+1]
+    unsigned long long *keys = nullptr;  // [cap_batch][J+1] packed peak keys
+    int32_t *lag = nullptr;
+    float *mag = nullptr;
+    double *norm = nullptr;
+    int32_t *ref_ids = nullptr;    // copy of the last correlate's ids
+    int32_t *err = nullptr;        // device error record
+    sidwt::TileList tiles;
+    int64_t last_B = -1;
+
+    // sidwt_correlate_host: pinned host staging and device copies of the inputs
+    void *h_stage = nullptr;
+    size_t h_stage_bytes = 0;
+    void *d_in = nullptr;
+    size_t d_in_bytes = 0;
+
+    // stage timing: events recorded around each stage while enabled
+    bool timing = false;
+    struct Mark {
+        int stage;  // 0 store, 1 group, 2 analyze, 3 correlate, 4 peaks
+        cudaEvent_t a, b;
+    };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> event_pool;
+    int64_t timed_correlate_calls = 0;
+    int64_t timed_launches = 0;
+};
+
+namespace sidwt {
+
+// stage timing (no-ops unless the plan's timing is on)
+struct StageTimer {
+    sidwt_plan *p;
+    int stage;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    StageTimer(sidwt_plan *p, int stage, cudaStream_t s, int launches);
+    ~StageTimer();
+};
+
+// error plumbing
+void set_error(const std::string &msg);
+sidwt_status cuda_fail(cudaError_t e, const char *what);
+
+// ---- lifting.cu ----
+// SIDWT tree of one stored pulse (x_dev: complex64[N] or int16x2[N]) into
+// reference slot ref of the plan, plus its energies.
+sidwt_status build_reference_tree(sidwt_plan *p, const void *x_dev, int32_t ref, cudaStream_t s);
+// Received analysis of B pulses into the plan's pyramid workspace (+ energies).
+sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStream_t s);
+int analyze_launch_count(const sidwt_plan *p);
+
+// ---- corr_simt.cu ----
+sidwt_status group_pulses(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t B, int tile_pulses,
+                          cudaStream_t s);
+sidwt_status correlate_simt(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t s);
+sidwt_status finalize_peaks(sidwt_plan *p, int64_t B, cudaStream_t s);
+
+}  // namespace sidwt

@@ -1,0 +1,272 @@
+"""Thin ctypes binding of libsidwt (include/sidwt.h).
+
+Argument marshalling only: every step of the correlation runs in the CUDA
+library.  PyTorch supplies device memory and the current CUDA stream.  The
+binding raises if the compiled library is missing; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+FILTERS = {"d4": 0, "legall53": 1, "cdf97": 2, "legall53_int": 3}
+PRECISIONS = {"fp32": 0, "bf16x3": 1, "tf32x3": 2}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUSY", 6: "EUNSUPPORTED"}
+
+
+class SidwtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [("store_ms", ctypes.c_double), ("group_ms", ctypes.c_double), ("analyze_ms", ctypes.c_double),
+                ("correlate_ms", ctypes.c_double), ("peaks_ms", ctypes.c_double),
+                ("correlate_calls", ctypes.c_int64), ("launches", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+
+
+def library_path() -> Path:
+    return _build.LIB
+
+
+def lib():
+    """Load libsidwt.so (built by __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not path.exists():
+        raise RuntimeError(f"libsidwt is not built ({path} missing): run __graft_entry__.build() first")
+    L = ctypes.CDLL(str(path))
+    L.sidwt_version.restype = ctypes.c_char_p
+    L.sidwt_last_error.restype = ctypes.c_char_p
+    L.sidwt_plan_create.argtypes = [ctypes.c_int, _i64, ctypes.c_int, ctypes.POINTER(_vp)]
+    L.sidwt_plan_destroy.argtypes = [_vp]
+    L.sidwt_plan_reserve.argtypes = [_vp, _i32, _i64]
+    L.sidwt_plan_num_refs.argtypes = [_vp]
+    L.sidwt_plan_num_refs.restype = _i32
+    L.sidwt_store_reference.argtypes = [_vp, _vp, ctypes.POINTER(_i32), _vp]
+    L.sidwt_reference_tree.argtypes = [_vp, _i32, _vp, _vp, _vp]
+    L.sidwt_analyze.argtypes = [_vp, _vp, _i64, _vp, _vp, _vp]
+    L.sidwt_correlate.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, _vp, _vp]
+    L.sidwt_peaks.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp]
+    L.sidwt_correlate_host.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp, _vp]
+    L.sidwt_check.argtypes = [_vp, _vp]
+    L.sidwt_reset_references.argtypes = [_vp]
+    L.sidwt_set_timing.argtypes = [_vp, ctypes.c_int]
+    L.sidwt_read_timing.argtypes = [_vp, ctypes.POINTER(Timing), ctypes.c_int]
+    for name in ("sidwt_plan_create", "sidwt_plan_destroy", "sidwt_plan_reserve", "sidwt_store_reference",
+                 "sidwt_reference_tree", "sidwt_analyze", "sidwt_correlate", "sidwt_peaks",
+                 "sidwt_correlate_host", "sidwt_check", "sidwt_reset_references", "sidwt_set_timing",
+                 "sidwt_read_timing"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def version() -> str:
+    return lib().sidwt_version().decode()
+
+
+def _raise(status: int):
+    if status != 0:
+        raise SidwtError(status, lib().sidwt_last_error().decode())
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _filter_id(f) -> int:
+    return FILTERS[f] if isinstance(f, str) else int(f)
+
+
+def _prec_id(p) -> int:
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+class Plan:
+    """A correlation plan: filter, pulse length N, depth J, and the resident
+    reference store (Sec. II-IV).  Device tensors must live on the current
+    CUDA device; complex pulses are complex64, integer pulses int16 [.., N, 2]."""
+
+    def __init__(self, filter, N: int, J: int):
+        self.filter = _filter_id(filter)
+        self.N = int(N)
+        self.J = int(J)
+        self.is_int = self.filter == 3
+        h = _vp()
+        _raise(lib().sidwt_plan_create(self.filter, self.N, self.J, ctypes.byref(h)))
+        self._h = h
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sidwt_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def num_refs(self) -> int:
+        return lib().sidwt_plan_num_refs(self._h)
+
+    @property
+    def pyr_elems(self) -> int:
+        return 2 * self.N - 2 * (self.N >> self.J)
+
+    def reserve(self, max_refs: int, max_batch: int):
+        _raise(lib().sidwt_plan_reserve(self._h, max_refs, max_batch))
+
+    # -- reference store ----------------------------------------------------
+    def _check_pulses(self, t: torch.Tensor, batched: bool):
+        if not t.is_cuda:
+            raise ValueError("pulses must be CUDA tensors")
+        if self.is_int:
+            if t.dtype != torch.int16 or t.shape[-2:] != (self.N, 2):
+                raise ValueError(f"integer plan expects int16 [..., {self.N}, 2]")
+        else:
+            if t.dtype != torch.complex64 or t.shape[-1] != self.N:
+                raise ValueError(f"float plan expects complex64 [..., {self.N}]")
+        if not t.is_contiguous():
+            raise ValueError("pulses must be contiguous")
+
+    def store_reference(self, x: torch.Tensor, stream=None) -> int:
+        self._check_pulses(x, False)
+        rid = _i32(-1)
+        _raise(lib().sidwt_store_reference(self._h, _ptr(x), ctypes.byref(rid), _stream(stream)))
+        return rid.value
+
+    def reference_tree(self, ref_id: int, stream=None):
+        dev = torch.cuda.current_device()
+        n = 2 * self.J * self.N
+        if self.is_int:
+            tree = torch.empty((n, 2), dtype=torch.int32, device=dev)
+        else:
+            tree = torch.empty(n, dtype=torch.complex64, device=dev)
+        en = torch.empty((2 << self.J) - 1, dtype=torch.float64, device=dev)
+        _raise(lib().sidwt_reference_tree(self._h, ref_id, _ptr(tree), _ptr(en), _stream(stream)))
+        return tree, en
+
+    # -- received side --------------------------------------------------------
+    def analyze(self, y: torch.Tensor, want_pyramid: bool = True, stream=None):
+        self._check_pulses(y, True)
+        B = y.shape[0]
+        dev = y.device
+        pyr = None
+        if want_pyramid:
+            if self.is_int:
+                pyr = torch.empty((B, self.pyr_elems, 2), dtype=torch.int32, device=dev)
+            else:
+                pyr = torch.empty((B, self.pyr_elems), dtype=torch.complex64, device=dev)
+        en = torch.empty((B, self.J + 1), dtype=torch.float64, device=dev)
+        _raise(lib().sidwt_analyze(self._h, _ptr(y), B, _ptr(pyr), _ptr(en), _stream(stream)))
+        return pyr, en
+
+    def analyze_into(self, y: torch.Tensor, pyr=None, energies=None, stream=None):
+        """Analysis into caller buffers (either may be None: kept in the plan only)."""
+        _raise(lib().sidwt_analyze(self._h, _ptr(y), y.shape[0], _ptr(pyr), _ptr(energies), _stream(stream)))
+
+    def correlate(self, ref_ids: torch.Tensor, y: torch.Tensor, precision="fp32", want_r: bool = False,
+                  r_out: torch.Tensor | None = None, stream=None):
+        self._check_pulses(y, True)
+        B = y.shape[0]
+        if ref_ids.dtype != torch.int32 or not ref_ids.is_cuda or ref_ids.numel() != B:
+            raise ValueError("ref_ids must be a CUDA int32 tensor with one id per pulse")
+        r = r_out
+        if want_r and r is None:
+            r = torch.empty((B, self.J + 1, self.N), dtype=torch.complex64, device=y.device)
+        _raise(lib().sidwt_correlate(self._h, _ptr(ref_ids), _ptr(y), B, _prec_id(precision), _ptr(r),
+                                     _stream(stream)))
+        return r
+
+    def peaks(self, B: int, stream=None):
+        dev = torch.cuda.current_device()
+        lag = torch.empty((B, self.J + 1), dtype=torch.int32, device=dev)
+        mag = torch.empty((B, self.J + 1), dtype=torch.float32, device=dev)
+        norm = torch.empty((B, self.J + 1), dtype=torch.float64, device=dev)
+        _raise(lib().sidwt_peaks(self._h, B, _ptr(lag), _ptr(mag), _ptr(norm), _stream(stream)))
+        return lag, mag, norm
+
+    def peaks_into(self, B: int, lag, mag, norm, stream=None):
+        _raise(lib().sidwt_peaks(self._h, B, _ptr(lag), _ptr(mag), _ptr(norm), _stream(stream)))
+
+    def correlate_host(self, ref_ids: torch.Tensor, y: torch.Tensor, precision="fp32", lag=None, mag=None,
+                       norm=None, stream=None):
+        """End-to-end call on host tensors (pinned or pageable): returns host peaks."""
+        B = y.shape[0]
+        if y.is_cuda or ref_ids.is_cuda:
+            raise ValueError("correlate_host takes host tensors")
+        if lag is None:
+            lag = torch.empty((B, self.J + 1), dtype=torch.int32)
+            mag = torch.empty((B, self.J + 1), dtype=torch.float32)
+            norm = torch.empty((B, self.J + 1), dtype=torch.float64)
+        _raise(lib().sidwt_correlate_host(self._h, _ptr(ref_ids), _ptr(y), B, _prec_id(precision), _ptr(lag),
+                                          _ptr(mag), _ptr(norm), _stream(stream)))
+        return lag, mag, norm
+
+    def check(self, stream=None):
+        _raise(lib().sidwt_check(self._h, _stream(stream)))
+
+    def reset_references(self):
+        _raise(lib().sidwt_reset_references(self._h))
+
+    def set_timing(self, on: bool = True):
+        _raise(lib().sidwt_set_timing(self._h, 1 if on else 0))
+
+    def read_timing(self, reset: bool = True) -> dict:
+        t = Timing()
+        _raise(lib().sidwt_read_timing(self._h, ctypes.byref(t), 1 if reset else 0))
+        return t.as_dict()
+
+
+def level_slices(N: int, J: int, l: int) -> tuple[slice, slice]:
+    """(c_l, d_l) element slices of a received pyramid row."""
+    K = N >> l
+    off = 2 * N - 4 * K
+    return slice(off, off + K), slice(off + K, off + 2 * K)
+
+
+def as_numpy_complex(t: torch.Tensor) -> np.ndarray:
+    """complex64 tensor, or int32 pairs [..., 2], as complex128 numpy."""
+    a = t.detach().cpu()
+    if a.dtype == torch.complex64:
+        return a.numpy().astype(np.complex128)
+    a = a.numpy().astype(np.float64)
+    return a[..., 0] + 1j * a[..., 1]
