@@ -33,7 +33,7 @@ sys.path.insert(0, str(ROOT))
 METRIC = "SIDWT-correlation GSamples/s (all lags, all scales)"
 UNIT = "GSamples/s"
 WORKLOAD = "two-reference batch: 4096 complex64 pulses x N=8192, J=5, LeGall 5/3 + CDF 9/7 (+ int16 reversible 5/3 analysis)"
-B, N, J = 4096, 8192, 5
+B, N, J = 4096, 8192, 5  # --pulses overrides B (smaller cases for profiling)
 FILTER_IDS = {"legall53": 1, "cdf97": 2}
 
 
@@ -193,6 +193,8 @@ def run_ours(args):
     from paper_cs_0607001_gb300 import multigpu as M
     from paper_cs_0607001_gb300 import sidwt as S
 
+    global B
+    B = args.pulses
     rank, world, local = M.init()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -327,7 +329,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "bf16x3", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "pulses": B, "N": N, "J": J, "pairs_per_step": pairs,
+        "config": {"workload": WORKLOAD if B == 4096 else WORKLOAD.replace("4096", str(B)), "pulses": B, "N": N, "J": J, "pairs_per_step": pairs,
                    "precision": prec, "l2": "inputs larger than L2 (268 MB complex64 + 134 MB int16 per step)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -355,6 +357,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--pulses", type=int, default=4096)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
