@@ -193,6 +193,28 @@ sidwt_status sidwt_read_timing(sidwt_plan *p, sidwt_timing *out, int reset);
  * SIDWT_EINVAL; the record is cleared. */
 sidwt_status sidwt_check(sidwt_plan *p, sidwt_stream stream);
 
+/* Allocation-free correlation against one stored signal.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory, for example a real-time receive loop that must not call
+ * cudaMalloc once it runs (an allocation can synchronise the device and stall
+ * for an unbounded time) or an application whose device memory belongs to
+ * another allocator.  It stores x_dev (one complex64[N] or int16[N][2]
+ * signal), correlates the B pulses of y_dev against it at all lags and scales
+ * on the FP32 path, and writes the peaks to lag_dev / mag_dev / norm_dev
+ * ([B][J+1], same meaning as sidwt_peaks; none may be NULL).
+ * All intermediates live in one 16 MiB static device array inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits; the call allocates nothing.  A call that needs more than 16 MiB
+ * (roughly 16 N (B + J) bytes, twice that for the integer filter) returns
+ * SIDWT_EINVAL with the size in the message; 1 <= B <= 65535.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call reuses the
+ * same array, so calls that overlap on the GPU (other streams, other host
+ * threads) race and corrupt each other: serialise them on one stream. */
+sidwt_status sidwt_correlate_static(sidwt_filter f, int64_t N, int J, const void *x_dev, const void *y_dev,
+                                    int64_t B, int32_t *lag_dev, float *mag_dev, double *norm_dev,
+                                    sidwt_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,10 +70,11 @@ def lib():
     L.sidwt_reset_references.argtypes = [_vp]
     L.sidwt_set_timing.argtypes = [_vp, ctypes.c_int]
     L.sidwt_read_timing.argtypes = [_vp, ctypes.POINTER(Timing), ctypes.c_int]
+    L.sidwt_correlate_static.argtypes = [ctypes.c_int, _i64, ctypes.c_int, _vp, _vp, _i64, _vp, _vp, _vp, _vp]
     for name in ("sidwt_plan_create", "sidwt_plan_destroy", "sidwt_plan_reserve", "sidwt_store_reference",
                  "sidwt_reference_tree", "sidwt_analyze", "sidwt_correlate", "sidwt_peaks",
                  "sidwt_correlate_host", "sidwt_check", "sidwt_reset_references", "sidwt_set_timing",
-                 "sidwt_read_timing"):
+                 "sidwt_read_timing", "sidwt_correlate_static"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -254,6 +255,16 @@ class Plan:
         t = Timing()
         _raise(lib().sidwt_read_timing(self._h, ctypes.byref(t), 1 if reset else 0))
         return t.as_dict()
+
+
+def correlate_static(filter, N: int, J: int, x: torch.Tensor, y: torch.Tensor, lag: torch.Tensor,
+                     mag: torch.Tensor, norm: torch.Tensor, stream=None):
+    """Allocation-free correlation of the pulses y against one stored signal x
+    (sidwt_correlate_static): the library uses its fixed static scratch array
+    and writes the peaks into the caller's lag / mag / norm [B, J+1] tensors."""
+    B = y.shape[0]
+    _raise(lib().sidwt_correlate_static(_filter_id(filter), int(N), int(J), _ptr(x), _ptr(y), B, _ptr(lag),
+                                        _ptr(mag), _ptr(norm), _stream(stream)))
 
 
 def level_slices(N: int, J: int, l: int) -> tuple[slice, slice]:
