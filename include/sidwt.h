@@ -65,7 +65,9 @@ typedef enum {
 
 typedef enum {
     SIDWT_PREC_FP32 = 0,  /* plain FP32 CUDA-core path ("plain")                      */
-    SIDWT_PREC_BF16X3 = 1, /* tcgen05 tensor cores, bf16 hi+lo split, FP32 accumulate */
+    SIDWT_PREC_BF16X3 = 1, /* tcgen05 tensor cores, bf16 hi+lo split (hi*hi + hi*lo + lo*hi),
+                              FP32 accumulate; scales whose band is shorter than 64 or
+                              not a multiple of 64 run on the FP32 path            */
     SIDWT_PREC_TF32X3 = 2  /* reserved: 3xTF32 split (returns SIDWT_EUNSUPPORTED)     */
 } sidwt_precision;
 
@@ -188,10 +190,22 @@ sidwt_status sidwt_set_timing(sidwt_plan *p, int enable);
  * them afterwards. */
 sidwt_status sidwt_read_timing(sidwt_plan *p, sidwt_timing *out, int reset);
 
-/* Synchronise `stream` and report device-side argument errors recorded by
- * earlier calls on this plan (an out-of-range reference id): SIDWT_OK or
- * SIDWT_EINVAL; the record is cleared. */
+/* Synchronise `stream` and report device-side errors recorded by earlier
+ * calls on this plan: SIDWT_EINVAL for an out-of-range reference id,
+ * SIDWT_ETIMEOUT if a tensor-core CTA gave up on one of its bounded waits
+ * (its results are then incomplete); SIDWT_OK otherwise.  The record is
+ * cleared. */
 sidwt_status sidwt_check(sidwt_plan *p, sidwt_stream stream);
+
+/* Diagnostic: one tcgen05 MMA (M = 128, N = 64, K = 16, bf16 in, f32 out)
+ * on fixed integer-valued operands laid out exactly as the tensor-core
+ * correlation lays them out (K-major A; the overlapping MN-major window as
+ * B), so that a host check can confirm the operand layouts on a given GPU.
+ * out_dev: float[128][64]; err_dev: int32 flag, bit 4 set if the bounded
+ * wait for the MMA ran out.  Operands: A[m][k] = ((7m + 3k) mod 11) - 5,
+ * window planes P in {1, 2} with W_P[t] = ((5t + 17P) mod 13) - 6 and
+ * B[k][n] = W_{1 + k/8}[8 (k mod 8) + n]. */
+sidwt_status sidwt_tc_selftest(float *out_dev, int32_t *err_dev, sidwt_stream stream);
 
 /* Allocation-free correlation against one stored signal.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate

@@ -13,6 +13,8 @@
 // keeps an MP x MQ block of complex accumulators and slides an MQ-sample
 // register window along k (one new shared load per k), so every k costs MP
 // received loads and one window load for 4 MP MQ FMAs.
+#include <algorithm>
+
 #include "sidwt_internal.cuh"
 
 namespace sidwt {
@@ -25,9 +27,11 @@ static_assert(kThreads == 256, "thread layout");
 constexpr int kMaxScales = 16;
 
 struct ScaleTab {
-    int nscales;
-    int64_t tile_begin[kMaxScales + 1];  // prefix over (variant, q-tile) blocks per scale
+    int nscales;                         // entries (a subset of the scales 0..J)
+    int scale[kMaxScales];               // scale j of entry e
+    int64_t tile_begin[kMaxScales + 1];  // prefix over (variant, q-tile) blocks per entry
     int qtiles[kMaxScales];
+    int nsub;                            // pulse sub-tiles of TP per grouping tile
 };
 
 __device__ __forceinline__ int wsidx(int t) { return t + (t >> 3); }  // pad 1 per 8: conflict-free window reads
@@ -42,22 +46,25 @@ __global__ void __launch_bounds__(kThreads, 2)
     __shared__ float2 ws[(TQ + TK) + (TQ + TK) / 8 + 1];
     __shared__ int64_t rowoff[TP];
 
-    const int pt = blockIdx.y;
+    const int pt = blockIdx.y / tab.nsub;
+    const int sub = blockIdx.y % tab.nsub;
     if (pt >= *ntiles) return;
     const int64_t bx = blockIdx.x;
-    int j = 0;
-    while (j + 1 < tab.nscales && bx >= tab.tile_begin[j + 1]) ++j;
-    const int64_t local = bx - tab.tile_begin[j];
-    const int qt = (int)(local % tab.qtiles[j]);
-    const int var = (int)(local / tab.qtiles[j]);
+    int e = 0;
+    while (e + 1 < tab.nscales && bx >= tab.tile_begin[e + 1]) ++e;
+    const int j = tab.scale[e];
+    const int64_t local = bx - tab.tile_begin[e];
+    const int qt = (int)(local % tab.qtiles[e]);
+    const int var = (int)(local / tab.qtiles[e]);
     const int lev = j < J ? j + 1 : J;
     const int64_t Kp = N >> lev;
     const int nbands = j < J ? 2 : 1;
     const int64_t q0 = (int64_t)qt * TQ;
 
     const int ref = tile_ref[pt];
-    const int start = tile_start[pt];
-    const int cnt = tile_count[pt];
+    const int start = tile_start[pt] + sub * TP;
+    const int cnt = min(TP, tile_count[pt] - sub * TP);
+    if (cnt <= 0) return;
     const float2 *Aband = tree + (int64_t)ref * tree_elems + 2 * N * (int64_t)(lev - 1) + (int64_t)var * Kp;
     const int64_t off_c = 2 * N - 4 * Kp;
 
@@ -215,7 +222,10 @@ __global__ void __launch_bounds__(1024) group_kernel(const int32_t *__restrict__
         }
         __syncthreads();
     }
-    if (tid == 0) *ntiles = carry_t;
+    if (tid == 0) {
+        ntiles[0] = carry_t;
+        ntiles[1] = carry_c;  // pulses with a valid reference id
+    }
     __syncthreads();
     for (int b = tid; b < B; b += blockDim.x) {
         const int r = ref_ids[b];
@@ -258,26 +268,33 @@ sidwt_status group_pulses(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t B, 
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "group launch");
 }
 
-sidwt_status correlate_simt(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t s) {
+sidwt_status correlate_simt(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t s, uint32_t scale_mask,
+                            int group_tile) {
     const int64_t N = p->N;
     const int J = p->J;
     ScaleTab tab{};
-    tab.nscales = J + 1;
     int64_t acc = 0;
+    int ne = 0;
     for (int j = 0; j <= J; ++j) {
+        if (!(scale_mask & (1u << j))) continue;
         const int lev = j < J ? j + 1 : J;
         const int64_t Kp = N >> lev;
-        tab.qtiles[j] = (int)((Kp + TQ - 1) / TQ);
-        tab.tile_begin[j] = acc;
-        acc += (int64_t)tab.qtiles[j] << lev;
+        tab.scale[ne] = j;
+        tab.qtiles[ne] = (int)((Kp + TQ - 1) / TQ);
+        tab.tile_begin[ne] = acc;
+        acc += (int64_t)tab.qtiles[ne] << lev;
+        ++ne;
     }
-    tab.tile_begin[J + 1] = acc;
-    const int64_t max_pt = (B + TP - 1) / TP + std::min<int64_t>(p->nrefs, B);
-    if (acc > 0x7fffffff || max_pt > 65535) {
+    if (ne == 0) return SIDWT_OK;
+    tab.nscales = ne;
+    tab.tile_begin[ne] = acc;
+    tab.nsub = (group_tile + TP - 1) / TP;
+    const int64_t max_pt = (B + group_tile - 1) / group_tile + std::min<int64_t>(p->nrefs, B);
+    if (acc > 0x7fffffff || max_pt * tab.nsub > 65535) {
         set_error("batch too large for one launch of the FP32 correlation");
         return SIDWT_EINVAL;
     }
-    dim3 grid((unsigned)acc, (unsigned)max_pt);
+    dim3 grid((unsigned)acc, (unsigned)(max_pt * tab.nsub));
     corr_simt_kernel<<<grid, kThreads, 0, s>>>(p->pyr_f, p->pyr_elems, p->tree_f, p->tree_elems, N, J,
                                                p->tiles.perm, p->tiles.tile_ref, p->tiles.tile_start,
                                                p->tiles.tile_count, p->tiles.ntiles, tab, p->keys, r_dev);

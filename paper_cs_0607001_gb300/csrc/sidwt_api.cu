@@ -21,8 +21,6 @@ sidwt_status cuda_fail(cudaError_t e, const char *what) {
     return SIDWT_ECUDA;
 }
 
-int simt_tile_pulses();
-
 template <typename T>
 static sidwt_status dalloc(T **ptr, size_t count, const char *what) {
     *ptr = nullptr;
@@ -220,7 +218,7 @@ sidwt_status sidwt_plan_create(sidwt_filter f, int64_t N, int J, sidwt_plan **ou
     p->xen_len = (int64_t(2) << J) - 1;
     p->pyr_elems = 2 * N - 2 * (N >> J);
     sidwt_status st = dalloc(&p->err, 1, "error record");
-    if (st == SIDWT_OK && (st = dalloc(&p->tiles.ntiles, 1, "tile count")) == SIDWT_OK) {
+    if (st == SIDWT_OK && (st = dalloc(&p->tiles.ntiles, 2, "tile count")) == SIDWT_OK) {
         cudaError_t e = cudaMemset(p->err, 0, sizeof(int32_t));
         if (e != cudaSuccess) st = cuda_fail(e, "memset");
     }
@@ -238,6 +236,7 @@ sidwt_status sidwt_plan_destroy(sidwt_plan *p) {
     if (!p) return SIDWT_OK;
     cudaDeviceSynchronize();
     free_batch(p);
+    free_tc(p);
     dfree(p->tree_f);
     dfree(p->tree_i);
     dfree(p->xen);
@@ -365,10 +364,11 @@ sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const vo
         set_error("ref_ids_dev is NULL");
         return SIDWT_EINVAL;
     }
-    if (prec != SIDWT_PREC_FP32) {
+    if (prec != SIDWT_PREC_FP32 && prec != SIDWT_PREC_BF16X3) {
         set_error("precision not available in this build");
         return SIDWT_EUNSUPPORTED;
     }
+    const bool tc = (prec == SIDWT_PREC_BF16X3);
     if (p->nrefs == 0 && B > 0) {
         set_error("no stored reference");
         return SIDWT_EINVAL;
@@ -380,7 +380,7 @@ sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const vo
     if (p->timing) ++p->timed_correlate_calls;
     {
         StageTimer t(p, 1, s, 1);
-        if ((st = group_pulses(p, ref_ids_dev, B, simt_tile_pulses(), s))) return st;
+        if ((st = group_pulses(p, ref_ids_dev, B, tc ? tc_group_tile() : simt_tile_pulses(), s))) return st;
     }
     {
         StageTimer t(p, 2, s, analyze_launch_count(p));
@@ -389,8 +389,12 @@ sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const vo
     cudaError_t e = cudaMemsetAsync(p->keys, 0, B * (p->J + 1) * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
     {
-        StageTimer t(p, 3, s, 1);
-        if ((st = correlate_simt(p, B, reinterpret_cast<float2 *>(r_dev), s))) return st;
+        StageTimer t(p, 3, s, tc ? tc_launch_count(p) : 1);
+        if (tc) {
+            if ((st = correlate_tc(p, B, reinterpret_cast<float2 *>(r_dev), s))) return st;
+        } else if ((st = correlate_simt(p, B, reinterpret_cast<float2 *>(r_dev), s))) {
+            return st;
+        }
     }
     StageTimer t(p, 4, s, 1);
     return finalize_peaks(p, B, s);
@@ -478,6 +482,7 @@ sidwt_status sidwt_correlate_host(sidwt_plan *p, const int32_t *ref_ids_host, co
 sidwt_status sidwt_reset_references(sidwt_plan *p) {
     CHECK_PLAN(p);
     p->nrefs = 0;
+    p->tc_packed = 0;
     return SIDWT_OK;
 }
 
@@ -530,6 +535,10 @@ sidwt_status sidwt_check(sidwt_plan *p, sidwt_stream stream) {
     if (h) {
         cudaMemsetAsync(p->err, 0, sizeof(int32_t), s);
         cudaStreamSynchronize(s);
+        if (h & 2) {
+            set_error("a tensor-core correlation CTA gave up on a bounded wait; its results are incomplete");
+            return SIDWT_ETIMEOUT;
+        }
         set_error("a correlate call received a reference id outside [0, num_refs)");
         return SIDWT_EINVAL;
     }

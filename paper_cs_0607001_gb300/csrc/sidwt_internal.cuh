@@ -86,7 +86,7 @@ struct TileList {  // per correlate: pulse tiles grouped by reference
     int32_t *tile_ref = nullptr;    // [max_tiles]
     int32_t *tile_start = nullptr;  // [max_tiles] offset into perm
     int32_t *tile_count = nullptr;  // [max_tiles]
-    int32_t *ntiles = nullptr;      // [1]
+    int32_t *ntiles = nullptr;      // [2]: tiles, pulses with a valid id
     int32_t *cursor = nullptr;      // [cap_refs] scratch
     int64_t max_tiles = 0;
 };
@@ -128,6 +128,15 @@ struct sidwt_plan {
     void *d_in = nullptr;
     size_t d_in_bytes = 0;
 
+    // tensor-core operands (per scale j): packed reference windows and the
+    // received bf16 hi/lo planes in grouped order
+    void *tc_ref[16] = {};
+    void *tc_ahi[16] = {};
+    void *tc_alo[16] = {};
+    int32_t tc_cap_refs = 0;
+    int64_t tc_cap_batch = 0;
+    int32_t tc_packed = 0;
+
     // stage timing: events recorded around each stage while enabled
     bool timing = false;
     struct Mark {
@@ -167,7 +176,17 @@ int analyze_launch_count(const sidwt_plan *p);
 // ---- corr_simt.cu ----
 sidwt_status group_pulses(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t B, int tile_pulses,
                           cudaStream_t s);
-sidwt_status correlate_simt(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t s);
+// scale_mask: bit j set = correlate scale j here; group_tile: pulses per grouping tile
+sidwt_status correlate_simt(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t s, uint32_t scale_mask = 0xffffffffu,
+                            int group_tile = 64);
+int simt_tile_pulses();
+
+// ---- corr_tc.cu ----
+sidwt_status correlate_tc(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t s);
+uint32_t tc_scale_mask(const sidwt_plan *p);
+int tc_group_tile();
+int tc_launch_count(const sidwt_plan *p);
+void free_tc(sidwt_plan *p);
 sidwt_status finalize_peaks(sidwt_plan *p, int64_t B, cudaStream_t s);
 
 }  // namespace sidwt

@@ -10,10 +10,6 @@
 
 #include "sidwt_internal.cuh"
 
-namespace sidwt {
-int simt_tile_pulses();
-}
-
 using namespace sidwt;
 
 namespace {
@@ -77,7 +73,7 @@ size_t layout(sidwt_plan &p, unsigned char *base, int64_t B, int32_t **ids_in) {
     p.tiles.tile_ref = c.take<int32_t>((size_t)p.tiles.max_tiles);
     p.tiles.tile_start = c.take<int32_t>((size_t)p.tiles.max_tiles);
     p.tiles.tile_count = c.take<int32_t>((size_t)p.tiles.max_tiles);
-    p.tiles.ntiles = c.take<int32_t>(1);
+    p.tiles.ntiles = c.take<int32_t>(2);
     p.tiles.cursor = c.take<int32_t>(1);
     p.err = c.take<int32_t>(1);
     return c.off;

@@ -71,10 +71,11 @@ def lib():
     L.sidwt_set_timing.argtypes = [_vp, ctypes.c_int]
     L.sidwt_read_timing.argtypes = [_vp, ctypes.POINTER(Timing), ctypes.c_int]
     L.sidwt_correlate_static.argtypes = [ctypes.c_int, _i64, ctypes.c_int, _vp, _vp, _i64, _vp, _vp, _vp, _vp]
+    L.sidwt_tc_selftest.argtypes = [_vp, _vp, _vp]
     for name in ("sidwt_plan_create", "sidwt_plan_destroy", "sidwt_plan_reserve", "sidwt_store_reference",
                  "sidwt_reference_tree", "sidwt_analyze", "sidwt_correlate", "sidwt_peaks",
                  "sidwt_correlate_host", "sidwt_check", "sidwt_reset_references", "sidwt_set_timing",
-                 "sidwt_read_timing", "sidwt_correlate_static"):
+                 "sidwt_read_timing", "sidwt_correlate_static", "sidwt_tc_selftest"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -265,6 +266,15 @@ def correlate_static(filter, N: int, J: int, x: torch.Tensor, y: torch.Tensor, l
     B = y.shape[0]
     _raise(lib().sidwt_correlate_static(_filter_id(filter), int(N), int(J), _ptr(x), _ptr(y), B, _ptr(lag),
                                         _ptr(mag), _ptr(norm), _stream(stream)))
+
+
+def tc_selftest(stream=None):
+    """Run the tensor-core layout self-test; returns (out [128, 64] float32, err flag)."""
+    dev = torch.cuda.current_device()
+    out = torch.zeros((128, 64), dtype=torch.float32, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    _raise(lib().sidwt_tc_selftest(_ptr(out), _ptr(err), _stream(stream)))
+    return out, err
 
 
 def level_slices(N: int, J: int, l: int) -> tuple[slice, slice]:

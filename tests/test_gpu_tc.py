@@ -1,0 +1,117 @@
+"""GPU parity of the tcgen05 bf16 hi+lo correlation (SIDWT_PREC_BF16X3).
+
+Error bound stated a priori: splitting a = a_h + a_l + e (bf16 round to
+nearest, unit roundoff 2^-8) and keeping a_h b_h + a_h b_l + a_l b_h leaves
+|a b - kept| <= 3 * 2^-16 |a| |b| per product; FP32 accumulation of K terms
+adds at most K * 2^-24 sum |a b|.  Per (pair, scale):
+    max_D |r_tc - r_oracle| <= (3 * 2^-16 + K_j 2^-24) max_v ||w_v|| ||u||
+with w_v the stored variant's bands and u the received bands (Cauchy-Schwarz).
+The tests also report the measured error relative to the peak."""
+import numpy as np
+import pytest
+import torch
+
+from paper_cs_0607001_gb300 import inputs
+from tests import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+
+def selftest_expected():
+    m = np.arange(128)[:, None]
+    k = np.arange(16)[None, :]
+    A = ((m * 7 + k * 3) % 11) - 5                       # [128, 16]
+    t = np.arange(320)
+    W = {P: ((t * 5 + P * 17) % 13) - 6 for P in (1, 2)}
+    B = np.zeros((16, 64))
+    for kk in range(16):
+        B[kk] = W[1 + kk // 8][8 * (kk % 8) + np.arange(64)]
+    return (A @ B).astype(np.float64), A, W
+
+
+def test_tc_operand_layouts_selftest():
+    from paper_cs_0607001_gb300 import sidwt
+    out, err = sidwt.tc_selftest()
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0, "bounded wait for the self-test MMA ran out"
+    got = out.cpu().numpy().astype(np.float64)
+    exp, A, W = selftest_expected()
+    if not np.array_equal(got, exp):
+        pytest.fail(f"tcgen05 self-test mismatch: max |diff| {np.abs(got - exp).max()}, "
+                    f"got[0,:8]={got[0, :8]}, expected[0,:8]={exp[0, :8]}, got[1,:8]={got[1, :8]}, "
+                    f"expected[1,:8]={exp[1, :8]}")
+
+
+def stated_bound(tree, pyr, N, J, j, Kj):
+    """(3 2^-16 + K 2^-24) max_v ||w_v|| ||u|| for scale j (tree and pyr from the oracle)."""
+    lev = j + 1 if j < J else J
+    Kp = N >> lev
+    base = 2 * N * (lev - 1)
+    A = tree[base:base + N].reshape(1 << lev, Kp)
+    Bb = tree[base + N:base + 2 * N].reshape(1 << lev, Kp)
+    off = 2 * N - 4 * Kp
+    if j < J:
+        wn = np.sqrt((np.abs(A) ** 2).sum(1) + (np.abs(Bb) ** 2).sum(1)).max()
+        un = np.linalg.norm(pyr[off:off + 2 * Kp])
+    else:
+        wn = np.sqrt((np.abs(A) ** 2).sum(1)).max()
+        un = np.linalg.norm(pyr[off:off + Kp])
+    return (3 * 2.0 ** -16 + Kj * 2.0 ** -24) * wn * un
+
+
+def run(fname, N, J, refs, y, ids, precision, want_r=True):
+    from paper_cs_0607001_gb300 import sidwt
+    with sidwt.Plan(fname, N, J) as p:
+        for x in refs:
+            p.store_reference(U.to_dev_c64(x))
+        r = p.correlate(torch.from_numpy(ids.astype(np.int32)).to(U.dev()), U.to_dev_c64(y), precision=precision,
+                        want_r=want_r)
+        lag, mag, norm = p.peaks(y.shape[0])
+        p.check()
+        torch.cuda.synchronize()
+        return r, lag.cpu().numpy(), mag.cpu().numpy(), norm.cpu().numpy()
+
+
+@pytest.mark.parametrize("fname,fid", list(U.FLOAT_FILTERS.items()))
+@pytest.mark.parametrize("N,J,B,nrefs", [(1024, 4, 150, 3), (256, 2, 130, 2), (4096, 6, 40, 1), (512, 3, 129, 2)])
+def test_bf16x3_matches_oracle_within_stated_bound(oracle, fname, fid, N, J, B, nrefs):
+    w = U.small_batch(nrefs, B, N, J, seed=1000 + N + B + fid)
+    r, lag, mag, norm = run(fname, N, J, w["refs"], w["y"], w["ref_ids"], "bf16x3")
+    X = w["refs"][w["ref_ids"]].astype(np.complex128)
+    Y = w["y"].astype(np.complex128)
+    lo, mo, no, ro, _ = oracle.correlate_batch(fid, X, Y, J, form=1, want_r=True)
+    trees = [oracle.tree_x(fid, x.astype(np.complex128), J)[0] for x in w["refs"]]
+    worst_rel = 0.0
+    for b in range(B):
+        rb = r[b].cpu().numpy().astype(np.complex128)
+        pyr, _ = oracle.pyramid_y(fid, Y[b], J)
+        for j in range(J + 1):
+            Kj = N >> j
+            err = np.abs(rb[j] - ro[b, j]).max()
+            bound = stated_bound(trees[w["ref_ids"][b]], pyr, N, J, j, Kj)
+            assert err <= bound, f"pulse {b} scale {j}: error {err:.3e} > stated bound {bound:.3e}"
+            worst_rel = max(worst_rel, err / np.abs(ro[b, j]).max())
+        U.check_peak_lags(lag[b], ro[b], 3 * 2.0 ** -16, what=f"{fname} pulse {b}")
+    assert worst_rel < 1e-4, worst_rel
+
+
+@pytest.mark.parametrize("fname", ["legall53", "cdf97"])
+def test_bf16x3_full_size_two_reference_batch_sampled(oracle, fname):
+    """4096 x N=8192, J=5 in the benchmark's launch shape; sampled pulses
+    against the oracle, all peaks against the FP32 path."""
+    fid = U.FLOAT_FILTERS[fname]
+    w = inputs.two_ref_batch(B=4096, N=8192, J=5)
+    r, lag, mag, norm = run(fname, 8192, 5, w["refs"], w["y"], w["ref_ids"], "bf16x3")
+    _, lag32, mag32, _ = run(fname, 8192, 5, w["refs"], w["y"], w["ref_ids"], "fp32", want_r=False)
+    assert (lag[:, 0] == w["delays"]).all()
+    assert np.mean(lag == lag32) > 0.99
+    sample = np.array([0, 7, 2047, 2048, 4095])
+    X = w["refs"][w["ref_ids"][sample]].astype(np.complex128)
+    Y = w["y"][sample].astype(np.complex128)
+    lo, mo, no, ro, _ = oracle.correlate_batch(fid, X, Y, 5, want_r=True)
+    for i, b in enumerate(sample):
+        rb = r[b].cpu().numpy().astype(np.complex128)
+        for j in range(6):
+            rel = np.abs(rb[j] - ro[i, j]).max() / np.abs(ro[i, j]).max()
+            assert rel < 1e-4, (b, j, rel)
+        U.check_peak_lags(lag[b], ro[i], 3 * 2.0 ** -16, what=f"{fname} pulse {b}")
