@@ -640,9 +640,10 @@ int tc_group_tile() { return tc::kTM; }
 
 int tc_launch_count(const sidwt_plan *p) {
     const uint32_t mask = tc_scale_mask(p);
+    const bool pack_refs = p->tc_packed < p->nrefs;
     int n = 0;
     for (int j = 0; j <= p->J; ++j)
-        if (mask & (1u << j)) n += 2;  // pack + correlation
+        if (mask & (1u << j)) n += pack_refs ? 3 : 2;  // (reference pack) + received pack + correlation
     if (((1u << (p->J + 1)) - 1u) & ~mask) n += 1;
     return n;
 }

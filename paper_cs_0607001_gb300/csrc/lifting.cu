@@ -88,6 +88,39 @@ __device__ __forceinline__ int2 to_i2<int2>(int2 v) { return v; }
 __device__ __forceinline__ double norm2d(float2 v) { return (double)v.x * v.x + (double)v.y * v.y; }
 __device__ __forceinline__ double norm2d(int2 v) { return (double)v.x * v.x + (double)v.y * v.y; }
 
+// Energy accumulator (eq. 1): squares in FP32, flushed into an FP64 sum every
+// 32 terms, so the FP64 pipe (slow on this part) sees one add per 32
+// samples while the FP32 rounding stays within 32 terms.
+struct EnAcc {
+    double d = 0.0;
+    float f = 0.0f;
+    int n = 0;
+    __device__ __forceinline__ void add(float x) {
+        f += x;
+        if (++n == 32) {
+            d += (double)f;
+            f = 0.0f;
+            n = 0;
+        }
+    }
+    __device__ __forceinline__ double total() const { return d + (double)f; }
+};
+__device__ __forceinline__ float sq2(float2 v) { return fmaf(v.x, v.x, v.y * v.y); }
+__device__ __forceinline__ long long sq2i(int2 v) { return (long long)v.x * v.x + (long long)v.y * v.y; }
+
+// Deterministic block sum of one int64 per thread, returned as double.
+__device__ double block_sum_i64(long long v, long long *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    long long t = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; ++i) t += red[i];
+    return (double)t;  // valid in thread 0
+}
+
 // Deterministic block sum of one double per thread (blockDim.x multiple of 32).
 __device__ double block_sum(double v, double *red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -225,151 +258,171 @@ __global__ void level_window_i(const TIn *__restrict__ in, int64_t in_stride, in
 // with b = 2^l - 1 + v.  Level 0 reads x, level l >= 1 the stored A band.
 template <typename TIn, typename TTree>
 __global__ void ref_energy_kernel(const TIn *__restrict__ x, const TTree *__restrict__ tree, int64_t N,
-                                  double *__restrict__ out) {
+                                  double *__restrict__ out);
+
+template <>
+__global__ void ref_energy_kernel<float2, float2>(const float2 *__restrict__ x, const float2 *__restrict__ tree,
+                                                  int64_t N, double *__restrict__ out) {
     __shared__ double red[32];
     const int b = blockIdx.x;
     int l = 0;
     while ((2 << l) - 1 <= b) ++l;
     const int v = b - ((1 << l) - 1);
     const int64_t K = N >> l;
-    double s = 0.0;
+    const float2 *X = l == 0 ? x : tree + 2 * N * (int64_t)(l - 1) + (int64_t)v * K;
+    EnAcc acc;
+    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) acc.add(sq2(X[k]));
+    const double t = block_sum(acc.total(), red);
+    if (threadIdx.x == 0) out[b] = t;
+}
+
+template <>
+__global__ void ref_energy_kernel<short2, int2>(const short2 *__restrict__ x, const int2 *__restrict__ tree,
+                                               int64_t N, double *__restrict__ out) {
+    __shared__ long long red[32];
+    const int b = blockIdx.x;
+    int l = 0;
+    while ((2 << l) - 1 <= b) ++l;
+    const int v = b - ((1 << l) - 1);
+    const int64_t K = N >> l;
+    long long acc = 0;
     if (l == 0) {
-        for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
-            TIn t = x[k];
-            s += (double)t.x * t.x + (double)t.y * t.y;
-        }
+        for (int64_t k = threadIdx.x; k < K; k += blockDim.x) acc += sq2i(make_int2(x[k].x, x[k].y));
     } else {
-        const TTree *A = tree + 2 * N * (int64_t)(l - 1) + (int64_t)v * K;
-        for (int64_t k = threadIdx.x; k < K; k += blockDim.x) s += norm2d(A[k]);
+        const int2 *A = tree + 2 * N * (int64_t)(l - 1) + (int64_t)v * K;
+        for (int64_t k = threadIdx.x; k < K; k += blockDim.x) acc += sq2i(A[k]);
     }
-    double t = block_sum(s, red);
+    const double t = block_sum_i64(acc, red);
     if (threadIdx.x == 0) out[b] = t;
 }
 
 // ---------------------------------------------------------------------------
 // Received analysis, all levels in one pass through shared memory.
+// Level l reads its input (the level l-1 approximation, natural order) from
+// one region and writes its approximation to the other; every thread
+// computes whole output pairs (c_l[n], d_l[n]) by running the lifting steps
+// in registers on a 5-pair window read as 128-bit (even, odd) loads, so a
+// level needs a single barrier.
 // ---------------------------------------------------------------------------
+constexpr int kAnalyzeThreads = 512;
+
+__device__ __forceinline__ int wrap_small(int m, int H) {
+    if (m < 0) m += H;
+    if (m >= H) m -= H;
+    if ((unsigned)m >= (unsigned)H) m = ((m % H) + H) % H;  // tiny levels (H < 3)
+    return m;
+}
+
 template <int F>
-__device__ __forceinline__ void smem_steps_f(float2 *E, float2 *O, int H, const LiftCoef &c) {
-    using Sh = LiftShape<F, SIDE_Y>;
+__device__ __forceinline__ void out_pair_f(const float2 *in, int H, int n, const LiftCoef &c, float2 &lo, float2 &hi) {
+    constexpr bool D4 = (F == SIDWT_D4);
+    const float4 *q = reinterpret_cast<const float4 *>(in);  // q[m] = (in[2m], in[2m+1])
+    float2 E[5], O[5];
+    if (D4) {
+        float4 prev = q[wrap_small(n - 3, H)];
 #pragma unroll
-    for (int s = 0; s < Sh::nsteps; ++s) {
-        float2 *X = Sh::target(s) ? O : E;
-        const float2 *Y = Sh::target(s) ? E : O;
-        const int nb = Sh::nb(s);
-        const float c0 = c.c0[s], c1 = c.c1[s];
-        for (int n = threadIdx.x; n < H; n += blockDim.x) {
-            int m = n + nb;
-            m = m < 0 ? m + H : (m >= H ? m - H : m);
-            X[n] = axpy2(X[n], c0, Y[n], c1, Y[m]);
+        for (int i = 0; i < 5; ++i) {
+            const float4 cur = q[wrap_small(n - 2 + i, H)];
+            E[i] = make_float2(cur.x, cur.y);
+            O[i] = make_float2(prev.z, prev.w);  // odd phase of D4: v[2m-1]
+            prev = cur;
         }
-        __syncthreads();
+    } else {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const float4 cur = q[wrap_small(n - 2 + i, H)];
+            E[i] = make_float2(cur.x, cur.y);
+            O[i] = make_float2(cur.z, cur.w);
+        }
     }
+    lift_window<F, SIDE_Y, 2>(E, O, c);
+    lo = scale2(c.ce, E[2]);
+    if (D4) hi = scale2(c.co, make_float2(E[2].x + O[1].x, E[2].y + O[1].y));
+    else hi = scale2(c.co, O[2]);
 }
 
-__device__ __forceinline__ void smem_steps_i(int2 *E, int2 *O, int H) {
-    // y side of the reversible 5/3
-    for (int n = threadIdx.x; n < H; n += blockDim.x) {
-        const int m = n == 0 ? H - 1 : n - 1;
-        E[n] = iadd_shr(E[n], O[n], O[m], 1, 1);
+__device__ __forceinline__ void out_pair_i(const int2 *in, int H, int n, int2 &lo, int2 &hi) {
+    const int4 *q = reinterpret_cast<const int4 *>(in);
+    int2 E[5], O[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const int4 cur = q[wrap_small(n - 2 + i, H)];
+        E[i] = make_int2(cur.x, cur.y);
+        O[i] = make_int2(cur.z, cur.w);
     }
-    __syncthreads();
-    for (int n = threadIdx.x; n < H; n += blockDim.x) {
-        const int m = n + 1 == H ? 0 : n + 1;
-        O[n] = isub_shr(O[n], E[n], E[m], 2, 2);
-    }
-    __syncthreads();
+    int53_window<SIDE_Y, 2>(E, O);
+    lo = E[2];
+    hi = O[2];
 }
 
-// One CTA per pulse.  Shared memory: 1.5 N elements of T.
+// One CTA per pulse.  Shared memory: 1.5 N elements of T (float2 or int2).
 template <int F, typename T>
-__global__ void __launch_bounds__(256) analyze_smem_kernel(const void *__restrict__ y_in, int64_t N, int J,
-                                                           float2 *__restrict__ pyr_f, int2 *__restrict__ pyr_i,
-                                                           int64_t pyr_elems, double *__restrict__ yen,
-                                                           LiftCoef c) {
+__global__ void __launch_bounds__(kAnalyzeThreads) analyze_smem_kernel(const void *__restrict__ y_in, int64_t N, int J,
+                                                                       float2 *__restrict__ pyr_f,
+                                                                       int2 *__restrict__ pyr_i, int64_t pyr_elems,
+                                                                       double *__restrict__ yen, LiftCoef c) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T *sm = reinterpret_cast<T *>(smraw);
     __shared__ double red[32];
+    __shared__ long long redi[32];
     constexpr bool INT = (F == SIDWT_LEGALL53_INT);
-    constexpr bool D4 = (F == SIDWT_D4);
     const int64_t b = blockIdx.x;
-    const int H1 = (int)(N / 2);
-    double en = 0.0;
+    const int Nh = (int)(N / 2);
+    EnAcc en;
+    long long eni = 0;
 
-    // level-1 load with the polyphase split fused in: element pairs
-    // (y[2n], y[2n+1]) arrive in one 128-bit (float) or 64-bit (int16) load
-    T *E = sm, *O = sm + H1;
+    // level-0 load, 128-bit (float) or 64-bit (int16 I/Q) per sample pair
     if constexpr (INT) {
-        const short4 *y4 = reinterpret_cast<const short4 *>(y_in) + b * H1;
-        for (int n = threadIdx.x; n < H1; n += blockDim.x) {
-            short4 v = y4[n];
-            int2 e = make_int2(v.x, v.y), o = make_int2(v.z, v.w);
-            E[n] = e;
-            O[n] = o;
-            en += norm2d(e) + norm2d(o);
+        const short4 *y4 = reinterpret_cast<const short4 *>(y_in) + b * Nh;
+        int4 *d4 = reinterpret_cast<int4 *>(sm);
+        for (int n = threadIdx.x; n < Nh; n += blockDim.x) {
+            const short4 v = y4[n];
+            d4[n] = make_int4(v.x, v.y, v.z, v.w);
+            eni += sq2i(make_int2(v.x, v.y)) + sq2i(make_int2(v.z, v.w));
         }
     } else {
-        const float4 *y4 = reinterpret_cast<const float4 *>(y_in) + b * H1;
-        for (int n = threadIdx.x; n < H1; n += blockDim.x) {
-            float4 v = y4[n];
-            float2 e = make_float2(v.x, v.y), o = make_float2(v.z, v.w);
-            E[n] = e;
-            if (D4) O[n + 1 == H1 ? 0 : n + 1] = o;  // odd phase of D4 is y[2n-1]
-            else O[n] = o;
-            en += norm2d(e) + norm2d(o);
+        const float4 *y4 = reinterpret_cast<const float4 *>(y_in) + b * Nh;
+        float4 *d4 = reinterpret_cast<float4 *>(sm);
+        for (int n = threadIdx.x; n < Nh; n += blockDim.x) {
+            const float4 v = y4[n];
+            d4[n] = v;
+            en.add(sq2(make_float2(v.x, v.y)));
+            en.add(sq2(make_float2(v.z, v.w)));
         }
     }
     {
-        double t = block_sum(en, red);
+        const double t = INT ? block_sum_i64(eni, redi) : block_sum(en.total(), red);
         if (threadIdx.x == 0) yen[b * (J + 1)] = t;
     }
     __syncthreads();
 
     for (int l = 1; l <= J; ++l) {
         const int H = (int)(N >> l);
-        // steps
-        if constexpr (INT) smem_steps_i(reinterpret_cast<int2 *>(E), reinterpret_cast<int2 *>(O), H);
-        else smem_steps_f<F>(reinterpret_cast<float2 *>(E), reinterpret_cast<float2 *>(O), H, c);
-        // outputs: c_l, d_l to HBM; c_l split into the next level's phases
+        const T *in = sm + ((l & 1) ? 0 : N);
+        T *out = sm + ((l & 1) ? N : 0);
         const int64_t off = b * pyr_elems + 2 * N - 4 * (int64_t)H;
-        const bool more = l < J;
-        const int Hn = H / 2;
-        T *En = sm + ((l + 1) % 2 == 0 ? N : 0);
-        T *On = En + Hn;
-        en = 0.0;
+        en = EnAcc();
+        eni = 0;
         for (int n = threadIdx.x; n < H; n += blockDim.x) {
             T lo, hi;
             if constexpr (INT) {
-                lo = E[n];
-                hi = O[n];
+                out_pair_i(reinterpret_cast<const int2 *>(in), H, n, lo, hi);
                 pyr_i[off + n] = lo;
                 pyr_i[off + H + n] = hi;
                 pyr_f[off + n] = to_f2(lo);
                 pyr_f[off + H + n] = to_f2(hi);
+                eni += sq2i(lo);
             } else {
-                const float2 e = E[n];
-                lo = scale2(c.ce, e);
-                if (D4) {
-                    const float2 om = O[n == 0 ? H - 1 : n - 1];
-                    hi = scale2(c.co, make_float2(e.x + om.x, e.y + om.y));
-                } else {
-                    hi = scale2(c.co, O[n]);
-                }
+                out_pair_f<F>(reinterpret_cast<const float2 *>(in), H, n, c, lo, hi);
                 pyr_f[off + n] = lo;
                 pyr_f[off + H + n] = hi;
+                en.add(sq2(lo));
             }
-            en += norm2d(lo);
-            if (more) {
-                if ((n & 1) == 0) En[n >> 1] = lo;
-                else if (D4) On[((n + 1) >> 1) == Hn ? 0 : ((n + 1) >> 1)] = lo;
-                else On[n >> 1] = lo;
-            }
+            out[n] = lo;
         }
-        double t = block_sum(en, red);
+        const double t = INT ? block_sum_i64(eni, redi) : block_sum(en.total(), red);
         if (threadIdx.x == 0) yen[b * (J + 1) + l] = t;
         __syncthreads();
-        E = En;
-        O = On;
     }
 }
 
@@ -378,29 +431,33 @@ __global__ void pyr_energy_kernel(const float2 *__restrict__ y, const float2 *__
                                   const int2 *__restrict__ pyr_i, const short2 *__restrict__ y_i, int64_t N, int J,
                                   int64_t pyr_elems, double *__restrict__ yen) {
     __shared__ double red[32];
+    __shared__ long long redi[32];
     const int64_t b = blockIdx.x;
     const int l = blockIdx.y;
     const int64_t K = N >> l;
-    double s = 0.0;
-    if (l == 0) {
-        if (y_i) {
+    const int64_t off = b * pyr_elems + 2 * N - 4 * K;
+    if (pyr_i) {
+        long long acc = 0;
+        if (l == 0) {
             for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
-                short2 t = y_i[b * N + k];
-                s += (double)t.x * t.x + (double)t.y * t.y;
+                const short2 t = y_i[b * N + k];
+                acc += sq2i(make_int2(t.x, t.y));
             }
         } else {
-            for (int64_t k = threadIdx.x; k < K; k += blockDim.x) s += norm2d(y[b * N + k]);
+            for (int64_t k = threadIdx.x; k < K; k += blockDim.x) acc += sq2i(pyr_i[off + k]);
         }
+        const double t = block_sum_i64(acc, redi);
+        if (threadIdx.x == 0) yen[b * (J + 1) + l] = t;
     } else {
-        const int64_t off = b * pyr_elems + 2 * N - 4 * K;
-        if (pyr_i) {
-            for (int64_t k = threadIdx.x; k < K; k += blockDim.x) s += norm2d(pyr_i[off + k]);
+        EnAcc acc;
+        if (l == 0) {
+            for (int64_t k = threadIdx.x; k < K; k += blockDim.x) acc.add(sq2(y[b * N + k]));
         } else {
-            for (int64_t k = threadIdx.x; k < K; k += blockDim.x) s += norm2d(pyr_f[off + k]);
+            for (int64_t k = threadIdx.x; k < K; k += blockDim.x) acc.add(sq2(pyr_f[off + k]));
         }
+        const double t = block_sum(acc.total(), red);
+        if (threadIdx.x == 0) yen[b * (J + 1) + l] = t;
     }
-    double t = block_sum(s, red);
-    if (threadIdx.x == 0) yen[b * (J + 1) + l] = t;
 }
 
 // ---------------------------------------------------------------------------
@@ -490,7 +547,7 @@ static cudaError_t launch_smem(sidwt_plan *p, const void *y, int64_t B, cudaStre
     auto k = analyze_smem_kernel<F, T>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<(unsigned)B, 256, smem, s>>>(y, p->N, p->J, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c);
+    k<<<(unsigned)B, kAnalyzeThreads, smem, s>>>(y, p->N, p->J, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c);
     return cudaGetLastError();
 }
 
