@@ -197,6 +197,71 @@ sidwt_status sidwt_read_timing(sidwt_plan *p, sidwt_timing *out, int reset);
  * cleared. */
 sidwt_status sidwt_check(sidwt_plan *p, sidwt_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Ragged batches: pulses of uneven length N, depth J and filter, each against
+ * its own stored signal, correlated in one persistent launch (all lags, all
+ * J+1 scales, peaks), optionally replayed as a CUDA graph.  Every pair is a
+ * batch of one, so the correlation runs on the CUDA cores in FP32; the work
+ * list is ordered by cost (largest first) and pulled by a persistent grid.
+ * Float filters only (D4, LeGall 5/3, CDF 9/7).  An object is not
+ * thread-safe and holds one batch in flight.
+ * ------------------------------------------------------------------------- */
+typedef struct sidwt_ragged sidwt_ragged;
+
+/* Create an empty ragged object.  Tile shapes come from the tuning cache
+ * named by the environment variable SIDWT_TUNE_CACHE when it exists
+ * (lines "log2(band length) shifts-per-thread"), else from defaults. */
+sidwt_status sidwt_ragged_create(sidwt_ragged **out);
+sidwt_status sidwt_ragged_destroy(sidwt_ragged *r);
+
+/* Pre-size the reference store (tree_elems = sum of 2 J N over the stored
+ * signals), the received pyramid (pyr_elems = sum of 2N - 2(N >> J) over a
+ * batch) and the peak slots (slots = sum of J + 1 over a batch). */
+sidwt_status sidwt_ragged_reserve(sidwt_ragged *r, int64_t tree_elems, int64_t pyr_elems, int64_t slots);
+
+int32_t sidwt_ragged_num_refs(const sidwt_ragged *r);
+
+/* Store one signal x_dev (complex64[N]) for filter f and depth J (same rules
+ * as sidwt_plan_create); its SIDWT tree and energies stay resident. */
+sidwt_status sidwt_ragged_store_reference(sidwt_ragged *r, sidwt_filter f, int64_t N, int J, const void *x_dev,
+                                          int32_t *ref_id_out, sidwt_stream stream);
+
+/* Correlate n_items pulses: item i is the complex64 pulse starting at element
+ * y_offsets_host[i] of y_dev (even offsets: 16-byte aligned pulses), whose
+ * length, depth and filter are those of reference ref_ids_host[i]; y_dev
+ * holds y_elems complex64 elements and every pulse must lie inside it (else
+ * SIDWT_EINVAL).  Peaks land in slots: item i's scales 0..J_i at slot
+ * sum_{i' < i} (J_i' + 1).  The host arrays are read before the call
+ * returns. */
+sidwt_status sidwt_ragged_correlate(sidwt_ragged *r, int64_t n_items, const int32_t *ref_ids_host,
+                                    const int64_t *y_offsets_host, const void *y_dev, int64_t y_elems,
+                                    sidwt_stream stream);
+
+/* Build and instantiate a CUDA graph of the whole batch (lifting, the
+ * persistent correlation, peaks) for this item layout and pulse buffer; the
+ * layout is copied to device memory owned by the graph.  Replay with
+ * sidwt_ragged_graph_launch after refilling y_dev in place.  launches_out
+ * (optional) receives the number of kernels in the graph. */
+sidwt_status sidwt_ragged_graph_create(sidwt_ragged *r, int64_t n_items, const int32_t *ref_ids_host,
+                                       const int64_t *y_offsets_host, const void *y_dev, int64_t y_elems,
+                                       int32_t *launches_out);
+sidwt_status sidwt_ragged_graph_launch(sidwt_ragged *r, sidwt_stream stream);
+
+/* Copy the last batch's peaks (n_slots = its sum of J_i + 1; same meaning as
+ * sidwt_peaks).  Any output may be NULL. */
+sidwt_status sidwt_ragged_peaks(sidwt_ragged *r, int64_t n_slots, int32_t *lag_dev, float *mag_dev, double *norm_dev,
+                                sidwt_stream stream);
+
+/* Autotune the shifts per thread of the correlation tiles for band lengths
+ * 2^8 .. 2^15 by timing each candidate (1, 2, 4, 8) on a synthetic pair, and
+ * write the choice to cache_path (or SIDWT_TUNE_CACHE; NULL and unset: not
+ * written).  Allocates and synchronises; call outside stream capture. */
+sidwt_status sidwt_ragged_autotune(sidwt_ragged *r, const char *cache_path, sidwt_stream stream);
+
+/* The current choice: mq_by_log2_band[k] shifts per thread for bands of
+ * length in [2^k, 2^(k+1)) (32 entries). */
+sidwt_status sidwt_ragged_tuning(const sidwt_ragged *r, int32_t *mq_by_log2_band);
+
 /* Diagnostic: one tcgen05 MMA (M = 128, N = 64, K = 16, bf16 in, f32 out)
  * on fixed integer-valued operands laid out exactly as the tensor-core
  * correlation lays them out (K-major A; the overlapping MN-major window as

@@ -355,25 +355,21 @@ __device__ __forceinline__ void out_pair_i(const int2 *in, int H, int n, int2 &l
     hi = O[2];
 }
 
-// One CTA per pulse.  Shared memory: 1.5 N elements of T (float2 or int2).
+// All J levels of one pulse by one CTA.  y: the pulse (complex64 or int16
+// I/Q); pyr_f / pyr_i: its pyramid row; yen: its J+1 energies.  Shared
+// memory: 1.5 N elements of T (float2 or int2).
 template <int F, typename T>
-__global__ void __launch_bounds__(kAnalyzeThreads) analyze_smem_kernel(const void *__restrict__ y_in, int64_t N, int J,
-                                                                       float2 *__restrict__ pyr_f,
-                                                                       int2 *__restrict__ pyr_i, int64_t pyr_elems,
-                                                                       double *__restrict__ yen, LiftCoef c) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T *sm = reinterpret_cast<T *>(smraw);
-    __shared__ double red[32];
-    __shared__ long long redi[32];
+__device__ __forceinline__ void analyze_one(const void *__restrict__ y, int64_t N, int J, float2 *__restrict__ pyr_f,
+                                            int2 *__restrict__ pyr_i, double *__restrict__ yen, const LiftCoef &c,
+                                            T *sm, double *red, long long *redi) {
     constexpr bool INT = (F == SIDWT_LEGALL53_INT);
-    const int64_t b = blockIdx.x;
     const int Nh = (int)(N / 2);
     EnAcc en;
     long long eni = 0;
 
     // level-0 load, 128-bit (float) or 64-bit (int16 I/Q) per sample pair
     if constexpr (INT) {
-        const short4 *y4 = reinterpret_cast<const short4 *>(y_in) + b * Nh;
+        const short4 *y4 = reinterpret_cast<const short4 *>(y);
         int4 *d4 = reinterpret_cast<int4 *>(sm);
         for (int n = threadIdx.x; n < Nh; n += blockDim.x) {
             const short4 v = y4[n];
@@ -381,7 +377,7 @@ __global__ void __launch_bounds__(kAnalyzeThreads) analyze_smem_kernel(const voi
             eni += sq2i(make_int2(v.x, v.y)) + sq2i(make_int2(v.z, v.w));
         }
     } else {
-        const float4 *y4 = reinterpret_cast<const float4 *>(y_in) + b * Nh;
+        const float4 *y4 = reinterpret_cast<const float4 *>(y);
         float4 *d4 = reinterpret_cast<float4 *>(sm);
         for (int n = threadIdx.x; n < Nh; n += blockDim.x) {
             const float4 v = y4[n];
@@ -392,7 +388,7 @@ __global__ void __launch_bounds__(kAnalyzeThreads) analyze_smem_kernel(const voi
     }
     {
         const double t = INT ? block_sum_i64(eni, redi) : block_sum(en.total(), red);
-        if (threadIdx.x == 0) yen[b * (J + 1)] = t;
+        if (threadIdx.x == 0) yen[0] = t;
     }
     __syncthreads();
 
@@ -400,7 +396,7 @@ __global__ void __launch_bounds__(kAnalyzeThreads) analyze_smem_kernel(const voi
         const int H = (int)(N >> l);
         const T *in = sm + ((l & 1) ? 0 : N);
         T *out = sm + ((l & 1) ? N : 0);
-        const int64_t off = b * pyr_elems + 2 * N - 4 * (int64_t)H;
+        const int64_t off = 2 * N - 4 * (int64_t)H;
         en = EnAcc();
         eni = 0;
         for (int n = threadIdx.x; n < H; n += blockDim.x) {
@@ -421,9 +417,40 @@ __global__ void __launch_bounds__(kAnalyzeThreads) analyze_smem_kernel(const voi
             out[n] = lo;
         }
         const double t = INT ? block_sum_i64(eni, redi) : block_sum(en.total(), red);
-        if (threadIdx.x == 0) yen[b * (J + 1) + l] = t;
+        if (threadIdx.x == 0) yen[l] = t;
         __syncthreads();
     }
+}
+
+// One CTA per pulse of a uniform batch.
+template <int F, typename T>
+__global__ void __launch_bounds__(kAnalyzeThreads) analyze_smem_kernel(const void *__restrict__ y_in, int64_t N, int J,
+                                                                       float2 *__restrict__ pyr_f,
+                                                                       int2 *__restrict__ pyr_i, int64_t pyr_elems,
+                                                                       double *__restrict__ yen, LiftCoef c) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double red[32];
+    __shared__ long long redi[32];
+    constexpr bool INT = (F == SIDWT_LEGALL53_INT);
+    const int64_t b = blockIdx.x;
+    const char *y = reinterpret_cast<const char *>(y_in) + b * N * (INT ? 4 : 8);
+    analyze_one<F, T>(y, N, J, pyr_f + b * pyr_elems, INT ? pyr_i + b * pyr_elems : nullptr, yen + b * (J + 1), c,
+                      reinterpret_cast<T *>(smraw), red, redi);
+}
+
+// One CTA per listed pulse of a ragged batch (float filters): item k has its
+// own N and J; its pulse, pyramid row and energies sit at the given offsets.
+template <int F>
+__global__ void __launch_bounds__(kAnalyzeThreads) analyze_ragged_kernel(const float2 *__restrict__ y,
+                                                                         const RaggedLift *__restrict__ items,
+                                                                         float2 *__restrict__ pyr,
+                                                                         double *__restrict__ yen, LiftCoef c) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double red[32];
+    __shared__ long long redi[32];
+    const RaggedLift it = items[blockIdx.x];
+    analyze_one<F, float2>(y + it.y_off, it.N, it.J, pyr + it.pyr_off, nullptr, yen + it.yen_off, c,
+                           reinterpret_cast<float2 *>(smraw), red, redi);
 }
 
 // Energies of the received pyramid for the window path (c_l read back).
@@ -463,7 +490,7 @@ __global__ void pyr_energy_kernel(const float2 *__restrict__ y, const float2 *__
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
-static constexpr int kSmemLimit = 227 * 1024;
+static constexpr int kSmemLimit = 227 * 1024 - 1024;  // dynamic budget; 1 KB left for static shared memory
 
 template <int F, typename TIn>
 static void launch_level_f(int side, const TIn *in, int64_t in_stride, int nrows, int nchild, int64_t K,
@@ -596,6 +623,130 @@ sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStre
                                         p->pyr_elems, p->yen);
     e = cudaGetLastError();
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "analysis (window path) launch");
+}
+
+// ---------------------------------------------------------------------------
+// Ragged batches
+// ---------------------------------------------------------------------------
+int64_t analyze_smem_max_n() { return (int64_t)kSmemLimit / 12; }
+
+// Per-level window lifting of long pulses: block (x, item) computes outputs
+// x*128.. of item's level l from its level l-1 approximation (y at l = 1).
+template <int F>
+__global__ void ragged_level_kernel(const float2 *__restrict__ y, const RaggedLift *__restrict__ items,
+                                    float2 *__restrict__ pyr, int l, LiftCoef c) {
+    const RaggedLift it = items[blockIdx.y];
+    if (l > it.J) return;
+    const int64_t N = it.N;
+    const int64_t K = N >> (l - 1), H = K / 2;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= H) return;
+    const float2 *v = (l == 1) ? y + it.y_off : pyr + it.pyr_off + (2 * N - 4 * K);
+    using Sh = LiftShape<F, SIDE_Y>;
+    float2 E[2 * WR + 1], O[2 * WR + 1];
+#pragma unroll
+    for (int i = 0; i <= 2 * WR; ++i) {
+        const int64_t m = n - WR + i;
+        E[i] = v[wrapi(2 * m, K)];
+        O[i] = v[wrapi(Sh::d4 ? 2 * m - 1 : 2 * m + 1, K)];
+    }
+    lift_window<F, SIDE_Y, WR>(E, O, c);
+    const float2 lo = scale2(c.ce, E[WR]);
+    float2 hi;
+    if (Sh::d4) hi = scale2(c.co, make_float2(E[WR].x + O[WR - 1].x, E[WR].y + O[WR - 1].y));
+    else hi = scale2(c.co, O[WR]);
+    float2 *o = pyr + it.pyr_off + (2 * N - 4 * H);
+    o[n] = lo;
+    o[H + n] = hi;
+}
+
+// Energies of long ragged pulses: block (level l, item).
+__global__ void ragged_energy_kernel(const float2 *__restrict__ y, const RaggedLift *__restrict__ items,
+                                     const float2 *__restrict__ pyr, double *__restrict__ yen) {
+    __shared__ double red[32];
+    const RaggedLift it = items[blockIdx.y];
+    const int l = blockIdx.x;
+    if (l > it.J) return;
+    const int64_t K = it.N >> l;
+    const float2 *v = l == 0 ? y + it.y_off : pyr + it.pyr_off + (2 * it.N - 4 * K);
+    EnAcc acc;
+    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) acc.add(sq2(v[k]));
+    const double t = block_sum(acc.total(), red);
+    if (threadIdx.x == 0) yen[it.yen_off + l] = t;
+}
+
+// The ragged kernels get the whole shared-memory budget once, outside any
+// stream capture, so that launching them needs no attribute call.
+cudaError_t prepare_ragged_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(analyze_ragged_kernel<SIDWT_D4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(analyze_ragged_kernel<SIDWT_LEGALL53>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(analyze_ragged_kernel<SIDWT_CDF97>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemLimit);
+    return e;
+}
+
+template <int F>
+static cudaError_t launch_ragged_smem(const float2 *y, const RaggedLift *items, int n, int64_t maxN, float2 *pyr,
+                                      double *yen, cudaStream_t s) {
+    const size_t smem = (size_t)(maxN + maxN / 2) * 8;
+    analyze_ragged_kernel<F><<<n, kAnalyzeThreads, smem, s>>>(y, items, pyr, yen, lift_coef(F, SIDE_Y));
+    return cudaGetLastError();
+}
+
+template <int F>
+static cudaError_t launch_ragged_window(const float2 *y, const RaggedLift *items, int n, int64_t maxN, int maxJ,
+                                        float2 *pyr, double *yen, cudaStream_t s) {
+    const LiftCoef c = lift_coef(F, SIDE_Y);
+    for (int l = 1; l <= maxJ; ++l) {
+        const int64_t H = maxN >> l;
+        dim3 g((unsigned)((H + 127) / 128), (unsigned)n);
+        ragged_level_kernel<F><<<g, 128, 0, s>>>(y, items, pyr, l, c);
+    }
+    dim3 g((unsigned)(maxJ + 1), (unsigned)n);
+    ragged_energy_kernel<<<g, 256, 0, s>>>(y, items, pyr, yen);
+    return cudaGetLastError();
+}
+
+// Items grouped by filter and path: groups[f] (shared-memory path) and
+// long_groups[f] (window path) are device item lists with their counts and
+// the largest N / J in each.
+sidwt_status analyze_ragged(const float2 *y, const RaggedLiftGroups &g, float2 *pyr, double *yen, cudaStream_t s,
+                            int *launches) {
+    cudaError_t e = cudaSuccess;
+    int nl = 0;
+    for (int f = 0; f < 3 && e == cudaSuccess; ++f) {
+        if (g.n_smem[f] > 0) {
+            switch (f) {
+            case SIDWT_D4: e = launch_ragged_smem<SIDWT_D4>(y, g.smem[f], g.n_smem[f], g.maxN_smem[f], pyr, yen, s); break;
+            case SIDWT_LEGALL53:
+                e = launch_ragged_smem<SIDWT_LEGALL53>(y, g.smem[f], g.n_smem[f], g.maxN_smem[f], pyr, yen, s);
+                break;
+            default: e = launch_ragged_smem<SIDWT_CDF97>(y, g.smem[f], g.n_smem[f], g.maxN_smem[f], pyr, yen, s);
+            }
+            ++nl;
+        }
+        if (e == cudaSuccess && g.n_long[f] > 0) {
+            switch (f) {
+            case SIDWT_D4:
+                e = launch_ragged_window<SIDWT_D4>(y, g.lng[f], g.n_long[f], g.maxN_long[f], g.maxJ_long[f], pyr, yen, s);
+                break;
+            case SIDWT_LEGALL53:
+                e = launch_ragged_window<SIDWT_LEGALL53>(y, g.lng[f], g.n_long[f], g.maxN_long[f], g.maxJ_long[f], pyr,
+                                                         yen, s);
+                break;
+            default:
+                e = launch_ragged_window<SIDWT_CDF97>(y, g.lng[f], g.n_long[f], g.maxN_long[f], g.maxJ_long[f], pyr,
+                                                      yen, s);
+            }
+            nl += g.maxJ_long[f] + 1;
+        }
+    }
+    if (launches) *launches = nl;
+    return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "ragged analysis launch");
 }
 
 }  // namespace sidwt

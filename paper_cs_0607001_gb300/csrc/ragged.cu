@@ -1,0 +1,846 @@
+// Ragged batches: thousands of pulses of uneven length N, depth J and
+// filter, each against its own stored signal, in one persistent correlation
+// launch (optionally replayed as a CUDA graph), with tile shapes chosen by an
+// autotuner.
+//
+// Every pair is a batch of one, so the correlation runs on the CUDA cores: a
+// work item is a block of circular shifts of one (pair, scale, variant) for
+// bands of 256 samples or more (each thread keeps MQ consecutive shifts and
+// slides an MQ-sample window along k, MQ picked per band-length bucket by the
+// autotuner), or several whole variants of a short band (one shift per
+// thread).  Work items are ordered by cost, largest first, and pulled by a
+// persistent grid from a device counter.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sidwt_internal.cuh"
+
+namespace sidwt {
+namespace rg {
+
+constexpr int kT = 256;     // threads per CTA
+constexpr int kTK = 64;     // k per staged chunk
+constexpr int kMaxMQ = 8;   // shifts per thread, large bands
+constexpr int kSmallBand = 256;
+constexpr int kWin = kT * kMaxMQ + kTK;  // window samples per chunk (upper bound)
+
+struct Item {
+    int64_t pyr_off;   // received pyramid row (float2 elements)
+    int64_t tree_off;  // stored SIDWT tree start
+    int64_t xen_off;   // stored energies start
+    int64_t slot;      // first of the J+1 peak slots (and received energies)
+    int32_t N, J, ref, pad;
+};
+
+struct Work {
+    int32_t item;
+    int16_t j;
+    int16_t mq;    // shifts per thread (large band) or 0 (short band: nvar whole variants)
+    int32_t v0;    // first variant
+    int32_t nvar;  // variants (short band)
+    int32_t q0;    // first shift (large band)
+    int32_t pad;
+};
+
+__device__ __forceinline__ int wpad(int t) { return t + (t >> 3); }
+
+__device__ __forceinline__ unsigned long long peak_key(float2 a, uint32_t D) {
+    const float m2 = a.x * a.x + a.y * a.y;
+    return ((unsigned long long)__float_as_uint(m2) << 32) | (unsigned long long)(0xFFFFFFFFu - D);
+}
+
+__device__ __forceinline__ unsigned long long block_max_key(unsigned long long k, unsigned long long *red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, k, o);
+        k = t > k ? t : k;
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = k;
+    __syncthreads();
+    unsigned long long m = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kT / 32; ++i) m = red[i] > m ? red[i] : m;
+    return m;
+}
+
+// Long band: shifts q0 + t*MQ + l of variant v; r[q] = sum_k conj(w[k - q]) u[k].
+template <int MQ>
+__device__ __forceinline__ void large_tile(const Item &it, const Work &wk, int lev, int Kp, int nb, const float2 *__restrict__ tree,
+                           const float2 *__restrict__ pyr, float2 *us, float2 *ws, unsigned long long *red,
+                           unsigned long long *keys) {
+    constexpr int TQ = kT * MQ;
+    const int tid = threadIdx.x;
+    const int N = it.N;
+    const int q0 = wk.q0, v = wk.v0;
+    const float2 *wa = tree + it.tree_off + 2 * (int64_t)N * (lev - 1) + (int64_t)v * Kp;
+    const float2 *ua = pyr + it.pyr_off + 2 * (int64_t)N - 4 * (int64_t)Kp;
+    float2 acc[MQ];
+#pragma unroll
+    for (int l = 0; l < MQ; ++l) acc[l] = make_float2(0.f, 0.f);
+    const int base = TQ - 1 - tid * MQ;
+    for (int band = 0; band < nb; ++band) {
+        const float2 *w = wa + (int64_t)band * N;
+        const float2 *u = ua + (int64_t)band * Kp;
+        for (int k0 = 0; k0 < Kp; k0 += kTK) {
+            __syncthreads();
+            for (int t = tid; t < kTK; t += kT) us[t] = (k0 + t < Kp) ? u[k0 + t] : make_float2(0.f, 0.f);
+            int idx = (k0 - q0 - (TQ - 1)) % Kp;
+            if (idx < 0) idx += Kp;
+            idx += tid;
+            for (int t = tid; t < TQ + kTK - 1; t += kT) {
+                while (idx >= Kp) idx -= Kp;
+                ws[wpad(t)] = w[idx];
+                idx += kT;
+            }
+            __syncthreads();
+            float2 wv[MQ];
+#pragma unroll
+            for (int l = 0; l < MQ; ++l) wv[l] = ws[wpad(base - l)];
+#pragma unroll 8
+            for (int kk = 0; kk < kTK; ++kk) {
+                if (kk > 0) {
+#pragma unroll
+                    for (int l = MQ - 1; l > 0; --l) wv[l] = wv[l - 1];
+                    wv[0] = ws[wpad(base + kk)];
+                }
+                const float2 uv = us[kk];
+#pragma unroll
+                for (int l = 0; l < MQ; ++l) {
+                    acc[l].x = fmaf(wv[l].x, uv.x, fmaf(wv[l].y, uv.y, acc[l].x));
+                    acc[l].y = fmaf(wv[l].x, uv.y, fmaf(-wv[l].y, uv.x, acc[l].y));
+                }
+            }
+        }
+    }
+    unsigned long long best = 0ull;
+#pragma unroll
+    for (int l = 0; l < MQ; ++l) {
+        const int q = q0 + tid * MQ + l;
+        if (q < Kp) {
+            const unsigned long long k = peak_key(acc[l], ((uint32_t)q << lev) + (uint32_t)v);
+            best = k > best ? k : best;
+        }
+    }
+    best = block_max_key(best, red);
+    if (threadIdx.x == 0 && best) atomicMax(&keys[it.slot + wk.j], best);
+}
+
+// Short band: variants v0 .. v0+nvar-1, one shift per thread.
+__device__ __forceinline__ void small_tile(const Item &it, const Work &wk, int lev, int Kp, int nb, const float2 *__restrict__ tree,
+                           const float2 *__restrict__ pyr, float2 *sm, unsigned long long *red,
+                           unsigned long long *keys) {
+    const int tid = threadIdx.x;
+    const int N = it.N;
+    const int nvar = wk.nvar;
+    float2 *u = sm;                   // nb * Kp
+    float2 *w = sm + nb * Kp;         // [band][variant][Kp]
+    const float2 *ua = pyr + it.pyr_off + 2 * (int64_t)N - 4 * (int64_t)Kp;
+    const float2 *wa = tree + it.tree_off + 2 * (int64_t)N * (lev - 1) + (int64_t)wk.v0 * Kp;
+    __syncthreads();
+    for (int t = tid; t < nb * Kp; t += kT) u[t] = ua[t];
+    for (int t = tid; t < nb * nvar * Kp; t += kT) {
+        const int band = t / (nvar * Kp), r = t % (nvar * Kp);
+        w[t] = wa[(int64_t)band * N + r];
+    }
+    __syncthreads();
+    unsigned long long best = 0ull;
+    if (tid < nvar * Kp) {
+        const int vi = tid / Kp, q = tid % Kp;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int band = 0; band < nb; ++band) {
+            const float2 *wb = w + (band * nvar + vi) * Kp;
+            const float2 *ub = u + band * Kp;
+            int idx = (Kp - q) % Kp;  // (k - q) mod Kp at k = 0
+            for (int k = 0; k < Kp; ++k) {
+                const float2 wv = wb[idx], uv = ub[k];
+                acc.x = fmaf(wv.x, uv.x, fmaf(wv.y, uv.y, acc.x));
+                acc.y = fmaf(wv.x, uv.y, fmaf(-wv.y, uv.x, acc.y));
+                if (++idx == Kp) idx = 0;
+            }
+        }
+        best = peak_key(acc, ((uint32_t)q << lev) + (uint32_t)(wk.v0 + vi));
+    }
+    best = block_max_key(best, red);
+    if (threadIdx.x == 0 && best) atomicMax(&keys[it.slot + wk.j], best);
+}
+
+__global__ void __launch_bounds__(kT, 2) corr_ragged_kernel(const Item *__restrict__ items, const Work *__restrict__ work,
+                                                         int nwork, int *counter, const float2 *__restrict__ tree,
+                                                         const float2 *__restrict__ pyr,
+                                                         unsigned long long *__restrict__ keys) {
+    __shared__ float2 us[kTK];
+    __shared__ float2 ws[kWin + kWin / 8 + 8];
+    __shared__ unsigned long long red[kT / 32];
+    __shared__ int s_w;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_w = atomicAdd(counter, 1);
+        __syncthreads();
+        const int w = s_w;
+        if (w >= nwork) break;
+        const Work wk = work[w];
+        const Item it = items[wk.item];
+        const int lev = wk.j < it.J ? wk.j + 1 : it.J;
+        const int Kp = it.N >> lev;
+        const int nb = wk.j < it.J ? 2 : 1;
+        switch (wk.mq) {
+        case 0: small_tile(it, wk, lev, Kp, nb, tree, pyr, ws, red, keys); break;
+        case 1: large_tile<1>(it, wk, lev, Kp, nb, tree, pyr, us, ws, red, keys); break;
+        case 2: large_tile<2>(it, wk, lev, Kp, nb, tree, pyr, us, ws, red, keys); break;
+        case 4: large_tile<4>(it, wk, lev, Kp, nb, tree, pyr, us, ws, red, keys); break;
+        default: large_tile<8>(it, wk, lev, Kp, nb, tree, pyr, us, ws, red, keys); break;
+        }
+    }
+}
+
+__global__ void finalize_ragged_kernel(const unsigned long long *__restrict__ keys, const int32_t *__restrict__ slot_item,
+                                       const Item *__restrict__ items, const double *__restrict__ xen,
+                                       const double *__restrict__ yen, int64_t nslots, int32_t *__restrict__ lag,
+                                       float *__restrict__ mag, double *__restrict__ norm) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nslots) return;
+    const Item it = items[slot_item[s]];
+    const int j = (int)(s - it.slot);
+    const unsigned long long k = keys[s];
+    if (k == 0ull) {
+        lag[s] = -1;
+        mag[s] = 0.f;
+        norm[s] = 0.0;
+        return;
+    }
+    const uint32_t D = 0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFull);
+    const float m = sqrtf(__uint_as_float((uint32_t)(k >> 32)));
+    lag[s] = (int32_t)D;
+    mag[s] = m;
+    const double den = sqrt(xen[it.xen_off + ((1 << j) - 1) + (D & ((1u << j) - 1u))] * yen[s]);
+    norm[s] = den > 0.0 ? (double)m / den : 0.0;
+}
+
+__global__ void fill_kernel(float2 *x, int64_t n, uint32_t seed) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t h = (uint32_t)i * 2654435761u ^ seed;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    x[i] = make_float2((float)(h & 0xffff) / 32768.f - 1.f, (float)(h >> 16) / 32768.f - 1.f);
+}
+
+}  // namespace rg
+}  // namespace sidwt
+
+using namespace sidwt;
+
+struct RefInfo {
+    int filter;
+    int64_t N;
+    int J;
+    int64_t tree_off, xen_off;
+};
+
+struct RaggedLayout {  // everything a batch needs on the device, built on the host
+    std::vector<rg::Item> items;
+    std::vector<rg::Work> work;
+    std::vector<RaggedLift> lift[2][3];  // [path: smem, long][filter]
+    std::vector<int32_t> slot_item;
+    int64_t pyr_elems = 0, slots = 0;
+    int64_t maxN[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    int maxJ_long[3] = {0, 0, 0};
+};
+
+struct DevLayout {  // device copy of a RaggedLayout
+    rg::Item *items = nullptr;
+    rg::Work *work = nullptr;
+    RaggedLift *lift = nullptr;
+    int32_t *slot_item = nullptr;
+    int64_t cap_items = 0, cap_work = 0, cap_lift = 0, cap_slots = 0;
+    RaggedLiftGroups groups;
+    int nwork = 0;
+};
+
+struct sidwt_ragged {
+    std::vector<RefInfo> refs;
+    float2 *tree = nullptr;
+    int64_t tree_cap = 0, tree_used = 0;
+    double *xen = nullptr;
+    int64_t xen_cap = 0, xen_used = 0;
+    // batch workspace
+    float2 *pyr = nullptr;
+    int64_t pyr_cap = 0;
+    double *yen = nullptr;
+    unsigned long long *keys = nullptr;
+    int32_t *lag = nullptr;
+    float *mag = nullptr;
+    double *norm = nullptr;
+    int64_t slot_cap = 0;
+    int *counter = nullptr;
+    DevLayout dl;       // layout of direct correlate calls
+    DevLayout gl;       // layout owned by the captured graph
+    void *h_stage = nullptr;
+    size_t h_stage_bytes = 0;
+    int64_t last_slots = -1;
+    // graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t graph_slots = 0;
+    int graph_launches = 0;
+    // tuning: shifts per thread by floor(log2(band length))
+    int mq_for[32];
+    int sms = 0;
+};
+
+namespace {
+
+template <typename T>
+sidwt_status grow(T **p, int64_t *cap, int64_t need, int64_t keep, const char *what) {
+    if (need <= *cap) return SIDWT_OK;
+    const int64_t nc = std::max<int64_t>(need, *cap * 2);
+    T *q = nullptr;
+    if (cudaMalloc(&q, (size_t)nc * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("device allocation failed: ") + what);
+        return SIDWT_ENOMEM;
+    }
+    if (*p) {
+        if (keep > 0) cudaMemcpy(q, *p, (size_t)keep * sizeof(T), cudaMemcpyDeviceToDevice);
+        cudaFree(*p);
+    }
+    *p = q;
+    *cap = nc;
+    return SIDWT_OK;
+}
+
+int default_mq(int lg) { return lg >= 11 ? 8 : (lg >= 10 ? 4 : (lg >= 9 ? 2 : 1)); }
+
+// Builds the device-side description of a batch on the host.
+sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_ids, const int64_t *y_off,
+                          int64_t y_elems, RaggedLayout &L) {
+    L = RaggedLayout();
+    L.items.resize((size_t)n);
+    const int64_t smem_max = analyze_smem_max_n();
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t rid = ref_ids[i];
+        if (rid < 0 || rid >= (int32_t)r->refs.size()) {
+            set_error("reference id out of range in item " + std::to_string(i));
+            return SIDWT_EINVAL;
+        }
+        if (y_off[i] < 0 || (y_off[i] & 1)) {
+            set_error("pulse offsets must be even and non-negative (16-byte aligned pulses)");
+            return SIDWT_EINVAL;
+        }
+        const RefInfo &ri = r->refs[(size_t)rid];
+        if (y_off[i] + ri.N > y_elems) {
+            set_error("item " + std::to_string(i) + " runs past the end of the pulse buffer");
+            return SIDWT_EINVAL;
+        }
+        rg::Item &it = L.items[(size_t)i];
+        it.pyr_off = L.pyr_elems;
+        it.tree_off = ri.tree_off;
+        it.xen_off = ri.xen_off;
+        it.slot = L.slots;
+        it.N = (int32_t)ri.N;
+        it.J = ri.J;
+        it.ref = rid;
+        it.pad = 0;
+        RaggedLift lf{y_off[i], L.pyr_elems, L.slots, (int32_t)ri.N, ri.J};
+        const int path = ri.N <= smem_max ? 0 : 1;
+        L.lift[path][ri.filter].push_back(lf);
+        L.maxN[path][ri.filter] = std::max<int64_t>(L.maxN[path][ri.filter], ri.N);
+        if (path) L.maxJ_long[ri.filter] = std::max(L.maxJ_long[ri.filter], ri.J);
+        for (int j = 0; j <= ri.J; ++j) L.slot_item.push_back((int32_t)i);
+        L.pyr_elems += 2 * ri.N - 2 * (ri.N >> ri.J);
+        L.slots += ri.J + 1;
+    }
+    // work items, bucketed by log2 of their cost, largest first
+    std::vector<std::vector<rg::Work>> buckets(64);
+    for (int64_t i = 0; i < n; ++i) {
+        const rg::Item &it = L.items[(size_t)i];
+        for (int j = 0; j <= it.J; ++j) {
+            const int lev = j < it.J ? j + 1 : it.J;
+            const int64_t Kp = (int64_t)it.N >> lev;
+            const int nb = j < it.J ? 2 : 1;
+            const int nv = 1 << lev;
+            if (Kp >= rg::kSmallBand) {
+                int lg = 0;
+                while ((int64_t(2) << lg) <= Kp) ++lg;
+                int mq = r->mq_for[std::min(lg, 31)];
+                while (mq > 1 && (int64_t)rg::kT * mq > Kp) mq >>= 1;
+                const int64_t TQ = (int64_t)rg::kT * mq;
+                const double cost = (double)TQ * nb * Kp;
+                int b = std::max(0, std::min(63, (int)std::log2(std::max(1.0, cost))));
+                for (int v = 0; v < nv; ++v)
+                    for (int64_t q0 = 0; q0 < Kp; q0 += TQ)
+                        buckets[b].push_back({(int32_t)i, (int16_t)j, (int16_t)mq, v, 1, (int32_t)q0, 0});
+            } else {
+                const int nvar = std::max<int>(1, (int)(rg::kT / Kp));
+                for (int v0 = 0; v0 < nv; v0 += nvar) {
+                    const int cnt = std::min(nvar, nv - v0);
+                    const double cost = (double)cnt * Kp * nb * Kp;
+                    int b = std::max(0, std::min(63, (int)std::log2(std::max(1.0, cost))));
+                    buckets[b].push_back({(int32_t)i, (int16_t)j, 0, v0, cnt, 0, 0});
+                }
+            }
+        }
+    }
+    for (int b = 63; b >= 0; --b) L.work.insert(L.work.end(), buckets[b].begin(), buckets[b].end());
+    if (L.work.size() > 0x7fffffff) {
+        set_error("too many work items");
+        return SIDWT_EINVAL;
+    }
+    return SIDWT_OK;
+}
+
+sidwt_status ensure_dev(DevLayout &d, const RaggedLayout &L) {
+    int64_t nl = 0;
+    for (int p = 0; p < 2; ++p)
+        for (int f = 0; f < 3; ++f) nl += (int64_t)L.lift[p][f].size();
+    sidwt_status st;
+    if ((st = grow(&d.items, &d.cap_items, (int64_t)L.items.size(), 0, "ragged items")) ||
+        (st = grow(&d.work, &d.cap_work, (int64_t)L.work.size(), 0, "ragged work list")) ||
+        (st = grow(&d.lift, &d.cap_lift, nl, 0, "ragged lifting list")) ||
+        (st = grow(&d.slot_item, &d.cap_slots, L.slots, 0, "ragged slot map")))
+        return st;
+    return SIDWT_OK;
+}
+
+// Copies a layout to the device (synchronously when stage is null).
+sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaStream_t s, bool sync) {
+    sidwt_status st = ensure_dev(d, L);
+    if (st) return st;
+    std::vector<RaggedLift> lift;
+    int64_t base = 0;
+    RaggedLiftGroups g;
+    for (int p = 0; p < 2; ++p)
+        for (int f = 0; f < 3; ++f) {
+            const auto &v = L.lift[p][f];
+            if (p == 0) {
+                g.smem[f] = d.lift + base;
+                g.n_smem[f] = (int)v.size();
+                g.maxN_smem[f] = L.maxN[0][f];
+            } else {
+                g.lng[f] = d.lift + base;
+                g.n_long[f] = (int)v.size();
+                g.maxN_long[f] = L.maxN[1][f];
+                g.maxJ_long[f] = L.maxJ_long[f];
+            }
+            lift.insert(lift.end(), v.begin(), v.end());
+            base += (int64_t)v.size();
+        }
+    d.groups = g;
+    d.nwork = (int)L.work.size();
+    const size_t b1 = L.items.size() * sizeof(rg::Item), b2 = L.work.size() * sizeof(rg::Work);
+    const size_t b3 = lift.size() * sizeof(RaggedLift), b4 = L.slot_item.size() * sizeof(int32_t);
+    cudaError_t e = cudaSuccess;
+    if (sync) {
+        if (b1) e = cudaMemcpy(d.items, L.items.data(), b1, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && b2) e = cudaMemcpy(d.work, L.work.data(), b2, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && b3) e = cudaMemcpy(d.lift, lift.data(), b3, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && b4) e = cudaMemcpy(d.slot_item, L.slot_item.data(), b4, cudaMemcpyHostToDevice);
+        return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "ragged layout upload");
+    }
+    // asynchronous: through the object's pinned staging buffer (the previous
+    // upload has been consumed once the stream reaches this point)
+    const size_t tot = b1 + b2 + b3 + b4 + 64;
+    if (tot > r->h_stage_bytes) {
+        cudaStreamSynchronize(s);
+        if (r->h_stage) cudaFreeHost(r->h_stage);
+        r->h_stage = nullptr;
+        r->h_stage_bytes = 0;
+        if (cudaMallocHost(&r->h_stage, tot * 2) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("pinned staging allocation failed");
+            return SIDWT_ENOMEM;
+        }
+        r->h_stage_bytes = tot * 2;
+    } else {
+        cudaStreamSynchronize(s);  // the staging buffer may still feed the previous call's copies
+    }
+    char *h = static_cast<char *>(r->h_stage);
+    size_t o = 0;
+    auto put = [&](void *dst, const void *src, size_t n) {
+        if (!n || e != cudaSuccess) return;
+        std::memcpy(h + o, src, n);
+        e = cudaMemcpyAsync(dst, h + o, n, cudaMemcpyHostToDevice, s);
+        o += (n + 15) & ~size_t(15);
+    };
+    put(d.items, L.items.data(), b1);
+    put(d.work, L.work.data(), b2);
+    put(d.lift, lift.data(), b3);
+    put(d.slot_item, L.slot_item.data(), b4);
+    return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "ragged layout upload");
+}
+
+sidwt_status ensure_workspace(sidwt_ragged *r, const RaggedLayout &L) {
+    sidwt_status st;
+    if ((st = grow(&r->pyr, &r->pyr_cap, L.pyr_elems, 0, "ragged pyramid"))) return st;
+    if (L.slots > r->slot_cap) {
+        int64_t c0 = r->slot_cap, c1 = r->slot_cap, c2 = r->slot_cap, c3 = r->slot_cap, c4 = r->slot_cap;
+        if ((st = grow(&r->yen, &c0, L.slots, 0, "ragged energies")) ||
+            (st = grow(&r->keys, &c1, L.slots, 0, "ragged keys")) || (st = grow(&r->lag, &c2, L.slots, 0, "ragged lags")) ||
+            (st = grow(&r->mag, &c3, L.slots, 0, "ragged magnitudes")) ||
+            (st = grow(&r->norm, &c4, L.slots, 0, "ragged norms")))
+            return st;
+        r->slot_cap = c0;
+    }
+    if (!r->counter && cudaMalloc(&r->counter, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("device allocation failed: work counter");
+        return SIDWT_ENOMEM;
+    }
+    return SIDWT_OK;
+}
+
+// The launches of one batch (all capturable).
+sidwt_status enqueue(sidwt_ragged *r, const DevLayout &d, int64_t slots, int64_t nitems, const float2 *y, cudaStream_t s,
+                     int *launches) {
+    int nl = 0;
+    sidwt_status st = analyze_ragged(y, d.groups, r->pyr, r->yen, s, &nl);
+    if (st) return st;
+    cudaError_t e = cudaMemsetAsync(r->keys, 0, (size_t)slots * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "ragged memset");
+    if (d.nwork > 0) {
+        rg::corr_ragged_kernel<<<r->sms * 2, rg::kT, 0, s>>>(d.items, d.work, d.nwork, r->counter, r->tree, r->pyr,
+                                                              r->keys);
+        ++nl;
+    }
+    if (slots > 0) {
+        rg::finalize_ragged_kernel<<<(unsigned)((slots + 255) / 256), 256, 0, s>>>(
+            r->keys, d.slot_item, d.items, r->xen, r->yen, slots, r->lag, r->mag, r->norm);
+        ++nl;
+    }
+    (void)nitems;
+    if (launches) *launches = nl;
+    e = cudaGetLastError();
+    return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "ragged correlation launch");
+}
+
+void load_tuning(sidwt_ragged *r, const char *path) {
+    for (int i = 0; i < 32; ++i) r->mq_for[i] = default_mq(i);
+    if (!path) path = std::getenv("SIDWT_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    int lg, mq;
+    while (std::fscanf(f, "%d %d", &lg, &mq) == 2)
+        if (lg >= 0 && lg < 32 && (mq == 1 || mq == 2 || mq == 4 || mq == 8)) r->mq_for[lg] = mq;
+    std::fclose(f);
+}
+
+}  // namespace
+
+extern "C" {
+
+sidwt_status sidwt_ragged_create(sidwt_ragged **out) {
+    if (!out) {
+        set_error("out is NULL");
+        return SIDWT_EINVAL;
+    }
+    *out = nullptr;
+    sidwt_ragged *r = new (std::nothrow) sidwt_ragged();
+    if (!r) {
+        set_error("host allocation failed");
+        return SIDWT_ENOMEM;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&r->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        r->sms = 152;
+    }
+    load_tuning(r, nullptr);
+    cudaError_t e = prepare_ragged_kernels();
+    if (e != cudaSuccess) {
+        delete r;
+        return cuda_fail(e, "ragged kernel attributes");
+    }
+    *out = r;
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_ragged_destroy(sidwt_ragged *r) {
+    if (!r) return SIDWT_OK;
+    cudaDeviceSynchronize();
+    if (r->exec) cudaGraphExecDestroy(r->exec);
+    if (r->graph) cudaGraphDestroy(r->graph);
+    for (DevLayout *d : {&r->dl, &r->gl}) {
+        cudaFree(d->items);
+        cudaFree(d->work);
+        cudaFree(d->lift);
+        cudaFree(d->slot_item);
+    }
+    cudaFree(r->tree);
+    cudaFree(r->xen);
+    cudaFree(r->pyr);
+    cudaFree(r->yen);
+    cudaFree(r->keys);
+    cudaFree(r->lag);
+    cudaFree(r->mag);
+    cudaFree(r->norm);
+    cudaFree(r->counter);
+    if (r->h_stage) cudaFreeHost(r->h_stage);
+    delete r;
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_ragged_reserve(sidwt_ragged *r, int64_t tree_elems, int64_t pyr_elems, int64_t slots) {
+    if (!r || tree_elems < 0 || pyr_elems < 0 || slots < 0) {
+        set_error("bad reservation");
+        return SIDWT_EINVAL;
+    }
+    cudaDeviceSynchronize();
+    sidwt_status st;
+    if ((st = grow(&r->tree, &r->tree_cap, tree_elems, r->tree_used, "ragged reference store"))) return st;
+    RaggedLayout L;
+    L.pyr_elems = pyr_elems;
+    L.slots = slots;
+    return ensure_workspace(r, L);
+}
+
+int32_t sidwt_ragged_num_refs(const sidwt_ragged *r) { return r ? (int32_t)r->refs.size() : -1; }
+
+sidwt_status sidwt_ragged_store_reference(sidwt_ragged *r, sidwt_filter f, int64_t N, int J, const void *x_dev,
+                                          int32_t *ref_id_out, sidwt_stream stream) {
+    if (!r || !x_dev || !ref_id_out) {
+        set_error("NULL argument");
+        return SIDWT_EINVAL;
+    }
+    if ((int)f < 0 || (int)f > 2) {
+        set_error("ragged batches take the float filters (D4, LeGall 5/3, CDF 9/7)");
+        return (int)f == 3 ? SIDWT_EUNSUPPORTED : SIDWT_EINVAL;
+    }
+    if (J < 1 || J > 15 || N < 2 || N > (int64_t(1) << 26) || N % (int64_t(1) << J) != 0) {
+        set_error("need 1 <= J <= 15, N a multiple of 2^J, N <= 2^26");
+        return SIDWT_EINVAL;
+    }
+    if (reinterpret_cast<uintptr_t>(x_dev) % 8) {
+        set_error("x_dev is misaligned");
+        return SIDWT_EINVAL;
+    }
+    const int64_t te = 2 * (int64_t)J * N, xe = (int64_t(2) << J) - 1;
+    if (r->tree_used + te > r->tree_cap || r->xen_used + xe > r->xen_cap) cudaDeviceSynchronize();
+    sidwt_status st;
+    if ((st = grow(&r->tree, &r->tree_cap, r->tree_used + te, r->tree_used, "ragged reference store")) ||
+        (st = grow(&r->xen, &r->xen_cap, r->xen_used + xe, r->xen_used, "ragged reference energies")))
+        return st;
+    sidwt_plan p;  // describes one reference slot; owns nothing
+    p.filter = (int)f;
+    p.N = N;
+    p.J = J;
+    p.tree_elems = te;
+    p.xen_len = xe;
+    p.tree_f = r->tree + r->tree_used;
+    p.xen = r->xen + r->xen_used;
+    if ((st = build_reference_tree(&p, x_dev, 0, reinterpret_cast<cudaStream_t>(stream)))) return st;
+    r->refs.push_back({(int)f, N, J, r->tree_used, r->xen_used});
+    r->tree_used += te;
+    r->xen_used += xe;
+    *ref_id_out = (int32_t)r->refs.size() - 1;
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_ragged_correlate(sidwt_ragged *r, int64_t n_items, const int32_t *ref_ids_host,
+                                    const int64_t *y_offsets_host, const void *y_dev, int64_t y_elems,
+                                    sidwt_stream stream) {
+    if (!r || n_items < 0 || (n_items > 0 && (!ref_ids_host || !y_offsets_host || !y_dev))) {
+        set_error("bad arguments");
+        return SIDWT_EINVAL;
+    }
+    if (reinterpret_cast<uintptr_t>(y_dev) % 16) {
+        set_error("y_dev must be 16-byte aligned");
+        return SIDWT_EINVAL;
+    }
+    RaggedLayout L;
+    sidwt_status st = build_layout(r, n_items, ref_ids_host, y_offsets_host, y_elems, L);
+    if (st) return st;
+    if ((st = ensure_workspace(r, L))) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if ((st = upload(r, r->dl, L, s, false))) return st;
+    r->last_slots = L.slots;
+    return enqueue(r, r->dl, L.slots, n_items, static_cast<const float2 *>(y_dev), s, nullptr);
+}
+
+sidwt_status sidwt_ragged_graph_create(sidwt_ragged *r, int64_t n_items, const int32_t *ref_ids_host,
+                                       const int64_t *y_offsets_host, const void *y_dev, int64_t y_elems,
+                                       int32_t *launches_out) {
+    if (!r || n_items < 0 || (n_items > 0 && (!ref_ids_host || !y_offsets_host || !y_dev))) {
+        set_error("bad arguments");
+        return SIDWT_EINVAL;
+    }
+    if (reinterpret_cast<uintptr_t>(y_dev) % 16) {
+        set_error("y_dev must be 16-byte aligned");
+        return SIDWT_EINVAL;
+    }
+    RaggedLayout L;
+    sidwt_status st = build_layout(r, n_items, ref_ids_host, y_offsets_host, y_elems, L);
+    if (st) return st;
+    if ((st = ensure_workspace(r, L))) return st;
+    if ((st = upload(r, r->gl, L, nullptr, true))) return st;
+    if (r->exec) cudaGraphExecDestroy(r->exec);
+    if (r->graph) cudaGraphDestroy(r->graph);
+    r->exec = nullptr;
+    r->graph = nullptr;
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return cuda_fail(cudaGetLastError(), "stream");
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return cuda_fail(e, "begin capture");
+    }
+    int nl = 0;
+    st = enqueue(r, r->gl, L.slots, n_items, static_cast<const float2 *>(y_dev), cs, &nl);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (st) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&r->exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e, "graph instantiate");
+    }
+    r->graph = g;
+    r->graph_slots = L.slots;
+    r->graph_launches = nl;
+    if (launches_out) *launches_out = nl;
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_ragged_graph_launch(sidwt_ragged *r, sidwt_stream stream) {
+    if (!r || !r->exec) {
+        set_error("no graph: call sidwt_ragged_graph_create first");
+        return SIDWT_EINVAL;
+    }
+    cudaError_t e = cudaGraphLaunch(r->exec, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    r->last_slots = r->graph_slots;
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_ragged_peaks(sidwt_ragged *r, int64_t n_slots, int32_t *lag_dev, float *mag_dev, double *norm_dev,
+                                sidwt_stream stream) {
+    if (!r || n_slots != r->last_slots) {
+        set_error("n_slots must equal the sum of J_i + 1 over the last batch");
+        return SIDWT_EINVAL;
+    }
+    if (n_slots == 0) return SIDWT_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (lag_dev) e = cudaMemcpyAsync(lag_dev, r->lag, n_slots * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && mag_dev)
+        e = cudaMemcpyAsync(mag_dev, r->mag, n_slots * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && norm_dev)
+        e = cudaMemcpyAsync(norm_dev, r->norm, n_slots * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "ragged peak copy");
+}
+
+sidwt_status sidwt_ragged_autotune(sidwt_ragged *r, const char *cache_path, sidwt_stream stream) {
+    if (!r) {
+        set_error("NULL argument");
+        return SIDWT_EINVAL;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // one synthetic pair per bucket: band length Kp = 2^lg at scale 0 (J = 1)
+    const int lg_lo = 8, lg_hi = 15;
+    const int64_t Nmax = int64_t(2) << lg_hi;
+    float2 *tree = nullptr, *pyr = nullptr;
+    unsigned long long *keys = nullptr;
+    int *counter = nullptr;
+    rg::Item *ditem = nullptr;
+    rg::Work *dwork = nullptr;
+    const int64_t max_work = 2 * (Nmax / 256);
+    if (cudaMalloc(&tree, 2 * Nmax * sizeof(float2)) != cudaSuccess || cudaMalloc(&pyr, 2 * Nmax * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&keys, 4 * sizeof(unsigned long long)) != cudaSuccess || cudaMalloc(&counter, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&ditem, sizeof(rg::Item)) != cudaSuccess || cudaMalloc(&dwork, max_work * sizeof(rg::Work)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(tree);
+        cudaFree(pyr);
+        cudaFree(keys);
+        cudaFree(counter);
+        cudaFree(ditem);
+        cudaFree(dwork);
+        set_error("autotune allocation failed");
+        return SIDWT_ENOMEM;
+    }
+    rg::fill_kernel<<<(unsigned)((2 * Nmax + 255) / 256), 256, 0, s>>>(tree, 2 * Nmax, 1u);
+    rg::fill_kernel<<<(unsigned)((2 * Nmax + 255) / 256), 256, 0, s>>>(pyr, 2 * Nmax, 2u);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::string report;
+    for (int lg = lg_lo; lg <= lg_hi; ++lg) {
+        const int64_t Kp = int64_t(1) << lg, N = 2 * Kp;
+        rg::Item it{0, 0, 0, 0, (int32_t)N, 1, 0, 0};
+        cudaMemcpyAsync(ditem, &it, sizeof(it), cudaMemcpyHostToDevice, s);
+        float best_ms = 1e30f;
+        int best_mq = default_mq(lg);
+        for (int mq : {1, 2, 4, 8}) {
+            const int64_t TQ = (int64_t)rg::kT * mq;
+            if (TQ > Kp) continue;
+            std::vector<rg::Work> w;
+            for (int v = 0; v < 2; ++v)
+                for (int64_t q0 = 0; q0 < Kp; q0 += TQ) w.push_back({0, 0, (int16_t)mq, v, 1, (int32_t)q0, 0});
+            cudaMemcpyAsync(dwork, w.data(), w.size() * sizeof(rg::Work), cudaMemcpyHostToDevice, s);
+            cudaStreamSynchronize(s);
+            float tot = 0.f;
+            for (int rep = 0; rep < 4; ++rep) {
+                cudaMemsetAsync(counter, 0, sizeof(int), s);
+                cudaEventRecord(e0, s);
+                rg::corr_ragged_kernel<<<r->sms * 2, rg::kT, 0, s>>>(ditem, dwork, (int)w.size(), counter, tree, pyr, keys);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tot += ms;
+            }
+            if (tot < best_ms) {
+                best_ms = tot;
+                best_mq = mq;
+            }
+        }
+        r->mq_for[lg] = best_mq;
+        report += std::to_string(lg) + " " + std::to_string(best_mq) + "\n";
+    }
+    for (int lg = lg_hi + 1; lg < 32; ++lg) r->mq_for[lg] = r->mq_for[lg_hi];
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(tree);
+    cudaFree(pyr);
+    cudaFree(keys);
+    cudaFree(counter);
+    cudaFree(ditem);
+    cudaFree(dwork);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    if (!cache_path) cache_path = std::getenv("SIDWT_TUNE_CACHE");
+    if (cache_path) {
+        FILE *f = std::fopen(cache_path, "w");
+        if (f) {
+            std::fputs(report.c_str(), f);
+            std::fclose(f);
+        }
+    }
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_ragged_tuning(const sidwt_ragged *r, int32_t *mq_by_log2_band /* [32] */) {
+    if (!r || !mq_by_log2_band) {
+        set_error("NULL argument");
+        return SIDWT_EINVAL;
+    }
+    for (int i = 0; i < 32; ++i) mq_by_log2_band[i] = r->mq_for[i];
+    return SIDWT_OK;
+}
+
+}  // extern "C"

@@ -78,6 +78,25 @@ struct LiftShape<SIDWT_D4, S> {
 // Host-side coefficient tables (double math, rounded once to float).
 LiftCoef lift_coef(int filter, int side);
 
+// One pulse of a ragged batch for the lifting kernels (element offsets).
+struct RaggedLift {
+    int64_t y_off;    // pulse start in the packed received buffer
+    int64_t pyr_off;  // pyramid row start
+    int64_t yen_off;  // energies start (J+1 values)
+    int32_t N, J;
+};
+
+// Device item lists of a ragged batch by filter (0 D4, 1 5/3, 2 9/7) and path.
+struct RaggedLiftGroups {
+    const RaggedLift *smem[3] = {nullptr, nullptr, nullptr};
+    int n_smem[3] = {0, 0, 0};
+    int64_t maxN_smem[3] = {0, 0, 0};
+    const RaggedLift *lng[3] = {nullptr, nullptr, nullptr};
+    int n_long[3] = {0, 0, 0};
+    int64_t maxN_long[3] = {0, 0, 0};
+    int maxJ_long[3] = {0, 0, 0};
+};
+
 // ---------------------------------------------------------------------------
 // Plan state.
 // ---------------------------------------------------------------------------
@@ -172,6 +191,11 @@ sidwt_status build_reference_tree(sidwt_plan *p, const void *x_dev, int32_t ref,
 // Received analysis of B pulses into the plan's pyramid workspace (+ energies).
 sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStream_t s);
 int analyze_launch_count(const sidwt_plan *p);
+// Ragged batch: all listed pulses, each with its own N, J and filter.
+sidwt_status analyze_ragged(const float2 *y, const RaggedLiftGroups &g, float2 *pyr, double *yen, cudaStream_t s,
+                            int *launches);
+int64_t analyze_smem_max_n();
+cudaError_t prepare_ragged_kernels();
 
 // ---- corr_simt.cu ----
 sidwt_status group_pulses(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t B, int tile_pulses,

@@ -72,10 +72,25 @@ def lib():
     L.sidwt_read_timing.argtypes = [_vp, ctypes.POINTER(Timing), ctypes.c_int]
     L.sidwt_correlate_static.argtypes = [ctypes.c_int, _i64, ctypes.c_int, _vp, _vp, _i64, _vp, _vp, _vp, _vp]
     L.sidwt_tc_selftest.argtypes = [_vp, _vp, _vp]
+    L.sidwt_ragged_create.argtypes = [ctypes.POINTER(_vp)]
+    L.sidwt_ragged_destroy.argtypes = [_vp]
+    L.sidwt_ragged_reserve.argtypes = [_vp, _i64, _i64, _i64]
+    L.sidwt_ragged_num_refs.argtypes = [_vp]
+    L.sidwt_ragged_num_refs.restype = _i32
+    L.sidwt_ragged_store_reference.argtypes = [_vp, ctypes.c_int, _i64, ctypes.c_int, _vp, ctypes.POINTER(_i32), _vp]
+    L.sidwt_ragged_correlate.argtypes = [_vp, _i64, _vp, _vp, _vp, _i64, _vp]
+    L.sidwt_ragged_graph_create.argtypes = [_vp, _i64, _vp, _vp, _vp, _i64, ctypes.POINTER(_i32)]
+    L.sidwt_ragged_graph_launch.argtypes = [_vp, _vp]
+    L.sidwt_ragged_peaks.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp]
+    L.sidwt_ragged_autotune.argtypes = [_vp, ctypes.c_char_p, _vp]
+    L.sidwt_ragged_tuning.argtypes = [_vp, _vp]
     for name in ("sidwt_plan_create", "sidwt_plan_destroy", "sidwt_plan_reserve", "sidwt_store_reference",
                  "sidwt_reference_tree", "sidwt_analyze", "sidwt_correlate", "sidwt_peaks",
                  "sidwt_correlate_host", "sidwt_check", "sidwt_reset_references", "sidwt_set_timing",
-                 "sidwt_read_timing", "sidwt_correlate_static", "sidwt_tc_selftest"):
+                 "sidwt_read_timing", "sidwt_correlate_static", "sidwt_tc_selftest", "sidwt_ragged_create",
+                 "sidwt_ragged_destroy", "sidwt_ragged_reserve", "sidwt_ragged_store_reference",
+                 "sidwt_ragged_correlate", "sidwt_ragged_graph_create", "sidwt_ragged_graph_launch",
+                 "sidwt_ragged_peaks", "sidwt_ragged_autotune", "sidwt_ragged_tuning"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -266,6 +281,100 @@ def correlate_static(filter, N: int, J: int, x: torch.Tensor, y: torch.Tensor, l
     B = y.shape[0]
     _raise(lib().sidwt_correlate_static(_filter_id(filter), int(N), int(J), _ptr(x), _ptr(y), B, _ptr(lag),
                                         _ptr(mag), _ptr(norm), _stream(stream)))
+
+
+class Ragged:
+    """Pulses of uneven length, depth and filter, each against its own stored
+    signal, correlated in one persistent launch (sidwt_ragged_*)."""
+
+    def __init__(self):
+        h = _vp()
+        _raise(lib().sidwt_ragged_create(ctypes.byref(h)))
+        self._h = h
+        self.refs = []  # (filter, N, J) per stored reference
+        self._layout = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sidwt_ragged_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def reserve(self, tree_elems: int, pyr_elems: int, slots: int):
+        _raise(lib().sidwt_ragged_reserve(self._h, tree_elems, pyr_elems, slots))
+
+    def store_reference(self, filter, N: int, J: int, x: torch.Tensor, stream=None) -> int:
+        if x.dtype != torch.complex64 or not x.is_cuda or x.numel() != N or not x.is_contiguous():
+            raise ValueError("reference must be a contiguous CUDA complex64 tensor of N samples")
+        rid = _i32(-1)
+        _raise(lib().sidwt_ragged_store_reference(self._h, _filter_id(filter), int(N), int(J), _ptr(x),
+                                                  ctypes.byref(rid), _stream(stream)))
+        self.refs.append((_filter_id(filter), int(N), int(J)))
+        return rid.value
+
+    def slots_of(self, ref_ids) -> tuple[np.ndarray, int]:
+        """First peak slot of every item and the total slot count."""
+        js = np.array([self.refs[int(r)][2] for r in ref_ids], dtype=np.int64)
+        first = np.concatenate([[0], np.cumsum(js + 1)[:-1]]) if len(js) else np.zeros(0, np.int64)
+        return first, int((js + 1).sum())
+
+    def _args(self, ref_ids, offsets):
+        ids = np.ascontiguousarray(np.asarray(ref_ids, dtype=np.int32))
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        if ids.shape != off.shape:
+            raise ValueError("one offset per item")
+        return ids, off
+
+    def correlate(self, ref_ids, offsets, y: torch.Tensor, stream=None) -> int:
+        """y: packed complex64 CUDA buffer; returns the number of peak slots."""
+        ids, off = self._args(ref_ids, offsets)
+        _raise(lib().sidwt_ragged_correlate(self._h, ids.size, ids.ctypes.data, off.ctypes.data, _ptr(y),
+                                            y.numel(), _stream(stream)))
+        self._layout = ids
+        return self.slots_of(ids)[1]
+
+    def graph_create(self, ref_ids, offsets, y: torch.Tensor) -> int:
+        ids, off = self._args(ref_ids, offsets)
+        n = _i32(0)
+        _raise(lib().sidwt_ragged_graph_create(self._h, ids.size, ids.ctypes.data, off.ctypes.data, _ptr(y),
+                                               y.numel(), ctypes.byref(n)))
+        self._graph_layout = ids
+        return n.value
+
+    def graph_launch(self, stream=None) -> int:
+        _raise(lib().sidwt_ragged_graph_launch(self._h, _stream(stream)))
+        self._layout = self._graph_layout
+        return self.slots_of(self._layout)[1]
+
+    def peaks(self, n_slots: int, stream=None):
+        dev = torch.cuda.current_device()
+        lag = torch.empty(n_slots, dtype=torch.int32, device=dev)
+        mag = torch.empty(n_slots, dtype=torch.float32, device=dev)
+        norm = torch.empty(n_slots, dtype=torch.float64, device=dev)
+        _raise(lib().sidwt_ragged_peaks(self._h, n_slots, _ptr(lag), _ptr(mag), _ptr(norm), _stream(stream)))
+        return lag, mag, norm
+
+    def peaks_into(self, n_slots: int, lag, mag, norm, stream=None):
+        _raise(lib().sidwt_ragged_peaks(self._h, n_slots, _ptr(lag), _ptr(mag), _ptr(norm), _stream(stream)))
+
+    def autotune(self, cache_path: str | None = None, stream=None):
+        _raise(lib().sidwt_ragged_autotune(self._h, cache_path.encode() if cache_path else None, _stream(stream)))
+
+    def tuning(self) -> np.ndarray:
+        out = np.zeros(32, np.int32)
+        _raise(lib().sidwt_ragged_tuning(self._h, out.ctypes.data))
+        return out
 
 
 def tc_selftest(stream=None):
