@@ -258,6 +258,16 @@ sidwt_status sidwt_ragged_peaks(sidwt_ragged *r, int64_t n_slots, int32_t *lag_d
  * written).  Allocates and synchronises; call outside stream capture. */
 sidwt_status sidwt_ragged_autotune(sidwt_ragged *r, const char *cache_path, sidwt_stream stream);
 
+/* Stage timing of direct sidwt_ragged_correlate calls (not graph replays),
+ * same meaning as sidwt_set_timing / sidwt_read_timing: analyze_ms (lifting),
+ * correlate_ms (the persistent correlation kernel), peaks_ms. */
+sidwt_status sidwt_ragged_set_timing(sidwt_ragged *r, int enable);
+sidwt_status sidwt_ragged_read_timing(sidwt_ragged *r, sidwt_timing *out, int reset);
+
+/* Forget every stored reference (ids restart at 0; capacity kept).  Must not
+ * be called while a batch using them is in flight. */
+sidwt_status sidwt_ragged_reset_references(sidwt_ragged *r);
+
 /* The current choice: mq_by_log2_band[k] shifts per thread for bands of
  * length in [2^k, 2^(k+1)) (32 entries). */
 sidwt_status sidwt_ragged_tuning(const sidwt_ragged *r, int32_t *mq_by_log2_band);

@@ -68,6 +68,9 @@ def lib():
         L.oracle_brute_xcorr.restype = None
         L.oracle_correlate_batch.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_long, ctypes.c_long, ctypes.c_int,
                                              ctypes.c_int, _i32p, _dp, _dp, _dp, ctypes.c_int]
+        _lp = ctypes.POINTER(ctypes.c_long)
+        L.oracle_correlate_mixed.argtypes = [ctypes.c_long, _ip, _lp, _ip, _lp, _lp, _dp, _dp, _i32p, _dp, _dp,
+                                             ctypes.c_int]
         L.oracle_cdf97_constants.argtypes = [_dp]
         L.oracle_cdf97_constants.restype = None
         _lib = L
@@ -221,3 +224,25 @@ def correlate_batch(filter_id: int, X, Y, J: int, form: int = 1, want_r: bool = 
         filter_id, _d(X.view(np.float64)), _d(Y.view(np.float64)), P, N, J, form, lag.ctypes.data_as(_i32p),
         _d(mag), _d(norm), _d(r.view(np.float64)) if r is not None else None, nthreads))
     return lag, mag, norm, r, used
+
+
+def correlate_mixed(filters, Ns, Js, x_packed, y_packed, offsets, nthreads: int = 0):
+    """Peaks of pairs of mixed shapes (packed complex inputs): returns
+    (lag, mag, norm) packed by slot (pair i's J_i + 1 scales) and threads used."""
+    f = np.ascontiguousarray(np.asarray(filters, dtype=np.intc))
+    n = np.ascontiguousarray(np.asarray(Ns, dtype=np.int_))
+    j = np.ascontiguousarray(np.asarray(Js, dtype=np.intc))
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int_))
+    slot = np.ascontiguousarray(np.concatenate([[0], np.cumsum(j + 1)[:-1]]).astype(np.int_))
+    S = int((j + 1).sum())
+    X = _c128(x_packed)
+    Y = _c128(y_packed)
+    lag = np.zeros(S, np.int32)
+    mag = np.zeros(S)
+    norm = np.zeros(S)
+    lp = ctypes.POINTER(ctypes.c_long)
+    used = _check(lib().oracle_correlate_mixed(
+        len(f), f.ctypes.data_as(_ip), n.ctypes.data_as(lp), j.ctypes.data_as(_ip), off.ctypes.data_as(lp),
+        slot.ctypes.data_as(lp), _d(X.view(np.float64)), _d(Y.view(np.float64)), lag.ctypes.data_as(_i32p), _d(mag),
+        _d(norm), nthreads))
+    return lag, mag, norm, used

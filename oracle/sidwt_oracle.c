@@ -696,3 +696,34 @@ int oracle_correlate_batch(int filter, const double *x, const double *y, long P,
     }
     return bad ? -1 : used;
 }
+
+/* Batch of pairs of mixed shapes: pair i has filter f[i], length N[i] and
+ * depth J[i]; x_i and y_i start at complex offset off[i] of the packed
+ * arrays; its J[i]+1 peak records start at slot[i].  Pairs run in parallel
+ * with OpenMP.  Returns the number of threads used, or -1 on a bad shape. */
+int oracle_correlate_mixed(long P, const int *f, const long *N, const int *J, const long *off, const long *slot,
+                           const double *x, const double *y, int32_t *lag, double *mag, double *norm,
+                           int nthreads) {
+    int used = 1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+    {
+#pragma omp single
+        used = omp_get_num_threads();
+    }
+#else
+    (void)nthreads;
+#endif
+    int bad = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+#endif
+    for (long i = 0; i < P; ++i) {
+        long s = slot[i];
+        if (oracle_correlate_batch(f[i], x + 2 * off[i], y + 2 * off[i], 1, N[i], J[i], 1, lag + s, mag + s,
+                                   norm + s, NULL, 1) < 0)
+            bad |= 1;
+    }
+    return bad ? -1 : used;
+}

@@ -571,11 +571,6 @@ sidwt_status correlate_tc(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t 
         if (e != cudaSuccess) return cuda_fail(e, "reference packing launch");
         p->tc_packed = p->nrefs;
     }
-    {
-        cudaError_t e = cudaFuncSetAttribute(tc::corr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             tc::kSmemBytes);
-        if (e != cudaSuccess) return cuda_fail(e, "tensor-core kernel attribute");
-    }
     const int64_t max_pt = (B + tc::kTM - 1) / tc::kTM + std::min<int64_t>(p->nrefs, B);
     for (int j = 0; j <= J; ++j) {
         if (!(mask & (1u << j))) continue;
@@ -638,6 +633,15 @@ sidwt_status correlate_tc(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t 
 
 int tc_group_tile() { return tc::kTM; }
 
+cudaError_t prepare_tc_kernels() {
+    cudaError_t e =
+        cudaFuncSetAttribute(tc::corr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc::tc_selftest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc::kSelftestSmem);
+    return e;
+}
+
 int tc_launch_count(const sidwt_plan *p) {
     const uint32_t mask = tc_scale_mask(p);
     const bool pack_refs = p->tc_packed < p->nrefs;
@@ -656,10 +660,9 @@ extern "C" sidwt_status sidwt_tc_selftest(float *out_dev, int32_t *err_dev, sidw
         set_error("out_dev and err_dev must not be NULL");
         return SIDWT_EINVAL;
     }
-    cudaError_t e = cudaFuncSetAttribute(tc::tc_selftest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         tc::kSelftestSmem);
-    if (e != cudaSuccess) return cuda_fail(e, "self-test attribute");
+    sidwt_status st = prepare_kernels();
+    if (st) return st;
     tc::tc_selftest_kernel<<<1, 128, tc::kSelftestSmem, reinterpret_cast<cudaStream_t>(stream)>>>(out_dev, err_dev);
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "self-test launch");
 }

@@ -571,11 +571,27 @@ sidwt_status build_reference_tree(sidwt_plan *p, const void *x_dev, int32_t ref,
 template <int F, typename T>
 static cudaError_t launch_smem(sidwt_plan *p, const void *y, int64_t B, cudaStream_t s, const LiftCoef &c) {
     const size_t smem = (size_t)(p->N + p->N / 2) * sizeof(T);
-    auto k = analyze_smem_kernel<F, T>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k<<<(unsigned)B, kAnalyzeThreads, smem, s>>>(y, p->N, p->J, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c);
+    analyze_smem_kernel<F, T><<<(unsigned)B, kAnalyzeThreads, smem, s>>>(y, p->N, p->J, p->pyr_f, p->pyr_i,
+                                                                       p->pyr_elems, p->yen, c);
     return cudaGetLastError();
+}
+
+// Shared-memory budgets of the analysis kernels, set once per device (see
+// prepare_kernels) so that no launch needs an attribute call.
+cudaError_t prepare_analysis_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(analyze_smem_kernel<SIDWT_D4, float2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(analyze_smem_kernel<SIDWT_LEGALL53, float2>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(analyze_smem_kernel<SIDWT_CDF97, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(analyze_smem_kernel<SIDWT_LEGALL53_INT, int2>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess) e = prepare_ragged_kernels();
+    return e;
 }
 
 int analyze_launch_count(const sidwt_plan *p) {

@@ -295,6 +295,11 @@ struct sidwt_ragged {
     // tuning: shifts per thread by floor(log2(band length))
     int mq_for[32];
     int sms = 0;
+    // stage timing of direct calls (CUDA events), as for plans
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;  // 4 per timed call: before lift, corr, peaks, after
+    double t_ms[3] = {0, 0, 0};
+    int64_t timed_calls = 0, timed_launches = 0;
 };
 
 namespace {
@@ -498,24 +503,43 @@ sidwt_status ensure_workspace(sidwt_ragged *r, const RaggedLayout &L) {
     return SIDWT_OK;
 }
 
-// The launches of one batch (all capturable).
+// The launches of one batch (all capturable; events only outside capture).
 sidwt_status enqueue(sidwt_ragged *r, const DevLayout &d, int64_t slots, int64_t nitems, const float2 *y, cudaStream_t s,
                      int *launches) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap);
+    const bool timed = r->timing && cap == cudaStreamCaptureStatusNone;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (timed)
+        for (int i = 0; i < 4; ++i)
+            if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+                cudaGetLastError();
+                return cuda_fail(cudaErrorMemoryAllocation, "timing events");
+            }
+    if (timed) cudaEventRecord(ev[0], s);
     int nl = 0;
     sidwt_status st = analyze_ragged(y, d.groups, r->pyr, r->yen, s, &nl);
     if (st) return st;
     cudaError_t e = cudaMemsetAsync(r->keys, 0, (size_t)slots * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_fail(e, "ragged memset");
+    if (timed) cudaEventRecord(ev[1], s);
     if (d.nwork > 0) {
         rg::corr_ragged_kernel<<<r->sms * 2, rg::kT, 0, s>>>(d.items, d.work, d.nwork, r->counter, r->tree, r->pyr,
                                                               r->keys);
         ++nl;
     }
+    if (timed) cudaEventRecord(ev[2], s);
     if (slots > 0) {
         rg::finalize_ragged_kernel<<<(unsigned)((slots + 255) / 256), 256, 0, s>>>(
             r->keys, d.slot_item, d.items, r->xen, r->yen, slots, r->lag, r->mag, r->norm);
         ++nl;
+    }
+    if (timed) {
+        cudaEventRecord(ev[3], s);
+        r->ev.insert(r->ev.end(), ev, ev + 4);
+        ++r->timed_calls;
+        r->timed_launches += nl;
     }
     (void)nitems;
     if (launches) *launches = nl;
@@ -557,10 +581,10 @@ sidwt_status sidwt_ragged_create(sidwt_ragged **out) {
         r->sms = 152;
     }
     load_tuning(r, nullptr);
-    cudaError_t e = prepare_ragged_kernels();
-    if (e != cudaSuccess) {
+    sidwt_status pst = prepare_kernels();
+    if (pst) {
         delete r;
-        return cuda_fail(e, "ragged kernel attributes");
+        return pst;
     }
     *out = r;
     return SIDWT_OK;
@@ -586,6 +610,7 @@ sidwt_status sidwt_ragged_destroy(sidwt_ragged *r) {
     cudaFree(r->mag);
     cudaFree(r->norm);
     cudaFree(r->counter);
+    for (auto e : r->ev) cudaEventDestroy(e);
     if (r->h_stage) cudaFreeHost(r->h_stage);
     delete r;
     return SIDWT_OK;
@@ -831,6 +856,57 @@ sidwt_status sidwt_ragged_autotune(sidwt_ragged *r, const char *cache_path, sidw
             std::fclose(f);
         }
     }
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_ragged_set_timing(sidwt_ragged *r, int enable) {
+    if (!r) {
+        set_error("NULL argument");
+        return SIDWT_EINVAL;
+    }
+    r->timing = enable != 0;
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_ragged_read_timing(sidwt_ragged *r, sidwt_timing *out, int reset) {
+    if (!r || !out) {
+        set_error("NULL argument");
+        return SIDWT_EINVAL;
+    }
+    for (size_t i = 0; i + 3 < r->ev.size(); i += 4) {
+        cudaError_t e = cudaEventSynchronize(r->ev[i + 3]);
+        if (e != cudaSuccess) return cuda_fail(e, "timing event");
+        float a = 0.f, b = 0.f, c = 0.f;
+        cudaEventElapsedTime(&a, r->ev[i], r->ev[i + 1]);
+        cudaEventElapsedTime(&b, r->ev[i + 1], r->ev[i + 2]);
+        cudaEventElapsedTime(&c, r->ev[i + 2], r->ev[i + 3]);
+        r->t_ms[0] += a;
+        r->t_ms[1] += b;
+        r->t_ms[2] += c;
+    }
+    for (auto e : r->ev) cudaEventDestroy(e);
+    r->ev.clear();
+    std::memset(out, 0, sizeof(*out));
+    out->analyze_ms = r->t_ms[0];
+    out->correlate_ms = r->t_ms[1];
+    out->peaks_ms = r->t_ms[2];
+    out->correlate_calls = r->timed_calls;
+    out->launches = r->timed_launches;
+    if (reset) {
+        r->t_ms[0] = r->t_ms[1] = r->t_ms[2] = 0.0;
+        r->timed_calls = r->timed_launches = 0;
+    }
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_ragged_reset_references(sidwt_ragged *r) {
+    if (!r) {
+        set_error("NULL argument");
+        return SIDWT_EINVAL;
+    }
+    r->refs.clear();
+    r->tree_used = 0;
+    r->xen_used = 0;
     return SIDWT_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -164,6 +165,21 @@ StageTimer::~StageTimer() {
     p->marks.push_back({stage, a, b});
 }
 
+sidwt_status prepare_kernels() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && done[dev]) return SIDWT_OK;
+    e = prepare_analysis_kernels();
+    if (e == cudaSuccess) e = prepare_tc_kernels();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel shared-memory attributes");
+    if (dev >= 0 && dev < 64) done[dev] = true;
+    return SIDWT_OK;
+}
+
 static bool is_pinned_host(const void *ptr) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
@@ -205,6 +221,8 @@ sidwt_status sidwt_plan_create(sidwt_filter f, int64_t N, int J, sidwt_plan **ou
         set_error("need 1 <= J <= 15, N a multiple of 2^J, N <= 2^26");
         return SIDWT_EINVAL;
     }
+    sidwt_status pst = prepare_kernels();
+    if (pst) return pst;
     sidwt_plan *p = new (std::nothrow) sidwt_plan();
     if (!p) {
         set_error("host allocation failed");

@@ -196,6 +196,11 @@ sidwt_status analyze_ragged(const float2 *y, const RaggedLiftGroups &g, float2 *
                             int *launches);
 int64_t analyze_smem_max_n();
 cudaError_t prepare_ragged_kernels();
+cudaError_t prepare_analysis_kernels();
+cudaError_t prepare_tc_kernels();
+// Sets every kernel's shared-memory budget once per device (outside any
+// stream capture); called by plan and ragged-object creation.
+sidwt_status prepare_kernels();
 
 // ---- corr_simt.cu ----
 sidwt_status group_pulses(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t B, int tile_pulses,

@@ -117,8 +117,10 @@ extern "C" sidwt_status sidwt_correlate_static(sidwt_filter f, int64_t N, int J,
                   std::to_string(kStaticScratchBytes) + "-byte static array; use sidwt_correlate or a smaller batch");
         return SIDWT_EINVAL;
     }
+    sidwt_status st = prepare_kernels();
+    if (st) return st;
     unsigned char *base = nullptr;
-    sidwt_status st = scratch_address(&base);
+    st = scratch_address(&base);
     if (st) return st;
     layout(p, base, B, &ids_in);
     p.nrefs = 1;

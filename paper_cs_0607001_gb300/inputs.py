@@ -139,3 +139,34 @@ def random_batch(n_refs: int, B: int, N: int, J: int, seed: int):
     snr = g.uniform(0.0, 20.0, size=B)
     y = echo(refs[ref_ids], D, snr, g)
     return {"refs": to_c64(refs), "y": to_c64(y), "ref_ids": ref_ids, "delays": D, "snr_db": snr, "N": N, "J": J}
+
+
+def ragged_batch(n: int = 10000, seed: int = 4, n_lo: int = 256, n_hi: int = 65536, j_lo: int = 3, j_hi: int = 8):
+    """n pulses of uneven length: N log-uniform in [n_lo, n_hi] rounded to a
+    multiple of 2^J (at least 2^J), J uniform in [j_lo, j_hi], filter uniform
+    over the float filters (0 D4, 1 LeGall 5/3, 2 CDF 9/7); half LFM chirps
+    (TB = N/8 clamped to [16, 4096]), half Barker-13 codes (samples per chip
+    so that the code spans about N/8); delays uniform, SNR uniform in
+    0-20 dB.  Each pulse has its own stored reference.  Returns packed
+    complex64 arrays (refs, y) with per-item offsets."""
+    g = rng(seed, 5)
+    J = g.integers(j_lo, j_hi + 1, size=n)
+    raw = np.exp(g.uniform(np.log(n_lo), np.log(n_hi), size=n))
+    N = np.maximum(np.round(raw / (1 << J)).astype(np.int64), 1) * (1 << J)
+    filt = g.integers(0, 3, size=n)
+    kind = g.integers(0, 2, size=n)
+    D = (g.uniform(0, 1, size=n) * N).astype(np.int64)
+    snr = g.uniform(0.0, 20.0, size=n)
+    off = np.concatenate([[0], np.cumsum(N)[:-1]]).astype(np.int64)
+    tot = int(N.sum())
+    refs = np.empty(tot, np.complex64)
+    ys = np.empty(tot, np.complex64)
+    for i in range(n):
+        Ni = int(N[i])
+        tb = int(min(max(Ni // 8, 16), 4096, Ni))
+        x = lfm(Ni, tb) if kind[i] == 0 else barker13(Ni, max(1, tb // 13))
+        y = echo(x, D[i:i + 1], snr[i:i + 1], g)[0]
+        refs[off[i]:off[i] + Ni] = x
+        ys[off[i]:off[i] + Ni] = y
+    return {"refs": refs, "y": ys, "offsets": off, "N": N, "J": J.astype(np.int64), "filter": filt,
+            "delays": D, "snr_db": snr}

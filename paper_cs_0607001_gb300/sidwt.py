@@ -84,13 +84,17 @@ def lib():
     L.sidwt_ragged_peaks.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp]
     L.sidwt_ragged_autotune.argtypes = [_vp, ctypes.c_char_p, _vp]
     L.sidwt_ragged_tuning.argtypes = [_vp, _vp]
+    L.sidwt_ragged_set_timing.argtypes = [_vp, ctypes.c_int]
+    L.sidwt_ragged_read_timing.argtypes = [_vp, ctypes.POINTER(Timing), ctypes.c_int]
+    L.sidwt_ragged_reset_references.argtypes = [_vp]
     for name in ("sidwt_plan_create", "sidwt_plan_destroy", "sidwt_plan_reserve", "sidwt_store_reference",
                  "sidwt_reference_tree", "sidwt_analyze", "sidwt_correlate", "sidwt_peaks",
                  "sidwt_correlate_host", "sidwt_check", "sidwt_reset_references", "sidwt_set_timing",
                  "sidwt_read_timing", "sidwt_correlate_static", "sidwt_tc_selftest", "sidwt_ragged_create",
                  "sidwt_ragged_destroy", "sidwt_ragged_reserve", "sidwt_ragged_store_reference",
                  "sidwt_ragged_correlate", "sidwt_ragged_graph_create", "sidwt_ragged_graph_launch",
-                 "sidwt_ragged_peaks", "sidwt_ragged_autotune", "sidwt_ragged_tuning"):
+                 "sidwt_ragged_peaks", "sidwt_ragged_autotune", "sidwt_ragged_tuning", "sidwt_ragged_set_timing",
+                 "sidwt_ragged_read_timing", "sidwt_ragged_reset_references"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -375,6 +379,18 @@ class Ragged:
         out = np.zeros(32, np.int32)
         _raise(lib().sidwt_ragged_tuning(self._h, out.ctypes.data))
         return out
+
+    def set_timing(self, on: bool = True):
+        _raise(lib().sidwt_ragged_set_timing(self._h, 1 if on else 0))
+
+    def read_timing(self, reset: bool = True) -> dict:
+        t = Timing()
+        _raise(lib().sidwt_ragged_read_timing(self._h, ctypes.byref(t), 1 if reset else 0))
+        return t.as_dict()
+
+    def reset_references(self):
+        _raise(lib().sidwt_ragged_reset_references(self._h))
+        self.refs = []
 
 
 def tc_selftest(stream=None):
