@@ -142,7 +142,10 @@ sidwt_status sidwt_analyze(sidwt_plan *p, const void *y_dev, int64_t B, void *py
  * ref_ids_dev: int32[B]; an id outside [0, num_refs) marks that pulse
  *   invalid (its peaks read lag -1) and is reported by sidwt_check.
  * y_dev: as for sidwt_analyze.
- * prec: SIDWT_PREC_FP32 or SIDWT_PREC_BF16X3.
+ * prec: SIDWT_PREC_FP32 or SIDWT_PREC_BF16X3.  Batches of at most 16
+ *   pulses run every pulse as a batch of one on the FP32 CUDA-core kernel of
+ *   the ragged path, whatever prec says (a tile of 64 or 128 pulses would be
+ *   mostly empty); the first call with a given B builds that work list.
  * r_dev: optional complex64[B][J+1][N], r_j[D] at [b][j][D]; NULL skips it
  *   (the full output is large: B (J+1) N 8 bytes). */
 sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const void *y_dev, int64_t B,
@@ -215,8 +218,9 @@ sidwt_status sidwt_ragged_create(sidwt_ragged **out);
 sidwt_status sidwt_ragged_destroy(sidwt_ragged *r);
 
 /* Pre-size the reference store (tree_elems = sum of 2 J N over the stored
- * signals), the received pyramid (pyr_elems = sum of 2N - 2(N >> J) over a
- * batch) and the peak slots (slots = sum of J + 1 over a batch). */
+ * signals; their energies are sized to match), the received pyramid
+ * (pyr_elems = sum of 2N - 2(N >> J) over a batch) and the peak slots
+ * (slots = sum of J + 1 over a batch). */
 sidwt_status sidwt_ragged_reserve(sidwt_ragged *r, int64_t tree_elems, int64_t pyr_elems, int64_t slots);
 
 int32_t sidwt_ragged_num_refs(const sidwt_ragged *r);
@@ -271,6 +275,67 @@ sidwt_status sidwt_ragged_reset_references(sidwt_ragged *r);
 /* The current choice: mq_by_log2_band[k] shifts per thread for bands of
  * length in [2^k, 2^(k+1)) (32 entries). */
 sidwt_status sidwt_ragged_tuning(const sidwt_ragged *r, int32_t *mq_by_log2_band);
+
+/* ---------------------------------------------------------------------------
+ * Serving loop.  Requests (one received complex64 pulse each, against one of
+ * the resident reference waveforms, with its own N, J and float filter)
+ * arrive at any time; a server thread batches them continuously.  The device
+ * is split into `lanes` CUDA streams with pre-reserved buffers; whenever a
+ * lane is idle the thread takes queued requests in arrival order while they
+ * fit the lane's share of memory_cap_bytes (request footprint about
+ * (32 + 16 J) N bytes), zero-pads each request's waveform to its N, builds
+ * the SIDWT trees and runs the ragged correlation, so batches overlap on the
+ * device.  A request larger than a lane's share is rejected (SIDWT_ENOMEM).
+ * Latency runs from sidwt_server_submit to the moment the server thread
+ * sees the lane's completion event.
+ * ------------------------------------------------------------------------- */
+typedef struct sidwt_server sidwt_server;
+
+typedef struct {
+    int32_t lanes;            /* concurrent batches (CUDA streams), 1..64          */
+    int32_t max_batch;        /* requests per batch                                */
+    int32_t max_j;            /* largest J a request may use (<= 15)               */
+    int64_t memory_cap_bytes; /* admission cap over all in-flight batches          */
+    int64_t max_lane_samples; /* sum of N one lane can hold (buffers pre-reserved) */
+} sidwt_server_config;
+
+typedef struct {
+    int64_t completed, rejected, batches, max_batch, samples, queued;
+    double p50_ms, p99_ms, max_ms; /* latency of completed requests              */
+    double span_s;                 /* first arrival to last completion            */
+} sidwt_server_stats;
+
+sidwt_status sidwt_server_create(const sidwt_server_config *cfg, sidwt_server **out);
+
+/* Make a reference waveform (complex64[len], host) resident; before start. */
+sidwt_status sidwt_server_add_waveform(sidwt_server *s, const void *x_host, int64_t len, int32_t *wave_id);
+
+/* Start the server thread (uses the device current at this call). */
+sidwt_status sidwt_server_start(sidwt_server *s);
+
+/* Queue one request: y_host points at N complex64 samples (pinned memory
+ * copies fastest) and must stay valid until the request finishes.  Returns
+ * at once with the request id. */
+sidwt_status sidwt_server_submit(sidwt_server *s, int32_t wave_id, sidwt_filter f, int64_t N, int J,
+                                 const void *y_host, int64_t *request_id);
+
+/* Bounded waits: SIDWT_ETIMEOUT if not finished within timeout_s; otherwise
+ * the request's own status (SIDWT_ENOMEM if it was rejected). */
+sidwt_status sidwt_server_wait(sidwt_server *s, int64_t request_id, double timeout_s);
+sidwt_status sidwt_server_drain(sidwt_server *s, double timeout_s);
+
+/* A finished request's peaks (J+1 entries each, as sidwt_peaks) and latency. */
+sidwt_status sidwt_server_result(sidwt_server *s, int64_t request_id, int32_t *lag_host, float *mag_host,
+                                 double *norm_host, double *latency_ms);
+
+/* Release a finished request's record. */
+sidwt_status sidwt_server_forget(sidwt_server *s, int64_t request_id);
+
+/* Counters and latency percentiles since the last reset. */
+sidwt_status sidwt_server_read_stats(sidwt_server *s, sidwt_server_stats *out, int reset);
+
+/* Finish queued and in-flight requests, stop the thread, free everything. */
+sidwt_status sidwt_server_destroy(sidwt_server *s);
 
 /* Diagnostic: one tcgen05 MMA (M = 128, N = 64, K = 16, bf16 in, f32 out)
  * on fixed integer-valued operands laid out exactly as the tensor-core

@@ -75,7 +75,7 @@ __device__ __forceinline__ unsigned long long block_max_key(unsigned long long k
 template <int MQ>
 __device__ __forceinline__ void large_tile(const Item &it, const Work &wk, int lev, int Kp, int nb, const float2 *__restrict__ tree,
                            const float2 *__restrict__ pyr, float2 *us, float2 *ws, unsigned long long *red,
-                           unsigned long long *keys) {
+                           unsigned long long *keys, float2 *R) {
     constexpr int TQ = kT * MQ;
     const int tid = threadIdx.x;
     const int N = it.N;
@@ -125,8 +125,10 @@ __device__ __forceinline__ void large_tile(const Item &it, const Work &wk, int l
     for (int l = 0; l < MQ; ++l) {
         const int q = q0 + tid * MQ + l;
         if (q < Kp) {
-            const unsigned long long k = peak_key(acc[l], ((uint32_t)q << lev) + (uint32_t)v);
+            const uint32_t D = ((uint32_t)q << lev) + (uint32_t)v;
+            const unsigned long long k = peak_key(acc[l], D);
             best = k > best ? k : best;
+            if (R) R[(it.slot + wk.j) * (int64_t)N + D] = acc[l];
         }
     }
     best = block_max_key(best, red);
@@ -136,7 +138,7 @@ __device__ __forceinline__ void large_tile(const Item &it, const Work &wk, int l
 // Short band: variants v0 .. v0+nvar-1, one shift per thread.
 __device__ __forceinline__ void small_tile(const Item &it, const Work &wk, int lev, int Kp, int nb, const float2 *__restrict__ tree,
                            const float2 *__restrict__ pyr, float2 *sm, unsigned long long *red,
-                           unsigned long long *keys) {
+                           unsigned long long *keys, float2 *R) {
     const int tid = threadIdx.x;
     const int N = it.N;
     const int nvar = wk.nvar;
@@ -166,7 +168,9 @@ __device__ __forceinline__ void small_tile(const Item &it, const Work &wk, int l
                 if (++idx == Kp) idx = 0;
             }
         }
-        best = peak_key(acc, ((uint32_t)q << lev) + (uint32_t)(wk.v0 + vi));
+        const uint32_t D = ((uint32_t)q << lev) + (uint32_t)(wk.v0 + vi);
+        best = peak_key(acc, D);
+        if (R) R[(it.slot + wk.j) * (int64_t)N + D] = acc;
     }
     best = block_max_key(best, red);
     if (threadIdx.x == 0 && best) atomicMax(&keys[it.slot + wk.j], best);
@@ -175,7 +179,7 @@ __device__ __forceinline__ void small_tile(const Item &it, const Work &wk, int l
 __global__ void __launch_bounds__(kT, 2) corr_ragged_kernel(const Item *__restrict__ items, const Work *__restrict__ work,
                                                          int nwork, int *counter, const float2 *__restrict__ tree,
                                                          const float2 *__restrict__ pyr,
-                                                         unsigned long long *__restrict__ keys) {
+                                                         unsigned long long *__restrict__ keys, float2 *R) {
     __shared__ float2 us[kTK];
     __shared__ float2 ws[kWin + kWin / 8 + 8];
     __shared__ unsigned long long red[kT / 32];
@@ -188,15 +192,16 @@ __global__ void __launch_bounds__(kT, 2) corr_ragged_kernel(const Item *__restri
         if (w >= nwork) break;
         const Work wk = work[w];
         const Item it = items[wk.item];
+        if (it.N == 0) continue;  // a pulse with an invalid reference id (uniform per CTA)
         const int lev = wk.j < it.J ? wk.j + 1 : it.J;
         const int Kp = it.N >> lev;
         const int nb = wk.j < it.J ? 2 : 1;
         switch (wk.mq) {
-        case 0: small_tile(it, wk, lev, Kp, nb, tree, pyr, ws, red, keys); break;
-        case 1: large_tile<1>(it, wk, lev, Kp, nb, tree, pyr, us, ws, red, keys); break;
-        case 2: large_tile<2>(it, wk, lev, Kp, nb, tree, pyr, us, ws, red, keys); break;
-        case 4: large_tile<4>(it, wk, lev, Kp, nb, tree, pyr, us, ws, red, keys); break;
-        default: large_tile<8>(it, wk, lev, Kp, nb, tree, pyr, us, ws, red, keys); break;
+        case 0: small_tile(it, wk, lev, Kp, nb, tree, pyr, ws, red, keys, R); break;
+        case 1: large_tile<1>(it, wk, lev, Kp, nb, tree, pyr, us, ws, red, keys, R); break;
+        case 2: large_tile<2>(it, wk, lev, Kp, nb, tree, pyr, us, ws, red, keys, R); break;
+        case 4: large_tile<4>(it, wk, lev, Kp, nb, tree, pyr, us, ws, red, keys, R); break;
+        default: large_tile<8>(it, wk, lev, Kp, nb, tree, pyr, us, ws, red, keys, R); break;
         }
     }
 }
@@ -222,6 +227,17 @@ __global__ void finalize_ragged_kernel(const unsigned long long *__restrict__ ke
     mag[s] = m;
     const double den = sqrt(xen[it.xen_off + ((1 << j) - 1) + (D & ((1u << j) - 1u))] * yen[s]);
     norm[s] = den > 0.0 ? (double)m / den : 0.0;
+}
+
+// Items of a uniform plan batch: pulse b uses reference ref_ids[b].
+__global__ void plan_items_kernel(const int32_t *__restrict__ ref_ids, int B, int nrefs, int N, int J,
+                                  int64_t pyr_elems, int64_t tree_elems, int64_t xen_len, Item *__restrict__ items) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const int r = ref_ids[b];
+    const bool ok = r >= 0 && r < nrefs;
+    items[b] = Item{(int64_t)b * pyr_elems, ok ? (int64_t)r * tree_elems : 0, ok ? (int64_t)r * xen_len : 0,
+                    (int64_t)b * (J + 1), ok ? N : 0, J, r, 0};
 }
 
 __global__ void fill_kernel(float2 *x, int64_t n, uint32_t seed) {
@@ -526,7 +542,7 @@ sidwt_status enqueue(sidwt_ragged *r, const DevLayout &d, int64_t slots, int64_t
     if (timed) cudaEventRecord(ev[1], s);
     if (d.nwork > 0) {
         rg::corr_ragged_kernel<<<r->sms * 2, rg::kT, 0, s>>>(d.items, d.work, d.nwork, r->counter, r->tree, r->pyr,
-                                                              r->keys);
+                                                              r->keys, nullptr);
         ++nl;
     }
     if (timed) cudaEventRecord(ev[2], s);
@@ -560,6 +576,103 @@ void load_tuning(sidwt_ragged *r, const char *path) {
 }
 
 }  // namespace
+
+namespace sidwt {
+
+// Small batches of a uniform plan: every pulse is a batch of one on the
+// persistent kernel (a 64-pulse SIMT tile would be mostly empty).
+struct PlanSmall {
+    rg::Item *items = nullptr;
+    rg::Work *work = nullptr;
+    int *counter = nullptr;
+    int64_t built_B = -1;
+    int nwork = 0;
+};
+
+void free_small(sidwt_plan *p) {
+    PlanSmall *ps = static_cast<PlanSmall *>(p->small);
+    if (!ps) return;
+    cudaFree(ps->items);
+    cudaFree(ps->work);
+    cudaFree(ps->counter);
+    delete ps;
+    p->small = nullptr;
+}
+
+// Allocates and fills the device work list for batches of B pulses (outside
+// any capture: later calls with the same B reuse it).
+sidwt_status prepare_small(sidwt_plan *p, int64_t B) {
+    PlanSmall *ps = static_cast<PlanSmall *>(p->small);
+    if (ps && ps->built_B == B) return SIDWT_OK;
+    free_small(p);
+    ps = new (std::nothrow) PlanSmall();
+    if (!ps) {
+        set_error("host allocation failed");
+        return SIDWT_ENOMEM;
+    }
+    p->small = ps;
+    std::vector<rg::Work> one;
+    for (int j = 0; j <= p->J; ++j) {
+        const int lev = j < p->J ? j + 1 : p->J;
+        const int64_t Kp = p->N >> lev;
+        const int nv = 1 << lev;
+        if (Kp >= rg::kSmallBand) {
+            int lg = 0;
+            while ((int64_t(2) << lg) <= Kp) ++lg;
+            int mq = default_mq(std::min(lg, 31));
+            while (mq > 1 && (int64_t)rg::kT * mq > Kp) mq >>= 1;
+            const int64_t TQ = (int64_t)rg::kT * mq;
+            for (int v = 0; v < nv; ++v)
+                for (int64_t q0 = 0; q0 < Kp; q0 += TQ) one.push_back({0, (int16_t)j, (int16_t)mq, v, 1, (int32_t)q0, 0});
+        } else {
+            const int nvar = std::max<int>(1, (int)(rg::kT / Kp));
+            for (int v0 = 0; v0 < nv; v0 += nvar) one.push_back({0, (int16_t)j, 0, v0, std::min(nvar, nv - v0), 0, 0});
+        }
+    }
+    std::vector<rg::Work> all;
+    all.reserve(one.size() * (size_t)B);
+    for (const auto &w : one)  // the largest work of every pulse first
+        for (int64_t b = 0; b < B; ++b) {
+            rg::Work x = w;
+            x.item = (int32_t)b;
+            all.push_back(x);
+        }
+    if (cudaMalloc(&ps->items, (size_t)B * sizeof(rg::Item)) != cudaSuccess ||
+        cudaMalloc(&ps->work, all.size() * sizeof(rg::Work)) != cudaSuccess ||
+        cudaMalloc(&ps->counter, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        free_small(p);
+        set_error("device allocation failed: small-batch work list");
+        return SIDWT_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpy(ps->work, all.data(), all.size() * sizeof(rg::Work), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "small-batch work list upload");
+    ps->nwork = (int)all.size();
+    ps->built_B = B;
+    return SIDWT_OK;
+}
+
+sidwt_status correlate_small(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t B, float2 *R, cudaStream_t s) {
+    PlanSmall *ps = static_cast<PlanSmall *>(p->small);
+    if (!ps || ps->built_B != B) {
+        set_error("small-batch work list not prepared");
+        return SIDWT_EINVAL;
+    }
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    rg::plan_items_kernel<<<1, 32, 0, s>>>(ref_ids_dev, (int)B, p->nrefs, (int)p->N, p->J, p->pyr_elems,
+                                           p->tree_elems, p->xen_len, ps->items);
+    cudaError_t e = cudaMemsetAsync(ps->counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    const int grid = std::min<int>(sms * 2, std::max(1, ps->nwork));
+    rg::corr_ragged_kernel<<<grid, rg::kT, 0, s>>>(ps->items, ps->work, ps->nwork, ps->counter, p->tree_f, p->pyr_f,
+                                                    p->keys, R);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "small-batch correlation launch");
+}
+
+}  // namespace sidwt
 
 extern "C" {
 
@@ -624,6 +737,8 @@ sidwt_status sidwt_ragged_reserve(sidwt_ragged *r, int64_t tree_elems, int64_t p
     cudaDeviceSynchronize();
     sidwt_status st;
     if ((st = grow(&r->tree, &r->tree_cap, tree_elems, r->tree_used, "ragged reference store"))) return st;
+    // a reference's energies (2^(J+1) - 1 values) never exceed its tree (2 J N >= 2^(J+1) elements)
+    if ((st = grow(&r->xen, &r->xen_cap, tree_elems, r->xen_used, "ragged reference energies"))) return st;
     RaggedLayout L;
     L.pyr_elems = pyr_elems;
     L.slots = slots;
@@ -822,7 +937,8 @@ sidwt_status sidwt_ragged_autotune(sidwt_ragged *r, const char *cache_path, sidw
             for (int rep = 0; rep < 4; ++rep) {
                 cudaMemsetAsync(counter, 0, sizeof(int), s);
                 cudaEventRecord(e0, s);
-                rg::corr_ragged_kernel<<<r->sms * 2, rg::kT, 0, s>>>(ditem, dwork, (int)w.size(), counter, tree, pyr, keys);
+                rg::corr_ragged_kernel<<<r->sms * 2, rg::kT, 0, s>>>(ditem, dwork, (int)w.size(), counter, tree, pyr, keys,
+                                                                      nullptr);
                 cudaEventRecord(e1, s);
                 cudaEventSynchronize(e1);
                 float ms = 0.f;

@@ -1,0 +1,527 @@
+// Serving loop: correlation requests (one received pulse each, against one
+// of the resident reference waveforms, with its own length N, depth J and
+// filter) arrive at any time; a server thread batches them continuously.
+//
+// The device is split into lanes (CUDA streams), each with a pre-reserved
+// ragged object and buffers.  Whenever a lane is idle the thread forms a
+// batch from the queue in arrival order, admitting requests while they fit
+// the lane's share of the memory cap, and enqueues the batch: pulse copies
+// in, each request's waveform zero-padded to its N, the SIDWT trees, the
+// ragged correlation, peaks out.  Requests that arrive while other lanes are
+// busy join the next idle lane, so batches overlap on the device.  A request
+// larger than a lane's share is rejected.  Every host wait is bounded.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "sidwt_internal.cuh"
+
+using namespace sidwt;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+struct Request {
+    int64_t id;
+    int32_t wave;
+    int filter;
+    int64_t N;
+    int J;
+    const void *y_host;
+    Clock::time_point arrival, done;
+    int64_t bytes = 0;
+    sidwt_status status = SIDWT_OK;
+    bool finished = false;
+    std::vector<int32_t> lag;
+    std::vector<float> mag;
+    std::vector<double> norm;
+};
+
+int64_t footprint(int64_t N, int J) {
+    // pulse, padded reference, SIDWT tree, pyramid, peak slots
+    return 8 * N + 8 * N + 16 * (int64_t)J * N + 16 * N + 64 * (J + 1);
+}
+
+__global__ void pad_kernel(const float2 *__restrict__ wave, int64_t wlen, float2 *__restrict__ x, int64_t N) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = i < wlen ? wave[i] : make_float2(0.f, 0.f);
+}
+
+struct Lane {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    sidwt_ragged *rg = nullptr;
+    float2 *y = nullptr, *x = nullptr;
+    int64_t cap_samples = 0;
+    int32_t *lag_d = nullptr;
+    float *mag_d = nullptr;
+    double *norm_d = nullptr;
+    int32_t *lag_h = nullptr;
+    float *mag_h = nullptr;
+    double *norm_h = nullptr;
+    int64_t cap_slots = 0;
+    bool busy = false;
+    std::vector<Request *> batch;
+    int64_t bytes = 0;
+};
+
+}  // namespace
+
+struct sidwt_server {
+    sidwt_server_config cfg;
+    std::vector<Lane> lanes;
+    std::vector<float2 *> waves;
+    std::vector<int64_t> wave_len;
+    std::mutex mu;
+    std::condition_variable cv_submit, cv_done;
+    std::deque<Request *> queue;
+    std::unordered_map<int64_t, Request *> reqs;
+    int64_t next_id = 0;
+    std::thread th;
+    bool running = false, stop = false;
+    int64_t in_flight_bytes = 0;
+    // statistics
+    std::vector<double> lat_ms;
+    int64_t completed = 0, rejected = 0, batches = 0, samples = 0;
+    Clock::time_point first_arrival, last_done;
+    bool any = false;
+    int64_t max_batch_seen = 0;
+};
+
+namespace {
+
+void complete_lane(sidwt_server *s, Lane &L) {
+    const auto now = Clock::now();
+    int64_t slot = 0;
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (Request *r : L.batch) {
+        const int n = r->J + 1;
+        r->lag.assign(L.lag_h + slot, L.lag_h + slot + n);
+        r->mag.assign(L.mag_h + slot, L.mag_h + slot + n);
+        r->norm.assign(L.norm_h + slot, L.norm_h + slot + n);
+        slot += n;
+        r->done = now;
+        r->finished = true;
+        s->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r->arrival).count());
+        s->samples += r->N;
+        ++s->completed;
+    }
+    s->last_done = now;
+    s->in_flight_bytes -= L.bytes;
+    L.bytes = 0;
+    L.batch.clear();
+    L.busy = false;
+    s->cv_done.notify_all();
+}
+
+void fail_lane(sidwt_server *s, Lane &L, sidwt_status st) {
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (Request *r : L.batch) {
+        r->status = st;
+        r->finished = true;
+        r->done = Clock::now();
+    }
+    s->in_flight_bytes -= L.bytes;
+    L.bytes = 0;
+    L.batch.clear();
+    L.busy = false;
+    s->cv_done.notify_all();
+}
+
+// Enqueue a formed batch on a lane (server thread only).
+sidwt_status launch_lane(sidwt_server *s, Lane &L) {
+    cudaStream_t st = L.stream;
+    sidwt_ragged_reset_references(L.rg);
+    std::vector<int32_t> ids;
+    std::vector<int64_t> offs;
+    int64_t off = 0, slots = 0;
+    for (Request *r : L.batch) {
+        cudaError_t e = cudaMemcpyAsync(L.y + off, r->y_host, (size_t)r->N * 8, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "request pulse copy");
+        const int64_t wl = std::min<int64_t>(s->wave_len[(size_t)r->wave], r->N);
+        pad_kernel<<<(unsigned)std::min<int64_t>(1024, (r->N + 255) / 256), 256, 0, st>>>(s->waves[(size_t)r->wave], wl,
+                                                                                        L.x + off, r->N);
+        int32_t rid = -1;
+        sidwt_status ss = sidwt_ragged_store_reference(L.rg, (sidwt_filter)r->filter, r->N, r->J, L.x + off, &rid,
+                                                       reinterpret_cast<sidwt_stream>(st));
+        if (ss) return ss;
+        ids.push_back(rid);
+        offs.push_back(off);
+        off += r->N;
+        slots += r->J + 1;
+    }
+    sidwt_status ss = sidwt_ragged_correlate(L.rg, (int64_t)ids.size(), ids.data(), offs.data(), L.y, off,
+                                             reinterpret_cast<sidwt_stream>(st));
+    if (ss) return ss;
+    ss = sidwt_ragged_peaks(L.rg, slots, L.lag_d, L.mag_d, L.norm_d, reinterpret_cast<sidwt_stream>(st));
+    if (ss) return ss;
+    cudaError_t e = cudaMemcpyAsync(L.lag_h, L.lag_d, slots * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.mag_h, L.mag_d, slots * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.norm_h, L.norm_d, slots * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(L.done, st);
+    return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "request result copy");
+}
+
+void serve(sidwt_server *s) {
+    const int64_t lane_budget = s->cfg.memory_cap_bytes / std::max(1, s->cfg.lanes);
+    for (;;) {
+        bool progressed = false;
+        for (Lane &L : s->lanes) {
+            if (L.busy) {
+                cudaError_t q = cudaEventQuery(L.done);
+                if (q == cudaSuccess) {
+                    complete_lane(s, L);
+                    progressed = true;
+                } else if (q != cudaErrorNotReady) {
+                    fail_lane(s, L, cuda_fail(q, "lane"));
+                }
+            }
+        }
+        for (Lane &L : s->lanes) {
+            if (L.busy) continue;
+            {
+                std::lock_guard<std::mutex> lock(s->mu);
+                int64_t bytes = 0, samples = 0, slots = 0;
+                while (!s->queue.empty() && (int64_t)L.batch.size() < s->cfg.max_batch) {
+                    Request *r = s->queue.front();
+                    const int64_t fb = footprint(r->N, r->J);
+                    if (fb > lane_budget || r->N > L.cap_samples || r->J + 1 > L.cap_slots) {
+                        // can never fit a lane: reject
+                        s->queue.pop_front();
+                        r->status = SIDWT_ENOMEM;
+                        r->finished = true;
+                        r->done = Clock::now();
+                        ++s->rejected;
+                        s->cv_done.notify_all();
+                        continue;
+                    }
+                    if (bytes + fb > lane_budget || samples + r->N > L.cap_samples || slots + r->J + 1 > L.cap_slots ||
+                        s->in_flight_bytes + bytes + fb > s->cfg.memory_cap_bytes)
+                        break;
+                    s->queue.pop_front();
+                    L.batch.push_back(r);
+                    bytes += fb;
+                    samples += r->N;
+                    slots += r->J + 1;
+                }
+                if (L.batch.empty()) continue;
+                L.bytes = bytes;
+                s->in_flight_bytes += bytes;
+                ++s->batches;
+                s->max_batch_seen = std::max<int64_t>(s->max_batch_seen, (int64_t)L.batch.size());
+                L.busy = true;
+            }
+            sidwt_status st = launch_lane(s, L);
+            if (st) fail_lane(s, L, st);
+            progressed = true;
+        }
+        std::unique_lock<std::mutex> lock(s->mu);
+        if (s->stop) {
+            bool idle = true;
+            for (Lane &L : s->lanes) idle = idle && !L.busy;
+            if (idle && s->queue.empty()) break;
+        }
+        if (!progressed) {
+            bool any_busy = false;
+            for (Lane &L : s->lanes) any_busy = any_busy || L.busy;
+            // idle: sleep until a submission; busy lanes: poll again shortly
+            if (!any_busy)
+                s->cv_submit.wait_for(lock, std::chrono::milliseconds(5));
+            else {
+                lock.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
+            }
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+sidwt_status sidwt_server_create(const sidwt_server_config *cfg, sidwt_server **out) {
+    if (!cfg || !out || cfg->lanes < 1 || cfg->lanes > 64 || cfg->memory_cap_bytes <= 0 || cfg->max_batch < 1 ||
+        cfg->max_lane_samples < 2 || cfg->max_j < 1 || cfg->max_j > 15) {
+        set_error("bad server configuration");
+        return SIDWT_EINVAL;
+    }
+    *out = nullptr;
+    sidwt_server *s = new (std::nothrow) sidwt_server();
+    if (!s) {
+        set_error("host allocation failed");
+        return SIDWT_ENOMEM;
+    }
+    s->cfg = *cfg;
+    s->lanes.resize((size_t)cfg->lanes);
+    const int64_t cap = cfg->max_lane_samples;
+    const int64_t slots = (int64_t)cfg->max_batch * (cfg->max_j + 1);
+    for (Lane &L : s->lanes) {
+        sidwt_status st = sidwt_ragged_create(&L.rg);
+        if (!st) st = sidwt_ragged_reserve(L.rg, 2 * (int64_t)cfg->max_j * cap, 2 * cap, slots);
+        if (st || cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMalloc(&L.y, cap * sizeof(float2)) != cudaSuccess || cudaMalloc(&L.x, cap * sizeof(float2)) != cudaSuccess ||
+            cudaMalloc(&L.lag_d, slots * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&L.mag_d, slots * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&L.norm_d, slots * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&L.lag_h, slots * sizeof(int32_t)) != cudaSuccess ||
+            cudaMallocHost(&L.mag_h, slots * sizeof(float)) != cudaSuccess ||
+            cudaMallocHost(&L.norm_h, slots * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            sidwt_server_destroy(s);
+            if (!st) set_error("server allocation failed");
+            return st ? st : SIDWT_ENOMEM;
+        }
+        L.cap_samples = cap;
+        L.cap_slots = slots;
+    }
+    *out = s;
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_server_add_waveform(sidwt_server *s, const void *x_host, int64_t len, int32_t *wave_id) {
+    if (!s || !x_host || len < 1 || !wave_id) {
+        set_error("bad waveform");
+        return SIDWT_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->running) {
+        set_error("add waveforms before sidwt_server_start");
+        return SIDWT_EBUSY;
+    }
+    float2 *d = nullptr;
+    if (cudaMalloc(&d, len * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("waveform allocation failed");
+        return SIDWT_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpy(d, x_host, len * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "waveform copy");
+    }
+    s->waves.push_back(d);
+    s->wave_len.push_back(len);
+    *wave_id = (int32_t)s->waves.size() - 1;
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_server_start(sidwt_server *s) {
+    if (!s) {
+        set_error("NULL server");
+        return SIDWT_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->running) return SIDWT_OK;
+    s->stop = false;
+    s->running = true;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    s->th = std::thread([s, dev] {
+        cudaSetDevice(dev);
+        serve(s);
+    });
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_server_submit(sidwt_server *s, int32_t wave_id, sidwt_filter f, int64_t N, int J,
+                                 const void *y_host, int64_t *request_id) {
+    if (!s || !y_host || !request_id) {
+        set_error("NULL argument");
+        return SIDWT_EINVAL;
+    }
+    if ((int)f < 0 || (int)f > 2 || J < 1 || J > s->cfg.max_j || N < 2 || N % (int64_t(1) << J) != 0) {
+        set_error("bad request shape (float filter, 1 <= J <= max_j, N a multiple of 2^J)");
+        return SIDWT_EINVAL;
+    }
+    Request *r = new (std::nothrow) Request();
+    if (!r) {
+        set_error("host allocation failed");
+        return SIDWT_ENOMEM;
+    }
+    r->wave = wave_id;
+    r->filter = (int)f;
+    r->N = N;
+    r->J = J;
+    r->y_host = y_host;
+    r->arrival = Clock::now();
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (wave_id < 0 || wave_id >= (int32_t)s->waves.size()) {
+            delete r;
+            set_error("unknown waveform");
+            return SIDWT_EINVAL;
+        }
+        r->id = s->next_id++;
+        if (!s->any) {
+            s->first_arrival = r->arrival;
+            s->any = true;
+        }
+        s->reqs[r->id] = r;
+        s->queue.push_back(r);
+    }
+    s->cv_submit.notify_one();
+    *request_id = r->id;
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_server_wait(sidwt_server *s, int64_t request_id, double timeout_s) {
+    if (!s) {
+        set_error("NULL server");
+        return SIDWT_EINVAL;
+    }
+    std::unique_lock<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(request_id);
+    if (it == s->reqs.end()) {
+        set_error("unknown request");
+        return SIDWT_EINVAL;
+    }
+    Request *r = it->second;
+    const bool ok = s->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s), [r] { return r->finished; });
+    if (!ok) {
+        set_error("request did not finish within the timeout");
+        return SIDWT_ETIMEOUT;
+    }
+    return r->status;
+}
+
+sidwt_status sidwt_server_result(sidwt_server *s, int64_t request_id, int32_t *lag_host, float *mag_host,
+                                 double *norm_host, double *latency_ms) {
+    if (!s) {
+        set_error("NULL server");
+        return SIDWT_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(request_id);
+    if (it == s->reqs.end()) {
+        set_error("unknown request");
+        return SIDWT_EINVAL;
+    }
+    Request *r = it->second;
+    if (!r->finished) {
+        set_error("request still in flight");
+        return SIDWT_EBUSY;
+    }
+    if (r->status) {
+        set_error(r->status == SIDWT_ENOMEM ? "request rejected: larger than a lane's share of the memory cap"
+                                            : "request failed");
+        return r->status;
+    }
+    const size_t n = r->lag.size();
+    if (lag_host) std::memcpy(lag_host, r->lag.data(), n * sizeof(int32_t));
+    if (mag_host) std::memcpy(mag_host, r->mag.data(), n * sizeof(float));
+    if (norm_host) std::memcpy(norm_host, r->norm.data(), n * sizeof(double));
+    if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->done - r->arrival).count();
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_server_drain(sidwt_server *s, double timeout_s) {
+    if (!s) {
+        set_error("NULL server");
+        return SIDWT_EINVAL;
+    }
+    std::unique_lock<std::mutex> lock(s->mu);
+    const bool ok = s->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s), [s] {
+        for (auto &kv : s->reqs)
+            if (!kv.second->finished) return false;
+        return true;
+    });
+    if (!ok) {
+        set_error("requests still in flight after the timeout");
+        return SIDWT_ETIMEOUT;
+    }
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_server_read_stats(sidwt_server *s, sidwt_server_stats *out, int reset) {
+    if (!s || !out) {
+        set_error("NULL argument");
+        return SIDWT_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->completed = s->completed;
+    out->rejected = s->rejected;
+    out->batches = s->batches;
+    out->max_batch = s->max_batch_seen;
+    out->samples = s->samples;
+    out->queued = (int64_t)s->queue.size();
+    if (!s->lat_ms.empty()) {
+        std::vector<double> v = s->lat_ms;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double p) { return v[(size_t)std::min<double>(v.size() - 1, p * (v.size() - 1) + 0.5)]; };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+        out->max_ms = v.back();
+    }
+    if (s->any && s->completed > 0)
+        out->span_s = std::chrono::duration<double>(s->last_done - s->first_arrival).count();
+    if (reset) {
+        s->lat_ms.clear();
+        s->completed = s->rejected = s->batches = s->samples = s->max_batch_seen = 0;
+        s->any = false;
+        for (auto &kv : s->reqs)
+            if (!kv.second->finished) {
+                s->any = true;
+                s->first_arrival = kv.second->arrival;
+                break;
+            }
+    }
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_server_forget(sidwt_server *s, int64_t request_id) {
+    if (!s) {
+        set_error("NULL server");
+        return SIDWT_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(request_id);
+    if (it == s->reqs.end() || !it->second->finished) {
+        set_error("unknown or unfinished request");
+        return SIDWT_EINVAL;
+    }
+    delete it->second;
+    s->reqs.erase(it);
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_server_destroy(sidwt_server *s) {
+    if (!s) return SIDWT_OK;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
+    }
+    s->cv_submit.notify_all();
+    if (s->th.joinable()) s->th.join();
+    cudaDeviceSynchronize();
+    for (Lane &L : s->lanes) {
+        if (L.rg) sidwt_ragged_destroy(L.rg);
+        if (L.stream) cudaStreamDestroy(L.stream);
+        if (L.done) cudaEventDestroy(L.done);
+        cudaFree(L.y);
+        cudaFree(L.x);
+        cudaFree(L.lag_d);
+        cudaFree(L.mag_d);
+        cudaFree(L.norm_d);
+        if (L.lag_h) cudaFreeHost(L.lag_h);
+        if (L.mag_h) cudaFreeHost(L.mag_h);
+        if (L.norm_h) cudaFreeHost(L.norm_h);
+    }
+    for (float2 *w : s->waves) cudaFree(w);
+    for (auto &kv : s->reqs) delete kv.second;
+    delete s;
+    return SIDWT_OK;
+}
+
+}  // extern "C"

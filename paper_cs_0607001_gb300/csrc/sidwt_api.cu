@@ -255,6 +255,7 @@ sidwt_status sidwt_plan_destroy(sidwt_plan *p) {
     cudaDeviceSynchronize();
     free_batch(p);
     free_tc(p);
+    free_small(p);
     dfree(p->tree_f);
     dfree(p->tree_i);
     dfree(p->xen);
@@ -396,6 +397,8 @@ sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const vo
     p->last_B = B;
     if (B == 0) return SIDWT_OK;
     if (p->timing) ++p->timed_correlate_calls;
+    const bool small = B <= kSmallBatch;
+    if (small && (st = prepare_small(p, B))) return st;
     {
         StageTimer t(p, 1, s, 1);
         if ((st = group_pulses(p, ref_ids_dev, B, tc ? tc_group_tile() : simt_tile_pulses(), s))) return st;
@@ -407,8 +410,10 @@ sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const vo
     cudaError_t e = cudaMemsetAsync(p->keys, 0, B * (p->J + 1) * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
     {
-        StageTimer t(p, 3, s, tc ? tc_launch_count(p) : 1);
-        if (tc) {
+        StageTimer t(p, 3, s, small ? 2 : (tc ? tc_launch_count(p) : 1));
+        if (small) {
+            if ((st = correlate_small(p, ref_ids_dev, B, reinterpret_cast<float2 *>(r_dev), s))) return st;
+        } else if (tc) {
             if ((st = correlate_tc(p, B, reinterpret_cast<float2 *>(r_dev), s))) return st;
         } else if ((st = correlate_simt(p, B, reinterpret_cast<float2 *>(r_dev), s))) {
             return st;

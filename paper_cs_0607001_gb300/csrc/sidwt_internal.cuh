@@ -166,6 +166,8 @@ struct sidwt_plan {
     std::vector<cudaEvent_t> event_pool;
     int64_t timed_correlate_calls = 0;
     int64_t timed_launches = 0;
+
+    void *small = nullptr;  // small-batch work list (ragged.cu)
 };
 
 namespace sidwt {
@@ -209,6 +211,12 @@ sidwt_status group_pulses(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t B, 
 sidwt_status correlate_simt(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t s, uint32_t scale_mask = 0xffffffffu,
                             int group_tile = 64);
 int simt_tile_pulses();
+
+// ---- ragged.cu: batches of a few pulses on the batch-of-one kernel ----
+constexpr int64_t kSmallBatch = 16;
+sidwt_status prepare_small(sidwt_plan *p, int64_t B);
+sidwt_status correlate_small(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t B, float2 *R, cudaStream_t s);
+void free_small(sidwt_plan *p);
 
 // ---- corr_tc.cu ----
 sidwt_status correlate_tc(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t s);

@@ -34,6 +34,21 @@ class Timing(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("max_j", ctypes.c_int32),
+                ("memory_cap_bytes", ctypes.c_int64), ("max_lane_samples", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("rejected", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("max_batch", ctypes.c_int64), ("samples", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("span_s", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -87,6 +102,16 @@ def lib():
     L.sidwt_ragged_set_timing.argtypes = [_vp, ctypes.c_int]
     L.sidwt_ragged_read_timing.argtypes = [_vp, ctypes.POINTER(Timing), ctypes.c_int]
     L.sidwt_ragged_reset_references.argtypes = [_vp]
+    L.sidwt_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]
+    L.sidwt_server_add_waveform.argtypes = [_vp, _vp, _i64, ctypes.POINTER(_i32)]
+    L.sidwt_server_start.argtypes = [_vp]
+    L.sidwt_server_submit.argtypes = [_vp, _i32, ctypes.c_int, _i64, ctypes.c_int, _vp, ctypes.POINTER(_i64)]
+    L.sidwt_server_wait.argtypes = [_vp, _i64, ctypes.c_double]
+    L.sidwt_server_drain.argtypes = [_vp, ctypes.c_double]
+    L.sidwt_server_result.argtypes = [_vp, _i64, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)]
+    L.sidwt_server_forget.argtypes = [_vp, _i64]
+    L.sidwt_server_read_stats.argtypes = [_vp, ctypes.POINTER(ServerStats), ctypes.c_int]
+    L.sidwt_server_destroy.argtypes = [_vp]
     for name in ("sidwt_plan_create", "sidwt_plan_destroy", "sidwt_plan_reserve", "sidwt_store_reference",
                  "sidwt_reference_tree", "sidwt_analyze", "sidwt_correlate", "sidwt_peaks",
                  "sidwt_correlate_host", "sidwt_check", "sidwt_reset_references", "sidwt_set_timing",
@@ -94,7 +119,10 @@ def lib():
                  "sidwt_ragged_destroy", "sidwt_ragged_reserve", "sidwt_ragged_store_reference",
                  "sidwt_ragged_correlate", "sidwt_ragged_graph_create", "sidwt_ragged_graph_launch",
                  "sidwt_ragged_peaks", "sidwt_ragged_autotune", "sidwt_ragged_tuning", "sidwt_ragged_set_timing",
-                 "sidwt_ragged_read_timing", "sidwt_ragged_reset_references"):
+                 "sidwt_ragged_read_timing", "sidwt_ragged_reset_references", "sidwt_server_create",
+                 "sidwt_server_add_waveform", "sidwt_server_start", "sidwt_server_submit", "sidwt_server_wait",
+                 "sidwt_server_drain", "sidwt_server_result", "sidwt_server_forget", "sidwt_server_read_stats",
+                 "sidwt_server_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -391,6 +419,79 @@ class Ragged:
     def reset_references(self):
         _raise(lib().sidwt_ragged_reset_references(self._h))
         self.refs = []
+
+
+class Server:
+    """Continuous-batching request loop (sidwt_server_*)."""
+
+    def __init__(self, lanes=4, max_batch=64, max_j=10, memory_cap_bytes=40 << 30, max_lane_samples=1 << 22):
+        cfg = ServerConfig(lanes, max_batch, max_j, memory_cap_bytes, max_lane_samples)
+        h = _vp()
+        _raise(lib().sidwt_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self.max_j = max_j
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sidwt_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def add_waveform(self, x: np.ndarray) -> int:
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.complex64))
+        wid = _i32(-1)
+        _raise(lib().sidwt_server_add_waveform(self._h, x.ctypes.data, x.size, ctypes.byref(wid)))
+        return wid.value
+
+    def start(self):
+        _raise(lib().sidwt_server_start(self._h))
+
+    def submit(self, wave: int, filter, N: int, J: int, y: torch.Tensor) -> int:
+        """y: host complex64 tensor of N samples (pinned is fastest); kept alive until finished."""
+        if y.is_cuda or y.dtype != torch.complex64 or y.numel() != N or not y.is_contiguous():
+            raise ValueError("y must be a contiguous host complex64 tensor of N samples")
+        rid = _i64(-1)
+        _raise(lib().sidwt_server_submit(self._h, wave, _filter_id(filter), int(N), int(J), _ptr(y),
+                                         ctypes.byref(rid)))
+        self._keep[rid.value] = (y, J)
+        return rid.value
+
+    def wait(self, rid: int, timeout_s: float = 30.0):
+        _raise(lib().sidwt_server_wait(self._h, rid, timeout_s))
+
+    def drain(self, timeout_s: float = 60.0):
+        _raise(lib().sidwt_server_drain(self._h, timeout_s))
+
+    def result(self, rid: int):
+        J = self._keep[rid][1]
+        lag = np.zeros(J + 1, np.int32)
+        mag = np.zeros(J + 1, np.float32)
+        norm = np.zeros(J + 1, np.float64)
+        lat = ctypes.c_double(0.0)
+        _raise(lib().sidwt_server_result(self._h, rid, lag.ctypes.data, mag.ctypes.data, norm.ctypes.data,
+                                         ctypes.byref(lat)))
+        return lag, mag, norm, lat.value
+
+    def forget(self, rid: int):
+        _raise(lib().sidwt_server_forget(self._h, rid))
+        self._keep.pop(rid, None)
+
+    def stats(self, reset: bool = False) -> dict:
+        st = ServerStats()
+        _raise(lib().sidwt_server_read_stats(self._h, ctypes.byref(st), 1 if reset else 0))
+        return st.as_dict()
 
 
 def tc_selftest(stream=None):
