@@ -85,28 +85,53 @@ __device__ __forceinline__ int2 to_i2<short2>(short2 v) { return make_int2(v.x, 
 template <>
 __device__ __forceinline__ int2 to_i2<int2>(int2 v) { return v; }
 
-__device__ __forceinline__ double norm2d(float2 v) { return (double)v.x * v.x + (double)v.y * v.y; }
-__device__ __forceinline__ double norm2d(int2 v) { return (double)v.x * v.x + (double)v.y * v.y; }
 
-// Energy accumulator (eq. 1): squares in FP32, flushed into an FP64 sum every
-// 32 terms, so the FP64 pipe (slow on this part) sees one add per 32
-// samples while the FP32 rounding stays within 32 terms.
+// Energy accumulator (eq. 1).  The FP64 pipe of this part runs at a small
+// fraction of FP32, so the sums are kept as unevaluated pairs of floats
+// (hi + lo, Knuth's TwoSum), which carry about 48 significant bits; squares
+// are formed in FP32 from the FP32 coefficients.  Only the final value of a
+// block sum is converted to double.
 struct EnAcc {
-    double d = 0.0;
-    float f = 0.0f;
-    int n = 0;
+    float hi = 0.0f, lo = 0.0f;
     __device__ __forceinline__ void add(float x) {
-        f += x;
-        if (++n == 32) {
-            d += (double)f;
-            f = 0.0f;
-            n = 0;
-        }
+        const float s = hi + x;
+        const float bb = s - hi;
+        const float e = (hi - (s - bb)) + (x - bb);
+        hi = s;
+        lo += e;
     }
-    __device__ __forceinline__ double total() const { return d + (double)f; }
+    __device__ __forceinline__ void add(const EnAcc &o) {
+        add(o.hi);
+        lo += o.lo;
+    }
+    __device__ __forceinline__ double total() const { return (double)hi + (double)lo; }
 };
 __device__ __forceinline__ float sq2(float2 v) { return fmaf(v.x, v.x, v.y * v.y); }
 __device__ __forceinline__ long long sq2i(int2 v) { return (long long)v.x * v.x + (long long)v.y * v.y; }
+
+// Deterministic block sum of one pair-of-floats accumulator per thread
+// (blockDim.x multiple of 32); the result, in double, is valid in thread 0.
+__device__ double block_sum(EnAcc v, float2 *red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        EnAcc t;
+        t.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        t.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v.add(t);
+    }
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = make_float2(v.hi, v.lo);
+    __syncthreads();
+    EnAcc t;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; ++i) {
+            EnAcc u;
+            u.hi = red[i].x;
+            u.lo = red[i].y;
+            t.add(u);
+        }
+    return t.total();
+}
 
 // Deterministic block sum of one int64 per thread, returned as double.
 __device__ double block_sum_i64(long long v, long long *red) {
@@ -119,19 +144,6 @@ __device__ double block_sum_i64(long long v, long long *red) {
     if (threadIdx.x == 0)
         for (int i = 0; i < nw; ++i) t += red[i];
     return (double)t;  // valid in thread 0
-}
-
-// Deterministic block sum of one double per thread (blockDim.x multiple of 32).
-__device__ double block_sum(double v, double *red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < nw; ++i) t += red[i];
-    return t;  // valid in thread 0
 }
 
 // ---------------------------------------------------------------------------
@@ -263,7 +275,7 @@ __global__ void ref_energy_kernel(const TIn *__restrict__ x, const TTree *__rest
 template <>
 __global__ void ref_energy_kernel<float2, float2>(const float2 *__restrict__ x, const float2 *__restrict__ tree,
                                                   int64_t N, double *__restrict__ out) {
-    __shared__ double red[32];
+    __shared__ float2 red[32];
     const int b = blockIdx.x;
     int l = 0;
     while ((2 << l) - 1 <= b) ++l;
@@ -272,7 +284,7 @@ __global__ void ref_energy_kernel<float2, float2>(const float2 *__restrict__ x, 
     const float2 *X = l == 0 ? x : tree + 2 * N * (int64_t)(l - 1) + (int64_t)v * K;
     EnAcc acc;
     for (int64_t k = threadIdx.x; k < K; k += blockDim.x) acc.add(sq2(X[k]));
-    const double t = block_sum(acc.total(), red);
+    const double t = block_sum(acc, red);
     if (threadIdx.x == 0) out[b] = t;
 }
 
@@ -361,7 +373,7 @@ __device__ __forceinline__ void out_pair_i(const int2 *in, int H, int n, int2 &l
 template <int F, typename T>
 __device__ __forceinline__ void analyze_one(const void *__restrict__ y, int64_t N, int J, float2 *__restrict__ pyr_f,
                                             int2 *__restrict__ pyr_i, double *__restrict__ yen, const LiftCoef &c,
-                                            T *sm, double *red, long long *redi) {
+                                            T *sm, float2 *red, long long *redi) {
     constexpr bool INT = (F == SIDWT_LEGALL53_INT);
     const int Nh = (int)(N / 2);
     EnAcc en;
@@ -387,7 +399,7 @@ __device__ __forceinline__ void analyze_one(const void *__restrict__ y, int64_t 
         }
     }
     {
-        const double t = INT ? block_sum_i64(eni, redi) : block_sum(en.total(), red);
+        const double t = INT ? block_sum_i64(eni, redi) : block_sum(en, red);
         if (threadIdx.x == 0) yen[0] = t;
     }
     __syncthreads();
@@ -416,7 +428,7 @@ __device__ __forceinline__ void analyze_one(const void *__restrict__ y, int64_t 
             }
             out[n] = lo;
         }
-        const double t = INT ? block_sum_i64(eni, redi) : block_sum(en.total(), red);
+        const double t = INT ? block_sum_i64(eni, redi) : block_sum(en, red);
         if (threadIdx.x == 0) yen[l] = t;
         __syncthreads();
     }
@@ -429,7 +441,7 @@ __global__ void __launch_bounds__(kAnalyzeThreads) analyze_smem_kernel(const voi
                                                                        int2 *__restrict__ pyr_i, int64_t pyr_elems,
                                                                        double *__restrict__ yen, LiftCoef c) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ double red[32];
+    __shared__ float2 red[32];
     __shared__ long long redi[32];
     constexpr bool INT = (F == SIDWT_LEGALL53_INT);
     const int64_t b = blockIdx.x;
@@ -446,7 +458,7 @@ __global__ void __launch_bounds__(kAnalyzeThreads) analyze_ragged_kernel(const f
                                                                          float2 *__restrict__ pyr,
                                                                          double *__restrict__ yen, LiftCoef c) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ double red[32];
+    __shared__ float2 red[32];
     __shared__ long long redi[32];
     const RaggedLift it = items[blockIdx.x];
     analyze_one<F, float2>(y + it.y_off, it.N, it.J, pyr + it.pyr_off, nullptr, yen + it.yen_off, c,
@@ -457,7 +469,7 @@ __global__ void __launch_bounds__(kAnalyzeThreads) analyze_ragged_kernel(const f
 __global__ void pyr_energy_kernel(const float2 *__restrict__ y, const float2 *__restrict__ pyr_f,
                                   const int2 *__restrict__ pyr_i, const short2 *__restrict__ y_i, int64_t N, int J,
                                   int64_t pyr_elems, double *__restrict__ yen) {
-    __shared__ double red[32];
+    __shared__ float2 red[32];
     __shared__ long long redi[32];
     const int64_t b = blockIdx.x;
     const int l = blockIdx.y;
@@ -482,7 +494,7 @@ __global__ void pyr_energy_kernel(const float2 *__restrict__ y, const float2 *__
         } else {
             for (int64_t k = threadIdx.x; k < K; k += blockDim.x) acc.add(sq2(pyr_f[off + k]));
         }
-        const double t = block_sum(acc.total(), red);
+        const double t = block_sum(acc, red);
         if (threadIdx.x == 0) yen[b * (J + 1) + l] = t;
     }
 }
@@ -679,7 +691,7 @@ __global__ void ragged_level_kernel(const float2 *__restrict__ y, const RaggedLi
 // Energies of long ragged pulses: block (level l, item).
 __global__ void ragged_energy_kernel(const float2 *__restrict__ y, const RaggedLift *__restrict__ items,
                                      const float2 *__restrict__ pyr, double *__restrict__ yen) {
-    __shared__ double red[32];
+    __shared__ float2 red[32];
     const RaggedLift it = items[blockIdx.y];
     const int l = blockIdx.x;
     if (l > it.J) return;
@@ -687,7 +699,7 @@ __global__ void ragged_energy_kernel(const float2 *__restrict__ y, const RaggedL
     const float2 *v = l == 0 ? y + it.y_off : pyr + it.pyr_off + (2 * it.N - 4 * K);
     EnAcc acc;
     for (int64_t k = threadIdx.x; k < K; k += blockDim.x) acc.add(sq2(v[k]));
-    const double t = block_sum(acc.total(), red);
+    const double t = block_sum(acc, red);
     if (threadIdx.x == 0) yen[it.yen_off + l] = t;
 }
 
