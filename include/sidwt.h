@@ -272,6 +272,25 @@ sidwt_status sidwt_ragged_read_timing(sidwt_ragged *r, sidwt_timing *out, int re
  * be called while a batch using them is in flight. */
 sidwt_status sidwt_ragged_reset_references(sidwt_ragged *r);
 
+/* Precision of later stores and correlations: SIDWT_PREC_FP32 (default; the
+ * CUDA-core kernel above) or SIDWT_PREC_BF16X3.  With BF16X3 each stored
+ * signal also keeps, for every scale whose band K' is at least 512 samples,
+ * its variants packed for the tensor cores (bf16 hi and lo, about 32 N bytes
+ * per such scale), and correlations run those scales as GEMMs on tcgen05:
+ * rows are the stored variants advanced by multiples of S (S = 128 or 256
+ * chosen per scale), columns the received band advanced by 0..S-1, so that
+ * one received pulse fills whole tiles (eq. 20 / 20a unchanged; bands that
+ * are not a multiple of 64 use the equivalent zero-padded linear form).
+ * Shorter bands, and signals stored before the switch, stay on the CUDA
+ * cores.  Error bound as for sidwt_correlate with BF16X3.
+ * SIDWT_EUNSUPPORTED for SIDWT_PREC_TF32X3. */
+sidwt_status sidwt_ragged_set_precision(sidwt_ragged *r, sidwt_precision prec);
+
+/* Synchronise `stream` and report device-side failures of earlier batches:
+ * SIDWT_ETIMEOUT if a tensor-core CTA gave up on a bounded wait (its results
+ * are incomplete), SIDWT_OK otherwise.  The record is cleared. */
+sidwt_status sidwt_ragged_check(sidwt_ragged *r, sidwt_stream stream);
+
 /* The current choice: mq_by_log2_band[k] shifts per thread for bands of
  * length in [2^k, 2^(k+1)) (32 entries). */
 sidwt_status sidwt_ragged_tuning(const sidwt_ragged *r, int32_t *mq_by_log2_band);

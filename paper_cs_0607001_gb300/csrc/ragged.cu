@@ -10,6 +10,7 @@
 // autotuner), or several whole variants of a short band (one shift per
 // thread).  Work items are ordered by cost, largest first, and pulled by a
 // persistent grid from a device counter.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -260,6 +261,7 @@ struct RefInfo {
     int64_t N;
     int J;
     int64_t tree_off, xen_off;
+    int64_t tc_off[16];  // stored tensor-core operand of scale j (bf16 elements), -1: none
 };
 
 struct RaggedLayout {  // everything a batch needs on the device, built on the host
@@ -267,6 +269,14 @@ struct RaggedLayout {  // everything a batch needs on the device, built on the h
     std::vector<rg::Work> work;
     std::vector<RaggedLift> lift[2][3];  // [path: smem, long][filter]
     std::vector<int32_t> slot_item;
+    // tensor-core part: one received-operand entry and two tensor maps per
+    // (pair, scale), tiles in cost order
+    std::vector<rtc::TcTile> tc_tiles;
+    std::vector<rtc::RecvEntry> recv;
+    std::vector<rtc::Shape> recv_shape;
+    std::vector<int64_t> recv_a_off;
+    std::vector<unsigned char> maps;
+    int64_t recv_elems = 0;
     int64_t pyr_elems = 0, slots = 0;
     int64_t maxN[2][3] = {{0, 0, 0}, {0, 0, 0}};
     int maxJ_long[3] = {0, 0, 0};
@@ -277,15 +287,26 @@ struct DevLayout {  // device copy of a RaggedLayout
     rg::Work *work = nullptr;
     RaggedLift *lift = nullptr;
     int32_t *slot_item = nullptr;
-    int64_t cap_items = 0, cap_work = 0, cap_lift = 0, cap_slots = 0;
+    rtc::TcTile *tc_tiles = nullptr;
+    rtc::RecvEntry *recv = nullptr;
+    unsigned char *maps = nullptr;
+    int64_t cap_items = 0, cap_work = 0, cap_lift = 0, cap_slots = 0, cap_tiles = 0, cap_recv = 0, cap_maps = 0;
     RaggedLiftGroups groups;
-    int nwork = 0;
+    int nwork = 0, n_tc_tiles = 0, n_recv = 0;
 };
 
 struct sidwt_ragged {
     std::vector<RefInfo> refs;
     float2 *tree = nullptr;
     int64_t tree_cap = 0, tree_used = 0;
+    // tensor-core path (SIDWT_PREC_BF16X3): stored operands of the references
+    // packed at store time, received operands of the current batch, error flag
+    int prec = SIDWT_PREC_FP32;
+    __nv_bfloat16 *tc_a = nullptr;
+    int64_t tc_a_cap = 0, tc_a_used = 0;
+    __nv_bfloat16 *tc_b = nullptr;
+    int64_t tc_b_cap = 0;
+    int32_t *err = nullptr;
     double *xen = nullptr;
     int64_t xen_cap = 0, xen_used = 0;
     // batch workspace
@@ -382,9 +403,44 @@ sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_i
     }
     // work items, bucketed by log2 of their cost, largest first
     std::vector<std::vector<rg::Work>> buckets(64);
+    std::vector<std::pair<int64_t, rtc::TcTile>> tct;  // (cost, tile)
     for (int64_t i = 0; i < n; ++i) {
         const rg::Item &it = L.items[(size_t)i];
+        const RefInfo &ri = r->refs[(size_t)it.ref];
         for (int j = 0; j <= it.J; ++j) {
+            rtc::Shape sh;
+            if (r->prec == SIDWT_PREC_BF16X3 && j < 16 && ri.tc_off[j] >= 0 && rtc::shape_for(it.N, it.J, j, &sh)) {
+                const int e = (int)L.recv.size();
+                rtc::RecvEntry re;
+                re.pyr_off = it.pyr_off;
+                re.out_off = L.recv_elems;
+                re.N = it.N;
+                re.Kp = (int32_t)sh.Kp;
+                re.lev = sh.lev;
+                re.nb = sh.nb;
+                re.Lc = (int32_t)sh.Lc;
+                re.k0 = sh.k0;
+                L.recv.push_back(re);
+                L.recv_shape.push_back(sh);
+                L.recv_a_off.push_back(ri.tc_off[j]);
+                L.recv_elems += (sh.b_elems + 63) / 64 * 64;
+                for (int t = 0; t < sh.tiles; ++t) {
+                    rtc::TcTile w;
+                    w.map = e;
+                    w.tile = t;
+                    w.nkb = sh.nkb;
+                    w.Kp = (int32_t)sh.Kp;
+                    w.gv = sh.gv;
+                    w.nv = sh.nv;
+                    w.nb = (int16_t)sh.nb;
+                    w.lev = (int16_t)sh.lev;
+                    w.S = (int16_t)sh.S;
+                    w.pad = 0;
+                    w.slot = it.slot + j;
+                    tct.push_back({(int64_t)sh.nb * sh.nkb * sh.S, w});
+                }
+                continue;
+            }
             const int lev = j < it.J ? j + 1 : it.J;
             const int64_t Kp = (int64_t)it.N >> lev;
             const int nb = j < it.J ? 2 : 1;
@@ -412,7 +468,11 @@ sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_i
         }
     }
     for (int b = 63; b >= 0; --b) L.work.insert(L.work.end(), buckets[b].begin(), buckets[b].end());
-    if (L.work.size() > 0x7fffffff) {
+    std::stable_sort(tct.begin(), tct.end(), [](const std::pair<int64_t, rtc::TcTile> &a,
+                                                const std::pair<int64_t, rtc::TcTile> &b) { return a.first > b.first; });
+    L.tc_tiles.reserve(tct.size());
+    for (const auto &x : tct) L.tc_tiles.push_back(x.second);
+    if (L.work.size() > 0x7fffffff || L.tc_tiles.size() > 0x7fffffff || L.recv.size() > 0x7fffffff) {
         set_error("too many work items");
         return SIDWT_EINVAL;
     }
@@ -427,8 +487,24 @@ sidwt_status ensure_dev(DevLayout &d, const RaggedLayout &L) {
     if ((st = grow(&d.items, &d.cap_items, (int64_t)L.items.size(), 0, "ragged items")) ||
         (st = grow(&d.work, &d.cap_work, (int64_t)L.work.size(), 0, "ragged work list")) ||
         (st = grow(&d.lift, &d.cap_lift, nl, 0, "ragged lifting list")) ||
-        (st = grow(&d.slot_item, &d.cap_slots, L.slots, 0, "ragged slot map")))
+        (st = grow(&d.slot_item, &d.cap_slots, L.slots, 0, "ragged slot map")) ||
+        (st = grow(&d.tc_tiles, &d.cap_tiles, (int64_t)L.tc_tiles.size(), 0, "tensor-core tile list")) ||
+        (st = grow(&d.recv, &d.cap_recv, (int64_t)L.recv.size(), 0, "tensor-core operand list")) ||
+        (st = grow(&d.maps, &d.cap_maps, (int64_t)L.maps.size(), 0, "tensor maps")))
         return st;
+    return SIDWT_OK;
+}
+
+// Tensor maps of the layout's tensor-core entries (needs the object's
+// operand buffers, so after ensure_workspace).
+sidwt_status encode_layout_maps(const sidwt_ragged *r, RaggedLayout &L) {
+    const size_t mb = rtc::map_bytes();
+    L.maps.assign(L.recv.size() * 2 * mb, 0);
+    for (size_t e = 0; e < L.recv.size(); ++e) {
+        sidwt_status st = rtc::encode_maps(L.maps.data() + e * 2 * mb, r->tc_a + L.recv_a_off[e],
+                                           r->tc_b + L.recv[e].out_off, L.recv_shape[e]);
+        if (st) return st;
+    }
     return SIDWT_OK;
 }
 
@@ -457,19 +533,26 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
         }
     d.groups = g;
     d.nwork = (int)L.work.size();
+    d.n_tc_tiles = (int)L.tc_tiles.size();
+    d.n_recv = (int)L.recv.size();
     const size_t b1 = L.items.size() * sizeof(rg::Item), b2 = L.work.size() * sizeof(rg::Work);
     const size_t b3 = lift.size() * sizeof(RaggedLift), b4 = L.slot_item.size() * sizeof(int32_t);
+    const size_t b5 = L.tc_tiles.size() * sizeof(rtc::TcTile), b6 = L.recv.size() * sizeof(rtc::RecvEntry);
+    const size_t b7 = L.maps.size();
     cudaError_t e = cudaSuccess;
     if (sync) {
         if (b1) e = cudaMemcpy(d.items, L.items.data(), b1, cudaMemcpyHostToDevice);
         if (e == cudaSuccess && b2) e = cudaMemcpy(d.work, L.work.data(), b2, cudaMemcpyHostToDevice);
         if (e == cudaSuccess && b3) e = cudaMemcpy(d.lift, lift.data(), b3, cudaMemcpyHostToDevice);
         if (e == cudaSuccess && b4) e = cudaMemcpy(d.slot_item, L.slot_item.data(), b4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && b5) e = cudaMemcpy(d.tc_tiles, L.tc_tiles.data(), b5, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && b6) e = cudaMemcpy(d.recv, L.recv.data(), b6, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && b7) e = cudaMemcpy(d.maps, L.maps.data(), b7, cudaMemcpyHostToDevice);
         return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "ragged layout upload");
     }
     // asynchronous: through the object's pinned staging buffer (the previous
     // upload has been consumed once the stream reaches this point)
-    const size_t tot = b1 + b2 + b3 + b4 + 64;
+    const size_t tot = b1 + b2 + b3 + b4 + b5 + b6 + b7 + 7 * 16;
     if (tot > r->h_stage_bytes) {
         cudaStreamSynchronize(s);
         if (r->h_stage) cudaFreeHost(r->h_stage);
@@ -496,6 +579,9 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
     put(d.work, L.work.data(), b2);
     put(d.lift, lift.data(), b3);
     put(d.slot_item, L.slot_item.data(), b4);
+    put(d.tc_tiles, L.tc_tiles.data(), b5);
+    put(d.recv, L.recv.data(), b6);
+    put(d.maps, L.maps.data(), b7);
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "ragged layout upload");
 }
 
@@ -511,6 +597,7 @@ sidwt_status ensure_workspace(sidwt_ragged *r, const RaggedLayout &L) {
             return st;
         r->slot_cap = c0;
     }
+    if ((st = grow(&r->tc_b, &r->tc_b_cap, L.recv_elems, 0, "received tensor-core operands"))) return st;
     if (!r->counter && cudaMalloc(&r->counter, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         set_error("device allocation failed: work counter");
@@ -540,6 +627,12 @@ sidwt_status enqueue(sidwt_ragged *r, const DevLayout &d, int64_t slots, int64_t
     if (e == cudaSuccess) e = cudaMemsetAsync(r->counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_fail(e, "ragged memset");
     if (timed) cudaEventRecord(ev[1], s);
+    if (d.n_recv > 0) {
+        if ((st = rtc::launch_pack_recv(r->pyr, d.recv, d.n_recv, r->tc_b, s)) ||
+            (st = rtc::launch_corr(d.maps, d.tc_tiles, d.n_tc_tiles, r->keys, r->err, r->sms, s)))
+            return st;
+        nl += 2;
+    }
     if (d.nwork > 0) {
         rg::corr_ragged_kernel<<<r->sms * 2, rg::kT, 0, s>>>(d.items, d.work, d.nwork, r->counter, r->tree, r->pyr,
                                                               r->keys, nullptr);
@@ -699,6 +792,13 @@ sidwt_status sidwt_ragged_create(sidwt_ragged **out) {
         delete r;
         return pst;
     }
+    if (cudaMalloc(&r->err, sizeof(int32_t)) != cudaSuccess || cudaMemset(r->err, 0, sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(r->err);
+        delete r;
+        set_error("device allocation failed: error flag");
+        return SIDWT_ENOMEM;
+    }
     *out = r;
     return SIDWT_OK;
 }
@@ -713,7 +813,13 @@ sidwt_status sidwt_ragged_destroy(sidwt_ragged *r) {
         cudaFree(d->work);
         cudaFree(d->lift);
         cudaFree(d->slot_item);
+        cudaFree(d->tc_tiles);
+        cudaFree(d->recv);
+        cudaFree(d->maps);
     }
+    cudaFree(r->tc_a);
+    cudaFree(r->tc_b);
+    cudaFree(r->err);
     cudaFree(r->tree);
     cudaFree(r->xen);
     cudaFree(r->pyr);
@@ -780,7 +886,26 @@ sidwt_status sidwt_ragged_store_reference(sidwt_ragged *r, sidwt_filter f, int64
     p.tree_f = r->tree + r->tree_used;
     p.xen = r->xen + r->xen_used;
     if ((st = build_reference_tree(&p, x_dev, 0, reinterpret_cast<cudaStream_t>(stream)))) return st;
-    r->refs.push_back({(int)f, N, J, r->tree_used, r->xen_used});
+    RefInfo ri{(int)f, N, J, r->tree_used, r->xen_used, {}};
+    for (int j = 0; j < 16; ++j) ri.tc_off[j] = -1;
+    if (r->prec == SIDWT_PREC_BF16X3) {
+        // stored tensor-core operands of the scales whose bands are long enough
+        int64_t need = r->tc_a_used;
+        for (int j = 0; j <= J && j < 16; ++j) {
+            rtc::Shape sh;
+            if (!rtc::shape_for(N, J, j, &sh)) continue;
+            ri.tc_off[j] = need;
+            need += (sh.a_elems + 63) / 64 * 64;
+        }
+        if (need > r->tc_a_used) {
+            if (need > r->tc_a_cap) cudaDeviceSynchronize();
+            if ((st = grow(&r->tc_a, &r->tc_a_cap, need, r->tc_a_used, "stored tensor-core operands"))) return st;
+            if ((st = rtc::pack_stored(p.tree_f, N, J, ri.tc_off, r->tc_a, reinterpret_cast<cudaStream_t>(stream))))
+                return st;
+            r->tc_a_used = need;
+        }
+    }
+    r->refs.push_back(ri);
     r->tree_used += te;
     r->xen_used += xe;
     *ref_id_out = (int32_t)r->refs.size() - 1;
@@ -801,7 +926,7 @@ sidwt_status sidwt_ragged_correlate(sidwt_ragged *r, int64_t n_items, const int3
     RaggedLayout L;
     sidwt_status st = build_layout(r, n_items, ref_ids_host, y_offsets_host, y_elems, L);
     if (st) return st;
-    if ((st = ensure_workspace(r, L))) return st;
+    if ((st = ensure_workspace(r, L)) || (st = encode_layout_maps(r, L))) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if ((st = upload(r, r->dl, L, s, false))) return st;
     r->last_slots = L.slots;
@@ -822,7 +947,7 @@ sidwt_status sidwt_ragged_graph_create(sidwt_ragged *r, int64_t n_items, const i
     RaggedLayout L;
     sidwt_status st = build_layout(r, n_items, ref_ids_host, y_offsets_host, y_elems, L);
     if (st) return st;
-    if ((st = ensure_workspace(r, L))) return st;
+    if ((st = ensure_workspace(r, L)) || (st = encode_layout_maps(r, L))) return st;
     if ((st = upload(r, r->gl, L, nullptr, true))) return st;
     if (r->exec) cudaGraphExecDestroy(r->exec);
     if (r->graph) cudaGraphDestroy(r->graph);
@@ -1023,6 +1148,42 @@ sidwt_status sidwt_ragged_reset_references(sidwt_ragged *r) {
     r->refs.clear();
     r->tree_used = 0;
     r->xen_used = 0;
+    r->tc_a_used = 0;
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_ragged_set_precision(sidwt_ragged *r, sidwt_precision prec) {
+    if (!r) {
+        set_error("NULL argument");
+        return SIDWT_EINVAL;
+    }
+    if (prec == SIDWT_PREC_TF32X3) {
+        set_error("3xTF32 is not implemented for ragged batches");
+        return SIDWT_EUNSUPPORTED;
+    }
+    if (prec != SIDWT_PREC_FP32 && prec != SIDWT_PREC_BF16X3) {
+        set_error("unknown precision");
+        return SIDWT_EINVAL;
+    }
+    r->prec = (int)prec;
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_ragged_check(sidwt_ragged *r, sidwt_stream stream) {
+    if (!r) {
+        set_error("NULL argument");
+        return SIDWT_EINVAL;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int32_t h = 0;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, r->err, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(r->err, 0, sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "ragged check");
+    if (h & 2) {
+        set_error("a tensor-core CTA gave up on a bounded wait; results are incomplete");
+        return SIDWT_ETIMEOUT;
+    }
     return SIDWT_OK;
 }
 

@@ -1,0 +1,458 @@
+// Batch-of-one correlation on the tcgen05 tensor cores (bf16 hi+lo split,
+// three products, FP32 accumulation in TMEM) for ragged batches and the
+// serving loop, where every received pulse has its own stored signal.
+//
+// With one received band u per stored signal the product of eq. 20 / 20a is
+// a matrix-vector product per variant, R_v[p] = sum_k conj(w_v[(k+p) mod K'])
+// u[k].  It becomes a GEMM by moving part of the advance p into the rows:
+// with p = S i - n (0 <= n < S) and k -> k + n,
+//     R_v[S i - n] = sum_k conj(w_v[k + S i]) u[k + n],
+// so row (v, i) of the stored operand is variant v advanced by S i, column n
+// of the received operand is u advanced by n, and every row shares the one
+// received operand.  The rows of all 2^lev variants (ceil(K'/S) each, padded
+// to groups of 8) fill the 128-row tiles; a tile has S columns.
+//
+// Both operands are windows, never materialised as matrices:
+//   * stored rows: for each residue c of k mod 8 the polyphase sequence
+//     P_c[s] = w[(k0 + c + 8 s) mod K'] is cut into rows of S/8 samples, so
+//     that row r of a K-block starting at sample 8 kb is row i + (8 kb)/(S/8)
+//     of that reshaped array; a 5-D TMA box {8 samples, 8 rows, 16 chunks
+//     (residue x Re/Im), 1 variant, hi+lo} fills one 8-row group of the
+//     K-major A tile ([hi/lo][chunk][row][16 B], 4 KB per group);
+//   * received columns: the overlapping MN-major window of the batched kernel
+//     (8 shifted copies U_c[t] = u[t + c + k0], planes Re, Im, -Re).
+// Band lengths that are a multiple of 64 use the circular form (k0 = 0, the
+// received copies wrap).  Other lengths use the equivalent linear form: the
+// received band is zero outside [0, K'), the contraction runs over
+// k in [-S, ceil(K'/64) 64), and the stored rows stay periodic.
+//
+// Persistent grid, one CTA per SM, tiles in cost order strided over the
+// CTAs.  Roles (192 threads): warp 0 TMA producer (2-stage ring), warp 1
+// TMEM allocation and MMA issue, warps 2-5 epilogue (peak keys).  The
+// producer runs ahead into the next tile; the MMA warp starts a tile once
+// the epilogue has drained the accumulators.  Every wait is bounded.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "tc_common.cuh"
+
+namespace sidwt {
+namespace rtc {
+
+using namespace sidwt::tc;
+
+constexpr int kThreads = 192;
+constexpr int kGroupBytes = 4096;             // [hi/lo][16 chunks][8 rows][16 B]
+constexpr int kStageA = 16 * kGroupBytes;     // 65536
+constexpr int kMaxBRow = (256 + 64) * 2;      // 640 bytes per window row at S = 256
+constexpr int kStageB = 2 * 24 * kMaxBRow;    // 30720
+constexpr int kBRegion = 2 * kStageB;
+constexpr int kARegion = 2 * kStageA;
+constexpr int kBarOff = kBRegion + kARegion;  // 192512
+constexpr int kSmemBytes = 227 * 1024;
+constexpr int kTmemCols = 512;
+constexpr int64_t kMinBand = 512;             // shorter bands stay on the CUDA cores
+constexpr int64_t kMaxBand = int64_t(1) << 24;
+
+__device__ __forceinline__ void tma_load_5d(void *dst, const void *map, uint64_t *bar, int c0, int c1, int c2, int c3,
+                                            int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];" ::"r"(saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(saddr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d_g(void *dst, const void *map, uint64_t *bar, int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(saddr(bar))
+        : "memory");
+}
+
+// The tensor maps live in global memory and are rewritten between batches
+// by copies from the host: order those writes before the TMA unit reads the
+// descriptors (tensor-map proxy acquire).
+__device__ __forceinline__ void tensormap_acquire(const void *map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
+
+// Number of 8-row groups of tile t that hold rows of an existing variant.
+__device__ __forceinline__ int valid_groups(const TcTile &w) {
+    const int g0 = 16 * w.tile, total = w.nv * w.gv;
+    return max(0, min(16, total - g0));
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    corr_pair_tc_kernel(const CUtensorMap *__restrict__ maps, const TcTile *__restrict__ tiles, int ntiles,
+                        unsigned long long *__restrict__ keys, int32_t *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *sB = base;
+    unsigned char *sA = base + kBRegion;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + kBarOff);
+    uint64_t *full = bar, *empty = bar + 2, *accf = bar + 4, *tfree = bar + 5, *drain = bar + 6;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 8);
+    volatile int *sflag = reinterpret_cast<volatile int *>(tmem_slot + 4);  // [0] error, [1] issued, [2] consumed
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if ((int)blockIdx.x >= ntiles) return;  // uniform: before any barrier or TMEM use
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(accf, 1);
+        mbar_init(tfree, 128);
+        mbar_init(drain, 1);
+        sflag[0] = 0;
+        sflag[1] = 0;
+        sflag[2] = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;
+            for (int t = blockIdx.x; t < ntiles && !sflag[0]; t += gridDim.x) {
+                const TcTile w = tiles[t];
+                const CUtensorMap *mA = maps + 2 * (int64_t)w.map;
+                const CUtensorMap *mB = mA + 1;
+                const int Lr = w.S >> 3;
+                const int bRow = (w.S + 64) * 2;
+                const int ng = valid_groups(w);
+                tensormap_acquire(mA);
+                tensormap_acquire(mB);
+                const uint32_t tx = (uint32_t)(ng * kGroupBytes + 48 * bRow);
+                for (int b = 0; b < w.nb && !sflag[0]; ++b)
+                    for (int kb = 0; kb < w.nkb; ++kb) {
+                        const int s = it & 1;
+                        if (it >= 2 && !mbar_wait(&empty[s], ((it >> 1) - 1) & 1)) {
+                            sflag[0] = 1;
+                            break;
+                        }
+                        if (sflag[0]) break;
+                        mbar_expect_tx(&full[s], tx);
+                        unsigned char *stA = sA + s * kStageA;
+                        unsigned char *stB = sB + s * kStageB;
+                        const int col = (8 * kb) % Lr, rsh = (8 * kb) / Lr;
+                        for (int g = 0; g < ng; ++g) {
+                            const int G = 16 * w.tile + g;
+                            const int v = G / w.gv, i0 = 8 * (G % w.gv);
+                            tma_load_5d(stA + g * kGroupBytes, mA, &full[s], col, i0 + rsh, 0, v, 2 * b);
+                        }
+                        tma_load_3d_g(stB, mB, &full[s], 0, 8 * kb, (2 * b) * 24);
+                        tma_load_3d_g(stB + 24 * bRow, mB, &full[s], 0, 8 * kb, (2 * b + 1) * 24);
+                        ++it;
+                    }
+            }
+            sflag[1] = it;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int it = 0, tc = 0;
+            for (int t = blockIdx.x; t < ntiles && !sflag[0]; t += gridDim.x, ++tc) {
+                const TcTile w = tiles[t];
+                if (tc > 0) {
+                    if (!mbar_wait(tfree, (tc - 1) & 1)) {
+                        sflag[0] = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                }
+                const uint32_t idesc = idesc_bf16(128, w.S);
+                const uint32_t bRow = (uint32_t)(w.S + 64) * 2;
+                bool first = true;
+                for (int b = 0; b < w.nb && !sflag[0]; ++b)
+                    for (int kb = 0; kb < w.nkb; ++kb) {
+                        const int s = it & 1;
+                        if (!mbar_wait(&full[s], (it >> 1) & 1)) {
+                            sflag[0] = 1;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t aHi = saddr(sA + s * kStageA), aLo = aHi + 2048;
+                        const uint32_t bHi = saddr(sB + s * kStageB), bLo = bHi + 24 * bRow;
+#pragma unroll 1
+                        for (int c = 0; c < 8; ++c) {
+                            // A: chunks (c, Re) and (c, Im) 128 B apart along K; 8-row groups 4 KB apart
+                            const uint64_t ah = sdesc(aHi + c * 256, 128, kGroupBytes);
+                            const uint64_t al = sdesc(aLo + c * 256, 128, kGroupBytes);
+#pragma unroll
+                            for (int acc = 0; acc < 2; ++acc) {
+                                // window rows c*3 + {0: Re u, 1: Im u, 2: -Re u}; Re uses (Re u, Im u),
+                                // Im uses (Im u, -Re u): next plane one row (bRow) further along K
+                                const uint32_t row = c * 3 + acc;
+                                const uint64_t bh = sdesc(bHi + row * bRow, bRow, 16);
+                                const uint64_t bl = sdesc(bLo + row * bRow, bRow, 16);
+                                const uint32_t d = tmem + acc * 256;
+                                mma_bf16(d, ah, bh, idesc, first ? 0u : 1u);
+                                mma_bf16(d, ah, bl, idesc, 1u);
+                                mma_bf16(d, al, bh, idesc, 1u);
+                            }
+                            first = false;
+                        }
+                        mma_commit(&empty[s]);
+                        ++it;
+                    }
+                if (sflag[0]) break;
+                mma_commit(accf);  // arrives once every MMA of this tile has completed
+            }
+            sflag[2] = it;
+            mma_commit(drain);  // every MMA issued by this CTA has completed
+            if (!mbar_wait(drain, 0)) sflag[0] = 1;
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = tile rows
+        const int q4 = warp & 3;
+        const int m = q4 * 32 + lane;
+        int tc = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tc) {
+            const TcTile w = tiles[t];
+            const bool ok = mbar_wait(accf, tc & 1);
+            tc_fence_after();
+            if (!__all_sync(0xffffffffu, ok && !sflag[0])) {  // warp-uniform before the aligned TMEM loads
+                sflag[0] = 1;
+                break;
+            }
+            const int G = 16 * w.tile + (m >> 3);
+            const int v = G / w.gv;
+            const int i = 8 * (G % w.gv) + (m & 7);
+            const bool valid = v < w.nv;
+            const int Kp = w.Kp;
+            // advance of column n: p = S i - n (mod K'); delay q = -p mod K'
+            int pm = (int)(((int64_t)w.S * i) % Kp);
+            unsigned long long best = 0ull;
+            const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
+            for (int c0 = 0; c0 < w.S; c0 += 32) {
+                uint32_t re[32], im[32];
+                TMEM_LD32(tl + c0, re);
+                TMEM_LD32(tl + 256 + c0, im);
+                tmem_wait_ld();
+#pragma unroll
+                for (int n = 0; n < 32; ++n) {
+                    const float xr = __uint_as_float(re[n]), xi = __uint_as_float(im[n]);
+                    const float m2 = xr * xr + xi * xi;
+                    const int q = pm == 0 ? 0 : Kp - pm;
+                    const uint32_t D = ((uint32_t)q << w.lev) + (uint32_t)v;
+                    const unsigned long long key =
+                        ((unsigned long long)__float_as_uint(m2) << 32) | (unsigned long long)(0xFFFFFFFFu - D);
+                    best = key > best ? key : best;
+                    pm = pm == 0 ? Kp - 1 : pm - 1;
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(tfree);
+            if (valid && best) atomicMax(&keys[w.slot], best);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 0 && sflag[0]) {
+        // let this CTA's own copies land before its shared memory is released
+        for (int k = sflag[2]; k < sflag[1]; ++k) mbar_wait(&full[k & 1], (k >> 1) & 1);
+        atomicOr(err, 2);
+    }
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---------------------------------------------------------------------------
+// Operand packing
+// ---------------------------------------------------------------------------
+struct StoreScale {
+    int64_t out_off;   // element offset in the stored-operand buffer
+    int64_t first;     // first flat index of this scale in the launch
+    int64_t count;     // elements of this scale
+    int64_t level_off; // 2 N (lev - 1): level lev in the SIDWT tree
+    int32_t Kp, nv, row, k0;  // row = Rs * Lr samples per (band, hi/lo, variant, chunk)
+};
+struct StoreScales {
+    StoreScale s[16];
+    int n;
+};
+
+// Stored operand of one signal: element [(2 b + h)][v][2 c + plane][s] =
+// hi or lo part of plane(w_{v,b}[(k0 + c + 8 s) mod K']), plane 0 Re, 1 Im.
+__global__ void pack_stored_kernel(const float2 *__restrict__ tree, int64_t N, StoreScales sc, int64_t total,
+                                   __nv_bfloat16 *__restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int k = 0;
+        while (k + 1 < sc.n && e >= sc.s[k + 1].first) ++k;
+        const StoreScale &z = sc.s[k];
+        const int64_t local = e - z.first;
+        const int64_t s = local % z.row;
+        int64_t rest = local / z.row;
+        const int ch = (int)(rest % 16);
+        rest /= 16;
+        const int v = (int)(rest % z.nv);
+        const int bh = (int)(rest / z.nv);
+        const int h = bh & 1, b = bh >> 1;
+        const int c = ch >> 1, plane = ch & 1;
+        int64_t idx = ((int64_t)z.k0 + c + 8 * s) % z.Kp;
+        if (idx < 0) idx += z.Kp;
+        const float2 x = tree[z.level_off + (int64_t)b * N + (int64_t)v * z.Kp + idx];
+        __nv_bfloat16 hi, lo;
+        split_bf16(plane ? x.y : x.x, hi, lo);
+        out[z.out_off + local] = h ? lo : hi;
+    }
+}
+
+// Received windows of one (pulse, scale): row ((2 b + h) 8 + c) 3 + plane
+// holds Lc samples U_c[t] = plane(u_b[t + c + k0]), plane 0 Re, 1 Im, 2 -Re,
+// u_b periodic (k0 = 0) or zero outside [0, K') (k0 < 0); hi or lo part.
+// Block (entry, residue c).
+__global__ void __launch_bounds__(256) pack_recv_kernel(const float2 *__restrict__ pyr, const RecvEntry *__restrict__ ent,
+                                                        __nv_bfloat16 *__restrict__ out) {
+    const RecvEntry e = ent[blockIdx.x];
+    const int c = blockIdx.y;
+    const int Kp = e.Kp;
+    for (int b = 0; b < e.nb; ++b) {
+        const float2 *u = pyr + e.pyr_off + 2 * (int64_t)e.N - 4 * (int64_t)Kp + (int64_t)b * Kp;
+        __nv_bfloat16 *hi_row = out + e.out_off + (int64_t)(((2 * b) * 8 + c) * 3) * e.Lc;
+        __nv_bfloat16 *lo_row = out + e.out_off + (int64_t)(((2 * b + 1) * 8 + c) * 3) * e.Lc;
+        for (int t = threadIdx.x; t < e.Lc; t += blockDim.x) {
+            int idx = t + c + e.k0;
+            float2 x = make_float2(0.f, 0.f);
+            if (e.k0 == 0) {
+                if (idx >= Kp) idx -= Kp;
+                x = u[idx];
+            } else if (idx >= 0 && idx < Kp) {
+                x = u[idx];
+            }
+            __nv_bfloat16 h0, l0, h1, l1, h2, l2;
+            split_bf16(x.x, h0, l0);
+            split_bf16(x.y, h1, l1);
+            split_bf16(-x.x, h2, l2);
+            hi_row[t] = h0;
+            hi_row[e.Lc + t] = h1;
+            hi_row[2 * (int64_t)e.Lc + t] = h2;
+            lo_row[t] = l0;
+            lo_row[e.Lc + t] = l1;
+            lo_row[2 * (int64_t)e.Lc + t] = l2;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static void fill_shape(int64_t N, int J, int j, int S, Shape *sh) {
+    sh->j = j;
+    sh->lev = j < J ? j + 1 : J;
+    sh->nb = j < J ? 2 : 1;
+    sh->nv = 1 << sh->lev;
+    sh->Kp = N >> sh->lev;
+    sh->S = S;
+    sh->Lr = S / 8;
+    const bool circ = sh->Kp % 64 == 0;
+    sh->k0 = circ ? 0 : -S;
+    sh->nkb = circ ? (int)(sh->Kp / 64) : (int)(((sh->Kp + 63) / 64 * 64 + S) / 64);
+    const int64_t rpv = (sh->Kp + S - 1) / S;
+    sh->gv = (int)((rpv + 7) / 8);
+    const int64_t groups = (int64_t)sh->nv * sh->gv;
+    sh->tiles = (int)((groups + 15) / 16);
+    sh->Rs = sh->gv * 8 + (8 * sh->nkb + sh->Lr - 1) / sh->Lr;
+    sh->a_elems = (int64_t)2 * sh->nb * sh->nv * 16 * sh->Rs * sh->Lr;
+    sh->Lc = (int64_t)64 * sh->nkb + S;
+    sh->b_elems = (int64_t)48 * sh->nb * sh->Lc;
+}
+
+// Tensor-core shape of scale j, or false when the band is too short (it
+// stays on the CUDA cores).  S minimises the padded MMA work, weighted by
+// the narrower tile's lower throughput per flop.
+bool shape_for(int64_t N, int J, int j, Shape *sh) {
+    const int lev = j < J ? j + 1 : J;
+    const int64_t Kp = N >> lev;
+    if (Kp < kMinBand || Kp > kMaxBand) return false;
+    double best = 1e300;
+    for (int S : {256, 128}) {
+        Shape t;
+        fill_shape(N, J, j, S, &t);
+        const double cost = (double)t.tiles * S * t.nkb * (S == 256 ? 1.0 : 1.25);
+        if (cost < best) {
+            best = cost;
+            *sh = t;
+        }
+    }
+    return true;
+}
+
+sidwt_status pack_stored(const float2 *tree, int64_t N, int J, const int64_t *a_off, void *abuf, cudaStream_t s) {
+    StoreScales sc;
+    std::memset(&sc, 0, sizeof(sc));
+    int64_t total = 0;
+    for (int j = 0; j <= J && j < 16; ++j) {
+        Shape sh;
+        if (a_off[j] < 0 || !shape_for(N, J, j, &sh)) continue;
+        StoreScale &z = sc.s[sc.n++];
+        z.out_off = a_off[j];
+        z.first = total;
+        z.count = sh.a_elems;
+        z.level_off = 2 * N * (int64_t)(sh.lev - 1);
+        z.Kp = (int32_t)sh.Kp;
+        z.nv = sh.nv;
+        z.row = sh.Rs * sh.Lr;
+        z.k0 = sh.k0;
+        total += sh.a_elems;
+    }
+    if (total == 0) return SIDWT_OK;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
+    pack_stored_kernel<<<(unsigned)blocks, 256, 0, s>>>(tree, N, sc, total, static_cast<__nv_bfloat16 *>(abuf));
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "stored tensor-core operand packing");
+}
+
+size_t map_bytes() { return sizeof(CUtensorMap); }
+
+sidwt_status encode_maps(void *two_maps, const void *a_base, const void *b_base, const Shape &sh) {
+    CUtensorMap *m = static_cast<CUtensorMap *>(two_maps);
+    const uint64_t lr2 = (uint64_t)sh.Lr * 2;
+    const uint64_t da[5] = {(uint64_t)sh.Lr, (uint64_t)sh.Rs, 16, (uint64_t)sh.nv, (uint64_t)(2 * sh.nb)};
+    const uint64_t sa[4] = {lr2, lr2 * sh.Rs, lr2 * sh.Rs * 16, lr2 * sh.Rs * 16 * sh.nv};
+    const uint32_t ba[5] = {8, 8, 16, 1, 2};
+    sidwt_status st = encode_nd(&m[0], const_cast<void *>(a_base), 5, da, sa, ba);
+    if (st) return st;
+    const uint64_t db[3] = {8, (uint64_t)sh.Lc / 8, (uint64_t)(48 * sh.nb)};
+    const uint64_t sb[2] = {16, (uint64_t)sh.Lc * 2};
+    const uint32_t bb[3] = {8, (uint32_t)(sh.S / 8 + 8), 24};
+    return encode_nd(&m[1], const_cast<void *>(b_base), 3, db, sb, bb);
+}
+
+sidwt_status launch_pack_recv(const float2 *pyr, const RecvEntry *e, int n, void *out, cudaStream_t s) {
+    if (n <= 0) return SIDWT_OK;
+    pack_recv_kernel<<<dim3((unsigned)n, 8), 256, 0, s>>>(pyr, e, static_cast<__nv_bfloat16 *>(out));
+    cudaError_t er = cudaGetLastError();
+    return er == cudaSuccess ? SIDWT_OK : cuda_fail(er, "received tensor-core operand packing");
+}
+
+sidwt_status launch_corr(const void *maps, const TcTile *tiles, int ntiles, unsigned long long *keys, int32_t *err,
+                         int sms, cudaStream_t s) {
+    if (ntiles <= 0) return SIDWT_OK;
+    const int grid = std::min(sms, ntiles);
+    corr_pair_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(static_cast<const CUtensorMap *>(maps), tiles, ntiles, keys,
+                                                            err);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "tensor-core pair correlation launch");
+}
+
+cudaError_t prepare_kernels() {
+    return cudaFuncSetAttribute(corr_pair_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+}
+
+}  // namespace rtc
+}  // namespace sidwt

@@ -226,4 +226,51 @@ int tc_launch_count(const sidwt_plan *p);
 void free_tc(sidwt_plan *p);
 sidwt_status finalize_peaks(sidwt_plan *p, int64_t B, cudaStream_t s);
 
+// ---- ragged_tc.cu: batch-of-one pairs on the tensor cores ----
+namespace rtc {
+
+// Operand geometry of one (pulse length N, depth J, scale j) on the
+// tensor cores.  Rows of the GEMM are (variant v, shift block i) of the
+// stored side, columns S consecutive advances; see ragged_tc.cu.
+struct Shape {
+    int j, lev, nb, nv;
+    int64_t Kp;   // band length K'
+    int S;        // advances per tile column block (MMA N) and per row
+    int Lr;       // S / 8: polyphase samples per stored row
+    int k0;       // first contraction index: 0 (circular, K' % 64 == 0) or -S (zero-padded)
+    int nkb;      // K-blocks of 64 per band
+    int gv;       // 8-row groups per variant
+    int Rs;       // stored rows of Lr samples per (band, hi/lo, variant, chunk)
+    int tiles;    // 128-row tiles of this (pair, scale)
+    int64_t a_elems;  // stored operand, bf16 elements
+    int64_t Lc;       // received window row length
+    int64_t b_elems;  // received operand, bf16 elements
+};
+
+struct TcTile {
+    int32_t map;   // maps[2 map]: stored operand, maps[2 map + 1]: received window
+    int32_t tile;  // first 8-row group = 16 tile
+    int32_t nkb, Kp, gv, nv;
+    int16_t nb, lev, S, pad;
+    int64_t slot;  // peak key of this (pair, scale)
+};
+
+struct RecvEntry {
+    int64_t pyr_off;  // received pyramid of the pulse (float2 elements)
+    int64_t out_off;  // received window rows (bf16 elements)
+    int32_t N, Kp, lev, nb, Lc, k0;
+};
+
+bool shape_for(int64_t N, int J, int j, Shape *sh);
+// Stored operand of every tensor-core scale of one signal whose SIDWT tree
+// starts at tree; a_off[j] = element offset in abuf (-1: scale not packed).
+sidwt_status pack_stored(const float2 *tree, int64_t N, int J, const int64_t *a_off, void *abuf, cudaStream_t s);
+sidwt_status encode_maps(void *two_maps, const void *a_base, const void *b_base, const Shape &sh);
+size_t map_bytes();
+sidwt_status launch_pack_recv(const float2 *pyr, const RecvEntry *e, int n, void *out, cudaStream_t s);
+sidwt_status launch_corr(const void *maps, const TcTile *tiles, int ntiles, unsigned long long *keys, int32_t *err,
+                         int sms, cudaStream_t s);
+cudaError_t prepare_kernels();
+
+}  // namespace rtc
 }  // namespace sidwt

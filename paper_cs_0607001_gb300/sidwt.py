@@ -102,6 +102,8 @@ def lib():
     L.sidwt_ragged_set_timing.argtypes = [_vp, ctypes.c_int]
     L.sidwt_ragged_read_timing.argtypes = [_vp, ctypes.POINTER(Timing), ctypes.c_int]
     L.sidwt_ragged_reset_references.argtypes = [_vp]
+    L.sidwt_ragged_set_precision.argtypes = [_vp, ctypes.c_int]
+    L.sidwt_ragged_check.argtypes = [_vp, _vp]
     L.sidwt_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]
     L.sidwt_server_add_waveform.argtypes = [_vp, _vp, _i64, ctypes.POINTER(_i32)]
     L.sidwt_server_start.argtypes = [_vp]
@@ -345,6 +347,13 @@ class Ragged:
 
     def reserve(self, tree_elems: int, pyr_elems: int, slots: int):
         _raise(lib().sidwt_ragged_reserve(self._h, tree_elems, pyr_elems, slots))
+
+    def set_precision(self, precision):
+        """'fp32' (default) or 'bf16x3': applies to later stores and correlations."""
+        _raise(lib().sidwt_ragged_set_precision(self._h, _prec_id(precision)))
+
+    def check(self, stream=None):
+        _raise(lib().sidwt_ragged_check(self._h, _stream(stream)))
 
     def store_reference(self, filter, N: int, J: int, x: torch.Tensor, stream=None) -> int:
         if x.dtype != torch.complex64 or not x.is_cuda or x.numel() != N or not x.is_contiguous():

@@ -1,0 +1,132 @@
+"""GPU parity of ragged batches on the tensor cores (sidwt_ragged_set_precision
+with SIDWT_PREC_BF16X3): every pair is a batch of one, its scales with bands
+of at least 512 samples run as tcgen05 GEMMs whose rows are the stored
+variants advanced by multiples of S and whose columns are the received band
+advanced by 0..S-1 (circular form for bands that are a multiple of 64,
+zero-padded linear form otherwise); shorter bands stay on the CUDA cores.
+
+Error bound, stated a priori as for the batched tensor-core path: per (pair,
+scale) every |r_j[D]| is off by at most
+    (3 * 2^-16 + K_j 2^-24) * max_v ||w_v|| * ||u||
+(bf16 hi+lo split without the lo*lo term, FP32 accumulation over K_j terms,
+Cauchy-Schwarz over the band).  The padded terms of the linear form are
+exact zeros and add nothing."""
+import numpy as np
+import pytest
+import torch
+
+from tests import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+# (filter id, N, J): circular bands, zero-padded bands (N = 8000, 40000: band
+# lengths not multiples of 64), several tiles per scale, bands at the 512
+# threshold, bands below it (CUDA cores), tiny pulses
+SPECS = [(1, 2048, 3), (2, 8000, 3), (0, 24576, 4), (1, 40000, 5), (2, 32768, 6), (0, 512, 3), (2, 96, 5),
+         (1, 6144, 3), (0, 1024, 1), (2, 3000, 2)]
+
+
+def build_batch(seed):
+    g = np.random.default_rng(seed)
+    refs, ys, delays = [], [], []
+    for (f, N, J) in SPECS:
+        x = (g.standard_normal(N) + 1j * g.standard_normal(N)) / np.sqrt(2)
+        D = int(g.integers(0, N))
+        y = np.roll(x, D) + 0.3 * (g.standard_normal(N) + 1j * g.standard_normal(N))
+        refs.append(x.astype(np.complex64))
+        ys.append(y.astype(np.complex64))
+        delays.append(D)
+    offsets = np.concatenate([[0], np.cumsum([s[1] for s in SPECS])[:-1]]).astype(np.int64)
+    return refs, np.concatenate(ys), offsets, delays
+
+
+def stated_bounds(oracle, f, N, J, x, y):
+    tree, _ = oracle.tree_x(f, x.astype(np.complex128), J)
+    pyr, _ = oracle.pyramid_y(f, y.astype(np.complex128), J)
+    out = []
+    for j in range(J + 1):
+        lev = j + 1 if j < J else J
+        Kp = N >> lev
+        base = 2 * N * (lev - 1)
+        A = tree[base:base + N].reshape(1 << lev, Kp)
+        Bb = tree[base + N:base + 2 * N].reshape(1 << lev, Kp)
+        off = 2 * N - 4 * Kp
+        if j < J:
+            wn = np.sqrt((np.abs(A) ** 2).sum(1) + (np.abs(Bb) ** 2).sum(1)).max()
+            un = np.linalg.norm(pyr[off:off + 2 * Kp])
+            Kj = 2 * Kp
+        else:
+            wn = np.sqrt((np.abs(A) ** 2).sum(1)).max()
+            un = np.linalg.norm(pyr[off:off + Kp])
+            Kj = Kp
+        out.append((3 * 2.0 ** -16 + Kj * 2.0 ** -24) * wn * un)
+    return np.array(out)
+
+
+def run(precision, refs, ypack, offsets, graph=False):
+    from paper_cs_0607001_gb300 import sidwt
+    with sidwt.Ragged() as rg:
+        rg.set_precision(precision)
+        ids = [rg.store_reference(f, N, J, U.to_dev_c64(x)) for (f, N, J), x in zip(SPECS, refs)]
+        yd = U.to_dev_c64(ypack)
+        n = rg.correlate(ids, offsets, yd)
+        lag, mag, norm = rg.peaks(n)
+        rg.check()
+        out = [lag.cpu().numpy(), mag.cpu().numpy(), norm.cpu().numpy()]
+        if graph:
+            rg.graph_create(ids, offsets, yd)
+            for _ in range(2):
+                n = rg.graph_launch()
+            lag2, mag2, norm2 = rg.peaks(n)
+            rg.check()
+            out += [lag2.cpu().numpy(), mag2.cpu().numpy()]
+        first, _ = rg.slots_of(ids)
+        torch.cuda.synchronize()
+    return first, out
+
+
+def test_ragged_bf16x3_matches_oracle_within_stated_bound(oracle):
+    refs, ypack, offsets, delays = build_batch(21)
+    first, (lag, mag, norm, lag_g, mag_g) = run("bf16x3", refs, ypack, offsets, graph=True)
+    np.testing.assert_array_equal(lag_g, lag)  # graph replay = direct call
+    np.testing.assert_array_equal(mag_g, mag)
+    Ns = [s[1] for s in SPECS]
+    Js = [s[2] for s in SPECS]
+    fs = [s[0] for s in SPECS]
+    lo, mo, no, used = oracle.correlate_mixed(fs, Ns, Js, np.concatenate(refs).astype(np.complex128),
+                                              ypack.astype(np.complex128), offsets)
+    for i, (f, N, J) in enumerate(SPECS):
+        sl = slice(first[i], first[i] + J + 1)
+        x = refs[i]
+        y = ypack[offsets[i]:offsets[i] + N]
+        bounds = stated_bounds(oracle, f, N, J, x, y)
+        r_or = oracle.correlate(f, x.astype(np.complex128), y.astype(np.complex128), J)
+        for j in range(J + 1):
+            g = int(lag[sl][j])
+            top = np.abs(r_or[j]).max()
+            rel = bounds[j] / top
+            U.check_peak_lags(lag[sl][j:j + 1], r_or[j:j + 1], rel, what=f"item {i} {SPECS[i]}")
+            assert abs(mag[sl][j] - np.abs(r_or[j][g])) <= bounds[j], (i, j, mag[sl][j], np.abs(r_or[j][g]), bounds[j])
+            if g == lo[first[i] + j]:
+                assert abs(norm[sl][j] - no[first[i] + j]) <= 2 * rel * no[first[i] + j] + 1e-6
+        assert lag[sl][0] == delays[i]
+
+
+def test_ragged_bf16x3_agrees_with_fp32_path():
+    refs, ypack, offsets, _ = build_batch(22)
+    _, (lag16, mag16, _) = run("bf16x3", refs, ypack, offsets)
+    _, (lag32, mag32, _) = run("fp32", refs, ypack, offsets)
+    assert np.mean(lag16 == lag32) > 0.95
+    same = lag16 == lag32
+    np.testing.assert_allclose(mag16[same], mag32[same], rtol=1e-3)
+
+
+def test_ragged_precision_arguments():
+    from paper_cs_0607001_gb300 import sidwt
+    with sidwt.Ragged() as rg:
+        with pytest.raises(sidwt.SidwtError, match="EUNSUPPORTED"):
+            rg.set_precision("tf32x3")
+        with pytest.raises(sidwt.SidwtError, match="EINVAL"):
+            rg.set_precision(7)
+        rg.set_precision("bf16x3")
+        rg.check()
