@@ -644,7 +644,7 @@ def run_serve_workload(args):
         y = inputs.echo(x, np.array([D]), np.array([float(g.uniform(0, 20))]), g)[0]
         pool.append((w, int(g.integers(0, 3)), N, J, torch.from_numpy(y.astype(np.complex64)).pin_memory(), D))
     srv = S.Server(lanes=args.lanes, max_batch=64, max_j=10, memory_cap_bytes=40 << 30,
-                   max_lane_samples=16 << 20)
+                   max_lane_samples=16 << 20, precision=args.precision)
     for w in waves:
         srv.add_waveform(w)
     srv.start()
@@ -685,10 +685,11 @@ def run_serve_workload(args):
     line = {
         "metric": METRIC, "value": best["gsamples_s"], "unit": UNIT, "n_gpus": 1, "steps": len(rates),
         "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
+        "dtype": "bf16x3" if args.precision == "bf16x3" else "f32", "data": "synthetic",
         "config": {"workload": "serving loop: 256 resident waveforms, Poisson requests of N log-uniform 512-262144 "
                                "(multiples of 2^J), J 3-10, mixed filters; 40 GB cap",
-                   "lanes": args.lanes, "pool": len(pool), "mean_flops_per_request": mean_flops},
+                   "lanes": args.lanes, "pool": len(pool), "mean_flops_per_request": mean_flops,
+                   "precision": args.precision},
         "latency_ms": {"p50": best["p50_ms"], "p99": best["p99_ms"], "what": "submit to completion, best rate"},
         "per_rate": per_rate,
         "peak_at_injected_delay_scale0": float(np.mean(hits)) if hits else None,
@@ -708,7 +709,7 @@ def main():
     ap.add_argument("--pulses", type=int, default=4096)
     ap.add_argument("--items", type=int, default=10000)
     ap.add_argument("--workload", default="two_ref", choices=["two_ref", "ragged", "single", "serve"])
-    ap.add_argument("--rates", default="50,100,200,400,800,1000")
+    ap.add_argument("--rates", default="250,500,1000,2000,4000,8000")
     ap.add_argument("--seconds", type=float, default=2.0)
     ap.add_argument("--lanes", type=int, default=4)
     ap.add_argument("--pool", type=int, default=256)

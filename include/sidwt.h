@@ -316,6 +316,9 @@ typedef struct {
     int32_t max_j;            /* largest J a request may use (<= 15)               */
     int64_t memory_cap_bytes; /* admission cap over all in-flight batches          */
     int64_t max_lane_samples; /* sum of N one lane can hold (buffers pre-reserved) */
+    int32_t precision;        /* SIDWT_PREC_FP32 or SIDWT_PREC_BF16X3 (the tensor-core
+                                 batch-of-one path of sidwt_ragged_set_precision; the
+                                 footprint then also counts its packed operands)     */
 } sidwt_server_config;
 
 typedef struct {

@@ -767,6 +767,12 @@ sidwt_status correlate_small(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t 
 
 }  // namespace sidwt
 
+sidwt_status sidwt::ragged_reserve_tc(sidwt_ragged *r, int64_t stored_elems, int64_t received_elems) {
+    sidwt_status st;
+    if ((st = grow(&r->tc_a, &r->tc_a_cap, stored_elems, r->tc_a_used, "stored tensor-core operands"))) return st;
+    return grow(&r->tc_b, &r->tc_b_cap, received_elems, 0, "received tensor-core operands");
+}
+
 extern "C" {
 
 sidwt_status sidwt_ragged_create(sidwt_ragged **out) {

@@ -392,6 +392,18 @@ bool shape_for(int64_t N, int J, int j, Shape *sh) {
     return true;
 }
 
+void operand_elems(int64_t N, int J, int64_t *stored, int64_t *received) {
+    int64_t a = 0, b = 0;
+    for (int j = 0; j <= J && j < 16; ++j) {
+        Shape sh;
+        if (!shape_for(N, J, j, &sh)) continue;
+        a += (sh.a_elems + 63) / 64 * 64;
+        b += (sh.b_elems + 63) / 64 * 64;
+    }
+    *stored = a;
+    *received = b;
+}
+
 sidwt_status pack_stored(const float2 *tree, int64_t N, int J, const int64_t *a_off, void *abuf, cudaStream_t s) {
     StoreScales sc;
     std::memset(&sc, 0, sizeof(sc));

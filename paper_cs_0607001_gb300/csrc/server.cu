@@ -47,9 +47,15 @@ struct Request {
     std::vector<double> norm;
 };
 
-int64_t footprint(int64_t N, int J) {
+int64_t footprint(int64_t N, int J, int precision) {
     // pulse, padded reference, SIDWT tree, pyramid, peak slots
-    return 8 * N + 8 * N + 16 * (int64_t)J * N + 16 * N + 64 * (J + 1);
+    int64_t b = 8 * N + 8 * N + 16 * (int64_t)J * N + 16 * N + 64 * (J + 1);
+    if (precision == SIDWT_PREC_BF16X3) {  // packed tensor-core operands (bf16)
+        int64_t a = 0, r = 0;
+        rtc::operand_elems(N, J, &a, &r);
+        b += 2 * (a + r);
+    }
+    return b;
 }
 
 __global__ void pad_kernel(const float2 *__restrict__ wave, int64_t wlen, float2 *__restrict__ x, int64_t N) {
@@ -194,7 +200,7 @@ void serve(sidwt_server *s) {
                 int64_t bytes = 0, samples = 0, slots = 0;
                 while (!s->queue.empty() && (int64_t)L.batch.size() < s->cfg.max_batch) {
                     Request *r = s->queue.front();
-                    const int64_t fb = footprint(r->N, r->J);
+                    const int64_t fb = footprint(r->N, r->J, s->cfg.precision);
                     if (fb > lane_budget || r->N > L.cap_samples || r->J + 1 > L.cap_slots) {
                         // can never fit a lane: reject
                         s->queue.pop_front();
@@ -251,7 +257,8 @@ extern "C" {
 
 sidwt_status sidwt_server_create(const sidwt_server_config *cfg, sidwt_server **out) {
     if (!cfg || !out || cfg->lanes < 1 || cfg->lanes > 64 || cfg->memory_cap_bytes <= 0 || cfg->max_batch < 1 ||
-        cfg->max_lane_samples < 2 || cfg->max_j < 1 || cfg->max_j > 15) {
+        cfg->max_lane_samples < 2 || cfg->max_j < 1 || cfg->max_j > 15 ||
+        (cfg->precision != SIDWT_PREC_FP32 && cfg->precision != SIDWT_PREC_BF16X3)) {
         set_error("bad server configuration");
         return SIDWT_EINVAL;
     }
@@ -268,6 +275,12 @@ sidwt_status sidwt_server_create(const sidwt_server_config *cfg, sidwt_server **
     for (Lane &L : s->lanes) {
         sidwt_status st = sidwt_ragged_create(&L.rg);
         if (!st) st = sidwt_ragged_reserve(L.rg, 2 * (int64_t)cfg->max_j * cap, 2 * cap, slots);
+        if (!st) st = sidwt_ragged_set_precision(L.rg, (sidwt_precision)cfg->precision);
+        if (!st && cfg->precision == SIDWT_PREC_BF16X3) {
+            int64_t a = 0, r = 0;
+            rtc::operand_elems(cap - cap % (int64_t(1) << cfg->max_j), cfg->max_j, &a, &r);
+            st = ragged_reserve_tc(L.rg, a + a / 2, r + r / 2);
+        }
         if (st || cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess ||
             cudaMalloc(&L.y, cap * sizeof(float2)) != cudaSuccess || cudaMalloc(&L.x, cap * sizeof(float2)) != cudaSuccess ||

@@ -262,6 +262,9 @@ struct RecvEntry {
 };
 
 bool shape_for(int64_t N, int J, int j, Shape *sh);
+// Tensor-core operand elements (bf16) of one (N, J) pulse: stored side and
+// received side, each rounded up per scale as the ragged object lays them out.
+void operand_elems(int64_t N, int J, int64_t *stored, int64_t *received);
 // Stored operand of every tensor-core scale of one signal whose SIDWT tree
 // starts at tree; a_off[j] = element offset in abuf (-1: scale not packed).
 sidwt_status pack_stored(const float2 *tree, int64_t N, int J, const int64_t *a_off, void *abuf, cudaStream_t s);
@@ -273,4 +276,7 @@ sidwt_status launch_corr(const void *maps, const TcTile *tiles, int ntiles, unsi
 cudaError_t prepare_kernels();
 
 }  // namespace rtc
+
+// ---- ragged.cu: pre-size a ragged object's tensor-core operand buffers ----
+sidwt_status ragged_reserve_tc(sidwt_ragged *r, int64_t stored_elems, int64_t received_elems);
 }  // namespace sidwt

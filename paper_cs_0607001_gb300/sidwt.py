@@ -36,7 +36,8 @@ class Timing(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("max_j", ctypes.c_int32),
-                ("memory_cap_bytes", ctypes.c_int64), ("max_lane_samples", ctypes.c_int64)]
+                ("memory_cap_bytes", ctypes.c_int64), ("max_lane_samples", ctypes.c_int64),
+                ("precision", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -433,8 +434,9 @@ class Ragged:
 class Server:
     """Continuous-batching request loop (sidwt_server_*)."""
 
-    def __init__(self, lanes=4, max_batch=64, max_j=10, memory_cap_bytes=40 << 30, max_lane_samples=1 << 22):
-        cfg = ServerConfig(lanes, max_batch, max_j, memory_cap_bytes, max_lane_samples)
+    def __init__(self, lanes=4, max_batch=64, max_j=10, memory_cap_bytes=40 << 30, max_lane_samples=1 << 22,
+                 precision="fp32"):
+        cfg = ServerConfig(lanes, max_batch, max_j, memory_cap_bytes, max_lane_samples, _prec_id(precision))
         h = _vp()
         _raise(lib().sidwt_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

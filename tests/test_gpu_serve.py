@@ -41,16 +41,17 @@ def waveforms():
 
 def new_server(**kw):
     from paper_cs_0607001_gb300 import sidwt
-    cfg = dict(lanes=3, max_batch=8, max_j=8, memory_cap_bytes=256 << 20, max_lane_samples=1 << 16)
+    cfg = dict(lanes=3, max_batch=8, max_j=8, memory_cap_bytes=512 << 20, max_lane_samples=1 << 16)
     cfg.update(kw)
     srv = sidwt.Server(**cfg)
     return srv
 
 
-def test_results_alone_equal_results_in_the_mix(oracle):
+@pytest.mark.parametrize("precision,rtol", [("fp32", 2e-5), ("bf16x3", 1e-4)])
+def test_results_alone_equal_results_in_the_mix(oracle, precision, rtol):
     waves = waveforms()
     reqs = make_requests(40, 11, waves)
-    with new_server() as srv:
+    with new_server(precision=precision) as srv:
         for w in waves:
             srv.add_waveform(w)
         srv.start()
@@ -74,7 +75,7 @@ def test_results_alone_equal_results_in_the_mix(oracle):
         lag, mag, norm, _, _ = oracle.correlate_batch(r["f"], r["x"][None].astype(np.complex128),
                                                       r["y"].numpy()[None].astype(np.complex128), r["J"])
         assert m[0][0] == r["D"] == lag[0, 0]
-        np.testing.assert_allclose(m[1], mag[0], rtol=2e-5)
+        np.testing.assert_allclose(m[1], mag[0], rtol=rtol)
 
 
 def test_oversized_request_is_rejected_and_others_served():
