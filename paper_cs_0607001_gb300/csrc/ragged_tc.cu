@@ -53,7 +53,9 @@ constexpr int kStageB = 2 * 24 * kMaxBRow;    // 30720
 constexpr int kBRegion = 2 * kStageB;
 constexpr int kARegion = 2 * kStageA;
 constexpr int kBarOff = kBRegion + kARegion;  // 192512
-constexpr int kSmemBytes = 227 * 1024;
+// what the kernel uses (rings, barriers, 1 KB alignment slack), so that a
+// CUDA-core CTA of the ragged kernel (about 20 KB) fits beside it on an SM
+constexpr int kSmemBytes = kBarOff + 128 + 1024;
 constexpr int kTmemCols = 512;
 constexpr int64_t kMinBand = 512;             // shorter bands stay on the CUDA cores
 constexpr int64_t kMaxBand = int64_t(1) << 24;
