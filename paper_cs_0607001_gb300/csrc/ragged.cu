@@ -307,10 +307,6 @@ struct sidwt_ragged {
     __nv_bfloat16 *tc_b = nullptr;
     int64_t tc_b_cap = 0;
     int32_t *err = nullptr;
-    // the CUDA-core tail of a mixed batch runs on a second stream, beside the
-    // tensor-core kernel (fork / join by events, capturable)
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double *xen = nullptr;
     int64_t xen_cap = 0, xen_used = 0;
     // batch workspace
@@ -632,25 +628,12 @@ sidwt_status enqueue(sidwt_ragged *r, const DevLayout &d, int64_t slots, int64_t
     if (e != cudaSuccess) return cuda_fail(e, "ragged memset");
     if (timed) cudaEventRecord(ev[1], s);
     if (d.n_recv > 0) {
-        // the CUDA-core part (short bands) beside the tensor-core kernel: one
-        // CTA per SM, which fits next to a tensor-core CTA
-        const bool fork = d.nwork > 0;
-        if (fork) {
-            e = cudaEventRecord(r->ev_fork, s);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(r->side, r->ev_fork, 0);
-            if (e != cudaSuccess) return cuda_fail(e, "fork");
-            rg::corr_ragged_kernel<<<r->sms, rg::kT, 0, r->side>>>(d.items, d.work, d.nwork, r->counter, r->tree,
-                                                                    r->pyr, r->keys, nullptr);
-            ++nl;
-            e = cudaEventRecord(r->ev_join, r->side);
-            if (e != cudaSuccess) return cuda_fail(e, "join");
-        }
         if ((st = rtc::launch_pack_recv(r->pyr, d.recv, d.n_recv, r->tc_b, s)) ||
             (st = rtc::launch_corr(d.maps, d.tc_tiles, d.n_tc_tiles, r->keys, r->err, r->sms, s)))
             return st;
         nl += 2;
-        if (fork && (e = cudaStreamWaitEvent(s, r->ev_join, 0)) != cudaSuccess) return cuda_fail(e, "join");
-    } else if (d.nwork > 0) {
+    }
+    if (d.nwork > 0) {
         rg::corr_ragged_kernel<<<r->sms * 2, rg::kT, 0, s>>>(d.items, d.work, d.nwork, r->counter, r->tree, r->pyr,
                                                               r->keys, nullptr);
         ++nl;
@@ -815,13 +798,10 @@ sidwt_status sidwt_ragged_create(sidwt_ragged **out) {
         delete r;
         return pst;
     }
-    if (cudaMalloc(&r->err, sizeof(int32_t)) != cudaSuccess || cudaMemset(r->err, 0, sizeof(int32_t)) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&r->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&r->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&r->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaMalloc(&r->err, sizeof(int32_t)) != cudaSuccess || cudaMemset(r->err, 0, sizeof(int32_t)) != cudaSuccess) {
         cudaGetLastError();
         sidwt_ragged_destroy(r);
-        set_error("device allocation failed: error flag, stream or events");
+        set_error("device allocation failed: error flag");
         return SIDWT_ENOMEM;
     }
     *out = r;
@@ -845,9 +825,6 @@ sidwt_status sidwt_ragged_destroy(sidwt_ragged *r) {
     cudaFree(r->tc_a);
     cudaFree(r->tc_b);
     cudaFree(r->err);
-    if (r->ev_fork) cudaEventDestroy(r->ev_fork);
-    if (r->ev_join) cudaEventDestroy(r->ev_join);
-    if (r->side) cudaStreamDestroy(r->side);
     cudaFree(r->tree);
     cudaFree(r->xen);
     cudaFree(r->pyr);

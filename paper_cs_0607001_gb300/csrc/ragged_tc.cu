@@ -57,7 +57,7 @@ constexpr int kBarOff = kBRegion + kARegion;  // 192512
 // CUDA-core CTA of the ragged kernel (about 20 KB) fits beside it on an SM
 constexpr int kSmemBytes = kBarOff + 128 + 1024;
 constexpr int kTmemCols = 512;
-constexpr int64_t kMinBand = 512;             // shorter bands stay on the CUDA cores
+constexpr int64_t kMinBand = 64;              // shorter bands stay on the CUDA cores
 constexpr int64_t kMaxBand = int64_t(1) << 24;
 
 __device__ __forceinline__ void tma_load_5d(void *dst, const void *map, uint64_t *bar, int c0, int c1, int c2, int c3,
@@ -331,8 +331,7 @@ __global__ void __launch_bounds__(256) pack_recv_kernel(const float2 *__restrict
             int idx = t + c + e.k0;
             float2 x = make_float2(0.f, 0.f);
             if (e.k0 == 0) {
-                if (idx >= Kp) idx -= Kp;
-                x = u[idx];
+                x = u[idx % Kp];  // the window may span several periods when K' < S + 8
             } else if (idx >= 0 && idx < Kp) {
                 x = u[idx];
             }
@@ -375,17 +374,17 @@ static void fill_shape(int64_t N, int J, int j, int S, Shape *sh) {
 }
 
 // Tensor-core shape of scale j, or false when the band is too short (it
-// stays on the CUDA cores).  S minimises the padded MMA work, weighted by
-// the narrower tile's lower throughput per flop.
+// stays on the CUDA cores).  S (256, 128 or 64) minimises the padded MMA
+// work, weighted by the narrower tiles' lower throughput per flop.
 bool shape_for(int64_t N, int J, int j, Shape *sh) {
     const int lev = j < J ? j + 1 : J;
     const int64_t Kp = N >> lev;
     if (Kp < kMinBand || Kp > kMaxBand) return false;
     double best = 1e300;
-    for (int S : {256, 128}) {
+    for (int S : {256, 128, 64}) {
         Shape t;
         fill_shape(N, J, j, S, &t);
-        const double cost = (double)t.tiles * S * t.nkb * (S == 256 ? 1.0 : 1.25);
+        const double cost = (double)t.tiles * S * t.nkb * (S == 256 ? 1.0 : (S == 128 ? 1.15 : 1.6));
         if (cost < best) {
             best = cost;
             *sh = t;

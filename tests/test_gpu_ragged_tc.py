@@ -1,6 +1,6 @@
 """GPU parity of ragged batches on the tensor cores (sidwt_ragged_set_precision
 with SIDWT_PREC_BF16X3): every pair is a batch of one, its scales with bands
-of at least 512 samples run as tcgen05 GEMMs whose rows are the stored
+of at least 64 samples run as tcgen05 GEMMs whose rows are the stored
 variants advanced by multiples of S and whose columns are the received band
 advanced by 0..S-1 (circular form for bands that are a multiple of 64,
 zero-padded linear form otherwise); shorter bands stay on the CUDA cores.
@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 # (filter id, N, J): circular bands, zero-padded bands (N = 8000, 40000: band
 # lengths not multiples of 64), several tiles per scale, bands at the 512
-# threshold, bands below it (CUDA cores), tiny pulses
+# threshold, bands below it (CUDA cores), tiny pulses; bands shorter than S
 SPECS = [(1, 2048, 3), (2, 8000, 3), (0, 24576, 4), (1, 40000, 5), (2, 32768, 6), (0, 512, 3), (2, 96, 5),
          (1, 6144, 3), (0, 1024, 1), (2, 3000, 2)]
 
