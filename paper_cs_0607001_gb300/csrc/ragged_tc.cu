@@ -85,6 +85,24 @@ __device__ __forceinline__ void tensormap_acquire(const void *map) {
                  : "memory");
 }
 
+// Wait on a phase that completes only after a whole tile's main loop: the
+// limit counts from the last K-block the MMA thread issued (*progress), so
+// that long tiles (and slowed-down runs under a profiler) do not trip it.
+__device__ __forceinline__ bool mbar_wait_progress(uint64_t *b, uint32_t parity, volatile int *progress) {
+    uint64_t t0 = now_ns();
+    int last = *progress;
+    while (!mbar_test(b, parity)) {
+        const int p = *progress;
+        if (p != last) {
+            last = p;
+            t0 = now_ns();
+        } else if (now_ns() - t0 > kWaitNs) {
+            return false;
+        }
+    }
+    return true;
+}
+
 // Number of 8-row groups of tile t that hold rows of an existing variant.
 __device__ __forceinline__ int valid_groups(const TcTile &w) {
     const int g0 = 16 * w.tile, total = w.nv * w.gv;
@@ -101,7 +119,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *bar = reinterpret_cast<uint64_t *>(base + kBarOff);
     uint64_t *full = bar, *empty = bar + 2, *accf = bar + 4, *tfree = bar + 5, *drain = bar + 6;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 8);
-    volatile int *sflag = reinterpret_cast<volatile int *>(tmem_slot + 4);  // [0] error, [1] issued, [2] consumed
+    // [0] error, [1] stages issued, [2] stages consumed, [3] K-blocks issued to the tensor cores so far
+    volatile int *sflag = reinterpret_cast<volatile int *>(tmem_slot + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if ((int)blockIdx.x >= ntiles) return;  // uniform: before any barrier or TMEM use
@@ -117,6 +136,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         sflag[0] = 0;
         sflag[1] = 0;
         sflag[2] = 0;
+        sflag[3] = 0;
         fence_barrier_init();
     }
     if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
@@ -208,6 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                         mma_commit(&empty[s]);
                         ++it;
+                        sflag[3] = it;
                     }
                 if (sflag[0]) break;
                 mma_commit(accf);  // arrives once every MMA of this tile has completed
@@ -223,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int tc = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tc) {
             const TcTile w = tiles[t];
-            const bool ok = mbar_wait(accf, tc & 1);
+            const bool ok = mbar_wait_progress(accf, tc & 1, &sflag[3]);
             tc_fence_after();
             if (!__all_sync(0xffffffffu, ok && !sflag[0])) {  // warp-uniform before the aligned TMEM loads
                 sflag[0] = 1;
@@ -317,34 +338,38 @@ __global__ void pack_stored_kernel(const float2 *__restrict__ tree, int64_t N, S
 // Received windows of one (pulse, scale): row ((2 b + h) 8 + c) 3 + plane
 // holds Lc samples U_c[t] = plane(u_b[t + c + k0]), plane 0 Re, 1 Im, 2 -Re,
 // u_b periodic (k0 = 0) or zero outside [0, K') (k0 < 0); hi or lo part.
-// Block (entry, residue c).
+// Block (entry, slice of t): all 8 residues of a slice, so that the band is
+// read from DRAM about once (the 8 shifted reads of a sample hit L1).
+constexpr int kRecvSlices = 8;
 __global__ void __launch_bounds__(256) pack_recv_kernel(const float2 *__restrict__ pyr, const RecvEntry *__restrict__ ent,
                                                         __nv_bfloat16 *__restrict__ out) {
     const RecvEntry e = ent[blockIdx.x];
-    const int c = blockIdx.y;
     const int Kp = e.Kp;
+    const int per = (e.Lc + kRecvSlices - 1) / kRecvSlices;
+    const int t0 = blockIdx.y * per, t1 = min(e.Lc, t0 + per);
     for (int b = 0; b < e.nb; ++b) {
         const float2 *u = pyr + e.pyr_off + 2 * (int64_t)e.N - 4 * (int64_t)Kp + (int64_t)b * Kp;
-        __nv_bfloat16 *hi_row = out + e.out_off + (int64_t)(((2 * b) * 8 + c) * 3) * e.Lc;
-        __nv_bfloat16 *lo_row = out + e.out_off + (int64_t)(((2 * b + 1) * 8 + c) * 3) * e.Lc;
-        for (int t = threadIdx.x; t < e.Lc; t += blockDim.x) {
-            int idx = t + c + e.k0;
-            float2 x = make_float2(0.f, 0.f);
-            if (e.k0 == 0) {
-                x = u[idx % Kp];  // the window may span several periods when K' < S + 8
-            } else if (idx >= 0 && idx < Kp) {
-                x = u[idx];
+        for (int c = 0; c < 8; ++c) {
+            __nv_bfloat16 *hi_row = out + e.out_off + (int64_t)(((2 * b) * 8 + c) * 3) * e.Lc;
+            __nv_bfloat16 *lo_row = out + e.out_off + (int64_t)(((2 * b + 1) * 8 + c) * 3) * e.Lc;
+            for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+                const int idx = t + c + e.k0;
+                float2 x = make_float2(0.f, 0.f);
+                if (e.k0 == 0)
+                    x = u[idx % Kp];  // the window may span several periods when K' < S + 8
+                else if (idx >= 0 && idx < Kp)
+                    x = u[idx];
+                __nv_bfloat16 h0, l0, h1, l1, h2, l2;
+                split_bf16(x.x, h0, l0);
+                split_bf16(x.y, h1, l1);
+                split_bf16(-x.x, h2, l2);
+                hi_row[t] = h0;
+                hi_row[e.Lc + t] = h1;
+                hi_row[2 * (int64_t)e.Lc + t] = h2;
+                lo_row[t] = l0;
+                lo_row[e.Lc + t] = l1;
+                lo_row[2 * (int64_t)e.Lc + t] = l2;
             }
-            __nv_bfloat16 h0, l0, h1, l1, h2, l2;
-            split_bf16(x.x, h0, l0);
-            split_bf16(x.y, h1, l1);
-            split_bf16(-x.x, h2, l2);
-            hi_row[t] = h0;
-            hi_row[e.Lc + t] = h1;
-            hi_row[2 * (int64_t)e.Lc + t] = h2;
-            lo_row[t] = l0;
-            lo_row[e.Lc + t] = l1;
-            lo_row[2 * (int64_t)e.Lc + t] = l2;
         }
     }
 }
@@ -448,7 +473,7 @@ sidwt_status encode_maps(void *two_maps, const void *a_base, const void *b_base,
 
 sidwt_status launch_pack_recv(const float2 *pyr, const RecvEntry *e, int n, void *out, cudaStream_t s) {
     if (n <= 0) return SIDWT_OK;
-    pack_recv_kernel<<<dim3((unsigned)n, 8), 256, 0, s>>>(pyr, e, static_cast<__nv_bfloat16 *>(out));
+    pack_recv_kernel<<<dim3((unsigned)n, kRecvSlices), 256, 0, s>>>(pyr, e, static_cast<__nv_bfloat16 *>(out));
     cudaError_t er = cudaGetLastError();
     return er == cudaSuccess ? SIDWT_OK : cuda_fail(er, "received tensor-core operand packing");
 }
