@@ -115,3 +115,33 @@ def test_bf16x3_full_size_two_reference_batch_sampled(oracle, fname):
             rel = np.abs(rb[j] - ro[i, j]).max() / np.abs(ro[i, j]).max()
             assert rel < 1e-4, (b, j, rel)
         U.check_peak_lags(lag[b], ro[i], 3 * 2.0 ** -16, what=f"{fname} pulse {b}")
+
+
+def test_bf16x3_many_reference_batch_sampled(oracle):
+    """64 references x 16384 pulses, N = 4096, J = 6, CDF 9/7 (pulse i echoes
+    reference i mod 64) in one call; sampled pulses against the oracle within
+    the stated bound, scale-0 peaks at the injected delays."""
+    from paper_cs_0607001_gb300 import sidwt
+    w = inputs.many_ref_batch(n_refs=64, B=16384, N=4096, J=6)
+    with sidwt.Plan("cdf97", 4096, 6) as p:
+        for x in w["refs"]:
+            p.store_reference(U.to_dev_c64(x))
+        ids = torch.from_numpy(w["ref_ids"].astype(np.int32)).to(U.dev())
+        r = p.correlate(ids, U.to_dev_c64(w["y"]), precision="bf16x3", want_r=True)
+        lag, mag, norm = p.peaks(16384)
+        p.check()
+        sample = np.array([0, 1, 63, 64, 4097, 8191, 12000, 16383])
+        rs = r[torch.from_numpy(sample).to(U.dev())].cpu().numpy().astype(np.complex128)
+        lag = lag.cpu().numpy()
+    assert np.mean(lag[:, 0] == w["delays"]) > 0.99
+    X = w["refs"][w["ref_ids"][sample]].astype(np.complex128)
+    Y = w["y"][sample].astype(np.complex128)
+    lo, mo, no, ro, _ = oracle.correlate_batch(2, X, Y, 6, want_r=True)
+    trees = {int(k): oracle.tree_x(2, w["refs"][k].astype(np.complex128), 6)[0] for k in set(w["ref_ids"][sample])}
+    for i, b in enumerate(sample):
+        pyr, _ = oracle.pyramid_y(2, Y[i], 6)
+        for j in range(7):
+            err = np.abs(rs[i, j] - ro[i, j]).max()
+            bound = stated_bound(trees[int(w["ref_ids"][b])], pyr, 4096, 6, j, 4096 >> j)
+            assert err <= bound, (b, j, err, bound)
+        U.check_peak_lags(lag[b], ro[i], 3 * 2.0 ** -16, what=f"pulse {b}")
