@@ -592,7 +592,7 @@ def run_sweep_workload(args):
            "kind": "oracle", "sample": f"{len(sample_r) * len(sample_p)} pairs (pulses 0-47 x references 0, 33), "
                                        f"all lags and scales, {cpu_s:.1f} s wall"}
     stream = torch.cuda.current_stream()
-    precisions = ["bf16x3", "fp32"] if args.no_plain is False else ["bf16x3"]
+    precisions = ["bf16x3", "tf32x3", "fp32"] if args.no_plain is False else ["bf16x3", "tf32x3"]
     res = {}
     lag_ref = None
     clocks = ClockSampler(0)

@@ -68,7 +68,10 @@ typedef enum {
     SIDWT_PREC_BF16X3 = 1, /* tcgen05 tensor cores, bf16 hi+lo split (hi*hi + hi*lo + lo*hi),
                               FP32 accumulate; scales whose band is shorter than 64 or
                               not a multiple of 64 run on the FP32 path            */
-    SIDWT_PREC_TF32X3 = 2  /* reserved: 3xTF32 split (returns SIDWT_EUNSUPPORTED)     */
+    SIDWT_PREC_TF32X3 = 2  /* tcgen05 tensor cores, 3xTF32 split (hi*hi + hi*lo + lo*hi of
+                              TF32-rounded parts), FP32 accumulate: FP32-grade accuracy;
+                              plans only (sidwt_correlate); scales whose band is
+                              shorter than 64 or not a multiple of 64 run on the FP32 path */
 } sidwt_precision;
 
 typedef enum {
@@ -142,7 +145,7 @@ sidwt_status sidwt_analyze(sidwt_plan *p, const void *y_dev, int64_t B, void *py
  * ref_ids_dev: int32[B]; an id outside [0, num_refs) marks that pulse
  *   invalid (its peaks read lag -1) and is reported by sidwt_check.
  * y_dev: as for sidwt_analyze.
- * prec: SIDWT_PREC_FP32 or SIDWT_PREC_BF16X3.  Batches of at most 16
+ * prec: SIDWT_PREC_FP32, SIDWT_PREC_BF16X3 or SIDWT_PREC_TF32X3.  Batches of at most 16
  *   pulses run every pulse as a batch of one on the FP32 CUDA-core kernel of
  *   the ragged path, whatever prec says (a tile of 64 or 128 pulses would be
  *   mostly empty); the first call with a given B builds that work list.

@@ -1,0 +1,496 @@
+// Per-scale all-lag correlation on the tcgen05 tensor cores with a 3xTF32
+// split (a = a_hi + a_lo, both rounded to TF32; products hi*hi + hi*lo +
+// lo*hi, FP32 accumulation in TMEM): FP32-grade accuracy at tensor-core
+// speed.
+//
+// Same products as the bf16 path (eq. 20 / 20a in advance form,
+// C[p][m] = sum_k conj(w[(k + p) mod K']) u_m[k]) with the roles of the
+// operands exchanged and only K-major layouts:
+//   * A (M = 128 rows) is the stored variant's window: row i is the advance
+//     p = p0 + r + 4 i, so with a copy W_r[t] = w[t + r] shifted by the
+//     residue r, element (i, k) sits at W_r[t0 + 4 i + k]: consecutive rows
+//     are 16 bytes apart and the K-major core matrices overlap (LBO 16 B,
+//     SBO 128 B).  One CTA owns one residue r and 128 advances spaced by 4
+//     (512 consecutive advances per r-quadruple of CTAs).
+//   * B (N = 256 columns) is 256 received pulses of one reference, K-major
+//     ([k/4][Re|Im][pulse][4 samples]), loaded by TMA as a plain box.
+// Re and Im: Re += A(wr) B(ur) + A(wi) B(ui), Im += A(wr) B(ui) + A(-wi) B(ur);
+// each with the three split products: 24 MMAs (M 128, N 256, K 8) per stage
+// of 16 samples.  The epilogue reduces the peak of every pulse over the
+// CTA's advances with a warp transpose-reduction and one atomicMax per
+// (warp, pulse).  Roles and bounded waits as in the bf16 kernel.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "tc_common.cuh"
+
+namespace sidwt {
+namespace tc32 {
+
+using namespace sidwt::tc;
+
+constexpr int kThreads = 192;
+constexpr int kTN = 256;                        // pulses per tile (MMA N)
+constexpr int kKB = 16;                         // samples per stage
+constexpr int kLagBlock = 512;                  // advances per (r-quadruple of) CTA
+constexpr int kWinChunks = 132;                 // window chunks of 4 samples: 4*127 + 15 < 528
+constexpr int kWinRowBytes = kWinChunks * 16;   // 2112
+constexpr int kARows = 3;                       // planes -Im, Re, Im of one residue
+constexpr int kABytes = 6400;                   // 3 rows x 2112 B, rounded up to 128
+constexpr int kBBytes = 4 * 2 * kTN * 16;       // [4 k-chunks][Re|Im][256][16 B] = 32768
+constexpr int kStage = 2 * kBBytes + 2 * kABytes;  // B hi, B lo, A hi, A lo = 78336
+constexpr int kBarOff = 2 * kStage;             // 156672
+constexpr int kSmemBytes = kBarOff + 128 + 1024;
+constexpr int kTmemCols = 512;
+constexpr int kRowsPerVariant = 24;             // hi/lo x 4 residues x 3 planes
+
+// Instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+// Round to TF32 (nearest, ties away from zero): the hi part, then the lo part
+// of the remainder.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+    hi = to_tf32(x);
+    lo = to_tf32(x - __uint_as_float(hi));
+}
+
+struct Args {
+    int64_t N;
+    int J, j, lev;
+    int Kp, nv, nbands, nlb;  // band length, variants, bands, 512-advance blocks per variant
+    int kb_per_band;          // K' / 16
+    int rows_per_ref;
+    const int32_t *perm;
+    const int32_t *tile_ref;
+    const int32_t *tile_start;
+    const int32_t *tile_count;
+    const int32_t *ntiles;
+    unsigned long long *keys;
+    float2 *R;
+    int32_t *err;
+};
+
+__device__ __forceinline__ unsigned long long kmax(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
+
+__global__ void __launch_bounds__(kThreads, 1)
+    corr_tc32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB_hi,
+                     const __grid_constant__ CUtensorMap mapB_lo, const Args a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + kBarOff);  // full[2], empty[2], accf
+    uint64_t *full = bar, *empty = bar + 2, *accf = bar + 4;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 8);
+    volatile int *sflag = reinterpret_cast<volatile int *>(tmem_slot + 4);  // [0] error, [1] issued, [2] consumed, [3] progress
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bx = blockIdx.x;
+    const int lb = bx % a.nlb;
+    const int r = (bx / a.nlb) & 3;
+    const int v = (bx / (a.nlb * 4)) % a.nv;
+    const int pt = bx / (a.nlb * 4 * a.nv);
+    if (pt >= a.ntiles[0]) return;  // uniform: before any barrier or TMEM use
+    const int row0 = a.tile_start[pt];
+    const int cnt = a.tile_count[pt];
+    const int ref = a.tile_ref[pt];
+    const int p0 = lb * kLagBlock;
+    const int nkb = a.nbands * a.kb_per_band;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(accf, 1);
+        sflag[0] = 0;
+        sflag[1] = 0;
+        sflag[2] = 0;
+        sflag[3] = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb & 1;
+                if (kb >= 2 && !mbar_wait(&empty[s], ((kb >> 1) - 1) & 1)) {
+                    sflag[0] = 1;
+                    break;
+                }
+                if (sflag[0]) break;
+                const int band = kb / a.kb_per_band;
+                const int kap0 = (kb % a.kb_per_band) * kKB;
+                unsigned char *st = base + s * kStage;
+                mbar_expect_tx(&full[s], 2 * kBBytes + 2 * kARows * kWinRowBytes);
+                const int z0 = ((band * a.Kp + kap0) >> 2) * 2;
+                tma_load_3d(st, &mapB_hi, &full[s], 0, row0, z0);
+                tma_load_3d(st + kBBytes, &mapB_lo, &full[s], 0, row0, z0);
+                const int rowbase = ref * a.rows_per_ref + (band * a.nv + v) * kRowsPerVariant;
+                const int chunk0 = (kap0 + p0) >> 2;
+                tma_load_3d(st + 2 * kBBytes, &mapA, &full[s], 0, chunk0, rowbase + r * kARows);
+                tma_load_3d(st + 2 * kBBytes + kABytes, &mapA, &full[s], 0, chunk0, rowbase + 12 + r * kARows);
+                ++issued;
+            }
+            sflag[1] = issued;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(128, kTN);
+            int consumed = 0;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb & 1;
+                if (!mbar_wait(&full[s], (kb >> 1) & 1)) {
+                    sflag[0] = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sb = saddr(base + s * kStage);
+                const uint32_t bHi = sb, bLo = sb + kBBytes;
+                const uint32_t aHi = sb + 2 * kBBytes, aLo = aHi + kABytes;
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    // A rows: 0 -Im w, 1 Re w, 2 Im w; K-direction 16 B (next 4 samples), 8 advances 128 B
+                    const uint32_t ao = (uint32_t)ks * 32;
+                    const uint64_t ah[3] = {sdesc(aHi + ao, 16, 128), sdesc(aHi + kWinRowBytes + ao, 16, 128),
+                                            sdesc(aHi + 2 * kWinRowBytes + ao, 16, 128)};
+                    const uint64_t al[3] = {sdesc(aLo + ao, 16, 128), sdesc(aLo + kWinRowBytes + ao, 16, 128),
+                                            sdesc(aLo + 2 * kWinRowBytes + ao, 16, 128)};
+                    // B planes Re u / Im u: [k-chunk][plane][256 pulses][16 B]; next k-chunk 8 KB, 8 pulses 128 B
+                    const uint32_t bo = (uint32_t)(2 * ks) * 2 * 4096;
+                    const uint64_t bh[2] = {sdesc(bHi + bo, 8192, 128), sdesc(bHi + bo + 4096, 8192, 128)};
+                    const uint64_t bl[2] = {sdesc(bLo + bo, 8192, 128), sdesc(bLo + bo + 4096, 8192, 128)};
+                    // (accumulator, A row, B plane): Re += wr ur + wi ui, Im += wr ui + (-wi) ur
+                    const int acc_of[4] = {0, 0, 1, 1}, arow[4] = {1, 2, 1, 0}, bpl[4] = {0, 1, 1, 0};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint32_t d = tmem + acc_of[q] * 256;
+                        const uint32_t first = (kb == 0 && ks == 0 && (q == 0 || q == 2)) ? 0u : 1u;
+                        mma_tf32(d, ah[arow[q]], bh[bpl[q]], idesc, first);
+                        mma_tf32(d, ah[arow[q]], bl[bpl[q]], idesc, 1u);
+                        mma_tf32(d, al[arow[q]], bh[bpl[q]], idesc, 1u);
+                    }
+                }
+                mma_commit(&empty[s]);
+                ++consumed;
+                sflag[3] = consumed;
+            }
+            sflag[2] = consumed;
+            mma_commit(accf);  // arrives once every MMA issued above has completed
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = advances m
+        const int q4 = warp & 3;
+        const int m = q4 * 32 + lane;
+        uint64_t t0 = now_ns();
+        int last = sflag[3];
+        bool ok = true;
+        while (!mbar_test(accf, 0)) {  // bounded from the MMA thread's last progress
+            const int pr = sflag[3];
+            if (pr != last) {
+                last = pr;
+                t0 = now_ns();
+            } else if (now_ns() - t0 > kWaitNs) {
+                ok = false;
+                break;
+            }
+        }
+        tc_fence_after();
+        if (!__all_sync(0xffffffffu, ok && !sflag[0])) {
+            sflag[0] = 1;
+        } else {
+            const int p = p0 + r + 4 * m;
+            const int pm = p % a.Kp;
+            const int q = pm == 0 ? 0 : a.Kp - pm;
+            const uint32_t D = ((uint32_t)q << a.lev) + (uint32_t)v;
+            const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
+            for (int c0 = 0; c0 < kTN; c0 += 32) {
+                uint32_t re[32], im[32];
+                TMEM_LD32(tl + c0, re);
+                TMEM_LD32(tl + 256 + c0, im);
+                tmem_wait_ld();
+                unsigned long long key[32];
+#pragma unroll
+                for (int n = 0; n < 32; ++n) {
+                    const float xr = __uint_as_float(re[n]), xi = __uint_as_float(im[n]);
+                    key[n] = ((unsigned long long)__float_as_uint(xr * xr + xi * xi) << 32) |
+                             (unsigned long long)(0xFFFFFFFFu - D);
+                    if (a.R && c0 + n < cnt) {
+                        const int64_t b = a.perm[row0 + c0 + n];
+                        a.R[(b * (a.J + 1) + a.j) * a.N + D] = make_float2(xr, xi);
+                    }
+                }
+                // transpose-reduce: afterwards lane i holds the max over the warp's
+                // 32 advances for pulse c0 + i
+#pragma unroll
+                for (int sh = 16; sh >= 1; sh >>= 1) {
+                    const bool upper = (lane & sh) != 0;
+#pragma unroll
+                    for (int i = 0; i < sh; ++i) {
+                        const unsigned long long send = upper ? key[i] : key[i + sh];
+                        const unsigned long long keep = upper ? key[i + sh] : key[i];
+                        key[i] = kmax(keep, __shfl_xor_sync(0xffffffffu, send, sh));
+                    }
+                }
+                if (c0 + lane < cnt && key[0]) {
+                    const int64_t b = a.perm[row0 + c0 + lane];
+                    atomicMax(&a.keys[b * (a.J + 1) + a.j], key[0]);
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 0 && sflag[0]) {
+        for (int kb = sflag[2]; kb < sflag[1]; ++kb) mbar_wait(&full[kb & 1], (kb >> 1) & 1);
+        atomicOr(a.err, 2);
+    }
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+}
+
+// Stored windows: row ((ref * nbands + band) * nv + v) * 24 + hilo * 12 + r * 3
+// + plane holds Lc TF32 values W[t] = plane(w[(t + r) mod K']) (plane 0: -Im,
+// 1: Re, 2: Im), hi or lo part.
+__global__ void pack_ref32_kernel(const float2 *__restrict__ tree, int64_t tree_elems, int64_t N, int lev, int nbands,
+                                  int ref0, int Lc, uint32_t *__restrict__ out) {
+    const int Kp = (int)(N >> lev), nv = 1 << lev;
+    const int rows_per_ref = nbands * nv * kRowsPerVariant;
+    const int64_t row = (int64_t)blockIdx.x + (int64_t)ref0 * rows_per_ref;
+    const int ref = (int)(row / rows_per_ref);
+    int rem = (int)(row % rows_per_ref);
+    const int plane = rem % 3;
+    rem /= 3;
+    const int r = rem % 4;
+    rem /= 4;
+    const int hilo = rem % 2;
+    rem /= 2;
+    const int vv = rem % nv;
+    const int band = rem / nv;
+    const float2 *w = tree + (int64_t)ref * tree_elems + 2 * N * (int64_t)(lev - 1) + (int64_t)band * N + (int64_t)vv * Kp;
+    uint32_t *o = out + row * Lc;
+    for (int t = threadIdx.x; t < Lc; t += blockDim.x) {
+        const float2 x = w[(t + r) % Kp];
+        const float val = plane == 0 ? -x.y : (plane == 1 ? x.x : x.y);
+        uint32_t hi, lo;
+        split_tf32(val, hi, lo);
+        o[t] = hilo ? lo : hi;
+    }
+}
+
+// Received operand of one scale: chunk ((k / 4) * 2 + plane) of row (pulse in
+// grouped order) holds 4 TF32 values u_plane[k .. k + 3] of the concatenated
+// bands (plane 0 Re, 1 Im).  Block: 64 samples x 32 rows.
+__global__ void __launch_bounds__(256) pack_rx32_kernel(const float2 *__restrict__ pyr, int64_t pyr_elems, int64_t off,
+                                                        const int32_t *__restrict__ perm,
+                                                        const int32_t *__restrict__ ntiles, int rows,
+                                                        uint32_t *__restrict__ bhi, uint32_t *__restrict__ blo) {
+    __shared__ float2 tile[32][65];
+    const int kb = blockIdx.x;  // 64 samples
+    const int r0 = blockIdx.y * 32;
+    const int nvalid = ntiles[1];
+    for (int e = threadIdx.x; e < 32 * 64; e += 256) {
+        const int i = e >> 6, k = e & 63;
+        const int r = r0 + i;
+        float2 v = make_float2(0.f, 0.f);
+        if (r < nvalid) v = pyr[(int64_t)perm[r] * pyr_elems + off + (int64_t)kb * 64 + k];
+        tile[i][k] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * 32; e += 256) {  // 16 k-chunks x 2 planes x 32 rows
+        const int cp = e >> 5, i = e & 31;
+        const int r = r0 + i;
+        if (r >= rows) continue;
+        const int kc = cp >> 1, plane = cp & 1;
+        uint4 h, l;
+        uint32_t *hp = reinterpret_cast<uint32_t *>(&h), *lp = reinterpret_cast<uint32_t *>(&l);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 v = tile[i][kc * 4 + q];
+            split_tf32(plane ? v.y : v.x, hp[q], lp[q]);
+        }
+        const int64_t o = (((int64_t)kb * 32 + cp) * rows + r) * 4;
+        *reinterpret_cast<uint4 *>(bhi + o) = h;
+        *reinterpret_cast<uint4 *>(blo + o) = l;
+    }
+}
+
+}  // namespace tc32
+
+// Scales the 3xTF32 path takes: band length a multiple of 64 (16-sample
+// stages and 64-sample packing blocks).
+uint32_t tc32_scale_mask(const sidwt_plan *p) {
+    uint32_t m = 0;
+    for (int j = 0; j <= p->J; ++j) {
+        const int lev = j < p->J ? j + 1 : p->J;
+        const int64_t Kp = p->N >> lev;
+        if (Kp >= 64 && Kp % 64 == 0 && Kp <= (int64_t(1) << 24)) m |= 1u << j;
+    }
+    return m;
+}
+
+static int tc32_lc(int64_t Kp) { return (int)(2 * Kp + 4 * tc32::kWinChunks); }
+static int tc32_rows_per_ref(const sidwt_plan *p, int j) {
+    const int lev = j < p->J ? j + 1 : p->J;
+    return (j < p->J ? 2 : 1) * (1 << lev) * tc32::kRowsPerVariant;
+}
+
+void free_tc32(sidwt_plan *p) {
+    for (int j = 0; j < 16; ++j) {
+        if (p->tc32_ref[j]) cudaFree(p->tc32_ref[j]);
+        if (p->tc32_bhi[j]) cudaFree(p->tc32_bhi[j]);
+        if (p->tc32_blo[j]) cudaFree(p->tc32_blo[j]);
+        p->tc32_ref[j] = p->tc32_bhi[j] = p->tc32_blo[j] = nullptr;
+    }
+    p->tc32_cap_refs = 0;
+    p->tc32_cap_batch = 0;
+    p->tc32_packed = 0;
+}
+
+static sidwt_status ensure_tc32(sidwt_plan *p) {
+    if (p->tc32_cap_refs >= p->cap_refs && p->tc32_cap_batch >= p->cap_batch) return SIDWT_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronise before tensor-core buffers");
+    free_tc32(p);
+    const uint32_t mask = tc32_scale_mask(p);
+    for (int j = 0; j <= p->J; ++j) {
+        if (!(mask & (1u << j))) continue;
+        const int lev = j < p->J ? j + 1 : p->J;
+        const int64_t Kp = p->N >> lev;
+        const int64_t Kj = (j < p->J ? 2 : 1) * Kp;
+        const size_t rb = (size_t)p->cap_refs * tc32_rows_per_ref(p, j) * tc32_lc(Kp) * 4;
+        const size_t bb = (size_t)Kj * 2 * p->cap_batch * 4;
+        if (cudaMalloc(&p->tc32_ref[j], rb) != cudaSuccess || cudaMalloc(&p->tc32_bhi[j], bb) != cudaSuccess ||
+            cudaMalloc(&p->tc32_blo[j], bb) != cudaSuccess) {
+            cudaGetLastError();
+            free_tc32(p);
+            set_error("device allocation failed for the 3xTF32 operands");
+            return SIDWT_ENOMEM;
+        }
+    }
+    p->tc32_cap_refs = p->cap_refs;
+    p->tc32_cap_batch = p->cap_batch;
+    p->tc32_packed = 0;
+    return SIDWT_OK;
+}
+
+sidwt_status correlate_tc32(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t s) {
+    sidwt_status st = ensure_tc32(p);
+    if (st) return st;
+    const uint32_t mask = tc32_scale_mask(p);
+    const int64_t N = p->N;
+    const int J = p->J;
+    if (p->tc32_packed < p->nrefs) {
+        for (int j = 0; j <= J; ++j) {
+            if (!(mask & (1u << j))) continue;
+            const int lev = j < J ? j + 1 : J;
+            const int nb = j < J ? 2 : 1;
+            const int64_t rows = (int64_t)(p->nrefs - p->tc32_packed) * tc32_rows_per_ref(p, j);
+            tc32::pack_ref32_kernel<<<(unsigned)rows, 256, 0, s>>>(p->tree_f, p->tree_elems, N, lev, nb, p->tc32_packed,
+                                                                  tc32_lc(N >> lev),
+                                                                  static_cast<uint32_t *>(p->tc32_ref[j]));
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "reference packing launch");
+        p->tc32_packed = p->nrefs;
+    }
+    const int64_t max_pt = (B + tc32::kTN - 1) / tc32::kTN + std::min<int64_t>(p->nrefs, B);
+    for (int j = 0; j <= J; ++j) {
+        if (!(mask & (1u << j))) continue;
+        const int lev = j < J ? j + 1 : J;
+        const int64_t Kp = N >> lev;
+        const int nb = j < J ? 2 : 1;
+        const int64_t Kj = nb * Kp;
+        uint32_t *bhi = static_cast<uint32_t *>(p->tc32_bhi[j]);
+        uint32_t *blo = static_cast<uint32_t *>(p->tc32_blo[j]);
+        {
+            dim3 g((unsigned)(Kj / 64), (unsigned)((B + 31) / 32));
+            tc32::pack_rx32_kernel<<<g, 256, 0, s>>>(p->pyr_f, p->pyr_elems, 2 * N - 4 * Kp, p->tiles.perm,
+                                                     p->tiles.ntiles, (int)B, bhi, blo);
+        }
+        // TF32 data is moved as pairs of 16-bit units: a 16-byte chunk is 8 units
+        CUtensorMap mA, mBh, mBl;
+        const uint64_t nchunk = (uint64_t)Kj / 4 * 2;
+        if ((st = tc::encode_3d(&mBh, bhi, 8, (uint64_t)B, nchunk, 16, 16 * (uint64_t)B, 8, tc32::kTN, 8)) ||
+            (st = tc::encode_3d(&mBl, blo, 8, (uint64_t)B, nchunk, 16, 16 * (uint64_t)B, 8, tc32::kTN, 8)))
+            return st;
+        const int Lc = tc32_lc(Kp);
+        const int rpr = tc32_rows_per_ref(p, j);
+        if ((st = tc::encode_3d(&mA, p->tc32_ref[j], 8, (uint64_t)(Lc / 4), (uint64_t)p->nrefs * rpr, 16,
+                                (uint64_t)Lc * 4, 8, tc32::kWinChunks, tc32::kARows)))
+            return st;
+        tc32::Args a{};
+        a.N = N;
+        a.J = J;
+        a.j = j;
+        a.lev = lev;
+        a.Kp = (int)Kp;
+        a.nv = 1 << lev;
+        a.nbands = nb;
+        a.nlb = (int)((Kp + tc32::kLagBlock - 1) / tc32::kLagBlock);
+        a.kb_per_band = (int)(Kp / tc32::kKB);
+        a.rows_per_ref = rpr;
+        a.perm = p->tiles.perm;
+        a.tile_ref = p->tiles.tile_ref;
+        a.tile_start = p->tiles.tile_start;
+        a.tile_count = p->tiles.tile_count;
+        a.ntiles = p->tiles.ntiles;
+        a.keys = p->keys;
+        a.R = r_dev;
+        a.err = p->err;
+        const int64_t grid = max_pt * a.nv * 4 * a.nlb;
+        if (grid > 0x7fffffff) {
+            set_error("batch too large for one tensor-core launch");
+            return SIDWT_EINVAL;
+        }
+        tc32::corr_tc32_kernel<<<(unsigned)grid, tc32::kThreads, tc32::kSmemBytes, s>>>(mA, mBh, mBl, a);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "3xTF32 correlation launch");
+    }
+    const uint32_t rest = ((1u << (J + 1)) - 1u) & ~mask;
+    if (rest) return correlate_simt(p, B, r_dev, s, rest, tc32::kTN);
+    return SIDWT_OK;
+}
+
+int tc32_group_tile() { return tc32::kTN; }
+
+int tc32_launch_count(const sidwt_plan *p) {
+    const uint32_t mask = tc32_scale_mask(p);
+    const bool pack_refs = p->tc32_packed < p->nrefs;
+    int n = 0;
+    for (int j = 0; j <= p->J; ++j)
+        if (mask & (1u << j)) n += pack_refs ? 3 : 2;
+    if (((1u << (p->J + 1)) - 1u) & ~mask) n += 1;
+    return n;
+}
+
+cudaError_t prepare_tc32_kernels() {
+    return cudaFuncSetAttribute(tc32::corr_tc32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc32::kSmemBytes);
+}
+
+}  // namespace sidwt

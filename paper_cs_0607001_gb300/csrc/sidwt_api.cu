@@ -176,6 +176,7 @@ sidwt_status prepare_kernels() {
     e = prepare_analysis_kernels();
     if (e == cudaSuccess) e = prepare_tc_kernels();
     if (e == cudaSuccess) e = rtc::prepare_kernels();
+    if (e == cudaSuccess) e = prepare_tc32_kernels();
     if (e != cudaSuccess) return cuda_fail(e, "kernel shared-memory attributes");
     if (dev >= 0 && dev < 64) done[dev] = true;
     return SIDWT_OK;
@@ -256,6 +257,7 @@ sidwt_status sidwt_plan_destroy(sidwt_plan *p) {
     cudaDeviceSynchronize();
     free_batch(p);
     free_tc(p);
+    free_tc32(p);
     free_small(p);
     dfree(p->tree_f);
     dfree(p->tree_i);
@@ -384,11 +386,12 @@ sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const vo
         set_error("ref_ids_dev is NULL");
         return SIDWT_EINVAL;
     }
-    if (prec != SIDWT_PREC_FP32 && prec != SIDWT_PREC_BF16X3) {
-        set_error("precision not available in this build");
-        return SIDWT_EUNSUPPORTED;
+    if (prec != SIDWT_PREC_FP32 && prec != SIDWT_PREC_BF16X3 && prec != SIDWT_PREC_TF32X3) {
+        set_error("unknown precision");
+        return SIDWT_EINVAL;
     }
     const bool tc = (prec == SIDWT_PREC_BF16X3);
+    const bool tc32 = (prec == SIDWT_PREC_TF32X3);
     if (p->nrefs == 0 && B > 0) {
         set_error("no stored reference");
         return SIDWT_EINVAL;
@@ -402,7 +405,8 @@ sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const vo
     if (small && (st = prepare_small(p, B))) return st;
     {
         StageTimer t(p, 1, s, 1);
-        if ((st = group_pulses(p, ref_ids_dev, B, tc ? tc_group_tile() : simt_tile_pulses(), s))) return st;
+        const int gt = tc ? tc_group_tile() : (tc32 ? tc32_group_tile() : simt_tile_pulses());
+        if ((st = group_pulses(p, ref_ids_dev, B, gt, s))) return st;
     }
     {
         StageTimer t(p, 2, s, analyze_launch_count(p));
@@ -411,11 +415,13 @@ sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const vo
     cudaError_t e = cudaMemsetAsync(p->keys, 0, B * (p->J + 1) * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
     {
-        StageTimer t(p, 3, s, small ? 2 : (tc ? tc_launch_count(p) : 1));
+        StageTimer t(p, 3, s, small ? 2 : (tc ? tc_launch_count(p) : (tc32 ? tc32_launch_count(p) : 1)));
         if (small) {
             if ((st = correlate_small(p, ref_ids_dev, B, reinterpret_cast<float2 *>(r_dev), s))) return st;
         } else if (tc) {
             if ((st = correlate_tc(p, B, reinterpret_cast<float2 *>(r_dev), s))) return st;
+        } else if (tc32) {
+            if ((st = correlate_tc32(p, B, reinterpret_cast<float2 *>(r_dev), s))) return st;
         } else if ((st = correlate_simt(p, B, reinterpret_cast<float2 *>(r_dev), s))) {
             return st;
         }
@@ -507,6 +513,7 @@ sidwt_status sidwt_reset_references(sidwt_plan *p) {
     CHECK_PLAN(p);
     p->nrefs = 0;
     p->tc_packed = 0;
+    p->tc32_packed = 0;
     return SIDWT_OK;
 }
 

@@ -155,6 +155,13 @@ struct sidwt_plan {
     int32_t tc_cap_refs = 0;
     int64_t tc_cap_batch = 0;
     int32_t tc_packed = 0;
+    // 3xTF32 operands (per scale j): stored windows, received hi / lo planes
+    void *tc32_ref[16] = {};
+    void *tc32_bhi[16] = {};
+    void *tc32_blo[16] = {};
+    int32_t tc32_cap_refs = 0;
+    int64_t tc32_cap_batch = 0;
+    int32_t tc32_packed = 0;
 
     // stage timing: events recorded around each stage while enabled
     bool timing = false;
@@ -225,6 +232,14 @@ int tc_group_tile();
 int tc_launch_count(const sidwt_plan *p);
 void free_tc(sidwt_plan *p);
 sidwt_status finalize_peaks(sidwt_plan *p, int64_t B, cudaStream_t s);
+
+// ---- corr_tc32.cu (3xTF32) ----
+sidwt_status correlate_tc32(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t s);
+uint32_t tc32_scale_mask(const sidwt_plan *p);
+int tc32_group_tile();
+int tc32_launch_count(const sidwt_plan *p);
+void free_tc32(sidwt_plan *p);
+cudaError_t prepare_tc32_kernels();
 
 // ---- ragged_tc.cu: batch-of-one pairs on the tensor cores ----
 namespace rtc {

@@ -42,8 +42,9 @@ def test_tc_operand_layouts_selftest():
                     f"expected[1,:8]={exp[1, :8]}")
 
 
-def stated_bound(tree, pyr, N, J, j, Kj):
-    """(3 2^-16 + K 2^-24) max_v ||w_v|| ||u|| for scale j (tree and pyr from the oracle)."""
+def stated_bound(tree, pyr, N, J, j, Kj, u=2.0 ** -16):
+    """(3 u + K 2^-24) max_v ||w_v|| ||u|| for scale j (tree and pyr from the
+    oracle); u = 2^-16 for the bf16 split, 2^-22 for 3xTF32."""
     lev = j + 1 if j < J else J
     Kp = N >> lev
     base = 2 * N * (lev - 1)
@@ -56,7 +57,7 @@ def stated_bound(tree, pyr, N, J, j, Kj):
     else:
         wn = np.sqrt((np.abs(A) ** 2).sum(1)).max()
         un = np.linalg.norm(pyr[off:off + Kp])
-    return (3 * 2.0 ** -16 + Kj * 2.0 ** -24) * wn * un
+    return (3 * u + Kj * 2.0 ** -24) * wn * un
 
 
 def run(fname, N, J, refs, y, ids, precision, want_r=True):
@@ -145,3 +146,28 @@ def test_bf16x3_many_reference_batch_sampled(oracle):
             bound = stated_bound(trees[int(w["ref_ids"][b])], pyr, 4096, 6, j, 4096 >> j)
             assert err <= bound, (b, j, err, bound)
         U.check_peak_lags(lag[b], ro[i], 3 * 2.0 ** -16, what=f"pulse {b}")
+
+
+@pytest.mark.parametrize("fname,fid", list(U.FLOAT_FILTERS.items()))
+@pytest.mark.parametrize("N,J,B,nrefs", [(1024, 4, 300, 3), (256, 2, 130, 2), (4096, 6, 40, 1), (512, 3, 257, 2)])
+def test_tf32x3_matches_oracle_within_stated_bound(oracle, fname, fid, N, J, B, nrefs):
+    """3xTF32: a = a_hi + a_lo, both rounded to TF32 (unit roundoff 2^-11);
+    dropping lo*lo and the two lo roundings leave <= 3 * 2^-22 |a||b| per
+    product, FP32 accumulation adds K 2^-24: the FP32 path's own bound."""
+    w = U.small_batch(nrefs, B, N, J, seed=2000 + N + B + fid)
+    r, lag, mag, norm = run(fname, N, J, w["refs"], w["y"], w["ref_ids"], "tf32x3")
+    X = w["refs"][w["ref_ids"]].astype(np.complex128)
+    Y = w["y"].astype(np.complex128)
+    lo, mo, no, ro, _ = oracle.correlate_batch(fid, X, Y, J, form=1, want_r=True)
+    trees = [oracle.tree_x(fid, x.astype(np.complex128), J)[0] for x in w["refs"]]
+    worst_rel = 0.0
+    for b in range(B):
+        rb = r[b].cpu().numpy().astype(np.complex128)
+        pyr, _ = oracle.pyramid_y(fid, Y[b], J)
+        for j in range(J + 1):
+            err = np.abs(rb[j] - ro[b, j]).max()
+            bound = stated_bound(trees[w["ref_ids"][b]], pyr, N, J, j, N >> j, u=2.0 ** -22)
+            assert err <= bound, f"pulse {b} scale {j}: error {err:.3e} > stated bound {bound:.3e}"
+            worst_rel = max(worst_rel, err / np.abs(ro[b, j]).max())
+        U.check_peak_lags(lag[b], ro[b], U.RTOL_FP32, what=f"{fname} pulse {b}")
+    assert worst_rel < U.RTOL_FP32, worst_rel
