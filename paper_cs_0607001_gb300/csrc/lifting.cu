@@ -450,6 +450,202 @@ __global__ void __launch_bounds__(kAnalyzeThreads) analyze_smem_kernel(const voi
                       reinterpret_cast<T *>(smraw), red, redi);
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined received analysis of a uniform batch: a persistent grid, each CTA
+// walking pulses b, b + G, ...  While the levels of one pulse run, a bulk
+// copy (TMA, cp.async.bulk) brings the next pulse into the other of two
+// input buffers, so the HBM reads stay in flight across the whole kernel.
+// Shared memory: two raw input buffers (N samples of the input type) and a
+// level-1 buffer W of N/2 elements of T; level l >= 2 alternates between W
+// and the current input buffer (free once level 1 has read it).  Energies:
+// warp partial sums per level, one cross-warp sum per pulse.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool pipe_wait(uint64_t *bar, uint32_t parity) {
+    uint64_t t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > 200ull * 1000 * 1000) return false;  // 200 ms
+    }
+}
+
+__device__ __forceinline__ void pipe_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Level-1 window of the integer path straight from the int16 I/Q input.
+__device__ __forceinline__ void out_pair_i16(const short2 *in, int H, int n, int2 &lo, int2 &hi) {
+    const short4 *q = reinterpret_cast<const short4 *>(in);
+    int2 E[5], O[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const short4 cur = q[wrap_small(n - 2 + i, H)];
+        E[i] = make_int2(cur.x, cur.y);
+        O[i] = make_int2(cur.z, cur.w);
+    }
+    int53_window<SIDE_Y, 2>(E, O);
+    lo = E[2];
+    hi = O[2];
+}
+
+constexpr int kPipeMaxLevels = 16;
+
+template <int F, typename T>
+__global__ void __launch_bounds__(kAnalyzeThreads) analyze_pipe_kernel(const void *__restrict__ y_in, int64_t N, int J,
+                                                                       int64_t B, float2 *__restrict__ pyr_f,
+                                                                       int2 *__restrict__ pyr_i, int64_t pyr_elems,
+                                                                       double *__restrict__ yen, LiftCoef c,
+                                                                       int32_t *__restrict__ err) {
+    constexpr bool INT = (F == SIDWT_LEGALL53_INT);
+    constexpr int IN_BYTES = INT ? 4 : 8;
+    extern __shared__ __align__(16) unsigned char smraw[];  // 16-byte aligned: enough for the bulk copies
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float2 redf[kPipeMaxLevels][kAnalyzeThreads / 32];
+    __shared__ long long redi[kPipeMaxLevels][kAnalyzeThreads / 32];
+    __shared__ int sfail;
+    const uint32_t bytes = (uint32_t)(N * IN_BYTES);
+    const size_t inb = ((size_t)bytes + 127) & ~(size_t)127;
+    unsigned char *const buf0 = smraw, *const buf1 = smraw + inb;
+    T *W = reinterpret_cast<T *>(smraw + 2 * inb);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int Nh = (int)(N / 2);
+    const char *y = reinterpret_cast<const char *>(y_in);
+    const int64_t G = gridDim.x;
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sfail = 0;
+    }
+    __syncthreads();
+    if (tid == 0) pipe_load(buf0, y + (int64_t)blockIdx.x * bytes, bytes, &bar[0]);
+    int i = 0;
+    int64_t issued = 1, landed = 0;  // copies issued / waited for (thread 0's bookkeeping)
+    for (int64_t b = blockIdx.x; b < B; b += G, ++i) {
+        const int s = i & 1;
+        unsigned char *const cur = s ? buf1 : buf0;
+        if (tid == 0 && b + G < B) {
+            // the other buffer held the previous pulse, whose reads and writes ended at the last barrier
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            pipe_load(s ? buf0 : buf1, y + (b + G) * (int64_t)bytes, bytes, &bar[s ^ 1]);
+            ++issued;
+        }
+        if (!pipe_wait(&bar[s], (uint32_t)((i >> 1) & 1))) sfail = 1;
+        __syncthreads();
+        if (sfail) break;
+        if (tid == 0) ++landed;
+        float2 *pf = pyr_f + b * pyr_elems;
+        int2 *pi = INT ? pyr_i + b * pyr_elems : nullptr;
+
+        // level-0 energy from the landed input
+        {
+            EnAcc en;
+            long long eni = 0;
+            if constexpr (INT) {
+                const short4 *q = reinterpret_cast<const short4 *>(cur);
+                for (int n = tid; n < Nh; n += blockDim.x) {
+                    const short4 v = q[n];
+                    eni += sq2i(make_int2(v.x, v.y)) + sq2i(make_int2(v.z, v.w));
+                }
+                for (int o = 16; o > 0; o >>= 1) eni += __shfl_xor_sync(0xffffffffu, eni, o);
+                if (lane == 0) redi[0][warp] = eni;
+            } else {
+                const float4 *q = reinterpret_cast<const float4 *>(cur);
+                for (int n = tid; n < Nh; n += blockDim.x) {
+                    const float4 v = q[n];
+                    en.add(sq2(make_float2(v.x, v.y)));
+                    en.add(sq2(make_float2(v.z, v.w)));
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    EnAcc t;
+                    t.hi = __shfl_xor_sync(0xffffffffu, en.hi, o);
+                    t.lo = __shfl_xor_sync(0xffffffffu, en.lo, o);
+                    en.add(t);
+                }
+                if (lane == 0) redf[0][warp] = make_float2(en.hi, en.lo);
+            }
+        }
+        for (int l = 1; l <= J; ++l) {
+            const int H = (int)(N >> l);
+            const int64_t off = 2 * N - 4 * (int64_t)H;
+            T *out = (l & 1) ? W : reinterpret_cast<T *>(cur);
+            const T *in = (l & 1) ? reinterpret_cast<const T *>(cur) : W;
+            EnAcc en;
+            long long eni = 0;
+            for (int n = tid; n < H; n += blockDim.x) {
+                T lo, hi;
+                if constexpr (INT) {
+                    if (l == 1)
+                        out_pair_i16(reinterpret_cast<const short2 *>(cur), H, n, lo, hi);
+                    else
+                        out_pair_i(reinterpret_cast<const int2 *>(in), H, n, lo, hi);
+                    pi[off + n] = lo;
+                    pi[off + H + n] = hi;
+                    pf[off + n] = to_f2(lo);
+                    pf[off + H + n] = to_f2(hi);
+                    eni += sq2i(lo);
+                } else {
+                    out_pair_f<F>(reinterpret_cast<const float2 *>(in), H, n, c, lo, hi);
+                    pf[off + n] = lo;
+                    pf[off + H + n] = hi;
+                    en.add(sq2(lo));
+                }
+                out[n] = lo;
+            }
+            if constexpr (INT) {
+                for (int o = 16; o > 0; o >>= 1) eni += __shfl_xor_sync(0xffffffffu, eni, o);
+                if (lane == 0) redi[l][warp] = eni;
+            } else {
+                for (int o = 16; o > 0; o >>= 1) {
+                    EnAcc t;
+                    t.hi = __shfl_xor_sync(0xffffffffu, en.hi, o);
+                    t.lo = __shfl_xor_sync(0xffffffffu, en.lo, o);
+                    en.add(t);
+                }
+                if (lane == 0) redf[l][warp] = make_float2(en.hi, en.lo);
+            }
+            __syncthreads();
+        }
+        if (tid <= J) {
+            if constexpr (INT) {
+                long long t = 0;
+                for (int w = 0; w < nw; ++w) t += redi[tid][w];
+                yen[b * (J + 1) + tid] = (double)t;
+            } else {
+                EnAcc t;
+                for (int w = 0; w < nw; ++w) {
+                    EnAcc u;
+                    u.hi = redf[tid][w].x;
+                    u.lo = redf[tid][w].y;
+                    t.add(u);
+                }
+                yen[b * (J + 1) + tid] = t.total();
+            }
+        }
+        // J = 0 cannot happen (J >= 1): the level loop's last barrier orders
+        // every read of cur and W before the next prefetch into cur
+    }
+    if (tid == 0 && sfail) {
+        // let this CTA's own copies land before its shared memory is released
+        for (int64_t k = landed; k < issued; ++k) pipe_wait(&bar[k & 1], (uint32_t)((k >> 1) & 1));
+        atomicOr(err, 2);
+    }
+}
+
 // One CTA per listed pulse of a ragged batch (float filters): item k has its
 // own N and J; its pulse, pyramid row and energies sit at the given offsets.
 template <int F>
@@ -503,6 +699,8 @@ __global__ void pyr_energy_kernel(const float2 *__restrict__ y, const float2 *__
 // Host launchers
 // ---------------------------------------------------------------------------
 static constexpr int kSmemLimit = 227 * 1024 - 1024;  // dynamic budget; 1 KB left for static shared memory
+// the pipelined kernel's static shared memory: barriers and 2 x 16 x 16 partial energies
+static constexpr int kPipeSmemLimit = 227 * 1024 - 8 * 1024;
 
 template <int F, typename TIn>
 static void launch_level_f(int side, const TIn *in, int64_t in_stride, int nrows, int nchild, int64_t K,
@@ -602,6 +800,18 @@ cudaError_t prepare_analysis_kernels() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(analyze_smem_kernel<SIDWT_LEGALL53_INT, int2>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(analyze_pipe_kernel<SIDWT_D4, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kPipeSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(analyze_pipe_kernel<SIDWT_LEGALL53, float2>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(analyze_pipe_kernel<SIDWT_CDF97, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kPipeSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(analyze_pipe_kernel<SIDWT_LEGALL53_INT, int2>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmemLimit);
     if (e == cudaSuccess) e = prepare_ragged_kernels();
     return e;
 }
@@ -618,6 +828,36 @@ sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStre
     const LiftCoef c = lift_coef(p->filter, SIDE_Y);
     const size_t smem = (size_t)(N + N / 2) * 8;
     cudaError_t e = cudaSuccess;
+    const size_t in_bytes = (size_t)N * (p->is_int ? 4 : 8);
+    const size_t pipe_smem = 2 * ((in_bytes + 127) & ~(size_t)127) + (size_t)(N / 2) * 8;
+    const uintptr_t yal = reinterpret_cast<uintptr_t>(y_dev);
+    if (pipe_smem <= (size_t)kPipeSmemLimit && in_bytes % 16 == 0 && yal % 16 == 0 && J < kPipeMaxLevels) {
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int per_sm = std::max(1, (int)((size_t)(228 * 1024) / (pipe_smem + 8 * 1024)));
+        const int64_t grid = std::min<int64_t>(B, (int64_t)sms * per_sm);
+        switch (p->filter) {
+        case SIDWT_D4:
+            analyze_pipe_kernel<SIDWT_D4, float2><<<(unsigned)grid, kAnalyzeThreads, pipe_smem, s>>>(
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err);
+            break;
+        case SIDWT_LEGALL53:
+            analyze_pipe_kernel<SIDWT_LEGALL53, float2><<<(unsigned)grid, kAnalyzeThreads, pipe_smem, s>>>(
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err);
+            break;
+        case SIDWT_CDF97:
+            analyze_pipe_kernel<SIDWT_CDF97, float2><<<(unsigned)grid, kAnalyzeThreads, pipe_smem, s>>>(
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err);
+            break;
+        default:
+            analyze_pipe_kernel<SIDWT_LEGALL53_INT, int2><<<(unsigned)grid, kAnalyzeThreads, pipe_smem, s>>>(
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err);
+            break;
+        }
+        e = cudaGetLastError();
+        return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "analysis launch");
+    }
     if (smem <= (size_t)kSmemLimit && B <= 0x7fffffff) {
         switch (p->filter) {
         case SIDWT_D4: e = launch_smem<SIDWT_D4, float2>(p, y_dev, B, s, c); break;
