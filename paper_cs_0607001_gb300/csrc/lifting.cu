@@ -189,6 +189,35 @@ __device__ __forceinline__ void lift_window(float2 (&E)[2 * R + 1], float2 (&O)[
     }
 }
 
+// The same steps on M consecutive pairs: afterwards entries [R, M - R) are
+// exact for a filter whose steps consume R neighbours on each side (several
+// outputs share one window).
+template <int F, int S, int M>
+__device__ __forceinline__ void lift_window_m(float2 (&E)[M], float2 (&O)[M], const LiftCoef &c) {
+    using Sh = LiftShape<F, S>;
+#pragma unroll
+    for (int s = 0; s < Sh::nsteps; ++s) {
+        const float c0 = c.c0[s], c1 = c.c1[s];
+        if (Sh::target(s) == 1) {
+            if (Sh::nb(s) > 0) {
+#pragma unroll
+                for (int i = 0; i < M - 1; ++i) O[i] = axpy2(O[i], c0, E[i], c1, E[i + 1]);
+            } else {
+#pragma unroll
+                for (int i = M - 1; i >= 1; --i) O[i] = axpy2(O[i], c0, E[i], c1, E[i - 1]);
+            }
+        } else {
+            if (Sh::nb(s) > 0) {
+#pragma unroll
+                for (int i = 0; i < M - 1; ++i) E[i] = axpy2(E[i], c0, O[i], c1, O[i + 1]);
+            } else {
+#pragma unroll
+                for (int i = M - 1; i >= 1; --i) E[i] = axpy2(E[i], c0, O[i], c1, O[i - 1]);
+            }
+        }
+    }
+}
+
 template <int S, int R>
 __device__ __forceinline__ void int53_window(int2 (&E)[2 * R + 1], int2 (&O)[2 * R + 1]) {
     if (S == SIDE_X) {
@@ -502,6 +531,7 @@ __device__ __forceinline__ void out_pair_i16(const short2 *in, int H, int n, int
 }
 
 constexpr int kPipeMaxLevels = 16;
+constexpr int kPipeOut = 4;  // output pairs per thread and window (float filters)
 
 template <int F, typename T>
 __global__ void __launch_bounds__(kAnalyzeThreads) analyze_pipe_kernel(const void *__restrict__ y_in, int64_t N, int J,
@@ -586,6 +616,55 @@ __global__ void __launch_bounds__(kAnalyzeThreads) analyze_pipe_kernel(const voi
             const T *in = (l & 1) ? reinterpret_cast<const T *>(cur) : W;
             EnAcc en;
             long long eni = 0;
+            if constexpr (!INT) {
+                // kPipeOut consecutive output pairs per thread from one window
+                constexpr int P = kPipeOut, R = 2, M = P + 2 * R;
+                constexpr bool D4 = (F == SIDWT_D4);
+                const float4 *q = reinterpret_cast<const float4 *>(in);
+                float2 *po = reinterpret_cast<float2 *>(out);
+                const bool even_h = (H & 1) == 0;
+                for (int n0 = tid * P; n0 < H; n0 += blockDim.x * P) {
+                    float2 E[M], O[M];
+                    float4 prev = D4 ? q[wrap_small(n0 - R - 1, H)] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int i = 0; i < M; ++i) {
+                        const float4 cur = q[wrap_small(n0 - R + i, H)];
+                        E[i] = make_float2(cur.x, cur.y);
+                        O[i] = D4 ? make_float2(prev.z, prev.w) : make_float2(cur.z, cur.w);  // D4 odd phase: v[2m-1]
+                        prev = cur;
+                    }
+                    lift_window_m<F, SIDE_Y, M>(E, O, c);
+                    float2 lo[P], hi[P];
+#pragma unroll
+                    for (int i = 0; i < P; ++i) {
+                        lo[i] = scale2(c.ce, E[R + i]);
+                        hi[i] = D4 ? scale2(c.co, make_float2(E[R + i].x + O[R + i - 1].x, E[R + i].y + O[R + i - 1].y))
+                                   : scale2(c.co, O[R + i]);
+                    }
+                    if (n0 + P <= H && even_h) {
+#pragma unroll
+                        for (int i = 0; i < P; i += 2) {
+                            const float4 l4 = make_float4(lo[i].x, lo[i].y, lo[i + 1].x, lo[i + 1].y);
+                            const float4 h4 = make_float4(hi[i].x, hi[i].y, hi[i + 1].x, hi[i + 1].y);
+                            *reinterpret_cast<float4 *>(pf + off + n0 + i) = l4;
+                            *reinterpret_cast<float4 *>(pf + off + H + n0 + i) = h4;
+                            *reinterpret_cast<float4 *>(po + n0 + i) = l4;
+                            en.add(sq2(lo[i]));
+                            en.add(sq2(lo[i + 1]));
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < P; ++i) {
+                            if (n0 + i < H) {
+                                pf[off + n0 + i] = lo[i];
+                                pf[off + H + n0 + i] = hi[i];
+                                po[n0 + i] = lo[i];
+                                en.add(sq2(lo[i]));
+                            }
+                        }
+                    }
+                }
+            } else
             for (int n = tid; n < H; n += blockDim.x) {
                 T lo, hi;
                 if constexpr (INT) {
