@@ -531,7 +531,9 @@ __device__ __forceinline__ void out_pair_i16(const short2 *in, int H, int n, int
 }
 
 constexpr int kPipeMaxLevels = 16;
-constexpr int kPipeOut = 4;  // output pairs per thread and window (float filters)
+// output pairs per thread and window (float filters); odd, so that the
+// threads' 16-byte window loads (stride 16 kPipeOut bytes) hit distinct banks
+constexpr int kPipeOut = 3;
 
 template <int F, typename T>
 __global__ void __launch_bounds__(kAnalyzeThreads) analyze_pipe_kernel(const void *__restrict__ y_in, int64_t N, int J,
@@ -622,7 +624,6 @@ __global__ void __launch_bounds__(kAnalyzeThreads) analyze_pipe_kernel(const voi
                 constexpr bool D4 = (F == SIDWT_D4);
                 const float4 *q = reinterpret_cast<const float4 *>(in);
                 float2 *po = reinterpret_cast<float2 *>(out);
-                const bool even_h = (H & 1) == 0;
                 for (int n0 = tid * P; n0 < H; n0 += blockDim.x * P) {
                     float2 E[M], O[M];
                     float4 prev = D4 ? q[wrap_small(n0 - R - 1, H)] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -641,26 +642,13 @@ __global__ void __launch_bounds__(kAnalyzeThreads) analyze_pipe_kernel(const voi
                         hi[i] = D4 ? scale2(c.co, make_float2(E[R + i].x + O[R + i - 1].x, E[R + i].y + O[R + i - 1].y))
                                    : scale2(c.co, O[R + i]);
                     }
-                    if (n0 + P <= H && even_h) {
 #pragma unroll
-                        for (int i = 0; i < P; i += 2) {
-                            const float4 l4 = make_float4(lo[i].x, lo[i].y, lo[i + 1].x, lo[i + 1].y);
-                            const float4 h4 = make_float4(hi[i].x, hi[i].y, hi[i + 1].x, hi[i + 1].y);
-                            *reinterpret_cast<float4 *>(pf + off + n0 + i) = l4;
-                            *reinterpret_cast<float4 *>(pf + off + H + n0 + i) = h4;
-                            *reinterpret_cast<float4 *>(po + n0 + i) = l4;
+                    for (int i = 0; i < P; ++i) {
+                        if (n0 + i < H) {
+                            pf[off + n0 + i] = lo[i];
+                            pf[off + H + n0 + i] = hi[i];
+                            po[n0 + i] = lo[i];
                             en.add(sq2(lo[i]));
-                            en.add(sq2(lo[i + 1]));
-                        }
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < P; ++i) {
-                            if (n0 + i < H) {
-                                pf[off + n0 + i] = lo[i];
-                                pf[off + H + n0 + i] = hi[i];
-                                po[n0 + i] = lo[i];
-                                en.add(sq2(lo[i]));
-                            }
                         }
                     }
                 }
