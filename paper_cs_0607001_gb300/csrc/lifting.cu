@@ -531,9 +531,9 @@ __device__ __forceinline__ void out_pair_i16(const short2 *in, int H, int n, int
 }
 
 constexpr int kPipeMaxLevels = 16;
-// output pairs per thread and window (float filters); odd, so that the
-// threads' 16-byte window loads (stride 16 kPipeOut bytes) hit distinct banks
-constexpr int kPipeOut = 3;
+// output pairs per thread and window (float filters); 1 keeps the threads'
+// window loads and pyramid stores unit-stride (measured fastest)
+constexpr int kPipeOut = 1;
 
 template <int F, typename T>
 __global__ void __launch_bounds__(kAnalyzeThreads) analyze_pipe_kernel(const void *__restrict__ y_in, int64_t N, int J,
