@@ -189,35 +189,6 @@ __device__ __forceinline__ void lift_window(float2 (&E)[2 * R + 1], float2 (&O)[
     }
 }
 
-// The same steps on M consecutive pairs: afterwards entries [R, M - R) are
-// exact for a filter whose steps consume R neighbours on each side (several
-// outputs share one window).
-template <int F, int S, int M>
-__device__ __forceinline__ void lift_window_m(float2 (&E)[M], float2 (&O)[M], const LiftCoef &c) {
-    using Sh = LiftShape<F, S>;
-#pragma unroll
-    for (int s = 0; s < Sh::nsteps; ++s) {
-        const float c0 = c.c0[s], c1 = c.c1[s];
-        if (Sh::target(s) == 1) {
-            if (Sh::nb(s) > 0) {
-#pragma unroll
-                for (int i = 0; i < M - 1; ++i) O[i] = axpy2(O[i], c0, E[i], c1, E[i + 1]);
-            } else {
-#pragma unroll
-                for (int i = M - 1; i >= 1; --i) O[i] = axpy2(O[i], c0, E[i], c1, E[i - 1]);
-            }
-        } else {
-            if (Sh::nb(s) > 0) {
-#pragma unroll
-                for (int i = 0; i < M - 1; ++i) E[i] = axpy2(E[i], c0, O[i], c1, O[i + 1]);
-            } else {
-#pragma unroll
-                for (int i = M - 1; i >= 1; --i) E[i] = axpy2(E[i], c0, O[i], c1, O[i - 1]);
-            }
-        }
-    }
-}
-
 template <int S, int R>
 __device__ __forceinline__ void int53_window(int2 (&E)[2 * R + 1], int2 (&O)[2 * R + 1]) {
     if (S == SIDE_X) {
@@ -385,9 +356,10 @@ __device__ __forceinline__ void out_pair_f(const float2 *in, int H, int n, const
 __device__ __forceinline__ void out_pair_i(const int2 *in, int H, int n, int2 &lo, int2 &hi) {
     const int4 *q = reinterpret_cast<const int4 *>(in);
     int2 E[5], O[5];
+    const bool interior = n >= 2 && n + 2 < H;
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        const int4 cur = q[wrap_small(n - 2 + i, H)];
+        const int4 cur = q[interior ? n - 2 + i : wrap_small(n - 2 + i, H)];
         E[i] = make_int2(cur.x, cur.y);
         O[i] = make_int2(cur.z, cur.w);
     }
@@ -519,9 +491,10 @@ __device__ __forceinline__ void pipe_load(void *dst, const void *src, uint32_t b
 __device__ __forceinline__ void out_pair_i16(const short2 *in, int H, int n, int2 &lo, int2 &hi) {
     const short4 *q = reinterpret_cast<const short4 *>(in);
     int2 E[5], O[5];
+    const bool interior = n >= 2 && n + 2 < H;
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        const short4 cur = q[wrap_small(n - 2 + i, H)];
+        const short4 cur = q[interior ? n - 2 + i : wrap_small(n - 2 + i, H)];
         E[i] = make_int2(cur.x, cur.y);
         O[i] = make_int2(cur.z, cur.w);
     }
@@ -531,9 +504,6 @@ __device__ __forceinline__ void out_pair_i16(const short2 *in, int H, int n, int
 }
 
 constexpr int kPipeMaxLevels = 16;
-// output pairs per thread and window (float filters); 1 keeps the threads'
-// window loads and pyramid stores unit-stride (measured fastest)
-constexpr int kPipeOut = 1;
 
 template <int F, typename T>
 __global__ void __launch_bounds__(kAnalyzeThreads) analyze_pipe_kernel(const void *__restrict__ y_in, int64_t N, int J,
@@ -597,11 +567,12 @@ __global__ void __launch_bounds__(kAnalyzeThreads) analyze_pipe_kernel(const voi
                 if (lane == 0) redi[0][warp] = eni;
             } else {
                 const float4 *q = reinterpret_cast<const float4 *>(cur);
+                float ens = 0.f;
                 for (int n = tid; n < Nh; n += blockDim.x) {
                     const float4 v = q[n];
-                    en.add(sq2(make_float2(v.x, v.y)));
-                    en.add(sq2(make_float2(v.z, v.w)));
+                    ens = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, ens))));
                 }
+                en.add(ens);
                 for (int o = 16; o > 0; o >>= 1) {
                     EnAcc t;
                     t.hi = __shfl_xor_sync(0xffffffffu, en.hi, o);
@@ -619,39 +590,44 @@ __global__ void __launch_bounds__(kAnalyzeThreads) analyze_pipe_kernel(const voi
             EnAcc en;
             long long eni = 0;
             if constexpr (!INT) {
-                // kPipeOut consecutive output pairs per thread from one window
-                constexpr int P = kPipeOut, R = 2, M = P + 2 * R;
+                // one output pair per thread and window; interior windows skip the
+                // periodic wrap, and the energy is a plain per-thread sum (at most
+                // a few dozen terms) made exact-ish by the compensated warp reduction
                 constexpr bool D4 = (F == SIDWT_D4);
                 const float4 *q = reinterpret_cast<const float4 *>(in);
                 float2 *po = reinterpret_cast<float2 *>(out);
-                for (int n0 = tid * P; n0 < H; n0 += blockDim.x * P) {
-                    float2 E[M], O[M];
-                    float4 prev = D4 ? q[wrap_small(n0 - R - 1, H)] : make_float4(0.f, 0.f, 0.f, 0.f);
+                float2 *pl = pf + off, *ph = pf + off + H;
+                float ens = 0.f;
+                for (int n = tid; n < H; n += blockDim.x) {
+                    float2 E[5], O[5];
+                    if (n >= 3 && n + 2 < H) {
+                        float4 prev = D4 ? q[n - 3] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                    for (int i = 0; i < M; ++i) {
-                        const float4 cur = q[wrap_small(n0 - R + i, H)];
-                        E[i] = make_float2(cur.x, cur.y);
-                        O[i] = D4 ? make_float2(prev.z, prev.w) : make_float2(cur.z, cur.w);  // D4 odd phase: v[2m-1]
-                        prev = cur;
-                    }
-                    lift_window_m<F, SIDE_Y, M>(E, O, c);
-                    float2 lo[P], hi[P];
+                        for (int i = 0; i < 5; ++i) {
+                            const float4 cur = q[n - 2 + i];
+                            E[i] = make_float2(cur.x, cur.y);
+                            O[i] = D4 ? make_float2(prev.z, prev.w) : make_float2(cur.z, cur.w);
+                            prev = cur;
+                        }
+                    } else {
+                        float4 prev = D4 ? q[wrap_small(n - 3, H)] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                    for (int i = 0; i < P; ++i) {
-                        lo[i] = scale2(c.ce, E[R + i]);
-                        hi[i] = D4 ? scale2(c.co, make_float2(E[R + i].x + O[R + i - 1].x, E[R + i].y + O[R + i - 1].y))
-                                   : scale2(c.co, O[R + i]);
-                    }
-#pragma unroll
-                    for (int i = 0; i < P; ++i) {
-                        if (n0 + i < H) {
-                            pf[off + n0 + i] = lo[i];
-                            pf[off + H + n0 + i] = hi[i];
-                            po[n0 + i] = lo[i];
-                            en.add(sq2(lo[i]));
+                        for (int i = 0; i < 5; ++i) {
+                            const float4 cur = q[wrap_small(n - 2 + i, H)];
+                            E[i] = make_float2(cur.x, cur.y);
+                            O[i] = D4 ? make_float2(prev.z, prev.w) : make_float2(cur.z, cur.w);  // D4 odd phase: v[2m-1]
+                            prev = cur;
                         }
                     }
+                    lift_window<F, SIDE_Y, 2>(E, O, c);
+                    const float2 lo = scale2(c.ce, E[2]);
+                    const float2 hi = D4 ? scale2(c.co, make_float2(E[2].x + O[1].x, E[2].y + O[1].y)) : scale2(c.co, O[2]);
+                    pl[n] = lo;
+                    ph[n] = hi;
+                    po[n] = lo;
+                    ens = fmaf(lo.x, lo.x, fmaf(lo.y, lo.y, ens));
                 }
+                en.add(ens);
             } else
             for (int n = tid; n < H; n += blockDim.x) {
                 T lo, hi;
