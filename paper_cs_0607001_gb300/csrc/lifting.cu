@@ -504,9 +504,10 @@ __device__ __forceinline__ void out_pair_i16(const short2 *in, int H, int n, int
 }
 
 constexpr int kPipeMaxLevels = 16;
+constexpr int kPipeThreads = 1024;  // one CTA per SM holds two pulses: all 32 warps hide the window latency
 
 template <int F, typename T>
-__global__ void __launch_bounds__(kAnalyzeThreads) analyze_pipe_kernel(const void *__restrict__ y_in, int64_t N, int J,
+__global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *__restrict__ y_in, int64_t N, int J,
                                                                        int64_t B, float2 *__restrict__ pyr_f,
                                                                        int2 *__restrict__ pyr_i, int64_t pyr_elems,
                                                                        double *__restrict__ yen, LiftCoef c,
@@ -515,8 +516,8 @@ __global__ void __launch_bounds__(kAnalyzeThreads) analyze_pipe_kernel(const voi
     constexpr int IN_BYTES = INT ? 4 : 8;
     extern __shared__ __align__(16) unsigned char smraw[];  // 16-byte aligned: enough for the bulk copies
     __shared__ __align__(8) uint64_t bar[2];
-    __shared__ float2 redf[kPipeMaxLevels][kAnalyzeThreads / 32];
-    __shared__ long long redi[kPipeMaxLevels][kAnalyzeThreads / 32];
+    __shared__ float2 redf[kPipeMaxLevels][kPipeThreads / 32];
+    __shared__ long long redi[kPipeMaxLevels][kPipeThreads / 32];
     __shared__ int sfail;
     const uint32_t bytes = (uint32_t)(N * IN_BYTES);
     const size_t inb = ((size_t)bytes + 127) & ~(size_t)127;
@@ -742,8 +743,8 @@ __global__ void pyr_energy_kernel(const float2 *__restrict__ y, const float2 *__
 // Host launchers
 // ---------------------------------------------------------------------------
 static constexpr int kSmemLimit = 227 * 1024 - 1024;  // dynamic budget; 1 KB left for static shared memory
-// the pipelined kernel's static shared memory: barriers and 2 x 16 x 16 partial energies
-static constexpr int kPipeSmemLimit = 227 * 1024 - 8 * 1024;
+// the pipelined kernel's static shared memory: barriers and 2 x 16 x 32 partial energies
+static constexpr int kPipeSmemLimit = 227 * 1024 - 10 * 1024;
 
 template <int F, typename TIn>
 static void launch_level_f(int side, const TIn *in, int64_t in_stride, int nrows, int nchild, int64_t K,
@@ -878,23 +879,23 @@ sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStre
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int per_sm = std::max(1, (int)((size_t)(228 * 1024) / (pipe_smem + 8 * 1024)));
+        const int per_sm = std::max(1, std::min(2048 / kPipeThreads, (int)((size_t)(228 * 1024) / (pipe_smem + 10 * 1024))));
         const int64_t grid = std::min<int64_t>(B, (int64_t)sms * per_sm);
         switch (p->filter) {
         case SIDWT_D4:
-            analyze_pipe_kernel<SIDWT_D4, float2><<<(unsigned)grid, kAnalyzeThreads, pipe_smem, s>>>(
+            analyze_pipe_kernel<SIDWT_D4, float2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
                 y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err);
             break;
         case SIDWT_LEGALL53:
-            analyze_pipe_kernel<SIDWT_LEGALL53, float2><<<(unsigned)grid, kAnalyzeThreads, pipe_smem, s>>>(
+            analyze_pipe_kernel<SIDWT_LEGALL53, float2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
                 y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err);
             break;
         case SIDWT_CDF97:
-            analyze_pipe_kernel<SIDWT_CDF97, float2><<<(unsigned)grid, kAnalyzeThreads, pipe_smem, s>>>(
+            analyze_pipe_kernel<SIDWT_CDF97, float2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
                 y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err);
             break;
         default:
-            analyze_pipe_kernel<SIDWT_LEGALL53_INT, int2><<<(unsigned)grid, kAnalyzeThreads, pipe_smem, s>>>(
+            analyze_pipe_kernel<SIDWT_LEGALL53_INT, int2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
                 y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err);
             break;
         }
