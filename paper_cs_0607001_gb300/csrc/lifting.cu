@@ -504,14 +504,14 @@ __device__ __forceinline__ void out_pair_i16(const short2 *in, int H, int n, int
 }
 
 constexpr int kPipeMaxLevels = 16;
-constexpr int kPipeThreads = 1024;  // one CTA per SM holds two pulses: all 32 warps hide the window latency
+constexpr int kPipeThreads = 512;
 
 template <int F, typename T>
 __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *__restrict__ y_in, int64_t N, int J,
                                                                        int64_t B, float2 *__restrict__ pyr_f,
                                                                        int2 *__restrict__ pyr_i, int64_t pyr_elems,
                                                                        double *__restrict__ yen, LiftCoef c,
-                                                                       int32_t *__restrict__ err) {
+                                                                       int32_t *__restrict__ err, int nbuf) {
     constexpr bool INT = (F == SIDWT_LEGALL53_INT);
     constexpr int IN_BYTES = INT ? 4 : 8;
     extern __shared__ __align__(16) unsigned char smraw[];  // 16-byte aligned: enough for the bulk copies
@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
     const uint32_t bytes = (uint32_t)(N * IN_BYTES);
     const size_t inb = ((size_t)bytes + 127) & ~(size_t)127;
     unsigned char *const buf0 = smraw, *const buf1 = smraw + inb;
-    T *W = reinterpret_cast<T *>(smraw + 2 * inb);
+    T *W = reinterpret_cast<T *>(smraw + nbuf * inb);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int Nh = (int)(N / 2);
     const char *y = reinterpret_cast<const char *>(y_in);
@@ -539,15 +539,24 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
     int i = 0;
     int64_t issued = 1, landed = 0;  // copies issued / waited for (thread 0's bookkeeping)
     for (int64_t b = blockIdx.x; b < B; b += G, ++i) {
-        const int s = i & 1;
+        // two buffers: pulse i in buffer i % 2, the next one loading meanwhile;
+        // one buffer: pulse i loads once pulse i - 1 is done (other CTAs on the
+        // SM overlap it)
+        const int s = nbuf == 2 ? (i & 1) : 0;
         unsigned char *const cur = s ? buf1 : buf0;
-        if (tid == 0 && b + G < B) {
-            // the other buffer held the previous pulse, whose reads and writes ended at the last barrier
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            pipe_load(s ? buf0 : buf1, y + (b + G) * (int64_t)bytes, bytes, &bar[s ^ 1]);
-            ++issued;
+        if (tid == 0) {
+            // the buffer written next held a finished pulse, whose accesses ended at the last barrier
+            if (nbuf == 2 && b + G < B) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                pipe_load(s ? buf0 : buf1, y + (b + G) * (int64_t)bytes, bytes, &bar[s ^ 1]);
+                ++issued;
+            } else if (nbuf == 1 && i > 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                pipe_load(buf0, y + b * (int64_t)bytes, bytes, &bar[0]);
+                ++issued;
+            }
         }
-        if (!pipe_wait(&bar[s], (uint32_t)((i >> 1) & 1))) sfail = 1;
+        if (!pipe_wait(&bar[s], (uint32_t)(nbuf == 2 ? ((i >> 1) & 1) : (i & 1)))) sfail = 1;
         __syncthreads();
         if (sfail) break;
         if (tid == 0) ++landed;
@@ -685,7 +694,8 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
     }
     if (tid == 0 && sfail) {
         // let this CTA's own copies land before its shared memory is released
-        for (int64_t k = landed; k < issued; ++k) pipe_wait(&bar[k & 1], (uint32_t)((k >> 1) & 1));
+        for (int64_t k = landed; k < issued; ++k)
+            pipe_wait(&bar[nbuf == 2 ? (k & 1) : 0], (uint32_t)(nbuf == 2 ? ((k >> 1) & 1) : (k & 1)));
         atomicOr(err, 2);
     }
 }
@@ -743,8 +753,8 @@ __global__ void pyr_energy_kernel(const float2 *__restrict__ y, const float2 *__
 // Host launchers
 // ---------------------------------------------------------------------------
 static constexpr int kSmemLimit = 227 * 1024 - 1024;  // dynamic budget; 1 KB left for static shared memory
-// the pipelined kernel's static shared memory: barriers and 2 x 16 x 32 partial energies
-static constexpr int kPipeSmemLimit = 227 * 1024 - 10 * 1024;
+// the pipelined kernel's static shared memory: barriers and 2 x 16 x 16 partial energies
+static constexpr int kPipeSmemLimit = 227 * 1024 - 8 * 1024;
 
 template <int F, typename TIn>
 static void launch_level_f(int side, const TIn *in, int64_t in_stride, int nrows, int nchild, int64_t K,
@@ -873,30 +883,35 @@ sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStre
     const size_t smem = (size_t)(N + N / 2) * 8;
     cudaError_t e = cudaSuccess;
     const size_t in_bytes = (size_t)N * (p->is_int ? 4 : 8);
-    const size_t pipe_smem = 2 * ((in_bytes + 127) & ~(size_t)127) + (size_t)(N / 2) * 8;
+    // one input buffer when two CTAs then fit on an SM (each overlaps the
+    // other's loads), else two buffers and a prefetch within the CTA
+    const size_t inb = (in_bytes + 127) & ~(size_t)127;
+    const size_t one_smem = inb + (size_t)(N / 2) * 8;
+    const int nbuf = 2 * (one_smem + 9 * 1024) <= (size_t)(228 * 1024) ? 1 : 2;
+    const size_t pipe_smem = nbuf * inb + (size_t)(N / 2) * 8;
     const uintptr_t yal = reinterpret_cast<uintptr_t>(y_dev);
     if (pipe_smem <= (size_t)kPipeSmemLimit && in_bytes % 16 == 0 && yal % 16 == 0 && J < kPipeMaxLevels) {
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int per_sm = std::max(1, std::min(2048 / kPipeThreads, (int)((size_t)(228 * 1024) / (pipe_smem + 10 * 1024))));
+        const int per_sm = std::max(1, std::min(2048 / kPipeThreads, (int)((size_t)(228 * 1024) / (pipe_smem + 9 * 1024))));
         const int64_t grid = std::min<int64_t>(B, (int64_t)sms * per_sm);
         switch (p->filter) {
         case SIDWT_D4:
             analyze_pipe_kernel<SIDWT_D4, float2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
-                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err);
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf);
             break;
         case SIDWT_LEGALL53:
             analyze_pipe_kernel<SIDWT_LEGALL53, float2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
-                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err);
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf);
             break;
         case SIDWT_CDF97:
             analyze_pipe_kernel<SIDWT_CDF97, float2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
-                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err);
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf);
             break;
         default:
             analyze_pipe_kernel<SIDWT_LEGALL53_INT, int2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
-                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err);
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf);
             break;
         }
         e = cudaGetLastError();
