@@ -883,11 +883,14 @@ sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStre
     const size_t smem = (size_t)(N + N / 2) * 8;
     cudaError_t e = cudaSuccess;
     const size_t in_bytes = (size_t)N * (p->is_int ? 4 : 8);
-    // one input buffer when two CTAs then fit on an SM (each overlaps the
-    // other's loads), else two buffers and a prefetch within the CTA
+    // two CTAs per SM with two input buffers each (prefetch within the CTA)
+    // when they fit; else two CTAs with one buffer (each overlaps the other's
+    // loads); else one CTA with two buffers
     const size_t inb = (in_bytes + 127) & ~(size_t)127;
     const size_t one_smem = inb + (size_t)(N / 2) * 8;
-    const int nbuf = 2 * (one_smem + 9 * 1024) <= (size_t)(228 * 1024) ? 1 : 2;
+    const size_t two_smem = one_smem + inb;
+    const size_t sm_bytes = 228 * 1024, per_cta = 9 * 1024;
+    const int nbuf = 2 * (two_smem + per_cta) <= sm_bytes ? 2 : (2 * (one_smem + per_cta) <= sm_bytes ? 1 : 2);
     const size_t pipe_smem = nbuf * inb + (size_t)(N / 2) * 8;
     const uintptr_t yal = reinterpret_cast<uintptr_t>(y_dev);
     if (pipe_smem <= (size_t)kPipeSmemLimit && in_bytes % 16 == 0 && yal % 16 == 0 && J < kPipeMaxLevels) {
