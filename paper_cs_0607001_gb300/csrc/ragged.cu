@@ -241,6 +241,78 @@ __global__ void plan_items_kernel(const int32_t *__restrict__ ref_ids, int B, in
                     (int64_t)b * (J + 1), ok ? N : 0, J, r, 0};
 }
 
+// Latency path for a few short pulses of a plan: every (pulse, scale,
+// variant, block of 32 delays) is its own CTA, and its 8 warps split the
+// contraction (k) into 8 slices, so that even one pulse spreads over the
+// whole GPU.  r_j[2^l q + v] = sum_k conj(w_v[(k - q) mod K']) u[k] per band
+// (eq. 20 / 20a with the variant delayed by q).
+struct LatScale {
+    int32_t j, lev, Kp, nv, nqb, first;
+};
+struct LatTable {
+    LatScale t[16];
+    int n;
+};
+constexpr int kLatMaxN = 8192;
+
+__global__ void __launch_bounds__(256) corr_latency_kernel(const float2 *__restrict__ tree, int64_t tree_elems,
+                                                           const float2 *__restrict__ pyr, int64_t pyr_elems,
+                                                           const int32_t *__restrict__ ref_ids, int nrefs, int64_t N,
+                                                           int J, LatTable tab, unsigned long long *__restrict__ keys,
+                                                           float2 *__restrict__ R) {
+    __shared__ float2 part[8][33];
+    const int b = blockIdx.y;
+    const int ref = ref_ids[b];
+    if (ref < 0 || ref >= nrefs) return;  // invalid pulse: its keys stay 0 (lag -1)
+    const int task = blockIdx.x;
+    int k = 0;
+    while (k + 1 < tab.n && task >= tab.t[k + 1].first) ++k;
+    const LatScale z = tab.t[k];
+    const int local = task - z.first;
+    const int v = local / z.nqb, qb = local % z.nqb;
+    const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+    const int q = qb * 32 + lane;
+    const int Kp = z.Kp;
+    const int nb = z.j < J ? 2 : 1;
+    const int K = nb * Kp;
+    const float2 *u0 = pyr + (int64_t)b * pyr_elems + 2 * N - 4 * (int64_t)Kp;
+    const float2 *w0 = tree + (int64_t)ref * tree_elems + 2 * N * (int64_t)(z.lev - 1) + (int64_t)v * Kp;
+    const int per = (K + 7) / 8;
+    const int k0 = slice * per, k1 = min(K, k0 + per);
+    const int qq = q < Kp ? q : 0;
+    float ar = 0.f, ai = 0.f;
+    for (int kk = k0; kk < k1; ++kk) {
+        const int band = kk >= Kp ? 1 : 0;
+        int idx = kk - band * Kp - qq;
+        if (idx < 0) idx += Kp;
+        const float2 wv = w0[(int64_t)band * N + idx];
+        const float2 uv = u0[kk];
+        ar = fmaf(wv.x, uv.x, fmaf(wv.y, uv.y, ar));
+        ai = fmaf(wv.x, uv.y, fmaf(-wv.y, uv.x, ai));
+    }
+    part[slice][lane] = make_float2(ar, ai);
+    __syncthreads();
+    if (slice == 0) {
+        float sr = 0.f, si = 0.f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            sr += part[i][lane].x;
+            si += part[i][lane].y;
+        }
+        unsigned long long key = 0ull;
+        if (q < Kp) {
+            const uint32_t D = ((uint32_t)q << z.lev) + (uint32_t)v;
+            key = peak_key(make_float2(sr, si), D);
+            if (R) R[((int64_t)b * (J + 1) + z.j) * N + D] = make_float2(sr, si);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, key, o);
+            key = t > key ? t : key;
+        }
+        if (lane == 0 && key) atomicMax(&keys[(int64_t)b * (J + 1) + z.j], key);
+    }
+}
+
 __global__ void fill_kernel(float2 *x, int64_t n, uint32_t seed) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -745,7 +817,28 @@ sidwt_status prepare_small(sidwt_plan *p, int64_t B) {
     return SIDWT_OK;
 }
 
+int small_launch_count(const sidwt_plan *p) { return p->N <= rg::kLatMaxN && p->J < 16 ? 1 : 2; }
+
 sidwt_status correlate_small(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t B, float2 *R, cudaStream_t s) {
+    if (p->N <= rg::kLatMaxN && p->J < 16) {
+        rg::LatTable tab;
+        std::memset(&tab, 0, sizeof(tab));
+        int total = 0;
+        for (int j = 0; j <= p->J; ++j) {
+            rg::LatScale &z = tab.t[tab.n++];
+            z.j = j;
+            z.lev = j < p->J ? j + 1 : p->J;
+            z.Kp = (int32_t)(p->N >> z.lev);
+            z.nv = 1 << z.lev;
+            z.nqb = (z.Kp + 31) / 32;
+            z.first = total;
+            total += z.nv * z.nqb;
+        }
+        rg::corr_latency_kernel<<<dim3((unsigned)total, (unsigned)B), 256, 0, s>>>(
+            p->tree_f, p->tree_elems, p->pyr_f, p->pyr_elems, ref_ids_dev, p->nrefs, p->N, p->J, tab, p->keys, R);
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "small-batch correlation launch");
+    }
     PlanSmall *ps = static_cast<PlanSmall *>(p->small);
     if (!ps || ps->built_B != B) {
         set_error("small-batch work list not prepared");

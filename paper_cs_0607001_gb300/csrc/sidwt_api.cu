@@ -415,7 +415,7 @@ sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const vo
     cudaError_t e = cudaMemsetAsync(p->keys, 0, B * (p->J + 1) * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
     {
-        StageTimer t(p, 3, s, small ? 2 : (tc ? tc_launch_count(p) : (tc32 ? tc32_launch_count(p) : 1)));
+        StageTimer t(p, 3, s, small ? small_launch_count(p) : (tc ? tc_launch_count(p) : (tc32 ? tc32_launch_count(p) : 1)));
         if (small) {
             if ((st = correlate_small(p, ref_ids_dev, B, reinterpret_cast<float2 *>(r_dev), s))) return st;
         } else if (tc) {
