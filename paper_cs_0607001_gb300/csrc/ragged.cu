@@ -259,10 +259,15 @@ __global__ void __launch_bounds__(256) corr_latency_kernel(const float2 *__restr
                                                            const float2 *__restrict__ pyr, int64_t pyr_elems,
                                                            const int32_t *__restrict__ ref_ids, int nrefs, int64_t N,
                                                            int J, LatTable tab, unsigned long long *__restrict__ keys,
-                                                           float2 *__restrict__ R) {
+                                                           float2 *__restrict__ R, int32_t *__restrict__ saved,
+                                                           int32_t *__restrict__ err) {
     __shared__ float2 part[8][33];
     const int b = blockIdx.y;
     const int ref = ref_ids[b];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // the ids the peak epilogue reads, and the error record
+        saved[b] = ref;
+        if (ref < 0 || ref >= nrefs) atomicOr(err, 1);
+    }
     if (ref < 0 || ref >= nrefs) return;  // invalid pulse: its keys stay 0 (lag -1)
     const int task = blockIdx.x;
     int k = 0;
@@ -817,10 +822,11 @@ sidwt_status prepare_small(sidwt_plan *p, int64_t B) {
     return SIDWT_OK;
 }
 
-int small_launch_count(const sidwt_plan *p) { return p->N <= rg::kLatMaxN && p->J < 16 ? 1 : 2; }
+bool small_uses_latency_kernel(const sidwt_plan *p) { return p->N <= rg::kLatMaxN && p->J < 16; }
+int small_launch_count(const sidwt_plan *p) { return small_uses_latency_kernel(p) ? 1 : 2; }
 
 sidwt_status correlate_small(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t B, float2 *R, cudaStream_t s) {
-    if (p->N <= rg::kLatMaxN && p->J < 16) {
+    if (small_uses_latency_kernel(p)) {
         rg::LatTable tab;
         std::memset(&tab, 0, sizeof(tab));
         int total = 0;
@@ -835,7 +841,8 @@ sidwt_status correlate_small(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t 
             total += z.nv * z.nqb;
         }
         rg::corr_latency_kernel<<<dim3((unsigned)total, (unsigned)B), 256, 0, s>>>(
-            p->tree_f, p->tree_elems, p->pyr_f, p->pyr_elems, ref_ids_dev, p->nrefs, p->N, p->J, tab, p->keys, R);
+            p->tree_f, p->tree_elems, p->pyr_f, p->pyr_elems, ref_ids_dev, p->nrefs, p->N, p->J, tab, p->keys, R,
+            p->ref_ids, p->err);
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "small-batch correlation launch");
     }

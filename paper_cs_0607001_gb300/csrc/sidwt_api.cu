@@ -402,8 +402,8 @@ sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const vo
     if (B == 0) return SIDWT_OK;
     if (p->timing) ++p->timed_correlate_calls;
     const bool small = B <= kSmallBatch;
-    if (small && (st = prepare_small(p, B))) return st;
-    {
+    if (small && !small_uses_latency_kernel(p) && (st = prepare_small(p, B))) return st;
+    if (!(small && small_uses_latency_kernel(p))) {
         StageTimer t(p, 1, s, 1);
         const int gt = tc ? tc_group_tile() : (tc32 ? tc32_group_tile() : simt_tile_pulses());
         if ((st = group_pulses(p, ref_ids_dev, B, gt, s))) return st;

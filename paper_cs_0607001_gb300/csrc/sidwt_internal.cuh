@@ -224,6 +224,8 @@ constexpr int64_t kSmallBatch = 16;
 sidwt_status prepare_small(sidwt_plan *p, int64_t B);
 sidwt_status correlate_small(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t B, float2 *R, cudaStream_t s);
 int small_launch_count(const sidwt_plan *p);
+// the latency kernel also records the ids and invalid-id errors (no grouping pass)
+bool small_uses_latency_kernel(const sidwt_plan *p);
 void free_small(sidwt_plan *p);
 
 // ---- corr_tc.cu ----
