@@ -362,6 +362,38 @@ sidwt_status sidwt_server_read_stats(sidwt_server *s, sidwt_server_stats *out, i
 /* Finish queued and in-flight requests, stop the thread, free everything. */
 sidwt_status sidwt_server_destroy(sidwt_server *s);
 
+/* ---------------------------------------------------------------------------
+ * Coarse-to-fine formation (Sec. IV eq. 21, Sec. V-B).
+ * ------------------------------------------------------------------------- */
+
+/* Eq. 21: one level of inverse y-side (dual) lifting -- the received
+ * pyramid's approximation c_{l-1} from its level-l bands (c_l, d_l), i.e. the
+ * synthesis that forms the finer resolution from the coarser one (perfect
+ * reconstruction of one sidwt_analyze level).  B rows; row b reads H complex64
+ * values at lo_dev + b * in_stride and at hi_dev + b * in_stride (so a
+ * pyramid level can be read in place: lo = pyramid + 2N - 4H, hi = lo + H,
+ * in_stride = the pyramid row length) and writes 2H values at
+ * out_dev + b * 2H.  Float filters only (SIDWT_EUNSUPPORTED for the integer
+ * filter); EINVAL unless 1 <= H <= 2^25, 0 <= B <= 65535, in_stride >= H and
+ * the buffers are 8-byte aligned. */
+sidwt_status sidwt_synthesize(sidwt_filter f, int64_t H, int64_t B, const void *lo_dev, const void *hi_dev,
+                              int64_t in_stride, void *out_dev, sidwt_stream stream);
+
+/* Coarse-to-fine peak search of B received pulses (Sec. V-B: the coarse scale
+ * is correlated first and the finer ones are formed from it; Sec. IV: the
+ * peak lag is the same at every scale within the scale's resolution).  Runs
+ * the received analysis, correlates scale J at every delay D (eq. 20a), and
+ * for j = J-1 down to 0 only at the delays within w_j = half_window 2^(j+1)
+ * of the scale-(j+1) peak (circularly; all delays once 2 w_j + 1 >= N),
+ * taking the largest |r_j| there (smallest delay on ties).  Per pulse about
+ * N^2 / 2^J + 4 half_window N J complex products instead of about 2 N^2.
+ * Output lag_dev int32[B][J+1] (delays; -1 for an invalid reference id,
+ * reported by sidwt_check) and mag_dev float[B][J+1] (|r_j| there).  FP32.
+ * Overwrites the plan's received pyramid; does not touch the peaks of
+ * sidwt_correlate.  EINVAL for half_window < 1. */
+sidwt_status sidwt_correlate_c2f(sidwt_plan *p, const int32_t *ref_ids_dev, const void *y_dev, int64_t B,
+                                 int half_window, int32_t *lag_dev, float *mag_dev, sidwt_stream stream);
+
 /* Diagnostic: one tcgen05 MMA (M = 128, N = 64, K = 16, bf16 in, f32 out)
  * on fixed integer-valued operands laid out exactly as the tensor-core
  * correlation lays them out (K-major A; the overlapping MN-major window as

@@ -354,6 +354,15 @@ static sidwt_status check_pulses(sidwt_plan *p, const void *y_dev, int64_t B) {
     return SIDWT_OK;
 }
 
+}  // extern "C"
+
+namespace sidwt {
+sidwt_status ensure_plan_batch(sidwt_plan *p, int64_t B) { return ensure_batch(p, std::max<int64_t>(B, 1)); }
+sidwt_status check_plan_pulses(sidwt_plan *p, const void *y_dev, int64_t B) { return check_pulses(p, y_dev, B); }
+}  // namespace sidwt
+
+extern "C" {
+
 sidwt_status sidwt_analyze(sidwt_plan *p, const void *y_dev, int64_t B, void *pyr_dev, double *energies_dev,
                            sidwt_stream stream) {
     CHECK_PLAN(p);

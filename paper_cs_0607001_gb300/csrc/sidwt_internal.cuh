@@ -189,6 +189,10 @@ struct StageTimer {
     ~StageTimer();
 };
 
+// plan workspaces and pulse-buffer checks shared with other entry points
+sidwt_status ensure_plan_batch(sidwt_plan *p, int64_t B);
+sidwt_status check_plan_pulses(sidwt_plan *p, const void *y_dev, int64_t B);
+
 // error plumbing
 void set_error(const std::string &msg);
 sidwt_status cuda_fail(cudaError_t e, const char *what);

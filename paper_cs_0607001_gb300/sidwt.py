@@ -88,6 +88,8 @@ def lib():
     L.sidwt_read_timing.argtypes = [_vp, ctypes.POINTER(Timing), ctypes.c_int]
     L.sidwt_correlate_static.argtypes = [ctypes.c_int, _i64, ctypes.c_int, _vp, _vp, _i64, _vp, _vp, _vp, _vp]
     L.sidwt_tc_selftest.argtypes = [_vp, _vp, _vp]
+    L.sidwt_synthesize.argtypes = [ctypes.c_int, _i64, _i64, _vp, _vp, _i64, _vp, _vp]
+    L.sidwt_correlate_c2f.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp]
     L.sidwt_ragged_create.argtypes = [ctypes.POINTER(_vp)]
     L.sidwt_ragged_destroy.argtypes = [_vp]
     L.sidwt_ragged_reserve.argtypes = [_vp, _i64, _i64, _i64]
@@ -295,6 +297,16 @@ class Plan:
 
     def check(self, stream=None):
         _raise(lib().sidwt_check(self._h, _stream(stream)))
+
+    def correlate_c2f(self, ref_ids: torch.Tensor, y: torch.Tensor, half_window: int = 2, stream=None):
+        """Coarse-to-fine peaks (sidwt_correlate_c2f): (lag, mag) [B][J+1]."""
+        self._check_pulses(y, True)
+        B = y.shape[0]
+        lag = torch.empty((B, self.J + 1), dtype=torch.int32, device=y.device)
+        mag = torch.empty((B, self.J + 1), dtype=torch.float32, device=y.device)
+        _raise(lib().sidwt_correlate_c2f(self._h, _ptr(ref_ids), _ptr(y), B, int(half_window), _ptr(lag), _ptr(mag),
+                                         _stream(stream)))
+        return lag, mag
 
     def reset_references(self):
         _raise(lib().sidwt_reset_references(self._h))
@@ -528,3 +540,18 @@ def as_numpy_complex(t: torch.Tensor) -> np.ndarray:
         return a.numpy().astype(np.complex128)
     a = a.numpy().astype(np.float64)
     return a[..., 0] + 1j * a[..., 1]
+
+
+def synthesize(filter, lo: torch.Tensor, hi: torch.Tensor, stream=None) -> torch.Tensor:
+    """Eq. 21 (sidwt_synthesize): c_{l-1} [B][2H] from the bands lo, hi [B][H]
+    (complex64 CUDA tensors whose rows may be strided views of one buffer)."""
+    if lo.dim() == 1:
+        lo, hi = lo[None], hi[None]
+    B, H = lo.shape
+    if lo.dtype != torch.complex64 or hi.dtype != torch.complex64 or lo.stride(1) != 1 or hi.stride(1) != 1 or \
+            lo.stride(0) != hi.stride(0):
+        raise ValueError("lo and hi: complex64 rows with unit inner stride and the same row stride")
+    out = torch.empty((B, 2 * H), dtype=torch.complex64, device=lo.device)
+    _raise(lib().sidwt_synthesize(_filter_id(filter), H, B, _ptr(lo), _ptr(hi), lo.stride(0) if B > 1 else H,
+                                  _ptr(out), _stream(stream)))
+    return out

@@ -1,0 +1,118 @@
+"""GPU parity of the coarse-to-fine formation (eq. 21 synthesis and the
+coarse-to-fine peak search of Sec. V-B) against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import coarse_to_fine as C
+from paper_cs_0607001_gb300 import inputs
+from tests import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("fname,fid", list(U.FLOAT_FILTERS.items()))
+@pytest.mark.parametrize("H", [64, 100, 3])
+def test_synthesis_matches_oracle_inverse(oracle, fname, fid, H):
+    from paper_cs_0607001_gb300 import sidwt
+    g = np.random.default_rng(H + fid)
+    B = 3
+    buf = (g.standard_normal((B, 2 * H + 5)) + 1j * g.standard_normal((B, 2 * H + 5))).astype(np.complex64)
+    d = U.to_dev_c64(buf)
+    out = sidwt.synthesize(fname, d[:, :H], d[:, H + 2:2 * H + 2]).cpu().numpy()
+    for b in range(B):
+        lo, hi = buf[b, :H].astype(np.complex128), buf[b, H + 2:2 * H + 2].astype(np.complex128)
+        exp = oracle.lift_level_inv(fid, 1, lo.real, hi.real) + 1j * oracle.lift_level_inv(fid, 1, lo.imag, hi.imag)
+        np.testing.assert_allclose(out[b], exp, rtol=0, atol=1e-5 * np.abs(exp).max())
+
+
+@pytest.mark.parametrize("fname,fid", list(U.FLOAT_FILTERS.items()))
+def test_synthesis_inverts_the_gpu_analysis(fname, fid):
+    """Perfect reconstruction on the device: every level of the received
+    pyramid synthesises back to the previous approximation."""
+    from paper_cs_0607001_gb300 import sidwt
+    N, J, B = 1024, 5, 4
+    w = U.small_batch(1, B, N, J, seed=50 + fid)
+    with sidwt.Plan(fname, N, J) as p:
+        y = U.to_dev_c64(w["y"])
+        pyr, _ = p.analyze(y)
+        prev = y
+        for l in range(1, J + 1):
+            H = N >> l
+            off = 2 * N - 4 * H
+            rec = sidwt.synthesize(fname, pyr[:, off:off + H], pyr[:, off + H:off + 2 * H])
+            ref = prev.cpu().numpy()
+            np.testing.assert_allclose(rec.cpu().numpy(), ref, rtol=0, atol=2e-5 * np.abs(ref).max())
+            prev = pyr[:, off:off + H]
+
+
+def check_c2f(lag, mag, r_or, h, what):
+    """Every step of the GPU's search is right given its own previous lag:
+    the chosen delay is a maximum of the oracle's |r_j| over the window around
+    the GPU's scale-(j+1) lag (within the FP32 tolerance), and its magnitude
+    matches the oracle's there."""
+    J = r_or.shape[0] - 1
+    N = r_or.shape[1]
+    for j in range(J, -1, -1):
+        cand = np.arange(N) if j == J else C.window(int(lag[j + 1]), h << (j + 1), N)
+        m = np.abs(r_or[j])
+        top = m[cand].max()
+        g = int(lag[j])
+        assert g in set(cand.tolist()), f"{what} scale {j}: lag {g} outside the window"
+        assert m[g] >= top * (1 - 1e-4), f"{what} scale {j}: lag {g} ({m[g]}) not a window maximum ({top})"
+        assert abs(mag[j] - m[g]) <= 2e-5 * np.abs(r_or[j]).max(), f"{what} scale {j}: magnitude"
+
+
+@pytest.mark.parametrize("fname,fid", list(U.FLOAT_FILTERS.items()))
+@pytest.mark.parametrize("N,J,h", [(1024, 4, 2), (2048, 6, 1), (640, 5, 3), (256, 2, 200)])
+def test_c2f_matches_oracle_search(oracle, fname, fid, N, J, h):
+    from paper_cs_0607001_gb300 import sidwt
+    B = 12
+    w = U.small_batch(2, B, N, J, seed=300 + N + fid)
+    with sidwt.Plan(fname, N, J) as p:
+        for x in w["refs"]:
+            p.store_reference(U.to_dev_c64(x))
+        ids = torch.from_numpy(w["ref_ids"].astype(np.int32)).to(U.dev())
+        lag, mag = p.correlate_c2f(ids, U.to_dev_c64(w["y"]), half_window=h)
+        p.check()
+        lag, mag = lag.cpu().numpy(), mag.cpu().numpy()
+    for b in range(B):
+        x = w["refs"][w["ref_ids"][b]].astype(np.complex128)
+        r_or = oracle.correlate(fid, x, w["y"][b].astype(np.complex128), J)
+        check_c2f(lag[b], mag[b], r_or, h, f"{fname} pulse {b}")
+        exp, _ = C.search(r_or, h)
+        assert lag[b, 0] == exp[0] or np.abs(r_or[0][lag[b, 0]]) >= np.abs(r_or[0]).max() * (1 - 1e-4)
+
+
+def test_c2f_finds_the_injected_delays_of_the_lfm_batch():
+    """LFM and Barker-13 echoes (N = 8192, J = 5, 0-20 dB): the coarse-to-fine
+    scale-0 lag is the injected delay and agrees with the full search."""
+    from paper_cs_0607001_gb300 import sidwt
+    w = inputs.two_ref_batch(B=512, N=8192, J=5)
+    with sidwt.Plan("cdf97", 8192, 5) as p:
+        for x in w["refs"]:
+            p.store_reference(U.to_dev_c64(x))
+        ids = torch.from_numpy(w["ref_ids"].astype(np.int32)).to(U.dev())
+        y = U.to_dev_c64(w["y"])
+        lag, _ = p.correlate_c2f(ids, y, half_window=2)
+        p.correlate(ids, y, precision="fp32")
+        full, _, _ = p.peaks(512)
+        lag, full = lag.cpu().numpy(), full.cpu().numpy()
+    assert np.mean(lag[:, 0] == w["delays"]) > 0.99
+    assert np.mean(lag[:, 0] == full[:, 0]) > 0.99
+
+
+def test_c2f_rejects_bad_arguments():
+    from paper_cs_0607001_gb300 import sidwt
+    with sidwt.Plan("legall53", 256, 3) as p:
+        p.store_reference(torch.ones(256, dtype=torch.complex64, device=U.dev()))
+        y = torch.zeros((2, 256), dtype=torch.complex64, device=U.dev())
+        with pytest.raises(sidwt.SidwtError, match="EINVAL"):
+            p.correlate_c2f(torch.zeros(2, dtype=torch.int32, device=U.dev()), y, half_window=0)
+        lag, _ = p.correlate_c2f(torch.tensor([0, 5], dtype=torch.int32, device=U.dev()), y, half_window=2)
+        assert (lag[1].cpu().numpy() == -1).all()
+        with pytest.raises(sidwt.SidwtError, match="EINVAL"):
+            p.check()
+    with pytest.raises(sidwt.SidwtError, match="EUNSUPPORTED"):
+        z = torch.zeros((1, 8), dtype=torch.complex64, device=U.dev())
+        sidwt.synthesize("legall53_int", z, z)
