@@ -5,11 +5,12 @@
 // the coarser one.  One thread per output pair runs the inverse steps on a
 // 5-pair window of the coarse bands.
 //
-// sidwt_correlate_c2f: correlate the coarsest scale J at every delay, then
-// each finer scale j only at the delays within h 2^(j+1) of the scale-(j+1)
-// peak (the peak lag is scale-invariant within the scale's resolution), so
-// the cost is about N^2 / 2^J + 4 h N J complex products per pulse instead
-// of about 2 N^2.  One CTA per pulse.
+// sidwt_correlate_c2f: correlate the coarsest scale J at every delay (the
+// batched FP32 kernel with only scale J selected), then each finer scale j
+// only at the delays within h 2^(j+1) of the scale-(j+1) peak (the peak lag
+// is scale-invariant within the scale's resolution), so the cost is about
+// N^2 / 2^J + 4 h N J complex products per pulse instead of about 2 N^2.
+// The window search runs one CTA per pulse.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -96,75 +97,37 @@ __device__ __forceinline__ unsigned long long c2f_key(float re, float im, uint32
     return ((unsigned long long)__float_as_uint(re * re + im * im) << 32) | (unsigned long long)(0xFFFFFFFFu - D);
 }
 
-__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long k, unsigned long long *red) {
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long t = __shfl_xor_sync(0xffffffffu, k, o);
-        k = t > k ? t : k;
-    }
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = k;
-    __syncthreads();
-    unsigned long long m = 0ull;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = red[w] > m ? red[w] : m;
-    return m;
-}
-
 constexpr int kC2fThreads = 256;
 
-// One pulse per CTA.  r_j[2^l q + v] = sum over the bands of
-// conj(w_v[(k - q) mod K']) u[k] (the variant delayed by q).
+// One pulse per CTA, after the scale-J correlation at every delay has left
+// its peak key in keys[b][J].  For j = J-1 down to 0 one warp per delay of
+// the window (lanes over k, coalesced):
+// r_j[2^l q + v] = sum over the bands of conj(w_v[(k - q) mod K']) u[k]
+// (the variant delayed by q).
 __global__ void __launch_bounds__(kC2fThreads) c2f_kernel(const float2 *__restrict__ tree, int64_t tree_elems,
                                                           const float2 *__restrict__ pyr, int64_t pyr_elems,
                                                           const int32_t *__restrict__ ref_ids, int nrefs, int64_t N,
-                                                          int J, int h, int32_t *__restrict__ lag,
-                                                          float *__restrict__ mag, int32_t *__restrict__ err) {
-    __shared__ unsigned long long red[kC2fThreads / 32];
+                                                          int J, int h, const unsigned long long *__restrict__ keys,
+                                                          int32_t *__restrict__ lag, float *__restrict__ mag) {
     __shared__ unsigned long long wkey[kC2fThreads / 32];
     const int b = blockIdx.x;
     const int ref = ref_ids[b];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    if (ref < 0 || ref >= nrefs) {
+    const unsigned long long kJ = keys[(int64_t)b * (J + 1) + J];
+    if (ref < 0 || ref >= nrefs || kJ == 0ull) {  // invalid pulse (recorded by the grouping pass)
         if (tid <= J) {
             lag[(int64_t)b * (J + 1) + tid] = -1;
             mag[(int64_t)b * (J + 1) + tid] = 0.f;
         }
-        if (tid == 0) atomicOr(err, 1);
         return;
     }
     const float2 *T = tree + (int64_t)ref * tree_elems;
     const float2 *P = pyr + (int64_t)b * pyr_elems;
-
-    // scale J: every delay, approximations only (eq. 20a)
-    uint32_t Dc;
-    {
-        const int lev = J;
-        const int Kp = (int)(N >> lev);
-        const float2 *u = P + 2 * N - 4 * (int64_t)Kp;
-        const float2 *A = T + 2 * N * (int64_t)(lev - 1);
-        unsigned long long best = 0ull;
-        for (int64_t D = tid; D < N; D += blockDim.x) {
-            const int q = (int)(D >> lev), v = (int)(D & ((1 << lev) - 1));
-            const float2 *w = A + (int64_t)v * Kp;
-            float ar = 0.f, ai = 0.f;
-            int idx = Kp - q;  // (k - q) mod K' at k = 0
-            if (idx == Kp) idx = 0;
-            for (int k = 0; k < Kp; ++k) {
-                const float2 wv = w[idx], uv = u[k];
-                ar = fmaf(wv.x, uv.x, fmaf(wv.y, uv.y, ar));
-                ai = fmaf(wv.x, uv.y, fmaf(-wv.y, uv.x, ai));
-                if (++idx == Kp) idx = 0;
-            }
-            const unsigned long long key = c2f_key(ar, ai, (uint32_t)D);
-            best = key > best ? key : best;
-        }
-        best = block_max_u64(best, red);
-        Dc = 0xFFFFFFFFu - (uint32_t)(best & 0xFFFFFFFFull);
-        if (tid == 0) {
-            lag[(int64_t)b * (J + 1) + J] = best ? (int32_t)Dc : -1;
-            mag[(int64_t)b * (J + 1) + J] = sqrtf(__uint_as_float((uint32_t)(best >> 32)));
-        }
+    uint32_t Dc = 0xFFFFFFFFu - (uint32_t)(kJ & 0xFFFFFFFFull);
+    if (tid == 0) {
+        lag[(int64_t)b * (J + 1) + J] = (int32_t)Dc;
+        mag[(int64_t)b * (J + 1) + J] = sqrtf(__uint_as_float((uint32_t)(kJ >> 32)));
     }
-    // finer scales: a window around the coarser peak; one warp per delay
     for (int j = J - 1; j >= 0; --j) {
         const int lev = j + 1;
         const int Kp = (int)(N >> lev);
@@ -273,10 +236,16 @@ sidwt_status sidwt_correlate_c2f(sidwt_plan *p, const int32_t *ref_ids_dev, cons
     sidwt_status st = check_plan_pulses(p, y_dev, B);
     if (st || (st = ensure_plan_batch(p, B))) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if ((st = analyze_batch(p, y_dev, B, s))) return st;
-    c2f_kernel<<<(unsigned)B, kC2fThreads, 0, s>>>(p->tree_f, p->tree_elems, p->pyr_f, p->pyr_elems, ref_ids_dev,
-                                                   p->nrefs, p->N, p->J, half_window, lag_dev, mag_dev, p->err);
-    cudaError_t e = cudaGetLastError();
+    // scale J at every delay on the FP32 correlation kernel (its peak key per
+    // pulse), then the windows of the finer scales
+    if ((st = group_pulses(p, ref_ids_dev, B, simt_tile_pulses(), s)) || (st = analyze_batch(p, y_dev, B, s)))
+        return st;
+    cudaError_t e = cudaMemsetAsync(p->keys, 0, B * (p->J + 1) * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    if ((st = correlate_simt(p, B, nullptr, s, 1u << p->J))) return st;
+    c2f_kernel<<<(unsigned)B, kC2fThreads, 0, s>>>(p->tree_f, p->tree_elems, p->pyr_f, p->pyr_elems, p->ref_ids,
+                                                   p->nrefs, p->N, p->J, half_window, p->keys, lag_dev, mag_dev);
+    e = cudaGetLastError();
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "coarse-to-fine launch");
 }
 
