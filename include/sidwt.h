@@ -394,6 +394,20 @@ sidwt_status sidwt_synthesize(sidwt_filter f, int64_t H, int64_t B, const void *
 sidwt_status sidwt_correlate_c2f(sidwt_plan *p, const int32_t *ref_ids_dev, const void *y_dev, int64_t B,
                                  int half_window, int32_t *lag_dev, float *mag_dev, sidwt_stream stream);
 
+/* Per-scale target detection (Sec. V-A, Fig. 6: point targets that a scale
+ * resolves show as separate peaks of |r_j| above a dB level; nearby targets
+ * merge at coarser scales).  r_dev: complex64[rows][N], e.g. the r_dev of
+ * sidwt_correlate ([B][J+1][N], rows = B (J+1)).  In each row, a detection is
+ * a delay D whose |r[D]| is a local maximum along the delay axis
+ * (circularly: greater than |r[D-1]|, not less than |r[D+1]|, so a flat top
+ * counts once) and at least the row's largest |r| times
+ * 10^(-threshold_db / 20).  count_dev int32[rows] receives the number of
+ * detections; lag_dev int32[rows][max_det] and mag_dev float[rows][max_det]
+ * the first max_det of them in increasing delay (|r| there).  FP32.
+ * EINVAL for negative sizes or threshold, NULL buffers. */
+sidwt_status sidwt_detect(const void *r_dev, int64_t rows, int64_t N, float threshold_db, int max_det,
+                          int32_t *count_dev, int32_t *lag_dev, float *mag_dev, sidwt_stream stream);
+
 /* Diagnostic: one tcgen05 MMA (M = 128, N = 64, K = 16, bf16 in, f32 out)
  * on fixed integer-valued operands laid out exactly as the tensor-core
  * correlation lays them out (K-major A; the overlapping MN-major window as

@@ -170,3 +170,30 @@ def ragged_batch(n: int = 10000, seed: int = 4, n_lo: int = 256, n_hi: int = 655
         ys[off[i]:off[i] + Ni] = y
     return {"refs": refs, "y": ys, "offsets": off, "N": N, "J": J.astype(np.int64), "filter": filt,
             "delays": D, "snr_db": snr}
+
+
+# Point-target offsets (samples) and reflectivity magnitudes of the
+# multi-target echoes: a pair one sample apart, two more targets a few
+# samples away, a fifth one further off (Sec. V-A, Fig. 6 narrative).
+MT_OFFSETS = np.array([0, 1, 5, 9, -16])
+MT_GAINS = np.array([1.0, 0.8, 0.9, 0.7, 0.6])
+
+
+def multi_target(B: int = 4096, N: int = 8192, J: int = 5, TB: int = 160, snr_db: float = 20.0, seed: int = 6):
+    """Echoes of five point targets per pulse (Sec. V-A): y = sum_k s_k x
+    delayed by D0 + offset_k, plus noise at snr_db relative to the strongest
+    echo; x an LFM chirp with time-bandwidth product TB; D0 uniform, the
+    reflectivities' phases uniform."""
+    g = rng(seed, 6)
+    x = lfm(N, TB)
+    D0 = g.integers(0, N, size=B)
+    ph = np.exp(2j * np.pi * g.uniform(0, 1, size=(B, MT_OFFSETS.shape[0])))
+    n = np.arange(N)
+    y = np.zeros((B, N), np.complex128)
+    for k in range(MT_OFFSETS.shape[0]):
+        idx = (n[None, :] - (D0[:, None] + MT_OFFSETS[k])) % N
+        y += (MT_GAINS[k] * ph[:, k])[:, None] * x[idx]
+    sigma = np.sqrt(pulse_power(x) / 10.0 ** (snr_db / 10.0) / 2.0)
+    y += sigma * (g.standard_normal((B, N)) + 1j * g.standard_normal((B, N)))
+    return {"refs": to_c64(x[None, :]), "y": to_c64(y), "ref_ids": np.zeros(B, np.int32), "delays": D0,
+            "offsets": MT_OFFSETS, "N": N, "J": J}

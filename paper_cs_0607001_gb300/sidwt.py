@@ -90,6 +90,7 @@ def lib():
     L.sidwt_tc_selftest.argtypes = [_vp, _vp, _vp]
     L.sidwt_synthesize.argtypes = [ctypes.c_int, _i64, _i64, _vp, _vp, _i64, _vp, _vp]
     L.sidwt_correlate_c2f.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp]
+    L.sidwt_detect.argtypes = [_vp, _i64, _i64, ctypes.c_float, ctypes.c_int, _vp, _vp, _vp, _vp]
     L.sidwt_ragged_create.argtypes = [ctypes.POINTER(_vp)]
     L.sidwt_ragged_destroy.argtypes = [_vp]
     L.sidwt_ragged_reserve.argtypes = [_vp, _i64, _i64, _i64]
@@ -555,3 +556,19 @@ def synthesize(filter, lo: torch.Tensor, hi: torch.Tensor, stream=None) -> torch
     _raise(lib().sidwt_synthesize(_filter_id(filter), H, B, _ptr(lo), _ptr(hi), lo.stride(0) if B > 1 else H,
                                   _ptr(out), _stream(stream)))
     return out
+
+
+def detect(r: torch.Tensor, threshold_db: float = 10.0, max_det: int = 32, stream=None):
+    """Per-row detections (sidwt_detect) of complex64 correlations r[..., N]:
+    (count [...], lag [..., max_det], mag [..., max_det])."""
+    if r.dtype != torch.complex64 or not r.is_cuda or not r.is_contiguous():
+        raise ValueError("r must be a contiguous CUDA complex64 tensor")
+    lead = tuple(r.shape[:-1])
+    N = r.shape[-1]
+    rows = int(np.prod(lead)) if lead else 1
+    count = torch.empty(lead, dtype=torch.int32, device=r.device)
+    lag = torch.full(lead + (max_det,), -1, dtype=torch.int32, device=r.device)
+    mag = torch.zeros(lead + (max_det,), dtype=torch.float32, device=r.device)
+    _raise(lib().sidwt_detect(_ptr(r), rows, N, float(threshold_db), int(max_det), _ptr(count), _ptr(lag), _ptr(mag),
+                              _stream(stream)))
+    return count, lag, mag
