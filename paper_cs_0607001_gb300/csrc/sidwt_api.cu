@@ -177,6 +177,7 @@ sidwt_status prepare_kernels() {
     if (e == cudaSuccess) e = prepare_tc_kernels();
     if (e == cudaSuccess) e = rtc::prepare_kernels();
     if (e == cudaSuccess) e = prepare_tc32_kernels();
+    if (e == cudaSuccess) e = prepare_detect_kernels();
     if (e != cudaSuccess) return cuda_fail(e, "kernel shared-memory attributes");
     if (dev >= 0 && dev < 64) done[dev] = true;
     return SIDWT_OK;

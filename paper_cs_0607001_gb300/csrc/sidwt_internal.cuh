@@ -247,6 +247,7 @@ int tc32_group_tile();
 int tc32_launch_count(const sidwt_plan *p);
 void free_tc32(sidwt_plan *p);
 cudaError_t prepare_tc32_kernels();
+cudaError_t prepare_detect_kernels();
 
 // ---- ragged_tc.cu: batch-of-one pairs on the tensor cores ----
 namespace rtc {

@@ -39,10 +39,11 @@ def check_row(count, lags, mags, r_or, thr, max_det, what):
     assert list(lags[:min(count, max_det)]) == sorted(lags[:min(count, max_det)])
 
 
-@pytest.mark.parametrize("thr", [10.0, 20.0])
-def test_detections_match_oracle(oracle, thr):
+@pytest.mark.parametrize("thr,N", [(10.0, 2048), (20.0, 2048), (10.0, 32768)])
+def test_detections_match_oracle(oracle, thr, N):
+    """N = 2048 rows take the shared-memory kernel, N = 32768 the streaming one."""
     from paper_cs_0607001_gb300 import sidwt
-    N, J, B = 2048, 4, 6
+    J, B = 4, 6 if N <= 2048 else 2
     w = inputs.multi_target(B=B, N=N, J=J, TB=160, snr_db=20.0, seed=9)
     with sidwt.Plan("cdf97", N, J) as p:
         p.store_reference(U.to_dev_c64(w["refs"][0]))
