@@ -110,6 +110,15 @@ sidwt_status sidwt_plan_reserve(sidwt_plan *p, int32_t max_refs, int64_t max_bat
 /* Number of stored references. */
 int32_t sidwt_plan_num_refs(const sidwt_plan *p);
 
+/* CDF 9/7 plans: use the member of the 9/7 family with free parameter t
+ * (Sec. III-C Case II: a = (1 - 2t) / (4 (t - 1)), b = -(t - 1)^2,
+ * g = 1 / (4 t (t - 1)), d = t^3 - (7/4) t^2 + t, x = sqrt(2) / t; t = 5/4
+ * gives Table I, t = 0 restores it).  Both sides use the same t, so the
+ * dual pairing and perfect reconstruction hold for every t.  EINVAL unless
+ * the plan is CDF 9/7 and 0.780 < t < 1.852, t != 1; EBUSY once a reference
+ * is stored. */
+sidwt_status sidwt_plan_set_cdf97_t(sidwt_plan *p, double t);
+
 /* Store a matching signal x (Sec. II eq. 5, Fig. 1 and 5): computes its SIDWT
  * tree -- for every level l = 1..J and variant v < 2^l, the level-l
  * approximation A and detail B of x delayed by v -- and the FP64 energies

@@ -91,6 +91,14 @@ def _check(rc):
     return rc
 
 
+def set_cdf97_t(t: float) -> None:
+    """Select the CDF 9/7 member with free parameter t (Sec. III-C Case II)
+    for every later 9/7 call of this process; t = 0 restores Table I."""
+    L = lib()
+    L.oracle_set_cdf97_t.argtypes = [ctypes.c_double]
+    _check(L.oracle_set_cdf97_t(float(t)))
+
+
 def cdf97_constants() -> np.ndarray:
     out = np.zeros(5)
     lib().oracle_cdf97_constants(_d(out))

@@ -67,12 +67,38 @@ static int64_t floordiv(int64_t a, int64_t b) {
 /* Lifting constants.                                                        */
 /* ------------------------------------------------------------------------ */
 
-/* CDF 9/7 rational lifting parameters, Table I (t = 5/4). */
-static const double L97_A = -3.0 / 2.0;
-static const double L97_B = -1.0 / 16.0;
-static const double L97_G = 4.0 / 5.0;
-static const double L97_D = 15.0 / 32.0;
-static double l97_x(void) { return 4.0 * sqrt(2.0) / 5.0; }
+/* CDF 9/7 lifting parameters a, b, g, d and the scale x.  By default the
+ * rational values of Table I (t = 5/4); oracle_set_cdf97_t selects another
+ * member of the family of Sec. III-C Case II:
+ *   a = (1 - 2t) / (4 (t - 1)), b = -(t - 1)^2, g = 1 / (4 t (t - 1)),
+ *   d = t^3 - (7/4) t^2 + t, x = sqrt(2) / t.                                */
+static double g97[5] = {-3.0 / 2.0, -1.0 / 16.0, 4.0 / 5.0, 15.0 / 32.0, 0.0};
+static int g97_table = 1;
+#define L97_A (g97[0])
+#define L97_B (g97[1])
+#define L97_G (g97[2])
+#define L97_D (g97[3])
+static double l97_x(void) { return g97_table ? 4.0 * sqrt(2.0) / 5.0 : g97[4]; }
+
+/* t = 0 restores Table I; -1 for t = 1 (where a and g are undefined). */
+int oracle_set_cdf97_t(double t) {
+    if (t == 0.0) {
+        g97[0] = -3.0 / 2.0;
+        g97[1] = -1.0 / 16.0;
+        g97[2] = 4.0 / 5.0;
+        g97[3] = 15.0 / 32.0;
+        g97_table = 1;
+        return 0;
+    }
+    if (fabs(t - 1.0) < 1e-9 || t == 0.0) return -1;
+    g97[0] = (1.0 - 2.0 * t) / (4.0 * (t - 1.0));
+    g97[1] = -(t - 1.0) * (t - 1.0);
+    g97[2] = 1.0 / (4.0 * t * (t - 1.0));
+    g97[3] = t * t * t - 1.75 * t * t + t;
+    g97[4] = sqrt(2.0) / t;
+    g97_table = 0;
+    return 0;
+}
 
 /* Exposed so that a test can compare them with the t-formulas of Sec. III-C. */
 void oracle_cdf97_constants(double out[5]) {

@@ -57,6 +57,28 @@ LiftCoef lift_coef(int filter, int side) {
     return c;
 }
 
+// CDF 9/7 with free parameter t (Sec. III-C Case II): a = (1 - 2t) / (4 (t - 1)),
+// b = -(t - 1)^2, g = 1 / (4 t (t - 1)), d = t^3 - 7/4 t^2 + t, x = sqrt(2) / t;
+// the same step structure as Table I (t = 5/4).
+LiftCoef lift_coef_97t(double t, int side) {
+    LiftCoef c{};
+    const double a = (1.0 - 2.0 * t) / (4.0 * (t - 1.0)), b = -(t - 1.0) * (t - 1.0);
+    const double g = 1.0 / (4.0 * t * (t - 1.0)), d = t * t * t - 1.75 * t * t + t;
+    const double x = std::sqrt(2.0) / t;
+    const double st[4] = {a, b, g, d};
+    for (int s = 0; s < 4; ++s) {
+        const double v = (side == SIDE_X) ? st[s] : -st[s];
+        c.c0[s] = c.c1[s] = (float)v;
+    }
+    c.ce = (float)((side == SIDE_X) ? x : 1.0 / x);
+    c.co = (float)((side == SIDE_X) ? 1.0 / x : x);
+    return c;
+}
+
+LiftCoef plan_coef(const sidwt_plan *p, int side) {
+    return (p->filter == SIDWT_CDF97 && p->t97 != 0.0) ? lift_coef_97t(p->t97, side) : lift_coef(p->filter, side);
+}
+
 // ---------------------------------------------------------------------------
 // Small helpers
 // ---------------------------------------------------------------------------
@@ -794,7 +816,7 @@ static void launch_level_int(int side, const TIn *in, int64_t in_stride, int nro
 sidwt_status build_reference_tree(sidwt_plan *p, const void *x_dev, int32_t ref, cudaStream_t s) {
     const int64_t N = p->N;
     const int J = p->J;
-    const LiftCoef c = lift_coef(p->filter, SIDE_X);
+    const LiftCoef c = plan_coef(p, SIDE_X);
     float2 *tf = p->tree_f + (int64_t)ref * p->tree_elems;
     double *xe = p->xen + (int64_t)ref * p->xen_len;
     if (!p->is_int) {
@@ -879,7 +901,7 @@ sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStre
     if (B == 0) return SIDWT_OK;
     const int64_t N = p->N;
     const int J = p->J;
-    const LiftCoef c = lift_coef(p->filter, SIDE_Y);
+    const LiftCoef c = plan_coef(p, SIDE_Y);
     const size_t smem = (size_t)(N + N / 2) * 8;
     cudaError_t e = cudaSuccess;
     const size_t in_bytes = (size_t)N * (p->is_int ? 4 : 8);

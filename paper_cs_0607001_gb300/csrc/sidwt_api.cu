@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -363,6 +364,24 @@ sidwt_status check_plan_pulses(sidwt_plan *p, const void *y_dev, int64_t B) { re
 }  // namespace sidwt
 
 extern "C" {
+
+sidwt_status sidwt_plan_set_cdf97_t(sidwt_plan *p, double t) {
+    CHECK_PLAN(p);
+    if (p->filter != SIDWT_CDF97) {
+        set_error("the free parameter t belongs to CDF 9/7 plans");
+        return SIDWT_EINVAL;
+    }
+    if (t != 0.0 && !(t > 0.780 && t < 1.852 && std::fabs(t - 1.0) > 1e-6)) {
+        set_error("need 0.780 < t < 1.852, t != 1 (or 0 for Table I)");
+        return SIDWT_EINVAL;
+    }
+    if (p->nrefs > 0) {
+        set_error("set t before storing references");
+        return SIDWT_EBUSY;
+    }
+    p->t97 = t;
+    return SIDWT_OK;
+}
 
 sidwt_status sidwt_analyze(sidwt_plan *p, const void *y_dev, int64_t B, void *pyr_dev, double *energies_dev,
                            sidwt_stream stream) {

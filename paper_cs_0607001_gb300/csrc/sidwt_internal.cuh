@@ -77,6 +77,7 @@ struct LiftShape<SIDWT_D4, S> {
 
 // Host-side coefficient tables (double math, rounded once to float).
 LiftCoef lift_coef(int filter, int side);
+LiftCoef lift_coef_97t(double t, int side);
 
 // One pulse of a ragged batch for the lifting kernels (element offsets).
 struct RaggedLift {
@@ -117,6 +118,7 @@ struct sidwt_plan {
     int64_t N = 0;
     int J = 0;
     bool is_int = false;
+    double t97 = 0.0;  // CDF 9/7 free parameter t (0: Table I)
 
     // reference store
     int32_t nrefs = 0, cap_refs = 0;
@@ -188,6 +190,9 @@ struct StageTimer {
     StageTimer(sidwt_plan *p, int stage, cudaStream_t s, int launches);
     ~StageTimer();
 };
+
+// the plan's lifting coefficients (its filter, and t for a CDF 9/7 plan)
+LiftCoef plan_coef(const sidwt_plan *p, int side);
 
 // plan workspaces and pulse-buffer checks shared with other entry points
 sidwt_status ensure_plan_batch(sidwt_plan *p, int64_t B);

@@ -90,6 +90,7 @@ def lib():
     L.sidwt_tc_selftest.argtypes = [_vp, _vp, _vp]
     L.sidwt_synthesize.argtypes = [ctypes.c_int, _i64, _i64, _vp, _vp, _i64, _vp, _vp]
     L.sidwt_correlate_c2f.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp]
+    L.sidwt_plan_set_cdf97_t.argtypes = [_vp, ctypes.c_double]
     L.sidwt_detect.argtypes = [_vp, _i64, _i64, ctypes.c_float, ctypes.c_int, _vp, _vp, _vp, _vp]
     L.sidwt_ragged_create.argtypes = [ctypes.POINTER(_vp)]
     L.sidwt_ragged_destroy.argtypes = [_vp]
@@ -298,6 +299,10 @@ class Plan:
 
     def check(self, stream=None):
         _raise(lib().sidwt_check(self._h, _stream(stream)))
+
+    def set_cdf97_t(self, t: float):
+        """CDF 9/7 family member with free parameter t (0: Table I); before storing references."""
+        _raise(lib().sidwt_plan_set_cdf97_t(self._h, float(t)))
 
     def correlate_c2f(self, ref_ids: torch.Tensor, y: torch.Tensor, half_window: int = 2, stream=None):
         """Coarse-to-fine peaks (sidwt_correlate_c2f): (lag, mag) [B][J+1]."""
