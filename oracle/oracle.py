@@ -23,7 +23,7 @@ SRC = HERE / "sidwt_oracle.c"
 BUILD_DIR = HERE / "_build"
 LIB = BUILD_DIR / "libsidwt_oracle.so"
 
-D4, LEGALL53, CDF97, LEGALL53_INT = 0, 1, 2, 3
+D4, LEGALL53, CDF97, LEGALL53_INT, CDF97_INT = 0, 1, 2, 3, 4
 SIDE_X, SIDE_Y = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -130,6 +130,28 @@ def int53_level(side: int, v) -> tuple[np.ndarray, np.ndarray]:
     _check(lib().oracle_int53_level(side, v.ctypes.data_as(_i64p), K, a.ctypes.data_as(_i64p),
                                     b.ctypes.data_as(_i64p)))
     return a, b
+
+
+def int97_level(side: int, v) -> tuple[np.ndarray, np.ndarray]:
+    L = lib()
+    L.oracle_int97_level.argtypes = [ctypes.c_int, _i64p, ctypes.c_long, _i64p, _i64p]
+    v = np.ascontiguousarray(np.asarray(v, dtype=np.int64))
+    a = np.zeros(v.shape[0] // 2, np.int64)
+    b = np.zeros(v.shape[0] // 2, np.int64)
+    _check(L.oracle_int97_level(side, v.ctypes.data_as(_i64p), v.shape[0], a.ctypes.data_as(_i64p),
+                                b.ctypes.data_as(_i64p)))
+    return a, b
+
+
+def int97_level_inv(side: int, a, b) -> np.ndarray:
+    L = lib()
+    L.oracle_int97_level_inv.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_long, _i64p]
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+    b = np.ascontiguousarray(np.asarray(b, dtype=np.int64))
+    v = np.zeros(2 * a.shape[0], np.int64)
+    _check(L.oracle_int97_level_inv(side, a.ctypes.data_as(_i64p), b.ctypes.data_as(_i64p), v.shape[0],
+                                    v.ctypes.data_as(_i64p)))
+    return v
 
 
 def int53_level_inv(side: int, a, b) -> np.ndarray:

@@ -46,6 +46,7 @@
 #define OR_LEGALL53 1
 #define OR_CDF97 2
 #define OR_LEGALL53_INT 3
+#define OR_CDF97_INT 4
 
 #define OR_SIDE_X 0 /* stored (matching) signal: primal analysis P~(z^-1) */
 #define OR_SIDE_Y 1 /* received signal: dual analysis P^T(z^-1)          */
@@ -371,6 +372,74 @@ int oracle_int53_level_inv(int side, const int64_t *a, const int64_t *b, long K,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Reversible integer CDF 9/7: the steps of Table I with dyadic constants     */
+/* (a = -3/2, b = -1/16, g = 205/256 ~ 4/5, d = 15/32), each update rounded   */
+/* to the nearest integer (floor(c s + 1/2)), the diagonal scalings dropped   */
+/* (x on one side, 1/x on the other: they cancel in the pairing).            */
+/* x side (P~): o += R(a (e[n] + e[n+1])); e += R(b (o[n] + o[n-1]));       */
+/*              o += R(g (e[n] + e[n+1])); e += R(d (o[n] + o[n-1])).        */
+/* y side (P^T): e -= R(a (o[n] + o[n-1])); o -= R(b (e[n] + e[n+1]));      */
+/*              e -= R(g (o[n] + o[n-1])); o -= R(d (e[n] + e[n+1])).        */
+/* ------------------------------------------------------------------------ */
+static const int64_t I97_K[4] = {-3, -1, 205, 15}; /* numerators of a, b, g, d */
+static const int I97_M[4] = {1, 4, 8, 5};          /* denominators 2^m          */
+
+/* R(k s / 2^m) = floor((k s + 2^(m-1)) / 2^m) */
+static int64_t rdy(int64_t k, int m, int64_t s) { return floordiv(k * s + ((int64_t)1 << (m - 1)), (int64_t)1 << m); }
+
+int oracle_int97_level(int side, const int64_t *v, long K, int64_t *a, int64_t *b) {
+    if (K < 2 || (K & 1)) return -1;
+    long H = K / 2;
+    int64_t *e = malloc(sizeof(int64_t) * H), *o = malloc(sizeof(int64_t) * H);
+    for (long n = 0; n < H; ++n) {
+        e[n] = v[2 * n];
+        o[n] = v[2 * n + 1];
+    }
+    for (int s = 0; s < 4; ++s) {
+        const int odd_target = (side == OR_SIDE_X) ? (s % 2 == 0) : (s % 2 == 1);
+        const int64_t k = (side == OR_SIDE_X) ? I97_K[s] : -I97_K[s];
+        if (odd_target) { /* o[n] += R(c (e[n] + e[n+1])) */
+            for (long n = 0; n < H; ++n) o[n] += rdy(k, I97_M[s], e[n] + e[wrap(n + 1, H)]);
+        } else { /* e[n] += R(c (o[n] + o[n-1])) */
+            for (long n = 0; n < H; ++n) e[n] += rdy(k, I97_M[s], o[n] + o[wrap(n - 1, H)]);
+        }
+    }
+    for (long n = 0; n < H; ++n) {
+        a[n] = e[n];
+        b[n] = o[n];
+    }
+    free(e);
+    free(o);
+    return 0;
+}
+
+int oracle_int97_level_inv(int side, const int64_t *a, const int64_t *b, long K, int64_t *v) {
+    if (K < 2 || (K & 1)) return -1;
+    long H = K / 2;
+    int64_t *e = malloc(sizeof(int64_t) * H), *o = malloc(sizeof(int64_t) * H);
+    for (long n = 0; n < H; ++n) {
+        e[n] = a[n];
+        o[n] = b[n];
+    }
+    for (int s = 3; s >= 0; --s) {
+        const int odd_target = (side == OR_SIDE_X) ? (s % 2 == 0) : (s % 2 == 1);
+        const int64_t k = (side == OR_SIDE_X) ? I97_K[s] : -I97_K[s];
+        if (odd_target) {
+            for (long n = 0; n < H; ++n) o[n] -= rdy(k, I97_M[s], e[n] + e[wrap(n + 1, H)]);
+        } else {
+            for (long n = 0; n < H; ++n) e[n] -= rdy(k, I97_M[s], o[n] + o[wrap(n - 1, H)]);
+        }
+    }
+    for (long n = 0; n < H; ++n) {
+        v[2 * n] = e[n];
+        v[2 * n + 1] = o[n];
+    }
+    free(e);
+    free(o);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Complex helpers: real transforms on Re and Im separately (eq. 19).        */
 /* Complex vectors are interleaved (re, im) doubles.                          */
 /* ------------------------------------------------------------------------ */
@@ -385,13 +454,16 @@ static int level_complex(int filter, int side, const double *v, long K, double *
         pi[k] = v[2 * k + 1];
     }
     int rc = 0;
-    if (filter == OR_LEGALL53_INT) {
+    if (filter == OR_LEGALL53_INT || filter == OR_CDF97_INT) {
         int64_t *iv = malloc(sizeof(int64_t) * K), *ia = malloc(sizeof(int64_t) * H),
                 *ib = malloc(sizeof(int64_t) * H);
         for (int part = 0; part < 2; ++part) {
             double *src = part ? pi : pr;
             for (long k = 0; k < K; ++k) iv[k] = (int64_t)llround(src[k]);
-            oracle_int53_level(side, iv, K, ia, ib);
+            if (filter == OR_CDF97_INT)
+                oracle_int97_level(side, iv, K, ia, ib);
+            else
+                oracle_int53_level(side, iv, K, ia, ib);
             for (long n = 0; n < H; ++n) {
                 (part ? ai : ar)[n] = (double)ia[n];
                 (part ? bi : br)[n] = (double)ib[n];
@@ -429,7 +501,7 @@ static void delay_complex(const double *v, long K, long D, double *out) {
 }
 
 static int check_shape(int filter, long N, int J) {
-    if (filter < 0 || filter > 3) return -1;
+    if (filter < 0 || filter > 4) return -1;
     if (J < 1 || J > 30 || N < 2) return -1;
     if (N % (1L << J) != 0) return -1;
     return 0;
@@ -538,7 +610,7 @@ fail:
  * the level-j detail (N>>j complex), for j >= 1. */
 int oracle_delayed_analysis_x(int filter, const double *x, long N, int j, long D, double *out,
                               double *det) {
-    if (filter < 0 || filter > 3 || j < 0 || N % (1L << j) != 0) return -1;
+    if (filter < 0 || filter > 4 || j < 0 || N % (1L << j) != 0) return -1;
     double *cur = malloc(sizeof(double) * 2 * N);
     double *b = malloc(sizeof(double) * 2 * N);
     delay_complex(x, N, D, cur);

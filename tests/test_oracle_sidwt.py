@@ -13,7 +13,7 @@ import pytest
 
 from paper_cs_0607001_gb300 import inputs
 
-FILTERS = [0, 1, 2, 3]
+FILTERS = [0, 1, 2, 3, 4]
 
 
 def crand(g, n):
@@ -21,7 +21,7 @@ def crand(g, n):
 
 
 def signal_for(f, g, N):
-    if f == 3:
+    if f in (3, 4):
         return (g.integers(-2000, 2000, size=N) + 1j * g.integers(-2000, 2000, size=N)).astype(np.complex128)
     return crand(g, N)
 
@@ -71,7 +71,7 @@ def test_correlation_forms_agree_and_scale0_is_brute_force(oracle, f, N, J):
     r0 = oracle.correlate(f, x, y, J, form=0)
     r1 = oracle.correlate(f, x, y, J, form=1)
     scale = np.linalg.norm(x) * np.linalg.norm(y)
-    if f == 3:
+    if f in (3, 4):
         # integer bands: the level-(j+1) form pairs integer details whose
         # scalings cancel, but the floor rounding makes the two forms differ
         # by a rounding-sized amount
