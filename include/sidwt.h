@@ -25,6 +25,12 @@
  *                      Sec. III-C Case I; pair (v[2n], v[2n+1]).
  *   SIDWT_CDF97        CDF 9/7 with the rational Table I constants: x side
  *                      P~(z^-1), y side P^T(z^-1) of Sec. III-C Case II.
+ *   SIDWT_CDF97_INT    reversible integer 9/7: the steps of Table I with
+ *                      dyadic constants a = -3/2, b = -1/16, g = 205/256
+ *                      (~ 4/5), d = 15/32, each update rounded to the nearest
+ *                      integer (floor(c s + 1/2)), scalings dropped (x on one
+ *                      side, 1/x on the other cancel in the pairing); int16
+ *                      I/Q in, int32 coefficients, bit-exact.
  *   SIDWT_LEGALL53_INT reversible integer 5/3 (Sec. I, V-B): floor-rounded
  *                      steps, diagonal scalings dropped; inputs int16 I/Q,
  *                      coefficients int32, bit-exact.
@@ -60,7 +66,8 @@ typedef enum {
     SIDWT_D4 = 0,
     SIDWT_LEGALL53 = 1,
     SIDWT_CDF97 = 2,
-    SIDWT_LEGALL53_INT = 3
+    SIDWT_LEGALL53_INT = 3,
+    SIDWT_CDF97_INT = 4
 } sidwt_filter;
 
 typedef enum {

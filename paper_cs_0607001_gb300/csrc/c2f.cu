@@ -187,7 +187,7 @@ extern "C" {
 
 sidwt_status sidwt_synthesize(sidwt_filter f, int64_t H, int64_t B, const void *lo_dev, const void *hi_dev,
                               int64_t in_stride, void *out_dev, sidwt_stream stream) {
-    if ((int)f == SIDWT_LEGALL53_INT) {
+    if ((int)f == SIDWT_LEGALL53_INT || (int)f == SIDWT_CDF97_INT) {
         set_error("synthesis takes the float filters");
         return SIDWT_EUNSUPPORTED;
     }

@@ -226,6 +226,45 @@ __device__ __forceinline__ void int53_window(int2 (&E)[2 * R + 1], int2 (&O)[2 *
     }
 }
 
+// Integer CDF 9/7 (dyadic Table I steps, rounded updates, no scaling):
+// R(c s) = floor((k s + 2^(m-1)) / 2^m) for c = k / 2^m, with a = -3/2,
+// b = -1/16, g = 205/256, d = 15/32 (x side; the y side negates them and
+// updates the other phase first).
+__device__ __forceinline__ int rdy(int k, int m, int s) {
+    return (int)(((long long)k * s + (1ll << (m - 1))) >> m);  // arithmetic shift: floor
+}
+__device__ __forceinline__ int2 iupd(int2 t, int k, int m, int2 p, int2 q) {
+    return make_int2(t.x + rdy(k, m, p.x + q.x), t.y + rdy(k, m, p.y + q.y));
+}
+
+template <int S, int R>
+__device__ __forceinline__ void int97_window(int2 (&E)[2 * R + 1], int2 (&O)[2 * R + 1]) {
+    constexpr int K[4] = {-3, -1, 205, 15}, M[4] = {1, 4, 8, 5};
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const bool odd = (S == SIDE_X) ? (s % 2 == 0) : (s % 2 == 1);
+        const int k = (S == SIDE_X) ? K[s] : -K[s];
+        if (odd) {
+#pragma unroll
+            for (int i = 0; i < 2 * R; ++i) O[i] = iupd(O[i], k, M[s], E[i], E[i + 1]);
+        } else {
+#pragma unroll
+            for (int i = 2 * R; i >= 1; --i) E[i] = iupd(E[i], k, M[s], O[i], O[i - 1]);
+        }
+    }
+}
+
+// The integer filter's window steps (F: SIDWT_LEGALL53_INT or SIDWT_CDF97_INT).
+template <int F, int S, int R>
+__device__ __forceinline__ void int_window(int2 (&E)[2 * R + 1], int2 (&O)[2 * R + 1]) {
+    if constexpr (F == SIDWT_CDF97_INT)
+        int97_window<S, R>(E, O);
+    else
+        int53_window<S, R>(E, O);
+}
+
+__host__ __device__ constexpr bool is_int_filter(int F) { return F == SIDWT_LEGALL53_INT || F == SIDWT_CDF97_INT; }
+
 constexpr int WR = 5;  // window radius
 
 // One analysis level over many rows by per-output recomputation.
@@ -260,7 +299,7 @@ __global__ void level_window_f(const TIn *__restrict__ in, int64_t in_stride, in
     hi[orow + n] = h;
 }
 
-template <int S, typename TIn>
+template <int F, int S, typename TIn>
 __global__ void level_window_i(const TIn *__restrict__ in, int64_t in_stride, int nrows, int nchild, int64_t K,
                                int2 *__restrict__ lo, int2 *__restrict__ hi, int64_t out_stride,
                                float2 *__restrict__ lo_f, float2 *__restrict__ hi_f) {
@@ -278,7 +317,7 @@ __global__ void level_window_i(const TIn *__restrict__ in, int64_t in_stride, in
         E[i] = to_i2(v[wrapi(2 * m - child, K)]);
         O[i] = to_i2(v[wrapi(2 * m + 1 - child, K)]);
     }
-    int53_window<S, WR>(E, O);
+    int_window<F, S, WR>(E, O);
     const int64_t o = (int64_t)(row + child * nrows) * out_stride + n;
     lo[o] = E[WR];
     hi[o] = O[WR];
@@ -375,6 +414,7 @@ __device__ __forceinline__ void out_pair_f(const float2 *in, int H, int n, const
     else hi = scale2(c.co, O[2]);
 }
 
+template <int F>
 __device__ __forceinline__ void out_pair_i(const int2 *in, int H, int n, int2 &lo, int2 &hi) {
     const int4 *q = reinterpret_cast<const int4 *>(in);
     int2 E[5], O[5];
@@ -385,7 +425,7 @@ __device__ __forceinline__ void out_pair_i(const int2 *in, int H, int n, int2 &l
         E[i] = make_int2(cur.x, cur.y);
         O[i] = make_int2(cur.z, cur.w);
     }
-    int53_window<SIDE_Y, 2>(E, O);
+    int_window<F, SIDE_Y, 2>(E, O);
     lo = E[2];
     hi = O[2];
 }
@@ -397,7 +437,7 @@ template <int F, typename T>
 __device__ __forceinline__ void analyze_one(const void *__restrict__ y, int64_t N, int J, float2 *__restrict__ pyr_f,
                                             int2 *__restrict__ pyr_i, double *__restrict__ yen, const LiftCoef &c,
                                             T *sm, float2 *red, long long *redi) {
-    constexpr bool INT = (F == SIDWT_LEGALL53_INT);
+    constexpr bool INT = is_int_filter(F);
     const int Nh = (int)(N / 2);
     EnAcc en;
     long long eni = 0;
@@ -437,7 +477,7 @@ __device__ __forceinline__ void analyze_one(const void *__restrict__ y, int64_t 
         for (int n = threadIdx.x; n < H; n += blockDim.x) {
             T lo, hi;
             if constexpr (INT) {
-                out_pair_i(reinterpret_cast<const int2 *>(in), H, n, lo, hi);
+                out_pair_i<F>(reinterpret_cast<const int2 *>(in), H, n, lo, hi);
                 pyr_i[off + n] = lo;
                 pyr_i[off + H + n] = hi;
                 pyr_f[off + n] = to_f2(lo);
@@ -466,7 +506,7 @@ __global__ void __launch_bounds__(kAnalyzeThreads) analyze_smem_kernel(const voi
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ float2 red[32];
     __shared__ long long redi[32];
-    constexpr bool INT = (F == SIDWT_LEGALL53_INT);
+    constexpr bool INT = is_int_filter(F);
     const int64_t b = blockIdx.x;
     const char *y = reinterpret_cast<const char *>(y_in) + b * N * (INT ? 4 : 8);
     analyze_one<F, T>(y, N, J, pyr_f + b * pyr_elems, INT ? pyr_i + b * pyr_elems : nullptr, yen + b * (J + 1), c,
@@ -510,6 +550,7 @@ __device__ __forceinline__ void pipe_load(void *dst, const void *src, uint32_t b
 }
 
 // Level-1 window of the integer path straight from the int16 I/Q input.
+template <int F>
 __device__ __forceinline__ void out_pair_i16(const short2 *in, int H, int n, int2 &lo, int2 &hi) {
     const short4 *q = reinterpret_cast<const short4 *>(in);
     int2 E[5], O[5];
@@ -520,7 +561,7 @@ __device__ __forceinline__ void out_pair_i16(const short2 *in, int H, int n, int
         E[i] = make_int2(cur.x, cur.y);
         O[i] = make_int2(cur.z, cur.w);
     }
-    int53_window<SIDE_Y, 2>(E, O);
+    int_window<F, SIDE_Y, 2>(E, O);
     lo = E[2];
     hi = O[2];
 }
@@ -534,7 +575,7 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
                                                                        int2 *__restrict__ pyr_i, int64_t pyr_elems,
                                                                        double *__restrict__ yen, LiftCoef c,
                                                                        int32_t *__restrict__ err, int nbuf) {
-    constexpr bool INT = (F == SIDWT_LEGALL53_INT);
+    constexpr bool INT = is_int_filter(F);
     constexpr int IN_BYTES = INT ? 4 : 8;
     extern __shared__ __align__(16) unsigned char smraw[];  // 16-byte aligned: enough for the bulk copies
     __shared__ __align__(8) uint64_t bar[2];
@@ -665,9 +706,9 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
                 T lo, hi;
                 if constexpr (INT) {
                     if (l == 1)
-                        out_pair_i16(reinterpret_cast<const short2 *>(cur), H, n, lo, hi);
+                        out_pair_i16<F>(reinterpret_cast<const short2 *>(cur), H, n, lo, hi);
                     else
-                        out_pair_i(reinterpret_cast<const int2 *>(in), H, n, lo, hi);
+                        out_pair_i<F>(reinterpret_cast<const int2 *>(in), H, n, lo, hi);
                     pi[off + n] = lo;
                     pi[off + H + n] = hi;
                     pf[off + n] = to_f2(lo);
@@ -803,14 +844,23 @@ static void launch_level_any(int filter, int side, const TIn *in, int64_t in_str
 }
 
 template <typename TIn>
-static void launch_level_int(int side, const TIn *in, int64_t in_stride, int nrows, int nchild, int64_t K, int2 *lo,
+static void launch_level_int(int filter, int side, const TIn *in, int64_t in_stride, int nrows, int nchild, int64_t K, int2 *lo,
                              int2 *hi, int64_t out_stride, float2 *lo_f, float2 *hi_f, cudaStream_t s) {
     const int64_t H = K / 2;
     dim3 grid((unsigned)((H + 127) / 128), (unsigned)(nrows * nchild));
     if (side == SIDE_X)
-        level_window_i<SIDE_X, TIn><<<grid, 128, 0, s>>>(in, in_stride, nrows, nchild, K, lo, hi, out_stride, lo_f, hi_f);
+        if (filter == SIDWT_CDF97_INT)
+            level_window_i<SIDWT_CDF97_INT, SIDE_X, TIn>
+                <<<grid, 128, 0, s>>>(in, in_stride, nrows, nchild, K, lo, hi, out_stride, lo_f, hi_f);
+        else
+            level_window_i<SIDWT_LEGALL53_INT, SIDE_X, TIn>
+                <<<grid, 128, 0, s>>>(in, in_stride, nrows, nchild, K, lo, hi, out_stride, lo_f, hi_f);
+    else if (filter == SIDWT_CDF97_INT)
+        level_window_i<SIDWT_CDF97_INT, SIDE_Y, TIn>
+            <<<grid, 128, 0, s>>>(in, in_stride, nrows, nchild, K, lo, hi, out_stride, lo_f, hi_f);
     else
-        level_window_i<SIDE_Y, TIn><<<grid, 128, 0, s>>>(in, in_stride, nrows, nchild, K, lo, hi, out_stride, lo_f, hi_f);
+        level_window_i<SIDWT_LEGALL53_INT, SIDE_Y, TIn>
+            <<<grid, 128, 0, s>>>(in, in_stride, nrows, nchild, K, lo, hi, out_stride, lo_f, hi_f);
 }
 
 sidwt_status build_reference_tree(sidwt_plan *p, const void *x_dev, int32_t ref, cudaStream_t s) {
@@ -843,9 +893,10 @@ sidwt_status build_reference_tree(sidwt_plan *p, const void *x_dev, int32_t ref,
             float2 *Af = tf + 2 * N * (int64_t)j;
             float2 *Bf = Af + N;
             if (j == 0)
-                launch_level_int(SIDE_X, reinterpret_cast<const short2 *>(x_dev), 0, 1, 2, K, A, B, K / 2, Af, Bf, s);
+                launch_level_int(p->filter, SIDE_X, reinterpret_cast<const short2 *>(x_dev), 0, 1, 2, K, A, B, K / 2, Af, Bf,
+                                 s);
             else
-                launch_level_int(SIDE_X, ti + 2 * N * (int64_t)(j - 1), K, nv, 2, K, A, B, K / 2, Af, Bf, s);
+                launch_level_int(p->filter, SIDE_X, ti + 2 * N * (int64_t)(j - 1), K, nv, 2, K, A, B, K / 2, Af, Bf, s);
         }
         ref_energy_kernel<short2, int2><<<(1 << (J + 1)) - 1, 256, 0, s>>>(
             reinterpret_cast<const short2 *>(x_dev), ti, N, xe);
@@ -888,6 +939,12 @@ cudaError_t prepare_analysis_kernels() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(analyze_pipe_kernel<SIDWT_LEGALL53_INT, int2>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(analyze_pipe_kernel<SIDWT_CDF97_INT, int2>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(analyze_smem_kernel<SIDWT_CDF97_INT, int2>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     if (e == cudaSuccess) e = prepare_ragged_kernels();
     return e;
 }
@@ -934,6 +991,10 @@ sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStre
             analyze_pipe_kernel<SIDWT_CDF97, float2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
                 y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf);
             break;
+        case SIDWT_CDF97_INT:
+            analyze_pipe_kernel<SIDWT_CDF97_INT, int2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf);
+            break;
         default:
             analyze_pipe_kernel<SIDWT_LEGALL53_INT, int2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
                 y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf);
@@ -947,6 +1008,7 @@ sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStre
         case SIDWT_D4: e = launch_smem<SIDWT_D4, float2>(p, y_dev, B, s, c); break;
         case SIDWT_LEGALL53: e = launch_smem<SIDWT_LEGALL53, float2>(p, y_dev, B, s, c); break;
         case SIDWT_CDF97: e = launch_smem<SIDWT_CDF97, float2>(p, y_dev, B, s, c); break;
+        case SIDWT_CDF97_INT: e = launch_smem<SIDWT_CDF97_INT, int2>(p, y_dev, B, s, c); break;
         default: e = launch_smem<SIDWT_LEGALL53_INT, int2>(p, y_dev, B, s, c); break;
         }
         return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "analysis launch");
@@ -961,10 +1023,10 @@ sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStre
             launch_level_any(p->filter, SIDE_Y, in, l == 1 ? N : p->pyr_elems, (int)B, 1, K, p->pyr_f + off,
                              p->pyr_f + off + (N >> l), p->pyr_elems, c, s);
         } else if (l == 1) {
-            launch_level_int(SIDE_Y, reinterpret_cast<const short2 *>(y_dev), N, (int)B, 1, K, p->pyr_i + off,
+            launch_level_int(p->filter, SIDE_Y, reinterpret_cast<const short2 *>(y_dev), N, (int)B, 1, K, p->pyr_i + off,
                              p->pyr_i + off + (N >> l), p->pyr_elems, p->pyr_f + off, p->pyr_f + off + (N >> l), s);
         } else {
-            launch_level_int(SIDE_Y, p->pyr_i + prev, p->pyr_elems, (int)B, 1, K, p->pyr_i + off,
+            launch_level_int(p->filter, SIDE_Y, p->pyr_i + prev, p->pyr_elems, (int)B, 1, K, p->pyr_i + off,
                              p->pyr_i + off + (N >> l), p->pyr_elems, p->pyr_f + off, p->pyr_f + off + (N >> l), s);
         }
     }

@@ -966,7 +966,7 @@ sidwt_status sidwt_ragged_store_reference(sidwt_ragged *r, sidwt_filter f, int64
     }
     if ((int)f < 0 || (int)f > 2) {
         set_error("ragged batches take the float filters (D4, LeGall 5/3, CDF 9/7)");
-        return (int)f == 3 ? SIDWT_EUNSUPPORTED : SIDWT_EINVAL;
+        return ((int)f == 3 || (int)f == 4) ? SIDWT_EUNSUPPORTED : SIDWT_EINVAL;
     }
     if (J < 1 || J > 15 || N < 2 || N > (int64_t(1) << 26) || N % (int64_t(1) << J) != 0) {
         set_error("need 1 <= J <= 15, N a multiple of 2^J, N <= 2^26");

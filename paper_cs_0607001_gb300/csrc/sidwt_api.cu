@@ -217,7 +217,7 @@ sidwt_status sidwt_plan_create(sidwt_filter f, int64_t N, int J, sidwt_plan **ou
         return SIDWT_EINVAL;
     }
     *out = nullptr;
-    if ((int)f < 0 || (int)f > 3) {
+    if ((int)f < 0 || (int)f > 4) {
         set_error("unknown filter");
         return SIDWT_EINVAL;
     }
@@ -235,7 +235,7 @@ sidwt_status sidwt_plan_create(sidwt_filter f, int64_t N, int J, sidwt_plan **ou
     p->filter = (int)f;
     p->N = N;
     p->J = J;
-    p->is_int = (f == SIDWT_LEGALL53_INT);
+    p->is_int = (f == SIDWT_LEGALL53_INT || f == SIDWT_CDF97_INT);
     p->tree_elems = 2 * (int64_t)J * N;
     p->xen_len = (int64_t(2) << J) - 1;
     p->pyr_elems = 2 * N - 2 * (N >> J);

@@ -84,7 +84,7 @@ size_t layout(sidwt_plan &p, unsigned char *base, int64_t B, int32_t **ids_in) {
 extern "C" sidwt_status sidwt_correlate_static(sidwt_filter f, int64_t N, int J, const void *x_dev,
                                                const void *y_dev, int64_t B, int32_t *lag_dev, float *mag_dev,
                                                double *norm_dev, sidwt_stream stream) {
-    if ((int)f < 0 || (int)f > 3) {
+    if ((int)f < 0 || (int)f > 4) {
         set_error("unknown filter");
         return SIDWT_EINVAL;
     }
@@ -96,7 +96,7 @@ extern "C" sidwt_status sidwt_correlate_static(sidwt_filter f, int64_t N, int J,
         set_error("need 1 <= B <= 65535 and non-NULL x, y, lag, mag and norm");
         return SIDWT_EINVAL;
     }
-    const bool is_int = (f == SIDWT_LEGALL53_INT);
+    const bool is_int = (f == SIDWT_LEGALL53_INT || f == SIDWT_CDF97_INT);
     if (reinterpret_cast<uintptr_t>(x_dev) % (is_int ? 4 : 8) ||
         reinterpret_cast<uintptr_t>(y_dev) % (is_int ? 8 : 16)) {
         set_error("x_dev / y_dev misaligned");

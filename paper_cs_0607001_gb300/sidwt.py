@@ -14,7 +14,7 @@ import torch
 
 from . import build as _build
 
-FILTERS = {"d4": 0, "legall53": 1, "cdf97": 2, "legall53_int": 3}
+FILTERS = {"d4": 0, "legall53": 1, "cdf97": 2, "legall53_int": 3, "cdf97_int": 4}
 PRECISIONS = {"fp32": 0, "bf16x3": 1, "tf32x3": 2}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUSY", 6: "EUNSUPPORTED"}
 
@@ -172,7 +172,7 @@ class Plan:
         self.filter = _filter_id(filter)
         self.N = int(N)
         self.J = int(J)
-        self.is_int = self.filter == 3
+        self.is_int = self.filter in (3, 4)
         h = _vp()
         _raise(lib().sidwt_plan_create(self.filter, self.N, self.J, ctypes.byref(h)))
         self._h = h

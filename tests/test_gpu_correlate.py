@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 def run_plan(fname, N, J, refs, y, ref_ids, precision="fp32", want_r=True):
     from paper_cs_0607001_gb300 import sidwt
     p = sidwt.Plan(fname, N, J)
-    is_int = fname == "legall53_int"
+    is_int = fname in ("legall53_int", "cdf97_int")
     for x in refs:
         p.store_reference(U.to_dev_i16(x) if is_int else U.to_dev_c64(x))
     yd = U.to_dev_i16(y) if is_int else U.to_dev_c64(y)
@@ -56,15 +56,17 @@ def test_correlation_matches_oracle(oracle, fname, fid, N, J, B, nrefs):
         np.testing.assert_allclose(norm[b], no[b], rtol=5e-5, atol=1e-6)
 
 
-def test_integer_plan_correlation_matches_oracle(oracle):
-    N, J, B = 512, 4, 70
+@pytest.mark.parametrize("fname,fid", [("legall53_int", 3), ("cdf97_int", 4)])
+@pytest.mark.parametrize("B", [70, 6])
+def test_integer_plan_correlation_matches_oracle(oracle, fname, fid, B):
+    N, J = 512, 4
     w = inputs.random_batch(n_refs=2, B=B, N=N, J=J, seed=9)
     refs = inputs.to_iq16(w["refs"].astype(np.complex128))
     y = inputs.to_iq16(w["y"].astype(np.complex128))
-    r, lag, mag, norm = run_plan("legall53_int", N, J, refs, y, w["ref_ids"])
+    r, lag, mag, norm = run_plan(fname, N, J, refs, y, w["ref_ids"])
     X = U.iq_to_complex(refs[w["ref_ids"]])
     Y = U.iq_to_complex(y)
-    _, _, no, ro, _ = oracle.correlate_batch(3, X, Y, J, form=1, want_r=True)
+    _, _, no, ro, _ = oracle.correlate_batch(fid, X, Y, J, form=1, want_r=True)
     for b in range(B):
         U.check_r(r[b], ro[b], what=f"int pulse {b}")
         U.check_peak_lags(lag[b], ro[b], U.RTOL_FP32, what=f"int pulse {b}")

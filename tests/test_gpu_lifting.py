@@ -53,53 +53,59 @@ def test_reference_tree_matches_oracle(oracle, fname, fid, N, J):
     np.testing.assert_allclose(en, eo, rtol=2e-6 * J)
 
 
+INT_FILTERS = [("legall53_int", 3), ("cdf97_int", 4)]
+
+
+@pytest.mark.parametrize("fname,fid", INT_FILTERS)
 @pytest.mark.parametrize("N,J", [(64, 3), (96, 5), (8192, 5), (1024, 10), (32768, 4)])
-def test_integer_53_received_pyramid_bit_exact(oracle, N, J):
+def test_integer_received_pyramid_bit_exact(oracle, fname, fid, N, J):
     from paper_cs_0607001_gb300 import sidwt
     B = 4
     g = np.random.default_rng(N * J)
     y = g.integers(-32768, 32768, size=(B, N, 2)).astype(np.int16)
-    with sidwt.Plan("legall53_int", N, J) as p:
+    with sidwt.Plan(fname, N, J) as p:
         pyr, en = p.analyze(U.to_dev_i16(y))
         torch.cuda.synchronize()
         pyr = pyr.cpu().numpy().astype(np.int64)
         en = en.cpu().numpy()
     for b in range(B):
-        po, eo = oracle.pyramid_y(3, U.iq_to_complex(y[b]), J)
+        po, eo = oracle.pyramid_y(fid, U.iq_to_complex(y[b]), J)
         np.testing.assert_array_equal(pyr[b, :, 0], po.real.astype(np.int64))
         np.testing.assert_array_equal(pyr[b, :, 1], po.imag.astype(np.int64))
         np.testing.assert_allclose(en[b], eo, rtol=1e-12)
 
 
+@pytest.mark.parametrize("fname,fid", INT_FILTERS)
 @pytest.mark.parametrize("N,J", [(64, 3), (96, 5), (8192, 5)])
-def test_integer_53_tree_bit_exact(oracle, N, J):
+def test_integer_tree_bit_exact(oracle, fname, fid, N, J):
     from paper_cs_0607001_gb300 import sidwt
     g = np.random.default_rng(N + 3)
     x = g.integers(-32768, 32768, size=(N, 2)).astype(np.int16)
-    with sidwt.Plan("legall53_int", N, J) as p:
+    with sidwt.Plan(fname, N, J) as p:
         p.store_reference(U.to_dev_i16(x))
         tree, en = p.reference_tree(0)
         torch.cuda.synchronize()
         tree = tree.cpu().numpy().astype(np.int64)
         en = en.cpu().numpy()
-    to, eo = oracle.tree_x(3, U.iq_to_complex(x), J)
+    to, eo = oracle.tree_x(fid, U.iq_to_complex(x), J)
     np.testing.assert_array_equal(tree[:, 0], to.real.astype(np.int64))
     np.testing.assert_array_equal(tree[:, 1], to.imag.astype(np.int64))
     np.testing.assert_allclose(en, eo, rtol=1e-12)
 
 
-def test_full_size_int16_batch_bit_exact_on_sampled_pulses(oracle):
+@pytest.mark.parametrize("fname,fid", INT_FILTERS)
+def test_full_size_int16_batch_bit_exact_on_sampled_pulses(oracle, fname, fid):
     """The 4096 x 8192, J = 5 int16 I/Q batch in one call; every coefficient
     of a seeded sample of pulses compared bit for bit."""
     from paper_cs_0607001_gb300 import inputs, sidwt
     w = inputs.two_ref_batch(B=4096, N=8192, J=5)
     yi = inputs.to_iq16(w["y"].astype(np.complex128))
-    with sidwt.Plan("legall53_int", 8192, 5) as p:
+    with sidwt.Plan(fname, 8192, 5) as p:
         pyr, _ = p.analyze(U.to_dev_i16(yi))
         torch.cuda.synchronize()
         sample = [0, 1, 2047, 2048, 3000, 4095]
         got = pyr[sample].cpu().numpy().astype(np.int64)
     for i, b in enumerate(sample):
-        po, _ = oracle.pyramid_y(3, U.iq_to_complex(yi[b]), 5)
+        po, _ = oracle.pyramid_y(fid, U.iq_to_complex(yi[b]), 5)
         np.testing.assert_array_equal(got[i, :, 0], po.real.astype(np.int64))
         np.testing.assert_array_equal(got[i, :, 1], po.imag.astype(np.int64))
