@@ -296,6 +296,16 @@ def run_ours(args):
     stage["store_ms_per_step"] = round(sum(t["store_ms"] for t in tims.values()) / args.steps + ti["store_ms"] /
                                        args.steps, 4)
     stage["int53_analyze_ms"] = round(ti["analyze_ms"] / args.steps, 4)
+    # the reversible integer 9/7 analysis of the same int16 batch (outside the step)
+    p97 = S.Plan("cdf97_int", N, J)
+    p97.reserve(1, B)
+    for _ in range(3):
+        p97.analyze_into(y_i16, None, int_en)
+    p97.set_timing(True)
+    for _ in range(5):
+        p97.analyze_into(y_i16, None, int_en)
+    stage["int97_analyze_ms"] = round(p97.read_timing(reset=True)["analyze_ms"] / 5, 4)
+    p97.close()
     corr_step_ms = sum(t[k] for t in tims.values() for k in ("group_ms", "analyze_ms", "correlate_ms", "peaks_ms")) \
         / args.steps
 
