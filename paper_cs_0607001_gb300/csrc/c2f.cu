@@ -142,14 +142,22 @@ __global__ void __launch_bounds__(kC2fThreads) c2f_kernel(const float2 *__restri
             if (D < 0) D += N;
             const int q = (int)(D >> lev), v = (int)(D & ((1 << lev) - 1));
             float ar = 0.f, ai = 0.f;
-            for (int k = lane; k < 2 * Kp; k += 32) {
-                const int band = k >= Kp ? 1 : 0;
-                int idx = k - band * Kp - q;
-                if (idx < 0) idx += Kp;
-                const float2 wv = A[(int64_t)band * N + (int64_t)v * Kp + idx];
-                const float2 uv = u[k];
-                ar = fmaf(wv.x, uv.x, fmaf(wv.y, uv.y, ar));
-                ai = fmaf(wv.x, uv.y, fmaf(-wv.y, uv.x, ai));
+            // per band, the delayed variant splits into two unwrapped runs:
+            // k in [q, K') reads w[k - q], k in [0, q) reads w[k - q + K']
+#pragma unroll 1
+            for (int band = 0; band < 2; ++band) {
+                const float2 *wb = A + (int64_t)band * N + (int64_t)v * Kp;
+                const float2 *ub = u + (int64_t)band * Kp;
+                for (int k = q + lane; k < Kp; k += 32) {
+                    const float2 wv = wb[k - q], uv = ub[k];
+                    ar = fmaf(wv.x, uv.x, fmaf(wv.y, uv.y, ar));
+                    ai = fmaf(wv.x, uv.y, fmaf(-wv.y, uv.x, ai));
+                }
+                for (int k = lane; k < q; k += 32) {
+                    const float2 wv = wb[k - q + Kp], uv = ub[k];
+                    ar = fmaf(wv.x, uv.x, fmaf(wv.y, uv.y, ar));
+                    ai = fmaf(wv.x, uv.y, fmaf(-wv.y, uv.x, ai));
+                }
             }
             for (int o = 16; o > 0; o >>= 1) {
                 ar += __shfl_xor_sync(0xffffffffu, ar, o);
