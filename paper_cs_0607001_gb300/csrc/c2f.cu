@@ -97,11 +97,12 @@ __device__ __forceinline__ unsigned long long c2f_key(float re, float im, uint32
     return ((unsigned long long)__float_as_uint(re * re + im * im) << 32) | (unsigned long long)(0xFFFFFFFFu - D);
 }
 
-constexpr int kC2fThreads = 256;
+constexpr int kC2fThreads = 512;
+constexpr int kC2fChunk = 256;  // delays per pass of the window (their band partial sums in shared memory)
 
 // One pulse per CTA, after the scale-J correlation at every delay has left
-// its peak key in keys[b][J].  For j = J-1 down to 0 one warp per delay of
-// the window (lanes over k, coalesced):
+// its peak key in keys[b][J].  For j = J-1 down to 0 one warp per (delay of
+// the window, band) (lanes over k, coalesced):
 // r_j[2^l q + v] = sum over the bands of conj(w_v[(k - q) mod K']) u[k]
 // (the variant delayed by q).
 __global__ void __launch_bounds__(kC2fThreads) c2f_kernel(const float2 *__restrict__ tree, int64_t tree_elems,
@@ -110,6 +111,7 @@ __global__ void __launch_bounds__(kC2fThreads) c2f_kernel(const float2 *__restri
                                                           int J, int h, const unsigned long long *__restrict__ keys,
                                                           int32_t *__restrict__ lag, float *__restrict__ mag) {
     __shared__ unsigned long long wkey[kC2fThreads / 32];
+    __shared__ float2 part[2 * kC2fChunk];
     const int b = blockIdx.x;
     const int ref = ref_ids[b];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -137,17 +139,18 @@ __global__ void __launch_bounds__(kC2fThreads) c2f_kernel(const float2 *__restri
         const int64_t cnt = 2 * w + 1 >= N ? N : 2 * w + 1;
         const int64_t start = 2 * w + 1 >= N ? 0 : (int64_t)Dc - w;
         unsigned long long best = 0ull;
-        for (int64_t i = warp; i < cnt; i += nw) {
-            int64_t D = (start + i) % N;
-            if (D < 0) D += N;
-            const int q = (int)(D >> lev), v = (int)(D & ((1 << lev) - 1));
-            float ar = 0.f, ai = 0.f;
-            // per band, the delayed variant splits into two unwrapped runs:
-            // k in [q, K') reads w[k - q], k in [0, q) reads w[k - q + K']
-#pragma unroll 1
-            for (int band = 0; band < 2; ++band) {
+        for (int64_t base = 0; base < cnt; base += kC2fChunk) {
+            const int nl = (int)(cnt - base < kC2fChunk ? cnt - base : kC2fChunk);
+            // one warp per (delay, band): the delayed variant splits into two
+            // unwrapped runs, k in [q, K') reads w[k - q], k in [0, q) w[k - q + K']
+            for (int it = warp; it < 2 * nl; it += nw) {
+                int64_t D = (start + base + (it >> 1)) % N;
+                if (D < 0) D += N;
+                const int band = it & 1;
+                const int q = (int)(D >> lev), v = (int)(D & ((1 << lev) - 1));
                 const float2 *wb = A + (int64_t)band * N + (int64_t)v * Kp;
                 const float2 *ub = u + (int64_t)band * Kp;
+                float ar = 0.f, ai = 0.f;
                 for (int k = q + lane; k < Kp; k += 32) {
                     const float2 wv = wb[k - q], uv = ub[k];
                     ar = fmaf(wv.x, uv.x, fmaf(wv.y, uv.y, ar));
@@ -158,13 +161,25 @@ __global__ void __launch_bounds__(kC2fThreads) c2f_kernel(const float2 *__restri
                     ar = fmaf(wv.x, uv.x, fmaf(wv.y, uv.y, ar));
                     ai = fmaf(wv.x, uv.y, fmaf(-wv.y, uv.x, ai));
                 }
+                for (int o = 16; o > 0; o >>= 1) {
+                    ar += __shfl_xor_sync(0xffffffffu, ar, o);
+                    ai += __shfl_xor_sync(0xffffffffu, ai, o);
+                }
+                if (lane == 0) part[it] = make_float2(ar, ai);
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                ar += __shfl_xor_sync(0xffffffffu, ar, o);
-                ai += __shfl_xor_sync(0xffffffffu, ai, o);
+            __syncthreads();
+            for (int l = tid; l < nl; l += blockDim.x) {
+                int64_t D = (start + base + l) % N;
+                if (D < 0) D += N;
+                const float2 a0 = part[2 * l], a1 = part[2 * l + 1];
+                const unsigned long long key = c2f_key(a0.x + a1.x, a0.y + a1.y, (uint32_t)D);
+                best = key > best ? key : best;
             }
-            const unsigned long long key = c2f_key(ar, ai, (uint32_t)D);
-            best = key > best ? key : best;
+            __syncthreads();
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, best, o);
+            best = t > best ? t : best;
         }
         if (lane == 0) wkey[warp] = best;
         __syncthreads();
