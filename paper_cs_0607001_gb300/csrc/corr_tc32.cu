@@ -4,20 +4,21 @@
 // speed.
 //
 // Same products as the bf16 path (eq. 20 / 20a in advance form,
-// C[m][p] = sum_k conj(w[(k + p) mod K']) u_m[k]).  kind::tf32 takes K = 8
-// per MMA, one 16-byte core matrix along K, so both operands are K-major:
-//   * A (M = 128 rows): 128 received pulses of one reference, K-major
-//     ([k/4][Re|Im][pulse][4 samples]), a plain TMA box.
-//   * B (N = 224 columns): the stored variant's window; column n is the
-//     advance p = p0 + r + 4 n, so with a copy W_r[t] = w[t + r] shifted by
-//     the residue r, element (k, n) sits at W_r[t0 + 4 n + k]: consecutive
-//     columns are 16 bytes apart and the K-major core matrices overlap
-//     (LBO 16 B, SBO 128 B).  One CTA owns one residue r and 224 advances
-//     spaced by 4 (896 consecutive advances per r-quadruple of CTAs).
-// Re += A(ur) B(wr) + A(ui) B(wi), Im += A(ui) B(wr) + A(ur) B(-wi), each
-// with the three split products: 24 MMAs (M 128, N 224, K 8) per stage of
-// 16 samples, 4-stage ring.  Roles, epilogue and bounded waits as in the
-// bf16 kernel.
+// C[p][m] = sum_k conj(w[(k + p) mod K']) u_m[k]) with the roles of the
+// operands exchanged and only K-major layouts:
+//   * A (M = 128 rows) is the stored variant's window: row i is the advance
+//     p = p0 + r + 4 i, so with a copy W_r[t] = w[t + r] shifted by the
+//     residue r, element (i, k) sits at W_r[t0 + 4 i + k]: consecutive rows
+//     are 16 bytes apart and the K-major core matrices overlap (LBO 16 B,
+//     SBO 128 B).  One CTA owns one residue r and 128 advances spaced by 4
+//     (512 consecutive advances per r-quadruple of CTAs).
+//   * B (N = 256 columns) is 256 received pulses of one reference, K-major
+//     ([k/4][Re|Im][pulse][4 samples]), loaded by TMA as a plain box.
+// Re and Im: Re += A(wr) B(ur) + A(wi) B(ui), Im += A(wr) B(ui) + A(-wi) B(ur);
+// each with the three split products: 24 MMAs (M 128, N 256, K 8) per stage
+// of 16 samples.  The epilogue reduces the peak of every pulse over the
+// CTA's advances with a warp transpose-reduction and one atomicMax per
+// (warp, pulse).  Roles and bounded waits as in the bf16 kernel.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -33,24 +34,19 @@ namespace tc32 {
 using namespace sidwt::tc;
 
 constexpr int kThreads = 192;
-constexpr int kTM = 128;                          // pulses per tile (MMA M)
-constexpr int kTN = 224;                          // advances per tile (MMA N), 4 apart
-constexpr int kKB = 16;                           // samples per stage
-constexpr int kStages = 4;
-constexpr int kLagBlock = 4 * kTN;                // consecutive advances per r-quadruple of CTAs
-constexpr int kWinChunks = 227;                   // window chunks of 4 samples: 4*223 + 15 < 908
-constexpr int kWinRowBytes = kWinChunks * 16;     // 3632
-constexpr int kBRows = 3;                         // planes -Im, Re, Im of one residue
-constexpr int kBBytes = 11008;                    // 3 rows x 3632 B, rounded up to 128
-constexpr int kABytes = 4 * 2 * kTM * 16;         // [4 k-chunks][Re|Im][128][16 B] = 16384
-constexpr int kStage = 2 * kABytes + 2 * kBBytes; // A hi, A lo, B hi, B lo = 54784
-constexpr int kBarOff = kStages * kStage;         // 219136
+constexpr int kTN = 256;                        // pulses per tile (MMA N)
+constexpr int kKB = 16;                         // samples per stage
+constexpr int kLagBlock = 512;                  // advances per (r-quadruple of) CTA
+constexpr int kWinChunks = 132;                 // window chunks of 4 samples: 4*127 + 15 < 528
+constexpr int kWinRowBytes = kWinChunks * 16;   // 2112
+constexpr int kARows = 3;                       // planes -Im, Re, Im of one residue
+constexpr int kABytes = 6400;                   // 3 rows x 2112 B, rounded up to 128
+constexpr int kBBytes = 4 * 2 * kTN * 16;       // [4 k-chunks][Re|Im][256][16 B] = 32768
+constexpr int kStage = 2 * kBBytes + 2 * kABytes;  // B hi, B lo, A hi, A lo = 78336
+constexpr int kBarOff = 2 * kStage;             // 156672
 constexpr int kSmemBytes = kBarOff + 128 + 1024;
 constexpr int kTmemCols = 512;
-constexpr int kRowsPerVariant = 24;               // hi/lo x 4 residues x 3 planes
-static_assert(kBRows * kWinRowBytes <= kBBytes && kBBytes % 128 == 0 && kStage % 128 == 0, "TMA destinations");
-static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
-static_assert(4 * (kTN - 1) + 2 * 8 <= 4 * kWinChunks, "window covers every column and sample of a stage");
+constexpr int kRowsPerVariant = 24;             // hi/lo x 4 residues x 3 planes
 
 // Instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
@@ -96,13 +92,13 @@ struct Args {
 __device__ __forceinline__ unsigned long long kmax(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    corr_tc32_kernel(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapA_hi,
-                     const __grid_constant__ CUtensorMap mapA_lo, const Args a) {
+    corr_tc32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB_hi,
+                     const __grid_constant__ CUtensorMap mapB_lo, const Args a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *bar = reinterpret_cast<uint64_t *>(base + kBarOff);  // full[4], empty[4], accf
-    uint64_t *full = bar, *empty = bar + kStages, *accf = bar + 2 * kStages;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2 * kStages + 2);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + kBarOff);  // full[2], empty[2], accf
+    uint64_t *full = bar, *empty = bar + 2, *accf = bar + 4;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 8);
     volatile int *sflag = reinterpret_cast<volatile int *>(tmem_slot + 4);  // [0] error, [1] issued, [2] consumed, [3] progress
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -119,7 +115,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int nkb = a.nbands * a.kb_per_band;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kStages; ++i) {
+        for (int i = 0; i < 2; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
@@ -140,8 +136,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             int issued = 0;
             for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % kStages;
-                if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1)) {
+                const int s = kb & 1;
+                if (kb >= 2 && !mbar_wait(&empty[s], ((kb >> 1) - 1) & 1)) {
                     sflag[0] = 1;
                     break;
                 }
@@ -149,53 +145,53 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int band = kb / a.kb_per_band;
                 const int kap0 = (kb % a.kb_per_band) * kKB;
                 unsigned char *st = base + s * kStage;
-                mbar_expect_tx(&full[s], 2 * kABytes + 2 * kBRows * kWinRowBytes);
+                mbar_expect_tx(&full[s], 2 * kBBytes + 2 * kARows * kWinRowBytes);
                 const int z0 = ((band * a.Kp + kap0) >> 2) * 2;
-                tma_load_3d(st, &mapA_hi, &full[s], 0, row0, z0);
-                tma_load_3d(st + kABytes, &mapA_lo, &full[s], 0, row0, z0);
+                tma_load_3d(st, &mapB_hi, &full[s], 0, row0, z0);
+                tma_load_3d(st + kBBytes, &mapB_lo, &full[s], 0, row0, z0);
                 const int rowbase = ref * a.rows_per_ref + (band * a.nv + v) * kRowsPerVariant;
                 const int chunk0 = (kap0 + p0) >> 2;
-                tma_load_3d(st + 2 * kABytes, &mapB, &full[s], 0, chunk0, rowbase + r * kBRows);
-                tma_load_3d(st + 2 * kABytes + kBBytes, &mapB, &full[s], 0, chunk0, rowbase + 12 + r * kBRows);
+                tma_load_3d(st + 2 * kBBytes, &mapA, &full[s], 0, chunk0, rowbase + r * kARows);
+                tma_load_3d(st + 2 * kBBytes + kABytes, &mapA, &full[s], 0, chunk0, rowbase + 12 + r * kARows);
                 ++issued;
             }
             sflag[1] = issued;
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(kTM, kTN);
+            const uint32_t idesc = idesc_tf32(128, kTN);
             int consumed = 0;
             for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % kStages;
-                if (!mbar_wait(&full[s], (kb / kStages) & 1)) {
+                const int s = kb & 1;
+                if (!mbar_wait(&full[s], (kb >> 1) & 1)) {
                     sflag[0] = 1;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t sb = saddr(base + s * kStage);
-                const uint32_t aHi = sb, aLo = sb + kABytes;
-                const uint32_t bHi = sb + 2 * kABytes, bLo = bHi + kBBytes;
+                const uint32_t bHi = sb, bLo = sb + kBBytes;
+                const uint32_t aHi = sb + 2 * kBBytes, aLo = aHi + kABytes;
 #pragma unroll
                 for (int ks = 0; ks < 2; ++ks) {
-                    // A planes Re u / Im u: [k-chunk][plane][128 pulses][16 B]; next k-chunk 4 KB, 8 pulses 128 B
-                    const uint32_t ao = (uint32_t)(2 * ks) * 2 * 2048;
-                    const uint64_t ah[2] = {sdesc(aHi + ao, 4096, 128), sdesc(aHi + ao + 2048, 4096, 128)};
-                    const uint64_t al[2] = {sdesc(aLo + ao, 4096, 128), sdesc(aLo + ao + 2048, 4096, 128)};
-                    // B rows 0 -Im w, 1 Re w, 2 Im w; K-direction 16 B (next 4 samples), 8 advances 128 B
-                    const uint32_t bo = (uint32_t)ks * 32;
-                    const uint64_t bh[3] = {sdesc(bHi + bo, 16, 128), sdesc(bHi + kWinRowBytes + bo, 16, 128),
-                                            sdesc(bHi + 2 * kWinRowBytes + bo, 16, 128)};
-                    const uint64_t bl[3] = {sdesc(bLo + bo, 16, 128), sdesc(bLo + kWinRowBytes + bo, 16, 128),
-                                            sdesc(bLo + 2 * kWinRowBytes + bo, 16, 128)};
-                    // (accumulator, A plane, B row): Re += ur wr + ui wi, Im += ui wr + ur (-wi)
-                    const int acc_of[4] = {0, 0, 1, 1}, apl[4] = {0, 1, 1, 0}, brow[4] = {1, 2, 1, 0};
+                    // A rows: 0 -Im w, 1 Re w, 2 Im w; K-direction 16 B (next 4 samples), 8 advances 128 B
+                    const uint32_t ao = (uint32_t)ks * 32;
+                    const uint64_t ah[3] = {sdesc(aHi + ao, 16, 128), sdesc(aHi + kWinRowBytes + ao, 16, 128),
+                                            sdesc(aHi + 2 * kWinRowBytes + ao, 16, 128)};
+                    const uint64_t al[3] = {sdesc(aLo + ao, 16, 128), sdesc(aLo + kWinRowBytes + ao, 16, 128),
+                                            sdesc(aLo + 2 * kWinRowBytes + ao, 16, 128)};
+                    // B planes Re u / Im u: [k-chunk][plane][256 pulses][16 B]; next k-chunk 8 KB, 8 pulses 128 B
+                    const uint32_t bo = (uint32_t)(2 * ks) * 2 * 4096;
+                    const uint64_t bh[2] = {sdesc(bHi + bo, 8192, 128), sdesc(bHi + bo + 4096, 8192, 128)};
+                    const uint64_t bl[2] = {sdesc(bLo + bo, 8192, 128), sdesc(bLo + bo + 4096, 8192, 128)};
+                    // (accumulator, A row, B plane): Re += wr ur + wi ui, Im += wr ui + (-wi) ur
+                    const int acc_of[4] = {0, 0, 1, 1}, arow[4] = {1, 2, 1, 0}, bpl[4] = {0, 1, 1, 0};
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const uint32_t d = tmem + acc_of[q] * 256;
                         const uint32_t first = (kb == 0 && ks == 0 && (q == 0 || q == 2)) ? 0u : 1u;
-                        mma_tf32(d, ah[apl[q]], bh[brow[q]], idesc, first);
-                        mma_tf32(d, ah[apl[q]], bl[brow[q]], idesc, 1u);
-                        mma_tf32(d, al[apl[q]], bh[brow[q]], idesc, 1u);
+                        mma_tf32(d, ah[arow[q]], bh[bpl[q]], idesc, first);
+                        mma_tf32(d, ah[arow[q]], bl[bpl[q]], idesc, 1u);
+                        mma_tf32(d, al[arow[q]], bh[bpl[q]], idesc, 1u);
                     }
                 }
                 mma_commit(&empty[s]);
@@ -206,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_commit(accf);  // arrives once every MMA issued above has completed
         }
     } else {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = pulses of the tile
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = advances m
         const int q4 = warp & 3;
         const int m = q4 * 32 + lane;
         uint64_t t0 = now_ns();
@@ -226,32 +222,44 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!__all_sync(0xffffffffu, ok && !sflag[0])) {
             sflag[0] = 1;
         } else {
-            const bool valid = m < cnt;
-            const int64_t b = valid ? a.perm[row0 + m] : 0;
-            unsigned long long best = 0ull;
-            // advance of column n: p = p0 + r + 4 n (mod K'); delay q = -p mod K'
-            int pm = (p0 + r) % a.Kp;
-            const int step = 4 % a.Kp;
+            const int p = p0 + r + 4 * m;
+            const int pm = p % a.Kp;
+            const int q = pm == 0 ? 0 : a.Kp - pm;
+            const uint32_t D = ((uint32_t)q << a.lev) + (uint32_t)v;
             const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
             for (int c0 = 0; c0 < kTN; c0 += 32) {
                 uint32_t re[32], im[32];
                 TMEM_LD32(tl + c0, re);
                 TMEM_LD32(tl + 256 + c0, im);
                 tmem_wait_ld();
+                unsigned long long key[32];
 #pragma unroll
                 for (int n = 0; n < 32; ++n) {
                     const float xr = __uint_as_float(re[n]), xi = __uint_as_float(im[n]);
-                    const int q = pm == 0 ? 0 : a.Kp - pm;
-                    const uint32_t D = ((uint32_t)q << a.lev) + (uint32_t)v;
-                    const unsigned long long key =
-                        ((unsigned long long)__float_as_uint(xr * xr + xi * xi) << 32) | (unsigned long long)(0xFFFFFFFFu - D);
-                    best = key > best ? key : best;
-                    if (a.R && valid) a.R[(b * (a.J + 1) + a.j) * a.N + D] = make_float2(xr, xi);
-                    pm += step;
-                    if (pm >= a.Kp) pm -= a.Kp;
+                    key[n] = ((unsigned long long)__float_as_uint(xr * xr + xi * xi) << 32) |
+                             (unsigned long long)(0xFFFFFFFFu - D);
+                    if (a.R && c0 + n < cnt) {
+                        const int64_t b = a.perm[row0 + c0 + n];
+                        a.R[(b * (a.J + 1) + a.j) * a.N + D] = make_float2(xr, xi);
+                    }
+                }
+                // transpose-reduce: afterwards lane i holds the max over the warp's
+                // 32 advances for pulse c0 + i
+#pragma unroll
+                for (int sh = 16; sh >= 1; sh >>= 1) {
+                    const bool upper = (lane & sh) != 0;
+#pragma unroll
+                    for (int i = 0; i < sh; ++i) {
+                        const unsigned long long send = upper ? key[i] : key[i + sh];
+                        const unsigned long long keep = upper ? key[i + sh] : key[i];
+                        key[i] = kmax(keep, __shfl_xor_sync(0xffffffffu, send, sh));
+                    }
+                }
+                if (c0 + lane < cnt && key[0]) {
+                    const int64_t b = a.perm[row0 + c0 + lane];
+                    atomicMax(&a.keys[b * (a.J + 1) + a.j], key[0]);
                 }
             }
-            if (valid && best) atomicMax(&a.keys[b * (a.J + 1) + a.j], best);
         }
     }
 
@@ -259,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     if (threadIdx.x == 0 && sflag[0]) {
-        for (int kb = sflag[2]; kb < sflag[1]; ++kb) mbar_wait(&full[kb % kStages], (kb / kStages) & 1);
+        for (int kb = sflag[2]; kb < sflag[1]; ++kb) mbar_wait(&full[kb & 1], (kb >> 1) & 1);
         atomicOr(a.err, 2);
     }
     __syncthreads();
@@ -346,7 +354,7 @@ uint32_t tc32_scale_mask(const sidwt_plan *p) {
     return m;
 }
 
-static int tc32_lc(int64_t Kp) { return (int)(2 * Kp + 4 * tc32::kWinChunks + 16); }
+static int tc32_lc(int64_t Kp) { return (int)(2 * Kp + 4 * tc32::kWinChunks); }
 static int tc32_rows_per_ref(const sidwt_plan *p, int j) {
     const int lev = j < p->J ? j + 1 : p->J;
     return (j < p->J ? 2 : 1) * (1 << lev) * tc32::kRowsPerVariant;
@@ -411,7 +419,7 @@ sidwt_status correlate_tc32(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_
         if (e != cudaSuccess) return cuda_fail(e, "reference packing launch");
         p->tc32_packed = p->nrefs;
     }
-    const int64_t max_pt = (B + tc32::kTM - 1) / tc32::kTM + std::min<int64_t>(p->nrefs, B);
+    const int64_t max_pt = (B + tc32::kTN - 1) / tc32::kTN + std::min<int64_t>(p->nrefs, B);
     for (int j = 0; j <= J; ++j) {
         if (!(mask & (1u << j))) continue;
         const int lev = j < J ? j + 1 : J;
@@ -426,15 +434,15 @@ sidwt_status correlate_tc32(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_
                                                      p->tiles.ntiles, (int)B, bhi, blo);
         }
         // TF32 data is moved as pairs of 16-bit units: a 16-byte chunk is 8 units
-        CUtensorMap mW, mUh, mUl;  // stored windows; received hi / lo
+        CUtensorMap mA, mBh, mBl;
         const uint64_t nchunk = (uint64_t)Kj / 4 * 2;
-        if ((st = tc::encode_3d(&mUh, bhi, 8, (uint64_t)B, nchunk, 16, 16 * (uint64_t)B, 8, tc32::kTM, 8)) ||
-            (st = tc::encode_3d(&mUl, blo, 8, (uint64_t)B, nchunk, 16, 16 * (uint64_t)B, 8, tc32::kTM, 8)))
+        if ((st = tc::encode_3d(&mBh, bhi, 8, (uint64_t)B, nchunk, 16, 16 * (uint64_t)B, 8, tc32::kTN, 8)) ||
+            (st = tc::encode_3d(&mBl, blo, 8, (uint64_t)B, nchunk, 16, 16 * (uint64_t)B, 8, tc32::kTN, 8)))
             return st;
         const int Lc = tc32_lc(Kp);
         const int rpr = tc32_rows_per_ref(p, j);
-        if ((st = tc::encode_3d(&mW, p->tc32_ref[j], 8, (uint64_t)(Lc / 4), (uint64_t)p->nrefs * rpr, 16,
-                                (uint64_t)Lc * 4, 8, tc32::kWinChunks, tc32::kBRows)))
+        if ((st = tc::encode_3d(&mA, p->tc32_ref[j], 8, (uint64_t)(Lc / 4), (uint64_t)p->nrefs * rpr, 16,
+                                (uint64_t)Lc * 4, 8, tc32::kWinChunks, tc32::kARows)))
             return st;
         tc32::Args a{};
         a.N = N;
@@ -460,16 +468,16 @@ sidwt_status correlate_tc32(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_
             set_error("batch too large for one tensor-core launch");
             return SIDWT_EINVAL;
         }
-        tc32::corr_tc32_kernel<<<(unsigned)grid, tc32::kThreads, tc32::kSmemBytes, s>>>(mW, mUh, mUl, a);
+        tc32::corr_tc32_kernel<<<(unsigned)grid, tc32::kThreads, tc32::kSmemBytes, s>>>(mA, mBh, mBl, a);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "3xTF32 correlation launch");
     }
     const uint32_t rest = ((1u << (J + 1)) - 1u) & ~mask;
-    if (rest) return correlate_simt(p, B, r_dev, s, rest, tc32::kTM);
+    if (rest) return correlate_simt(p, B, r_dev, s, rest, tc32::kTN);
     return SIDWT_OK;
 }
 
-int tc32_group_tile() { return tc32::kTM; }
+int tc32_group_tile() { return tc32::kTN; }
 
 int tc32_launch_count(const sidwt_plan *p) {
     const uint32_t mask = tc32_scale_mask(p);
