@@ -180,13 +180,9 @@ sidwt_status sidwt_peaks(sidwt_plan *p, int64_t B, int32_t *lag_dev, float *mag_
                          sidwt_stream stream);
 
 /* End-to-end call on host buffers: copies ref_ids_host and y_host to the
- * device (through pinned staging owned by the plan when they are pageable),
- * correlates, and copies the peaks back; returns after the stream has
- * finished.  Batches of 2048 pulses or more go in up to 4 chunks: every
- * chunk's copy is queued at once on a stream of the plan, and each chunk is
- * correlated on `stream` while the next one arrives; the plan then keeps only
- * the last chunk's peaks, so a following sidwt_peaks returns EINVAL.  Any
- * output pointer may be NULL.  Same layouts as sidwt_correlate / sidwt_peaks. */
+ * device (through pinned staging owned by the plan), correlates, and copies
+ * the peaks back; returns after the stream has finished.  Any output pointer
+ * may be NULL.  Same layouts as sidwt_correlate / sidwt_peaks. */
 sidwt_status sidwt_correlate_host(sidwt_plan *p, const int32_t *ref_ids_host, const void *y_host, int64_t B,
                                   sidwt_precision prec, int32_t *lag_host, float *mag_host, double *norm_host,
                                   sidwt_stream stream);

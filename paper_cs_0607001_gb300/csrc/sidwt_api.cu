@@ -269,9 +269,6 @@ sidwt_status sidwt_plan_destroy(sidwt_plan *p) {
     dfree(p->err);
     if (p->h_stage) cudaFreeHost(p->h_stage);
     if (p->d_in) cudaFree(p->d_in);
-    for (cudaEvent_t ev : p->copy_done)
-        if (ev) cudaEventDestroy(ev);
-    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     for (auto &m : p->marks) {
         cudaEventDestroy(m.a);
         cudaEventDestroy(m.b);
@@ -527,51 +524,17 @@ sidwt_status sidwt_correlate_host(sidwt_plan *p, const int32_t *ref_ids_host, co
         ysrc = p->h_stage;
         isrc = static_cast<char *>(p->h_stage) + ybytes;
     }
-    // Large batches go in chunks: all host-to-device copies are queued at
-    // once on the plan's copy stream, and chunk k is correlated (on the
-    // caller's stream) while chunk k + 1 is still arriving.
-    const int64_t row = p->N * (p->is_int ? 4 : 8);
-    const int nchunk = B >= 2048 ? (int)std::min<int64_t>(kHostChunks, B / 1024) : 1;
-    cudaError_t e = cudaSuccess;
-    if (nchunk > 1 && !p->copy_stream) {
-        e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking);
-        for (int c = 0; e == cudaSuccess && c < kHostChunks; ++c)
-            e = cudaEventCreateWithFlags(&p->copy_done[c], cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_fail(e, "copy stream");
-    }
-    cudaStream_t cs = nchunk > 1 ? p->copy_stream : s;
-    if (nchunk > 1) {  // the copy stream must not overwrite inputs an earlier call still reads
-        e = cudaEventRecord(p->copy_done[0], s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, p->copy_done[0], 0);
-    }
-    for (int c = 0; e == cudaSuccess && c < nchunk; ++c) {
-        const int64_t b0 = B * c / nchunk, b1 = B * (c + 1) / nchunk;
-        e = cudaMemcpyAsync(dy + b0 * row, static_cast<const char *>(ysrc) + b0 * row, (size_t)(b1 - b0) * row,
-                            cudaMemcpyHostToDevice, cs);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(dids + b0, static_cast<const int32_t *>(isrc) + b0, (size_t)(b1 - b0) * sizeof(int32_t),
-                                cudaMemcpyHostToDevice, cs);
-        if (e == cudaSuccess && nchunk > 1) e = cudaEventRecord(p->copy_done[c], cs);
-    }
+    cudaError_t e = cudaMemcpyAsync(dy, ysrc, ybytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dids, isrc, ibytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
-    const int J1 = p->J + 1;
-    for (int c = 0; c < nchunk; ++c) {
-        const int64_t b0 = B * c / nchunk, b1 = B * (c + 1) / nchunk, nb = b1 - b0;
-        if (nchunk > 1 && (e = cudaStreamWaitEvent(s, p->copy_done[c], 0)) != cudaSuccess)
-            return cuda_fail(e, "copy event");
-        sidwt_status st = sidwt_correlate(p, dids + b0, dy + b0 * row, nb, prec, nullptr, stream);
-        if (st) return st;
-        const size_t n = (size_t)nb * J1, o = (size_t)b0 * J1;
-        if (lag_host) e = cudaMemcpyAsync(lag_host + o, p->lag, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess && mag_host)
-            e = cudaMemcpyAsync(mag_host + o, p->mag, n * sizeof(float), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess && norm_host)
-            e = cudaMemcpyAsync(norm_host + o, p->norm, n * sizeof(double), cudaMemcpyDeviceToHost, s);
-        if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
-    }
-    // in chunks the plan keeps only the last chunk's peaks: sidwt_peaks then refuses (EINVAL)
-    p->last_B = nchunk > 1 ? -1 : B;
-    e = cudaStreamSynchronize(s);
+    sidwt_status st = sidwt_correlate(p, dids, dy, B, prec, nullptr, stream);
+    if (st) return st;
+    const size_t n = (size_t)B * (p->J + 1);
+    if (lag_host) e = cudaMemcpyAsync(lag_host, p->lag, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && mag_host) e = cudaMemcpyAsync(mag_host, p->mag, n * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && norm_host)
+        e = cudaMemcpyAsync(norm_host, p->norm, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "device-to-host copy");
 }
 

@@ -148,8 +148,6 @@ struct sidwt_plan {
     size_t h_stage_bytes = 0;
     void *d_in = nullptr;
     size_t d_in_bytes = 0;
-    cudaStream_t copy_stream = nullptr;  // chunked host-to-device copies
-    cudaEvent_t copy_done[4] = {};
 
     // tensor-core operands (per scale j): packed reference windows and the
     // received bf16 hi/lo planes in grouped order
@@ -182,8 +180,6 @@ struct sidwt_plan {
 };
 
 namespace sidwt {
-
-constexpr int kHostChunks = 4;  // sidwt_correlate_host splits batches of >= 2048 pulses into up to 4 chunks
 
 // stage timing (no-ops unless the plan's timing is on)
 struct StageTimer {

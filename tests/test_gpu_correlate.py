@@ -174,25 +174,3 @@ def test_host_entry_point_matches_device_entry_point():
         torch.cuda.synchronize()
         for a, b in ((lh, ld), (mh, md), (nh, nd), (lp, ld)):
             np.testing.assert_array_equal(a.numpy(), b.cpu().numpy())
-
-
-@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
-def test_chunked_host_entry_point_matches_one_device_call(precision):
-    """Batches of 2048+ pulses go through the host entry point in chunks whose
-    copies overlap the correlation; the peaks equal one device call's."""
-    from paper_cs_0607001_gb300 import sidwt
-    w = inputs.random_batch(n_refs=3, B=4100, N=256, J=3, seed=13)
-    with sidwt.Plan("cdf97", 256, 3) as p:
-        for x in w["refs"]:
-            p.store_reference(U.to_dev_c64(x))
-        ids = torch.from_numpy(w["ref_ids"].astype(np.int32))
-        y = torch.from_numpy(w["y"]).pin_memory()
-        lh, mh, nh = p.correlate_host(ids.pin_memory(), y, precision=precision)
-        with pytest.raises(sidwt.SidwtError, match="EINVAL"):
-            p.peaks(4100)
-        p.correlate(ids.to(U.dev()), y.to(U.dev()), precision=precision)
-        ld, md, nd = p.peaks(4100)
-        torch.cuda.synchronize()
-    np.testing.assert_array_equal(lh.numpy(), ld.cpu().numpy())
-    np.testing.assert_allclose(mh.numpy(), md.cpu().numpy(), rtol=1e-6)
-    np.testing.assert_allclose(nh.numpy(), nd.cpu().numpy(), rtol=1e-6)
