@@ -162,9 +162,11 @@ sidwt_status sidwt_analyze(sidwt_plan *p, const void *y_dev, int64_t B, void *py
  *   invalid (its peaks read lag -1) and is reported by sidwt_check.
  * y_dev: as for sidwt_analyze.
  * prec: SIDWT_PREC_FP32, SIDWT_PREC_BF16X3 or SIDWT_PREC_TF32X3.  Batches of at most 16
- *   pulses run every pulse as a batch of one on the FP32 CUDA-core kernel of
- *   the ragged path, whatever prec says (a tile of 64 or 128 pulses would be
- *   mostly empty); the first call with a given B builds that work list.
+ *   pulses run in FP32 on the CUDA cores whatever prec says (a tile of 64 or
+ *   128 pulses would be mostly empty): for N <= 8192 one CTA per (pulse,
+ *   scale, variant, 32 delays) with the contraction split over its warps
+ *   (the latency path), else the batch-of-one kernel of the ragged path, whose
+ *   work list the first call with a given B builds.
  * r_dev: optional complex64[B][J+1][N], r_j[D] at [b][j][D]; NULL skips it
  *   (the full output is large: B (J+1) N 8 bytes). */
 sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const void *y_dev, int64_t B,
@@ -221,12 +223,17 @@ sidwt_status sidwt_check(sidwt_plan *p, sidwt_stream stream);
 
 /* ---------------------------------------------------------------------------
  * Ragged batches: pulses of uneven length N, depth J and filter, each against
- * its own stored signal, correlated in one persistent launch (all lags, all
- * J+1 scales, peaks), optionally replayed as a CUDA graph.  Every pair is a
- * batch of one, so the correlation runs on the CUDA cores in FP32; the work
- * list is ordered by cost (largest first) and pulled by a persistent grid.
- * Float filters only (D4, LeGall 5/3, CDF 9/7).  An object is not
- * thread-safe and holds one batch in flight.
+ * its own stored signal, correlated by persistent launches (all lags, all
+ * J+1 scales, peaks), optionally replayed as one CUDA graph.  Every pair is a
+ * batch of one.  In FP32 (the default) the correlation runs on the CUDA
+ * cores: a work list over (pair, scale, variant, block of delays), ordered by
+ * cost (largest first) and pulled by a persistent grid.  With
+ * sidwt_ragged_set_precision(SIDWT_PREC_BF16X3) the scales whose bands have
+ * at least 64 samples run as tcgen05 GEMMs instead (see there).  Float
+ * filters only (D4, LeGall 5/3, CDF 9/7).  An object is not thread-safe and
+ * holds one batch in flight; a graph refers to the object's buffers, so a
+ * later call that grows them (more or longer references, a larger batch)
+ * invalidates it.
  * ------------------------------------------------------------------------- */
 typedef struct sidwt_ragged sidwt_ragged;
 
