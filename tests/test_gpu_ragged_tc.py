@@ -130,3 +130,40 @@ def test_ragged_precision_arguments():
             rg.set_precision(7)
         rg.set_precision("bf16x3")
         rg.check()
+
+
+def test_full_size_ragged_batch_sampled(oracle):
+    """The 10000-pulse ragged batch (N log-uniform 256-65536, J 3-8, mixed
+    filters) in the benchmark's configuration (BF16x3, one graph replay):
+    every pulse's scale-0 peak at its injected delay, and a stratified sample
+    of the shorter pulses against the oracle within the stated bound."""
+    from paper_cs_0607001_gb300 import inputs, sidwt
+    w = inputs.ragged_batch(n=10000)
+    Ns, Js, fs, off = w["N"], w["J"], w["filter"], w["offsets"]
+    refs = torch.from_numpy(w["refs"]).to(U.dev())
+    y = torch.from_numpy(w["y"]).to(U.dev())
+    with sidwt.Ragged() as rg:
+        rg.set_precision("bf16x3")
+        ids = [rg.store_reference(int(fs[i]), int(Ns[i]), int(Js[i]), refs[off[i]:off[i] + Ns[i]])
+               for i in range(len(Ns))]
+        rg.graph_create(ids, off, y)
+        n = rg.graph_launch()
+        lag, mag, norm = rg.peaks(n)
+        rg.check()
+        first, _ = rg.slots_of(ids)
+        lag, mag = lag.cpu().numpy(), mag.cpu().numpy()
+    assert (lag[first] == w["delays"]).all()
+    order = np.argsort(Ns, kind="stable")
+    small = order[Ns[order] <= 4096]
+    pick = small[np.linspace(0, len(small) - 1, 16).astype(int)]
+    for i in pick:
+        N, J, f = int(Ns[i]), int(Js[i]), int(fs[i])
+        x = w["refs"][off[i]:off[i] + N].astype(np.complex128)
+        yy = w["y"][off[i]:off[i] + N].astype(np.complex128)
+        r_or = oracle.correlate(f, x, yy, J)
+        bounds = stated_bounds(oracle, f, N, J, x, yy)
+        for j in range(J + 1):
+            g = int(lag[first[i] + j])
+            assert abs(mag[first[i] + j] - np.abs(r_or[j][g])) <= bounds[j], (i, j)
+            U.check_peak_lags(lag[first[i] + j:first[i] + j + 1], r_or[j:j + 1], bounds[j] / np.abs(r_or[j]).max(),
+                              what=f"item {i} scale {j}")

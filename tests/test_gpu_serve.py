@@ -125,3 +125,37 @@ def test_bad_requests_rejected_on_submit():
             srv.submit(9, "cdf97", 128, 3, y)  # unknown waveform
         with pytest.raises(sidwt.SidwtError, match="EINVAL"):
             srv.submit(0, "legall53_int", 128, 3, y)
+
+
+def test_long_requests_alone_equal_mix_and_find_their_delays():
+    """Requests of the serving workload's long end (N = 2^17, 2^18 and a
+    non-power-of-two length, J up to 10) on the tensor-core path: the
+    scale-0 peak at the injected delay, and the same results alone and
+    mixed with short requests."""
+    from paper_cs_0607001_gb300 import sidwt
+    waves = waveforms()
+    g = np.random.default_rng(21)
+    specs = [(1 << 17, 10), (1 << 18, 9), (3 * (1 << 15), 8)]
+    longs = []
+    for N, J in specs:
+        x = np.zeros(N, np.complex128)
+        x[:len(waves[0])] = waves[0]
+        D = int(g.integers(0, N))
+        y = np.roll(x, D) + 0.05 * (g.standard_normal(N) + 1j * g.standard_normal(N))
+        longs.append({"N": N, "J": J, "D": D, "y": torch.from_numpy(y.astype(np.complex64)).pin_memory()})
+    shorts = make_requests(12, 22, waves)
+    with new_server(precision="bf16x3", memory_cap_bytes=4 << 30, max_lane_samples=1 << 20) as srv:
+        for wv in waves:
+            srv.add_waveform(wv)
+        srv.start()
+        mix = [srv.submit(0, "cdf97", r["N"], r["J"], r["y"]) for r in longs]
+        mix += [srv.submit(r["wave"], r["f"], r["N"], r["J"], r["y"]) for r in shorts]
+        srv.drain(300.0)
+        got = [srv.result(i) for i in mix[:len(longs)]]
+        for r, m in zip(longs, got):
+            assert m[0][0] == r["D"]
+            rid = srv.submit(0, "cdf97", r["N"], r["J"], r["y"])
+            srv.wait(rid, 300.0)
+            a = srv.result(rid)
+            np.testing.assert_array_equal(a[0], m[0])
+            np.testing.assert_allclose(a[1], m[1], rtol=1e-6)

@@ -174,3 +174,25 @@ def test_tf32x3_matches_oracle_within_stated_bound(oracle, fname, fid, N, J, B, 
     # measured: about 2e-5 of the peak at K ~ 1e3, set by the tensor cores'
     # FP32 accumulation rather than by the split (same order as bf16x3)
     assert worst_rel < 1e-4, worst_rel
+
+
+def test_fp32_many_reference_batch_sampled(oracle):
+    """The same 64 x 16384 batch on the plain FP32 path: sampled pulses within
+    the FP32 tolerance, scale-0 peaks at the injected delays."""
+    from paper_cs_0607001_gb300 import sidwt
+    w = inputs.many_ref_batch(n_refs=64, B=16384, N=4096, J=6)
+    with sidwt.Plan("cdf97", 4096, 6) as p:
+        for x in w["refs"]:
+            p.store_reference(U.to_dev_c64(x))
+        ids = torch.from_numpy(w["ref_ids"].astype(np.int32)).to(U.dev())
+        r = p.correlate(ids, U.to_dev_c64(w["y"]), precision="fp32", want_r=True)
+        lag, _, _ = p.peaks(16384)
+        sample = np.array([5, 640, 9999, 16380])
+        rs = r[torch.from_numpy(sample).to(U.dev())].cpu().numpy().astype(np.complex128)
+        lag = lag.cpu().numpy()
+    assert np.mean(lag[:, 0] == w["delays"]) > 0.99
+    X = w["refs"][w["ref_ids"][sample]].astype(np.complex128)
+    Y = w["y"][sample].astype(np.complex128)
+    _, _, _, ro, _ = oracle.correlate_batch(2, X, Y, 6, want_r=True)
+    for i in range(len(sample)):
+        U.check_r(rs[i], ro[i], what=f"pulse {sample[i]}")
