@@ -144,7 +144,7 @@ def test_long_requests_alone_equal_mix_and_find_their_delays():
         y = np.roll(x, D) + 0.05 * (g.standard_normal(N) + 1j * g.standard_normal(N))
         longs.append({"N": N, "J": J, "D": D, "y": torch.from_numpy(y.astype(np.complex64)).pin_memory()})
     shorts = make_requests(12, 22, waves)
-    with new_server(precision="bf16x3", memory_cap_bytes=4 << 30, max_lane_samples=1 << 20) as srv:
+    with new_server(precision="bf16x3", memory_cap_bytes=4 << 30, max_lane_samples=1 << 20, max_j=10) as srv:
         for wv in waves:
             srv.add_waveform(wv)
         srv.start()
