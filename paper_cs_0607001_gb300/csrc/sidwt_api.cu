@@ -269,11 +269,6 @@ sidwt_status sidwt_plan_destroy(sidwt_plan *p) {
     dfree(p->err);
     if (p->h_stage) cudaFreeHost(p->h_stage);
     if (p->d_in) cudaFree(p->d_in);
-    for (int c = 0; c < kCopyStreams; ++c) {
-        if (p->copy_done[c]) cudaEventDestroy(p->copy_done[c]);
-        if (p->copy_stream[c]) cudaStreamDestroy(p->copy_stream[c]);
-    }
-    if (p->copy_start) cudaEventDestroy(p->copy_start);
     for (auto &m : p->marks) {
         cudaEventDestroy(m.a);
         cudaEventDestroy(m.b);
@@ -529,34 +524,7 @@ sidwt_status sidwt_correlate_host(sidwt_plan *p, const int32_t *ref_ids_host, co
         ysrc = p->h_stage;
         isrc = static_cast<char *>(p->h_stage) + ybytes;
     }
-    // Large inputs are copied as kCopyStreams concurrent pieces on streams of
-    // the plan (several copy engines share the host link), joined by events.
-    cudaError_t e = cudaSuccess;
-    const int pieces = ybytes >= (size_t(64) << 20) ? kCopyStreams : 1;
-    if (pieces > 1 && !p->copy_stream[0]) {
-        for (int c = 0; e == cudaSuccess && c < kCopyStreams; ++c) {
-            e = cudaStreamCreateWithFlags(&p->copy_stream[c], cudaStreamNonBlocking);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->copy_done[c], cudaEventDisableTiming);
-        }
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->copy_start, cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_fail(e, "copy streams");
-    }
-    if (pieces > 1) {
-        // the copies must not overwrite inputs that earlier work on `stream` still reads
-        e = cudaEventRecord(p->copy_start, s);
-        const size_t step = ((ybytes + pieces - 1) / pieces + 255) & ~size_t(255);
-        for (int c = 0; e == cudaSuccess && c < pieces; ++c) {
-            const size_t o = (size_t)c * step, n = o < ybytes ? std::min(step, ybytes - o) : 0;
-            e = cudaStreamWaitEvent(p->copy_stream[c], p->copy_start, 0);
-            if (e == cudaSuccess && n)
-                e = cudaMemcpyAsync(dy + o, static_cast<const char *>(ysrc) + o, n, cudaMemcpyHostToDevice,
-                                    p->copy_stream[c]);
-            if (e == cudaSuccess) e = cudaEventRecord(p->copy_done[c], p->copy_stream[c]);
-        }
-        for (int c = 0; e == cudaSuccess && c < pieces; ++c) e = cudaStreamWaitEvent(s, p->copy_done[c], 0);
-    } else {
-        e = cudaMemcpyAsync(dy, ysrc, ybytes, cudaMemcpyHostToDevice, s);
-    }
+    cudaError_t e = cudaMemcpyAsync(dy, ysrc, ybytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dids, isrc, ibytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
     sidwt_status st = sidwt_correlate(p, dids, dy, B, prec, nullptr, stream);

@@ -148,9 +148,6 @@ struct sidwt_plan {
     size_t h_stage_bytes = 0;
     void *d_in = nullptr;
     size_t d_in_bytes = 0;
-    cudaStream_t copy_stream[4] = {};  // concurrent host-to-device copy pieces
-    cudaEvent_t copy_done[4] = {};
-    cudaEvent_t copy_start = nullptr;
 
     // tensor-core operands (per scale j): packed reference windows and the
     // received bf16 hi/lo planes in grouped order
@@ -183,8 +180,6 @@ struct sidwt_plan {
 };
 
 namespace sidwt {
-
-constexpr int kCopyStreams = 4;  // sidwt_correlate_host copies inputs of 64 MB or more in 4 concurrent pieces
 
 // stage timing (no-ops unless the plan's timing is on)
 struct StageTimer {
