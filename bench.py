@@ -997,7 +997,7 @@ def run_serve_workload(args):
                          "rejected": st["rejected"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
                          "gsamples_s": st["samples"] / max(st["span_s"], 1e-9) / 1e9,
                          "req_s": st["completed"] / max(st["span_s"], 1e-9), "batches": st["batches"],
-                         "max_batch": st["max_batch"]})
+                         "max_batch": st["max_batch"], "ref_hits": st["ref_hits"], "ref_stores": st["ref_stores"]})
     srv.close()
     best = max(per_rate, key=lambda r: r["gsamples_s"])
     line = {

@@ -330,7 +330,10 @@ sidwt_status sidwt_ragged_tuning(const sidwt_ragged *r, int32_t *mq_by_log2_band
  * fit the lane's share of memory_cap_bytes (request footprint about
  * (32 + 16 J) N bytes), zero-pads each request's waveform to its N, builds
  * the SIDWT trees and runs the ragged correlation, so batches overlap on the
- * device.  A request larger than a lane's share is rejected (SIDWT_ENOMEM).
+ * device.  Each lane keeps the stored trees it built, keyed by (waveform,
+ * filter, N, J), until its pre-reserved stores are full (then it starts
+ * afresh): a request whose key is resident on its lane skips the stored-side
+ * analysis.  A request larger than a lane's share is rejected (SIDWT_ENOMEM).
  * Latency runs from sidwt_server_submit to the moment the server thread
  * sees the lane's completion event.
  * ------------------------------------------------------------------------- */
@@ -351,6 +354,9 @@ typedef struct {
     int64_t completed, rejected, batches, max_batch, samples, queued;
     double p50_ms, p99_ms, max_ms; /* latency of completed requests              */
     double span_s;                 /* first arrival to last completion            */
+    int64_t ref_hits;              /* requests whose stored SIDWT tree was already
+                                      resident on their lane (no re-analysis)    */
+    int64_t ref_stores;            /* stored trees built for requests            */
 } sidwt_server_stats;
 
 sidwt_status sidwt_server_create(const sidwt_server_config *cfg, sidwt_server **out);

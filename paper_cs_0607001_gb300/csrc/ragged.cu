@@ -867,6 +867,11 @@ sidwt_status correlate_small(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t 
 
 }  // namespace sidwt
 
+bool sidwt::ragged_room(const sidwt_ragged *r, int64_t tree_elems, int64_t xen_elems, int64_t tc_elems) {
+    return r->tree_used + tree_elems <= r->tree_cap && r->xen_used + xen_elems <= r->xen_cap &&
+           r->tc_a_used + tc_elems <= r->tc_a_cap;
+}
+
 sidwt_status sidwt::ragged_reserve_tc(sidwt_ragged *r, int64_t stored_elems, int64_t received_elems) {
     sidwt_status st;
     if ((st = grow(&r->tc_a, &r->tc_a_cap, stored_elems, r->tc_a_used, "stored tensor-core operands"))) return st;

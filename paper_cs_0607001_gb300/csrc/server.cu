@@ -79,7 +79,14 @@ struct Lane {
     bool busy = false;
     std::vector<Request *> batch;
     int64_t bytes = 0;
+    // stored signals resident in this lane's ragged object, keyed by
+    // (waveform, filter, N, J): a repeated request reuses its SIDWT tree
+    std::unordered_map<uint64_t, int32_t> cache;
 };
+
+uint64_t ref_key(int32_t wave, int filter, int64_t N, int J) {
+    return (uint64_t)(uint32_t)wave | ((uint64_t)filter << 20) | ((uint64_t)J << 24) | ((uint64_t)N << 32);
+}
 
 }  // namespace
 
@@ -102,6 +109,7 @@ struct sidwt_server {
     Clock::time_point first_arrival, last_done;
     bool any = false;
     int64_t max_batch_seen = 0;
+    int64_t ref_hits = 0, ref_stores = 0;
 };
 
 namespace {
@@ -141,30 +149,76 @@ void fail_lane(sidwt_server *s, Lane &L, sidwt_status st) {
     L.bytes = 0;
     L.batch.clear();
     L.busy = false;
+    // what the failed batch stored may be incomplete
+    L.cache.clear();
+    sidwt_ragged_reset_references(L.rg);
     s->cv_done.notify_all();
+}
+
+// Elements one more stored signal takes in a lane's ragged object.
+void store_needs(const sidwt_server *s, int64_t N, int J, int64_t *tree, int64_t *xen, int64_t *tc) {
+    *tree = 2 * (int64_t)J * N;
+    *xen = (int64_t(2) << J) - 1;
+    int64_t a = 0, b = 0;
+    if (s->cfg.precision == SIDWT_PREC_BF16X3) rtc::operand_elems(N, J, &a, &b);
+    *tc = a;
 }
 
 // Enqueue a formed batch on a lane (server thread only).
 sidwt_status launch_lane(sidwt_server *s, Lane &L) {
     cudaStream_t st = L.stream;
-    sidwt_ragged_reset_references(L.rg);
+    // the batch's signals not yet resident must fit the lane's reserved
+    // stores; otherwise start the cache afresh (nothing of it is in flight:
+    // the lane is idle)
+    {
+        int64_t t = 0, x = 0, c = 0;
+        std::unordered_map<uint64_t, int> seen;
+        for (Request *r : L.batch) {
+            const uint64_t k = ref_key(r->wave, r->filter, r->N, r->J);
+            if (L.cache.count(k) || seen.count(k)) continue;
+            seen[k] = 1;
+            int64_t a, b2, d;
+            store_needs(s, r->N, r->J, &a, &b2, &d);
+            t += a;
+            x += b2;
+            c += d;
+        }
+        if (!ragged_room(L.rg, t, x, c)) {
+            sidwt_ragged_reset_references(L.rg);
+            L.cache.clear();
+        }
+    }
     std::vector<int32_t> ids;
     std::vector<int64_t> offs;
-    int64_t off = 0, slots = 0;
+    int64_t off = 0, slots = 0, hits = 0, misses = 0;
     for (Request *r : L.batch) {
         cudaError_t e = cudaMemcpyAsync(L.y + off, r->y_host, (size_t)r->N * 8, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "request pulse copy");
-        const int64_t wl = std::min<int64_t>(s->wave_len[(size_t)r->wave], r->N);
-        pad_kernel<<<(unsigned)std::min<int64_t>(1024, (r->N + 255) / 256), 256, 0, st>>>(s->waves[(size_t)r->wave], wl,
-                                                                                        L.x + off, r->N);
+        const uint64_t key = ref_key(r->wave, r->filter, r->N, r->J);
+        auto it = L.cache.find(key);
         int32_t rid = -1;
-        sidwt_status ss = sidwt_ragged_store_reference(L.rg, (sidwt_filter)r->filter, r->N, r->J, L.x + off, &rid,
-                                                       reinterpret_cast<sidwt_stream>(st));
-        if (ss) return ss;
+        if (it != L.cache.end()) {
+            rid = it->second;
+            ++hits;
+        } else {
+            const int64_t wl = std::min<int64_t>(s->wave_len[(size_t)r->wave], r->N);
+            pad_kernel<<<(unsigned)std::min<int64_t>(1024, (r->N + 255) / 256), 256, 0, st>>>(
+                s->waves[(size_t)r->wave], wl, L.x + off, r->N);
+            sidwt_status ss = sidwt_ragged_store_reference(L.rg, (sidwt_filter)r->filter, r->N, r->J, L.x + off, &rid,
+                                                           reinterpret_cast<sidwt_stream>(st));
+            if (ss) return ss;
+            L.cache[key] = rid;
+            ++misses;
+        }
         ids.push_back(rid);
         offs.push_back(off);
         off += r->N;
         slots += r->J + 1;
+    }
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->ref_hits += hits;
+        s->ref_stores += misses;
     }
     sidwt_status ss = sidwt_ragged_correlate(L.rg, (int64_t)ids.size(), ids.data(), offs.data(), L.y, off,
                                              reinterpret_cast<sidwt_stream>(st));
@@ -469,6 +523,8 @@ sidwt_status sidwt_server_read_stats(sidwt_server *s, sidwt_server_stats *out, i
     out->max_batch = s->max_batch_seen;
     out->samples = s->samples;
     out->queued = (int64_t)s->queue.size();
+    out->ref_hits = s->ref_hits;
+    out->ref_stores = s->ref_stores;
     if (!s->lat_ms.empty()) {
         std::vector<double> v = s->lat_ms;
         std::sort(v.begin(), v.end());
@@ -482,6 +538,7 @@ sidwt_status sidwt_server_read_stats(sidwt_server *s, sidwt_server_stats *out, i
     if (reset) {
         s->lat_ms.clear();
         s->completed = s->rejected = s->batches = s->samples = s->max_batch_seen = 0;
+        s->ref_hits = s->ref_stores = 0;
         s->any = false;
         for (auto &kv : s->reqs)
             if (!kv.second->finished) {

@@ -307,4 +307,6 @@ cudaError_t prepare_kernels();
 
 // ---- ragged.cu: pre-size a ragged object's tensor-core operand buffers ----
 sidwt_status ragged_reserve_tc(sidwt_ragged *r, int64_t stored_elems, int64_t received_elems);
+// whether the reserved stores hold that many more elements without growing
+bool ragged_room(const sidwt_ragged *r, int64_t tree_elems, int64_t xen_elems, int64_t tc_elems);
 }  // namespace sidwt

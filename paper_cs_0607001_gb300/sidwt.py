@@ -44,7 +44,7 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("rejected", ctypes.c_int64), ("batches", ctypes.c_int64),
                 ("max_batch", ctypes.c_int64), ("samples", ctypes.c_int64), ("queued", ctypes.c_int64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("span_s", ctypes.c_double)]
+                ("span_s", ctypes.c_double), ("ref_hits", ctypes.c_int64), ("ref_stores", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -159,3 +159,45 @@ def test_long_requests_alone_equal_mix_and_find_their_delays():
             a = srv.result(rid)
             np.testing.assert_array_equal(a[0], m[0])
             np.testing.assert_allclose(a[1], m[1], rtol=1e-6)
+
+
+def test_lane_keeps_stored_trees_and_starts_afresh_when_full(oracle):
+    """A lane reuses the stored tree of a (waveform, filter, N, J) it already
+    holds; once its reserved stores are full it starts afresh.  Results stay
+    those of the oracle throughout."""
+    waves = waveforms()
+    g = np.random.default_rng(17)
+
+    def req(w, f, N, J):
+        x = np.zeros(N, np.complex128)
+        L = min(len(waves[w]), N)
+        x[:L] = waves[w][:L]
+        D = int(g.integers(0, N))
+        y = np.roll(x, D) + 0.05 * (g.standard_normal(N) + 1j * g.standard_normal(N))
+        return {"wave": w, "f": f, "N": N, "J": J, "D": D, "x": x,
+                "y": torch.from_numpy(y.astype(np.complex64)).pin_memory()}
+
+    few = [req(w, f, 1024, 3) for w, f in [(0, 0), (1, 1), (2, 2)]]
+    # 5 waves x 3 filters x 3 (N, J): 45 distinct keys, far more than one
+    # lane's stores hold (2 * max_j * max_lane_samples elements)
+    many = [req(w, f, N, J) for w in range(5) for f in range(3) for (N, J) in [(1024, 3), (2048, 4), (512, 2)]]
+    with new_server(lanes=1, max_batch=4, max_j=4, max_lane_samples=8192) as srv:
+        for w in waves:
+            srv.add_waveform(w)
+        srv.start()
+        seq = few * 4 + many + few
+        out = []
+        for r in seq:
+            rid = srv.submit(r["wave"], r["f"], r["N"], r["J"], r["y"])
+            srv.wait(rid, 60.0)
+            out.append(srv.result(rid))
+        st = srv.stats()
+    assert st["completed"] == len(seq)
+    assert st["ref_hits"] + st["ref_stores"] == len(seq)
+    assert st["ref_hits"] >= 9, st  # the repeats of the first three keys
+    assert st["ref_stores"] >= len(many) + 3, st  # every distinct key built at least once
+    for r, m in zip(seq, out):
+        lag, mag, _, _, _ = oracle.correlate_batch(r["f"], r["x"][None], r["y"].numpy()[None].astype(np.complex128),
+                                                   r["J"])
+        assert m[0][0] == r["D"] == lag[0, 0]
+        np.testing.assert_allclose(m[1], mag[0], rtol=2e-5)
