@@ -645,14 +645,11 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
                     const float4 v = q[n];
                     ens = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, ens))));
                 }
-                en.add(ens);
-                for (int o = 16; o > 0; o >>= 1) {
-                    EnAcc t;
-                    t.hi = __shfl_xor_sync(0xffffffffu, en.hi, o);
-                    t.lo = __shfl_xor_sync(0xffffffffu, en.lo, o);
-                    en.add(t);
-                }
-                if (lane == 0) redf[0][warp] = make_float2(en.hi, en.lo);
+                // a thread's partial is a plain FP32 sum of N / 256 squares
+                // at most; the warp tree adds five roundings more, so the
+                // compensated sum is kept for the cross-warp total only
+                for (int o = 16; o > 0; o >>= 1) ens += __shfl_xor_sync(0xffffffffu, ens, o);
+                if (lane == 0) redf[0][warp] = make_float2(ens, 0.f);
             }
         }
         for (int l = 1; l <= J; ++l) {
@@ -726,13 +723,9 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
                 for (int o = 16; o > 0; o >>= 1) eni += __shfl_xor_sync(0xffffffffu, eni, o);
                 if (lane == 0) redi[l][warp] = eni;
             } else {
-                for (int o = 16; o > 0; o >>= 1) {
-                    EnAcc t;
-                    t.hi = __shfl_xor_sync(0xffffffffu, en.hi, o);
-                    t.lo = __shfl_xor_sync(0xffffffffu, en.lo, o);
-                    en.add(t);
-                }
-                if (lane == 0) redf[l][warp] = make_float2(en.hi, en.lo);
+                float v = en.hi + en.lo;  // one plain FP32 partial (see level 0)
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) redf[l][warp] = make_float2(v, 0.f);
             }
             __syncthreads();
         }
