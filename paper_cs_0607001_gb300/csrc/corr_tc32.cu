@@ -12,6 +12,10 @@
 //     are 16 bytes apart and the K-major core matrices overlap (LBO 16 B,
 //     SBO 128 B).  One CTA owns one residue r and 128 advances spaced by 4
 //     (512 consecutive advances per r-quadruple of CTAs).
+//     Bands shorter than 512 put G variants in one tile instead: variant g's
+//     window (K'/4 + 4 chunks) starts at row g (K'/4 + 4) of the same
+//     overlapping layout, so rows g (K'/4 + 4) + i, i < K'/4, are its advances
+//     r + 4 i and the 4 rows between windows are discarded.
 //   * B (N = 256 columns) is 256 received pulses of one reference, K-major
 //     ([k/4][Re|Im][pulse][4 samples]), loaded by TMA as a plain box.
 // Re and Im: Re += A(wr) B(ur) + A(wi) B(ui), Im += A(wr) B(ui) + A(-wi) B(ur);
@@ -40,10 +44,12 @@ constexpr int kLagBlock = 512;                  // advances per (r-quadruple of)
 constexpr int kWinChunks = 132;                 // window chunks of 4 samples: 4*127 + 15 < 528
 constexpr int kWinRowBytes = kWinChunks * 16;   // 2112
 constexpr int kARows = 3;                       // planes -Im, Re, Im of one residue
-constexpr int kABytes = 6400;                   // 3 rows x 2112 B, rounded up to 128
+constexpr int kABytes = 6528;                   // 3 planes x 2176 B (2112 B rounded up to 128)
 constexpr int kBBytes = 4 * 2 * kTN * 16;       // [4 k-chunks][Re|Im][256][16 B] = 32768
-constexpr int kStage = 2 * kBBytes + 2 * kABytes;  // B hi, B lo, A hi, A lo = 78336
-constexpr int kBarOff = 2 * kStage;             // 156672
+constexpr int kStage = 2 * kBBytes + 2 * kABytes;  // B hi, B lo, A hi, A lo = 78592
+static_assert(kARows * ((kWinRowBytes + 127) / 128 * 128) <= kABytes, "three plane windows per hi/lo region");
+static_assert(kStage % 128 == 0 && kBBytes % 128 == 0 && kABytes % 128 == 0, "TMA destinations 128-byte aligned");
+constexpr int kBarOff = 2 * kStage;             // 157184
 constexpr int kSmemBytes = kBarOff + 128 + 1024;
 constexpr int kTmemCols = 512;
 constexpr int kRowsPerVariant = 24;             // hi/lo x 4 residues x 3 planes
@@ -79,6 +85,7 @@ struct Args {
     int Kp, nv, nbands, nlb;  // band length, variants, bands, 512-advance blocks per variant
     int kb_per_band;          // K' / 16
     int rows_per_ref;
+    int G, cg, nvg;           // variants per tile, window chunks per variant, variant groups
     const int32_t *perm;
     const int32_t *tile_ref;
     const int32_t *tile_start;
@@ -90,6 +97,15 @@ struct Args {
 };
 
 __device__ __forceinline__ unsigned long long kmax(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2,
+                                            int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(saddr(bar))
+        : "memory");
+}
 
 __global__ void __launch_bounds__(kThreads, 1)
     corr_tc32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB_hi,
@@ -105,8 +121,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int bx = blockIdx.x;
     const int lb = bx % a.nlb;
     const int r = (bx / a.nlb) & 3;
-    const int v = (bx / (a.nlb * 4)) % a.nv;
-    const int pt = bx / (a.nlb * 4 * a.nv);
+    const int v0 = ((bx / (a.nlb * 4)) % a.nvg) * a.G;  // first variant of the tile
+    const int pt = bx / (a.nlb * 4 * a.nvg);
+    // one plane's windows: G * cg chunks, the plane regions 128-byte aligned (TMA destinations)
+    const uint32_t box_bytes = (uint32_t)(a.G * a.cg * 16);
+    const uint32_t pitch = (box_bytes + 127u) & ~127u;
     if (pt >= a.ntiles[0]) return;  // uniform: before any barrier or TMEM use
     const int row0 = a.tile_start[pt];
     const int cnt = a.tile_count[pt];
@@ -145,14 +164,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int band = kb / a.kb_per_band;
                 const int kap0 = (kb % a.kb_per_band) * kKB;
                 unsigned char *st = base + s * kStage;
-                mbar_expect_tx(&full[s], 2 * kBBytes + 2 * kARows * kWinRowBytes);
+                mbar_expect_tx(&full[s], 2 * kBBytes + 2 * kARows * box_bytes);
                 const int z0 = ((band * a.Kp + kap0) >> 2) * 2;
                 tma_load_3d(st, &mapB_hi, &full[s], 0, row0, z0);
                 tma_load_3d(st + kBBytes, &mapB_lo, &full[s], 0, row0, z0);
-                const int rowbase = ref * a.rows_per_ref + (band * a.nv + v) * kRowsPerVariant;
+                // A: per (hi/lo, plane) the windows of the tile's G variants, back to back
+                const int vblock = ref * (a.rows_per_ref / kRowsPerVariant) + band * a.nv + v0;
                 const int chunk0 = (kap0 + p0) >> 2;
-                tma_load_3d(st + 2 * kBBytes, &mapA, &full[s], 0, chunk0, rowbase + r * kARows);
-                tma_load_3d(st + 2 * kBBytes + kABytes, &mapA, &full[s], 0, chunk0, rowbase + 12 + r * kARows);
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int q = 0; q < kARows; ++q)
+                        tma_load_4d(st + 2 * kBBytes + h * kABytes + q * pitch, &mapA, &full[s], 0, chunk0,
+                                    h * 12 + r * kARows + q, vblock);
                 ++issued;
             }
             sflag[1] = issued;
@@ -175,10 +199,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int ks = 0; ks < 2; ++ks) {
                     // A rows: 0 -Im w, 1 Re w, 2 Im w; K-direction 16 B (next 4 samples), 8 advances 128 B
                     const uint32_t ao = (uint32_t)ks * 32;
-                    const uint64_t ah[3] = {sdesc(aHi + ao, 16, 128), sdesc(aHi + kWinRowBytes + ao, 16, 128),
-                                            sdesc(aHi + 2 * kWinRowBytes + ao, 16, 128)};
-                    const uint64_t al[3] = {sdesc(aLo + ao, 16, 128), sdesc(aLo + kWinRowBytes + ao, 16, 128),
-                                            sdesc(aLo + 2 * kWinRowBytes + ao, 16, 128)};
+                    const uint64_t ah[3] = {sdesc(aHi + ao, 16, 128), sdesc(aHi + pitch + ao, 16, 128),
+                                            sdesc(aHi + 2 * pitch + ao, 16, 128)};
+                    const uint64_t al[3] = {sdesc(aLo + ao, 16, 128), sdesc(aLo + pitch + ao, 16, 128),
+                                            sdesc(aLo + 2 * pitch + ao, 16, 128)};
                     // B planes Re u / Im u: [k-chunk][plane][256 pulses][16 B]; next k-chunk 8 KB, 8 pulses 128 B
                     const uint32_t bo = (uint32_t)(2 * ks) * 2 * 4096;
                     const uint64_t bh[2] = {sdesc(bHi + bo, 8192, 128), sdesc(bHi + bo + 4096, 8192, 128)};
@@ -222,10 +246,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!__all_sync(0xffffffffu, ok && !sflag[0])) {
             sflag[0] = 1;
         } else {
-            const int p = p0 + r + 4 * m;
+            // row m: variant v0 + g, advance p0 + r + 4 i (rows between windows are discarded)
+            const int g = m / a.cg, i = m - g * a.cg;
+            const bool valid = g < a.G && v0 + g < a.nv && p0 + r + 4 * i < a.Kp;
+            const int p = p0 + r + 4 * i;
             const int pm = p % a.Kp;
             const int q = pm == 0 ? 0 : a.Kp - pm;
-            const uint32_t D = ((uint32_t)q << a.lev) + (uint32_t)v;
+            const uint32_t D = ((uint32_t)q << a.lev) + (uint32_t)(v0 + g);
             const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
             for (int c0 = 0; c0 < kTN; c0 += 32) {
                 uint32_t re[32], im[32];
@@ -236,9 +263,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int n = 0; n < 32; ++n) {
                     const float xr = __uint_as_float(re[n]), xi = __uint_as_float(im[n]);
-                    key[n] = ((unsigned long long)__float_as_uint(xr * xr + xi * xi) << 32) |
-                             (unsigned long long)(0xFFFFFFFFu - D);
-                    if (a.R && c0 + n < cnt) {
+                    key[n] = valid ? ((unsigned long long)__float_as_uint(xr * xr + xi * xi) << 32) |
+                                         (unsigned long long)(0xFFFFFFFFu - D)
+                                   : 0ull;
+                    if (a.R && valid && c0 + n < cnt) {
                         const int64_t b = a.perm[row0 + c0 + n];
                         a.R[(b * (a.J + 1) + a.j) * a.N + D] = make_float2(xr, xi);
                     }
@@ -355,6 +383,21 @@ uint32_t tc32_scale_mask(const sidwt_plan *p) {
 }
 
 static int tc32_lc(int64_t Kp) { return (int)(2 * Kp + 4 * tc32::kWinChunks); }
+
+// Variants per tile for a band of Kp samples: one (rows = 128 advances of a
+// 512-advance block) unless Kp < 512; then G windows of Kp/4 + 4 chunks, the
+// last window's advances within the 128 rows and all windows within the
+// 132-chunk plane.
+static void tc32_group(int64_t Kp, int nv, int *G, int *cg) {
+    *G = 1;
+    *cg = tc32::kWinChunks;
+    if (Kp >= tc32::kLagBlock) return;
+    const int c = (int)(Kp / 4 + 4);
+    int g = 1;
+    while ((g + 1) * c <= tc32::kWinChunks && g * c + (int)(Kp / 4) <= 128 && g + 1 <= nv) ++g;
+    *G = g;
+    *cg = c;
+}
 static int tc32_rows_per_ref(const sidwt_plan *p, int j) {
     const int lev = j < p->J ? j + 1 : p->J;
     return (j < p->J ? 2 : 1) * (1 << lev) * tc32::kRowsPerVariant;
@@ -441,9 +484,16 @@ sidwt_status correlate_tc32(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_
             return st;
         const int Lc = tc32_lc(Kp);
         const int rpr = tc32_rows_per_ref(p, j);
-        if ((st = tc::encode_3d(&mA, p->tc32_ref[j], 8, (uint64_t)(Lc / 4), (uint64_t)p->nrefs * rpr, 16,
-                                (uint64_t)Lc * 4, 8, tc32::kWinChunks, tc32::kARows)))
-            return st;
+        int G = 1, cg = tc32::kWinChunks;
+        tc32_group(Kp, 1 << lev, &G, &cg);
+        {
+            // [variant block][24 rows: hi/lo, residue, plane][Lc / 4 chunks][16 B]; box: one row of G blocks
+            const uint64_t dims[4] = {8, (uint64_t)(Lc / 4), (uint64_t)tc32::kRowsPerVariant,
+                                      (uint64_t)p->nrefs * rpr / tc32::kRowsPerVariant};
+            const uint64_t strides[3] = {16, (uint64_t)Lc * 4, (uint64_t)Lc * 4 * tc32::kRowsPerVariant};
+            const uint32_t box[4] = {8, (uint32_t)cg, 1, (uint32_t)G};
+            if ((st = tc::encode_nd(&mA, p->tc32_ref[j], 4, dims, strides, box))) return st;
+        }
         tc32::Args a{};
         a.N = N;
         a.J = J;
@@ -455,6 +505,9 @@ sidwt_status correlate_tc32(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_
         a.nlb = (int)((Kp + tc32::kLagBlock - 1) / tc32::kLagBlock);
         a.kb_per_band = (int)(Kp / tc32::kKB);
         a.rows_per_ref = rpr;
+        a.G = G;
+        a.cg = cg;
+        a.nvg = (a.nv + G - 1) / G;
         a.perm = p->tiles.perm;
         a.tile_ref = p->tiles.tile_ref;
         a.tile_start = p->tiles.tile_start;
@@ -463,7 +516,7 @@ sidwt_status correlate_tc32(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_
         a.keys = p->keys;
         a.R = r_dev;
         a.err = p->err;
-        const int64_t grid = max_pt * a.nv * 4 * a.nlb;
+        const int64_t grid = max_pt * a.nvg * 4 * a.nlb;
         if (grid > 0x7fffffff) {
             set_error("batch too large for one tensor-core launch");
             return SIDWT_EINVAL;
