@@ -435,9 +435,15 @@ def run_ragged_workload(args):
     y = torch.from_numpy(w["y"]).to(dev)
     slots = int((Js + 1).sum())
 
+    tune_s = {}
+
     def make(precision):
         r = S.Ragged()
         r.set_precision(precision)
+        # tile shapes of both paths tuned on this GPU before the references are stored
+        t0 = time.perf_counter()
+        r.autotune()
+        tune_s[precision] = time.perf_counter() - t0
         r.reserve(int((2 * Js * Ns).sum()), int((2 * Ns - 2 * (Ns >> Js)).sum()), slots)
         return r, [r.store_reference(int(fs[i]), int(Ns[i]), int(Js[i]), refs[off[i]:off[i] + Ns[i]]) for i in range(n)]
 
@@ -533,6 +539,9 @@ def run_ragged_workload(args):
         "stages_ms_direct_call": {"analyze_ms": t["analyze_ms"], "correlate_ms": t["correlate_ms"],
                                   "peaks_ms": t["peaks_ms"]},
         "tuning_mq_by_log2_band": rg.tuning()[8:16].tolist(),
+        "tuning_tc_weights_by_log2_band": {str(S_): [round(float(v), 3) for v in rg.tc_weights()[k, 6:17]]
+                                           for k, S_ in enumerate((256, 128, 64))},
+        "autotune_s": tune_s,
         "vs_plain": None if plain is None else {
             "plain_correlate_ms": plain["correlate_ms"], "this_correlate_ms": t["correlate_ms"],
             "speedup": plain["correlate_ms"] / t["correlate_ms"],

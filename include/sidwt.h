@@ -282,11 +282,22 @@ sidwt_status sidwt_ragged_graph_launch(sidwt_ragged *r, sidwt_stream stream);
 sidwt_status sidwt_ragged_peaks(sidwt_ragged *r, int64_t n_slots, int32_t *lag_dev, float *mag_dev, double *norm_dev,
                                 sidwt_stream stream);
 
-/* Autotune the shifts per thread of the correlation tiles for band lengths
- * 2^8 .. 2^15 by timing each candidate (1, 2, 4, 8) on a synthetic pair, and
- * write the choice to cache_path (or SIDWT_TUNE_CACHE; NULL and unset: not
- * written).  Allocates and synchronises; call outside stream capture. */
+/* Autotune the correlation tiles and write the choice to cache_path (or
+ * SIDWT_TUNE_CACHE; NULL and unset: not written; sidwt_ragged_create reads
+ * SIDWT_TUNE_CACHE).  CUDA-core tiles: the shifts per thread for band
+ * lengths 2^8 .. 2^15, each candidate (1, 2, 4, 8) timed on a synthetic
+ * pair.  Tensor-core tiles: for band lengths 2^6 .. 2^14, every tile width S
+ * (256, 128, 64 advances) timed on a synthetic pair's tiles replicated over
+ * the SMs; the weight of a width is its time per padded MMA element relative
+ * to S = 256, and a reference stored afterwards takes, per scale, the width
+ * of least weighted padded work (references stored before keep theirs).
+ * Allocates and synchronises; call outside stream capture.  SIDWT_ETIMEOUT
+ * if a timed kernel's bounded wait ran out. */
 sidwt_status sidwt_ragged_autotune(sidwt_ragged *r, const char *cache_path, sidwt_stream stream);
+
+/* The tensor-core width weights in use: w[k * 25 + b] for width 256 (k = 0),
+ * 128 (1), 64 (2) and bands of 2^b .. 2^(b+1) - 1 samples. */
+sidwt_status sidwt_ragged_tc_weights(const sidwt_ragged *r, float *w /* [3 * 25] */);
 
 /* Stage timing of direct sidwt_ragged_correlate calls (not graph replays),
  * same meaning as sidwt_set_timing / sidwt_read_timing: analyze_ms (lifting),

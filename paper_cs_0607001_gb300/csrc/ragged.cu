@@ -339,6 +339,7 @@ struct RefInfo {
     int J;
     int64_t tree_off, xen_off;
     int64_t tc_off[16];  // stored tensor-core operand of scale j (bf16 elements), -1: none
+    int16_t tc_S[16];    // its tile width, fixed when it was packed
 };
 
 struct RaggedLayout {  // everything a batch needs on the device, built on the host
@@ -406,8 +407,10 @@ struct sidwt_ragged {
     cudaGraphExec_t exec = nullptr;
     int64_t graph_slots = 0;
     int graph_launches = 0;
-    // tuning: shifts per thread by floor(log2(band length))
+    // tuning: shifts per thread by floor(log2(band length)); tensor-core tile
+    // width weights (applied to references stored afterwards)
     int mq_for[32];
+    rtc::TcWeights tcw;
     int sms = 0;
     // stage timing of direct calls (CUDA events), as for plans
     bool timing = false;
@@ -486,7 +489,8 @@ sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_i
         const RefInfo &ri = r->refs[(size_t)it.ref];
         for (int j = 0; j <= it.J; ++j) {
             rtc::Shape sh;
-            if (r->prec == SIDWT_PREC_BF16X3 && j < 16 && ri.tc_off[j] >= 0 && rtc::shape_for(it.N, it.J, j, &sh)) {
+            if (r->prec == SIDWT_PREC_BF16X3 && j < 16 && ri.tc_off[j] >= 0 &&
+                rtc::shape_with(it.N, it.J, j, ri.tc_S[j], &sh)) {
                 const int e = (int)L.recv.size();
                 rtc::RecvEntry re;
                 re.pyr_off = it.pyr_off;
@@ -733,15 +737,26 @@ sidwt_status enqueue(sidwt_ragged *r, const DevLayout &d, int64_t slots, int64_t
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "ragged correlation launch");
 }
 
+// Cache file lines: "<log2 band> <shifts per thread>" for the CUDA-core
+// tiles, "tc <tile width> <log2 band> <weight>" for the tensor-core tiles.
 void load_tuning(sidwt_ragged *r, const char *path) {
     for (int i = 0; i < 32; ++i) r->mq_for[i] = default_mq(i);
+    rtc::default_weights(&r->tcw);
     if (!path) path = std::getenv("SIDWT_TUNE_CACHE");
     if (!path) return;
     FILE *f = std::fopen(path, "r");
     if (!f) return;
-    int lg, mq;
-    while (std::fscanf(f, "%d %d", &lg, &mq) == 2)
-        if (lg >= 0 && lg < 32 && (mq == 1 || mq == 2 || mq == 4 || mq == 8)) r->mq_for[lg] = mq;
+    char line[128];
+    while (std::fgets(line, sizeof line, f)) {
+        int lg, mq, S;
+        float w;
+        if (std::sscanf(line, "tc %d %d %f", &S, &lg, &w) == 3) {
+            const int k = S == 256 ? 0 : (S == 128 ? 1 : (S == 64 ? 2 : -1));
+            if (k >= 0 && lg >= 0 && lg < rtc::kTcBuckets && w > 0.1f && w < 100.f) r->tcw.w[k][lg] = w;
+        } else if (std::sscanf(line, "%d %d", &lg, &mq) == 2) {
+            if (lg >= 0 && lg < 32 && (mq == 1 || mq == 2 || mq == 4 || mq == 8)) r->mq_for[lg] = mq;
+        }
+    }
     std::fclose(f);
 }
 
@@ -996,21 +1011,26 @@ sidwt_status sidwt_ragged_store_reference(sidwt_ragged *r, sidwt_filter f, int64
     p.tree_f = r->tree + r->tree_used;
     p.xen = r->xen + r->xen_used;
     if ((st = build_reference_tree(&p, x_dev, 0, reinterpret_cast<cudaStream_t>(stream)))) return st;
-    RefInfo ri{(int)f, N, J, r->tree_used, r->xen_used, {}};
-    for (int j = 0; j < 16; ++j) ri.tc_off[j] = -1;
+    RefInfo ri{(int)f, N, J, r->tree_used, r->xen_used, {}, {}};
+    for (int j = 0; j < 16; ++j) {
+        ri.tc_off[j] = -1;
+        ri.tc_S[j] = 0;
+    }
     if (r->prec == SIDWT_PREC_BF16X3) {
         // stored tensor-core operands of the scales whose bands are long enough
         int64_t need = r->tc_a_used;
         for (int j = 0; j <= J && j < 16; ++j) {
             rtc::Shape sh;
-            if (!rtc::shape_for(N, J, j, &sh)) continue;
+            if (!rtc::shape_for(N, J, j, &sh, &r->tcw)) continue;
             ri.tc_off[j] = need;
+            ri.tc_S[j] = (int16_t)sh.S;
             need += (sh.a_elems + 63) / 64 * 64;
         }
         if (need > r->tc_a_used) {
             if (need > r->tc_a_cap) cudaDeviceSynchronize();
             if ((st = grow(&r->tc_a, &r->tc_a_cap, need, r->tc_a_used, "stored tensor-core operands"))) return st;
-            if ((st = rtc::pack_stored(p.tree_f, N, J, ri.tc_off, r->tc_a, reinterpret_cast<cudaStream_t>(stream))))
+            if ((st = rtc::pack_stored(p.tree_f, N, J, ri.tc_off, ri.tc_S, r->tc_a,
+                                       reinterpret_cast<cudaStream_t>(stream))))
                 return st;
             r->tc_a_used = need;
         }
@@ -1120,6 +1140,150 @@ sidwt_status sidwt_ragged_peaks(sidwt_ragged *r, int64_t n_slots, int32_t *lag_d
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "ragged peak copy");
 }
 
+namespace {
+
+// Tensor-core tile widths: for each band bucket 2^lg (lg 6..14; longer bands
+// keep the 2^14 weights) one synthetic pair at scale 3 of J = 4 (N = 2^(lg+4):
+// 16 variants, so every tile is full; both bands, circular form) is packed
+// with every width and its tiles, replicated to keep every SM busy, are timed
+// on the persistent kernel.  A width's weight is its time per padded MMA
+// element (tiles x 128 rows x S columns x K) relative to width 256.
+sidwt_status tune_tc(sidwt_ragged *r, cudaStream_t s, std::string *report) {
+    const int lg_lo = 6, lg_hi = 14;
+    const int widths[3] = {256, 128, 64};
+    int64_t amax = 0, bmax = 0, tmax = 0;
+    for (int lg = lg_lo; lg <= lg_hi; ++lg)
+        for (int S : widths) {
+            rtc::Shape sh;
+            if (!rtc::shape_with(int64_t(16) << lg, 4, 3, S, &sh)) continue;
+            amax = std::max(amax, sh.a_elems);
+            bmax = std::max(bmax, sh.b_elems);
+        }
+    for (int lg = lg_lo; lg <= lg_hi; ++lg)
+        tmax = std::max<int64_t>(tmax, (int64_t)r->sms * std::min(64, std::max(2, 1 << std::max(0, 16 - lg))));
+    const int64_t Nmax = int64_t(16) << lg_hi;
+    float2 *tree = nullptr, *pyr = nullptr;
+    __nv_bfloat16 *abuf = nullptr, *bbuf = nullptr;
+    unsigned char *maps = nullptr;
+    rtc::TcTile *dt = nullptr;
+    rtc::RecvEntry *dre = nullptr;
+    unsigned long long *keys = nullptr;
+    int32_t *err = nullptr;
+    const size_t mb = rtc::map_bytes();
+    auto release = [&]() {
+        cudaFree(tree);
+        cudaFree(pyr);
+        cudaFree(abuf);
+        cudaFree(bbuf);
+        cudaFree(maps);
+        cudaFree(dt);
+        cudaFree(dre);
+        cudaFree(keys);
+        cudaFree(err);
+    };
+    if (cudaMalloc(&tree, 8 * Nmax * sizeof(float2)) != cudaSuccess ||  // 2 J N, J = 4
+        cudaMalloc(&pyr, 2 * Nmax * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&abuf, amax * sizeof(__nv_bfloat16)) != cudaSuccess ||
+        cudaMalloc(&bbuf, bmax * sizeof(__nv_bfloat16)) != cudaSuccess || cudaMalloc(&maps, 2 * mb) != cudaSuccess ||
+        cudaMalloc(&dt, tmax * sizeof(rtc::TcTile)) != cudaSuccess ||
+        cudaMalloc(&dre, sizeof(rtc::RecvEntry)) != cudaSuccess ||
+        cudaMalloc(&keys, sizeof(unsigned long long)) != cudaSuccess || cudaMalloc(&err, sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        set_error("autotune allocation failed");
+        return SIDWT_ENOMEM;
+    }
+    rg::fill_kernel<<<(unsigned)((8 * Nmax + 255) / 256), 256, 0, s>>>(tree, 8 * Nmax, 3u);
+    rg::fill_kernel<<<(unsigned)((2 * Nmax + 255) / 256), 256, 0, s>>>(pyr, 2 * Nmax, 4u);
+    cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<unsigned char> hmaps(2 * mb);
+    sidwt_status st = SIDWT_OK;
+    rtc::TcWeights w = r->tcw;
+    for (int lg = lg_lo; lg <= lg_hi && !st; ++lg) {
+        const int64_t Kp = int64_t(1) << lg, N = 16 * Kp;
+        double per[3] = {0, 0, 0};
+        for (int k = 0; k < 3 && !st; ++k) {
+            const int S = widths[k];
+            rtc::Shape sh;
+            rtc::shape_with(N, 4, 3, S, &sh);
+            int64_t a_off[16];
+            int16_t S_of[16];
+            for (int j = 0; j < 16; ++j) {
+                a_off[j] = -1;
+                S_of[j] = 0;
+            }
+            a_off[3] = 0;
+            S_of[3] = (int16_t)S;
+            if ((st = rtc::pack_stored(tree, N, 4, a_off, S_of, abuf, s))) break;
+            const rtc::RecvEntry re{0, 0, (int32_t)N, (int32_t)Kp, sh.lev, sh.nb, (int32_t)sh.Lc, sh.k0};
+            cudaMemcpyAsync(dre, &re, sizeof(re), cudaMemcpyHostToDevice, s);
+            if ((st = rtc::launch_pack_recv(pyr, dre, 1, bbuf, s))) break;
+            if ((st = rtc::encode_maps(hmaps.data(), abuf, bbuf, sh))) break;
+            cudaMemcpyAsync(maps, hmaps.data(), 2 * mb, cudaMemcpyHostToDevice, s);
+            const int n = r->sms * std::min(64, std::max(2, 1 << std::max(0, 16 - lg)));
+            std::vector<rtc::TcTile> tl((size_t)n);
+            for (int t = 0; t < n; ++t) {
+                rtc::TcTile &x = tl[(size_t)t];
+                x.map = 0;
+                x.tile = t % sh.tiles;
+                x.nkb = sh.nkb;
+                x.Kp = (int32_t)Kp;
+                x.gv = sh.gv;
+                x.nv = sh.nv;
+                x.nb = (int16_t)sh.nb;
+                x.lev = (int16_t)sh.lev;
+                x.S = (int16_t)S;
+                x.pad = 0;
+                x.slot = 0;
+            }
+            cudaMemcpyAsync(dt, tl.data(), (size_t)n * sizeof(rtc::TcTile), cudaMemcpyHostToDevice, s);
+            cudaStreamSynchronize(s);  // the host staging buffers are reused
+            float tot = 0.f;
+            for (int rep = 0; rep < 4 && !st; ++rep) {
+                cudaEventRecord(e0, s);
+                st = rtc::launch_corr(maps, dt, n, keys, err, r->sms, s);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tot += ms;
+            }
+            per[k] = (double)tot / ((double)n * S * sh.nkb);
+        }
+        if (st) break;
+        for (int k = 0; k < 3; ++k) {
+            const float v = per[0] > 0 ? (float)(per[k] / per[0]) : w.w[k][lg];
+            w.w[k][lg] = std::min(50.f, std::max(0.2f, v));
+            *report += "tc " + std::to_string(widths[k]) + " " + std::to_string(lg) + " " + std::to_string(w.w[k][lg]) + "\n";
+        }
+    }
+    int32_t herr = 0;
+    if (!st) {
+        cudaMemcpy(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) st = cuda_fail(e, "tensor-core autotune");
+        else if (herr) {
+            set_error("tensor-core autotune: a kernel wait timed out");
+            st = SIDWT_ETIMEOUT;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    release();
+    if (st) return st;
+    for (int lg = lg_hi + 1; lg < rtc::kTcBuckets; ++lg)
+        for (int k = 0; k < 3; ++k) w.w[k][lg] = w.w[k][lg_hi];
+    for (int lg = 0; lg < lg_lo; ++lg)
+        for (int k = 0; k < 3; ++k) w.w[k][lg] = w.w[k][lg_lo];
+    r->tcw = w;
+    return SIDWT_OK;
+}
+
+}  // namespace
+
 sidwt_status sidwt_ragged_autotune(sidwt_ragged *r, const char *cache_path, sidwt_stream stream) {
     if (!r) {
         set_error("NULL argument");
@@ -1134,7 +1298,11 @@ sidwt_status sidwt_ragged_autotune(sidwt_ragged *r, const char *cache_path, sidw
     int *counter = nullptr;
     rg::Item *ditem = nullptr;
     rg::Work *dwork = nullptr;
-    const int64_t max_work = 2 * (Nmax / 256);
+    // each candidate runs the pair's work items replicated until the largest
+    // shift count gives every SM four items: throughput, as in a real batch,
+    // rather than the latency of one pair
+    const int64_t lags_target = (int64_t)4 * r->sms * rg::kT * rg::kMaxMQ;
+    const int64_t max_work = 2 * lags_target / rg::kT + 2 * Nmax / rg::kT + 64;
     if (cudaMalloc(&tree, 2 * Nmax * sizeof(float2)) != cudaSuccess || cudaMalloc(&pyr, 2 * Nmax * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&keys, 4 * sizeof(unsigned long long)) != cudaSuccess || cudaMalloc(&counter, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&ditem, sizeof(rg::Item)) != cudaSuccess || cudaMalloc(&dwork, max_work * sizeof(rg::Work)) != cudaSuccess) {
@@ -1164,8 +1332,11 @@ sidwt_status sidwt_ragged_autotune(sidwt_ragged *r, const char *cache_path, sidw
             const int64_t TQ = (int64_t)rg::kT * mq;
             if (TQ > Kp) continue;
             std::vector<rg::Work> w;
-            for (int v = 0; v < 2; ++v)
-                for (int64_t q0 = 0; q0 < Kp; q0 += TQ) w.push_back({0, 0, (int16_t)mq, v, 1, (int32_t)q0, 0});
+            const int64_t reps = std::max<int64_t>(1, (lags_target + 2 * Kp - 1) / (2 * Kp));
+            for (int64_t k = 0; k < reps; ++k)
+                for (int v = 0; v < 2; ++v)
+                    for (int64_t q0 = 0; q0 < Kp; q0 += TQ) w.push_back({0, 0, (int16_t)mq, v, 1, (int32_t)q0, 0});
+            if ((int64_t)w.size() > max_work) continue;  // cannot happen: max_work bounds reps x items
             cudaMemcpyAsync(dwork, w.data(), w.size() * sizeof(rg::Work), cudaMemcpyHostToDevice, s);
             cudaStreamSynchronize(s);
             float tot = 0.f;
@@ -1199,6 +1370,8 @@ sidwt_status sidwt_ragged_autotune(sidwt_ragged *r, const char *cache_path, sidw
     cudaFree(dwork);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    sidwt_status st = tune_tc(r, s, &report);
+    if (st) return st;
     if (!cache_path) cache_path = std::getenv("SIDWT_TUNE_CACHE");
     if (cache_path) {
         FILE *f = std::fopen(cache_path, "w");
@@ -1303,6 +1476,16 @@ sidwt_status sidwt_ragged_tuning(const sidwt_ragged *r, int32_t *mq_by_log2_band
         return SIDWT_EINVAL;
     }
     for (int i = 0; i < 32; ++i) mq_by_log2_band[i] = r->mq_for[i];
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_ragged_tc_weights(const sidwt_ragged *r, float *w) {
+    if (!r || !w) {
+        set_error("NULL argument");
+        return SIDWT_EINVAL;
+    }
+    for (int k = 0; k < 3; ++k)
+        for (int b = 0; b < rtc::kTcBuckets; ++b) w[k * rtc::kTcBuckets + b] = r->tcw.w[k][b];
     return SIDWT_OK;
 }
 

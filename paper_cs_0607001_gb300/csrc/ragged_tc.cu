@@ -377,6 +377,14 @@ __global__ void __launch_bounds__(256) pack_recv_kernel(const float2 *__restrict
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+void default_weights(TcWeights *t) {
+    for (int b = 0; b < kTcBuckets; ++b) {
+        t->w[0][b] = 1.0f;
+        t->w[1][b] = 1.15f;
+        t->w[2][b] = 1.6f;
+    }
+}
+
 static void fill_shape(int64_t N, int J, int j, int S, Shape *sh) {
     sh->j = j;
     sh->lev = j < J ? j + 1 : J;
@@ -398,18 +406,35 @@ static void fill_shape(int64_t N, int J, int j, int S, Shape *sh) {
     sh->b_elems = (int64_t)48 * sh->nb * sh->Lc;
 }
 
+bool shape_with(int64_t N, int J, int j, int S, Shape *sh) {
+    const int lev = j < J ? j + 1 : J;
+    const int64_t Kp = N >> lev;
+    if (Kp < kMinBand || Kp > kMaxBand || (S != 256 && S != 128 && S != 64)) return false;
+    fill_shape(N, J, j, S, sh);
+    return true;
+}
+
 // Tensor-core shape of scale j, or false when the band is too short (it
 // stays on the CUDA cores).  S (256, 128 or 64) minimises the padded MMA
-// work, weighted by the narrower tiles' lower throughput per flop.
-bool shape_for(int64_t N, int J, int j, Shape *sh) {
+// work, weighted by each width's cost per padded element in the band's
+// log2 bucket (defaults, or measured by the autotuner).
+bool shape_for(int64_t N, int J, int j, Shape *sh, const TcWeights *w) {
     const int lev = j < J ? j + 1 : J;
     const int64_t Kp = N >> lev;
     if (Kp < kMinBand || Kp > kMaxBand) return false;
+    TcWeights def;
+    if (!w) {
+        default_weights(&def);
+        w = &def;
+    }
+    int b = 0;
+    while (b + 1 < kTcBuckets && (int64_t(2) << b) <= Kp) ++b;  // floor(log2 Kp)
     double best = 1e300;
-    for (int S : {256, 128, 64}) {
+    const int widths[3] = {256, 128, 64};
+    for (int k = 0; k < 3; ++k) {
         Shape t;
-        fill_shape(N, J, j, S, &t);
-        const double cost = (double)t.tiles * S * t.nkb * (S == 256 ? 1.0 : (S == 128 ? 1.15 : 1.6));
+        fill_shape(N, J, j, widths[k], &t);
+        const double cost = (double)t.tiles * widths[k] * t.nkb * w->w[k][b];
         if (cost < best) {
             best = cost;
             *sh = t;
@@ -430,13 +455,14 @@ void operand_elems(int64_t N, int J, int64_t *stored, int64_t *received) {
     *received = b;
 }
 
-sidwt_status pack_stored(const float2 *tree, int64_t N, int J, const int64_t *a_off, void *abuf, cudaStream_t s) {
+sidwt_status pack_stored(const float2 *tree, int64_t N, int J, const int64_t *a_off, const int16_t *S_of, void *abuf,
+                         cudaStream_t s) {
     StoreScales sc;
     std::memset(&sc, 0, sizeof(sc));
     int64_t total = 0;
     for (int j = 0; j <= J && j < 16; ++j) {
         Shape sh;
-        if (a_off[j] < 0 || !shape_for(N, J, j, &sh)) continue;
+        if (a_off[j] < 0 || !shape_with(N, J, j, S_of[j], &sh)) continue;
         StoreScale &z = sc.s[sc.n++];
         z.out_off = a_off[j];
         z.first = total;

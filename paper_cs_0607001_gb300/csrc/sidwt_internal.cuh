@@ -289,13 +289,25 @@ struct RecvEntry {
     int32_t N, Kp, lev, nb, Lc, k0;
 };
 
-bool shape_for(int64_t N, int J, int j, Shape *sh);
+// Relative cost per padded MMA element of each tile width (index 0: S = 256,
+// 1: 128, 2: 64) by floor(log2 K'): defaults, or measured by the autotuner.
+constexpr int kTcBuckets = 25;
+struct TcWeights {
+    float w[3][kTcBuckets];
+};
+void default_weights(TcWeights *t);
+// The shape of scale j with tile width S (false: band outside the tensor-core range).
+bool shape_with(int64_t N, int J, int j, int S, Shape *sh);
+// The cheapest width under the weights (nullptr: defaults).
+bool shape_for(int64_t N, int J, int j, Shape *sh, const TcWeights *w = nullptr);
 // Tensor-core operand elements (bf16) of one (N, J) pulse: stored side and
 // received side, each rounded up per scale as the ragged object lays them out.
 void operand_elems(int64_t N, int J, int64_t *stored, int64_t *received);
 // Stored operand of every tensor-core scale of one signal whose SIDWT tree
-// starts at tree; a_off[j] = element offset in abuf (-1: scale not packed).
-sidwt_status pack_stored(const float2 *tree, int64_t N, int J, const int64_t *a_off, void *abuf, cudaStream_t s);
+// starts at tree; a_off[j] = element offset in abuf (-1: scale not packed),
+// S_of[j] its tile width.
+sidwt_status pack_stored(const float2 *tree, int64_t N, int J, const int64_t *a_off, const int16_t *S_of, void *abuf,
+                         cudaStream_t s);
 sidwt_status encode_maps(void *two_maps, const void *a_base, const void *b_base, const Shape &sh);
 size_t map_bytes();
 sidwt_status launch_pack_recv(const float2 *pyr, const RecvEntry *e, int n, void *out, cudaStream_t s);

@@ -104,6 +104,7 @@ def lib():
     L.sidwt_ragged_peaks.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp]
     L.sidwt_ragged_autotune.argtypes = [_vp, ctypes.c_char_p, _vp]
     L.sidwt_ragged_tuning.argtypes = [_vp, _vp]
+    L.sidwt_ragged_tc_weights.argtypes = [_vp, _vp]
     L.sidwt_ragged_set_timing.argtypes = [_vp, ctypes.c_int]
     L.sidwt_ragged_read_timing.argtypes = [_vp, ctypes.POINTER(Timing), ctypes.c_int]
     L.sidwt_ragged_reset_references.argtypes = [_vp]
@@ -434,6 +435,12 @@ class Ragged:
     def tuning(self) -> np.ndarray:
         out = np.zeros(32, np.int32)
         _raise(lib().sidwt_ragged_tuning(self._h, out.ctypes.data))
+        return out
+
+    def tc_weights(self) -> np.ndarray:
+        """[3, 25]: cost weight of tile width 256 / 128 / 64 by log2 band length."""
+        out = np.zeros((3, 25), np.float32)
+        _raise(lib().sidwt_ragged_tc_weights(self._h, out.ctypes.data))
         return out
 
     def set_timing(self, on: bool = True):

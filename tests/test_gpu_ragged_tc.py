@@ -63,11 +63,15 @@ def stated_bounds(oracle, f, N, J, x, y):
     return np.array(out)
 
 
-def run(precision, refs, ypack, offsets, graph=False):
+def run(precision, refs, ypack, offsets, graph=False, tune_after=None, cache=None):
     from paper_cs_0607001_gb300 import sidwt
     with sidwt.Ragged() as rg:
         rg.set_precision(precision)
-        ids = [rg.store_reference(f, N, J, U.to_dev_c64(x)) for (f, N, J), x in zip(SPECS, refs)]
+        ids = []
+        for k, ((f, N, J), x) in enumerate(zip(SPECS, refs)):
+            if k == tune_after:
+                rg.autotune(cache)
+            ids.append(rg.store_reference(f, N, J, U.to_dev_c64(x)))
         yd = U.to_dev_c64(ypack)
         n = rg.correlate(ids, offsets, yd)
         lag, mag, norm = rg.peaks(n)
@@ -85,11 +89,7 @@ def run(precision, refs, ypack, offsets, graph=False):
     return first, out
 
 
-def test_ragged_bf16x3_matches_oracle_within_stated_bound(oracle):
-    refs, ypack, offsets, delays = build_batch(21)
-    first, (lag, mag, norm, lag_g, mag_g) = run("bf16x3", refs, ypack, offsets, graph=True)
-    np.testing.assert_array_equal(lag_g, lag)  # graph replay = direct call
-    np.testing.assert_array_equal(mag_g, mag)
+def check_against_oracle(oracle, refs, ypack, offsets, delays, first, lag, mag, norm):
     Ns = [s[1] for s in SPECS]
     Js = [s[2] for s in SPECS]
     fs = [s[0] for s in SPECS]
@@ -110,6 +110,45 @@ def test_ragged_bf16x3_matches_oracle_within_stated_bound(oracle):
             if g == lo[first[i] + j]:
                 assert abs(norm[sl][j] - no[first[i] + j]) <= 2 * rel * no[first[i] + j] + 1e-6
         assert lag[sl][0] == delays[i]
+
+
+def test_ragged_bf16x3_matches_oracle_within_stated_bound(oracle):
+    refs, ypack, offsets, delays = build_batch(21)
+    first, (lag, mag, norm, lag_g, mag_g) = run("bf16x3", refs, ypack, offsets, graph=True)
+    np.testing.assert_array_equal(lag_g, lag)  # graph replay = direct call
+    np.testing.assert_array_equal(mag_g, mag)
+    check_against_oracle(oracle, refs, ypack, offsets, delays, first, lag, mag, norm)
+
+
+def test_ragged_bf16x3_tile_widths_autotuned(oracle, tmp_path):
+    """The autotuner times every tensor-core tile width per band bucket;
+    references stored before it keep their widths, the ones stored after take
+    the tuned choice, and one batch mixing both stays within the bound."""
+    from paper_cs_0607001_gb300 import sidwt
+    refs, ypack, offsets, delays = build_batch(23)
+    cache = tmp_path / "tune.txt"
+    first, (lag, mag, norm) = run("bf16x3", refs, ypack, offsets, tune_after=len(SPECS) // 2, cache=str(cache))
+    check_against_oracle(oracle, refs, ypack, offsets, delays, first, lag, mag, norm)
+    tc = [l.split() for l in cache.read_text().split("\n") if l.startswith("tc ")]
+    assert len(tc) == 27
+    w = {(int(a), int(b)): float(c) for _, a, b, c in tc}
+    assert all(w[(256, lg)] == 1.0 for lg in range(6, 15))
+    assert all(0.2 <= v <= 50 for v in w.values())
+    with sidwt.Ragged() as rg:  # a new object reads the cache through SIDWT_TUNE_CACHE only
+        np.testing.assert_allclose(rg.tc_weights()[1, 6:15], 1.15)
+
+
+@pytest.mark.parametrize("width", [256, 128, 64])
+def test_ragged_bf16x3_each_tile_width(oracle, tmp_path, monkeypatch, width):
+    """Every tile width on its own (a tuning cache that makes the other two
+    widths 50x dearer, read by sidwt_ragged_create): same bound."""
+    lines = [f"tc {S} {lg} {1.0 if S == width else 50.0}" for S in (256, 128, 64) for lg in range(25)]
+    cache = tmp_path / "forced.txt"
+    cache.write_text("\n".join(lines) + "\n")
+    monkeypatch.setenv("SIDWT_TUNE_CACHE", str(cache))
+    refs, ypack, offsets, delays = build_batch(24)
+    first, (lag, mag, norm) = run("bf16x3", refs, ypack, offsets)
+    check_against_oracle(oracle, refs, ypack, offsets, delays, first, lag, mag, norm)
 
 
 def test_ragged_bf16x3_agrees_with_fp32_path():
