@@ -1011,6 +1011,10 @@ def run_serve_workload(args):
                          "max_batch": st["max_batch"], "ref_hits": st["ref_hits"], "ref_stores": st["ref_stores"]})
     srv.close()
     best = max(per_rate, key=lambda r: r["gsamples_s"])
+    # latency is quoted at the highest offered rate the loop keeps up with
+    # (completions within 5 % of arrivals); above it the queue grows
+    kept = [r for r in per_rate if r["req_s"] >= 0.95 * r["offered_req_s"]]
+    lat = max(kept, key=lambda r: r["rate_req_s"]) if kept else min(per_rate, key=lambda r: r["rate_req_s"])
     line = {
         "metric": METRIC, "value": best["gsamples_s"], "unit": UNIT, "n_gpus": 1, "steps": len(rates),
         "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1019,7 +1023,9 @@ def run_serve_workload(args):
                                "(multiples of 2^J), J 3-10, mixed filters; 40 GB cap",
                    "lanes": args.lanes, "pool": len(pool), "mean_flops_per_request": mean_flops,
                    "precision": args.precision},
-        "latency_ms": {"p50": best["p50_ms"], "p99": best["p99_ms"], "what": "submit to completion, best rate"},
+        "latency_ms": {"p50": lat["p50_ms"], "p99": lat["p99_ms"], "rate_req_s": lat["rate_req_s"],
+                       "what": "submit to completion at the highest offered rate the loop keeps up with"},
+        "saturated_latency_ms": {"p50": best["p50_ms"], "p99": best["p99_ms"], "rate_req_s": best["rate_req_s"]},
         "per_rate": per_rate,
         "peak_at_injected_delay_scale0": float(np.mean(hits)) if hits else None,
     }
