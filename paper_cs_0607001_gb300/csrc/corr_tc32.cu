@@ -17,7 +17,9 @@
 //     overlapping layout, so rows g (K'/4 + 4) + i, i < K'/4, are its advances
 //     r + 4 i and the 4 rows between windows are discarded.
 //   * B (N = 256 columns) is 256 received pulses of one reference, K-major
-//     ([k/4][Re|Im][pulse][4 samples]), loaded by TMA as a plain box.
+//     in the 64-byte swizzled layout ([k/16][Re|Im][pulse][16 samples]: one
+//     64-byte row per pulse and plane), so the TMA box moves 64-byte rows
+//     rather than 16-byte core-matrix rows.
 // Re and Im: Re += A(wr) B(ur) + A(wi) B(ui), Im += A(wr) B(ui) + A(-wi) B(ur);
 // each with the three split products: 24 MMAs (M 128, N 256, K 8) per stage
 // of 16 samples.  The epilogue reduces the peak of every pulse over the
@@ -45,11 +47,12 @@ constexpr int kWinChunks = 132;                 // window chunks of 4 samples: 4
 constexpr int kWinRowBytes = kWinChunks * 16;   // 2112
 constexpr int kARows = 3;                       // planes -Im, Re, Im of one residue
 constexpr int kABytes = 6528;                   // 3 planes x 2176 B (2112 B rounded up to 128)
-constexpr int kBBytes = 4 * 2 * kTN * 16;       // [4 k-chunks][Re|Im][256][16 B] = 32768
-constexpr int kStage = 2 * kBBytes + 2 * kABytes;  // B hi, B lo, A hi, A lo = 78592
+constexpr int kBBytes = 2 * kTN * 64;           // [Re|Im][256 pulses][64 B, swizzled] = 32768
+constexpr int kStage = (2 * kBBytes + 2 * kABytes + 1023) / 1024 * 1024;  // B hi, B lo, A hi, A lo: 78848
 static_assert(kARows * ((kWinRowBytes + 127) / 128 * 128) <= kABytes, "three plane windows per hi/lo region");
-static_assert(kStage % 128 == 0 && kBBytes % 128 == 0 && kABytes % 128 == 0, "TMA destinations 128-byte aligned");
-constexpr int kBarOff = 2 * kStage;             // 157184
+static_assert(kStage % 1024 == 0 && kBBytes % 1024 == 0 && kABytes % 128 == 0,
+              "TMA destinations 128-byte aligned, swizzled B planes on 1024-byte boundaries");
+constexpr int kBarOff = 2 * kStage;             // 157696
 constexpr int kSmemBytes = kBarOff + 128 + 1024;
 constexpr int kTmemCols = 512;
 constexpr int kRowsPerVariant = 24;             // hi/lo x 4 residues x 3 planes
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int kap0 = (kb % a.kb_per_band) * kKB;
                 unsigned char *st = base + s * kStage;
                 mbar_expect_tx(&full[s], 2 * kBBytes + 2 * kARows * box_bytes);
-                const int z0 = ((band * a.Kp + kap0) >> 2) * 2;
+                const int z0 = ((band * a.Kp + kap0) >> 4) * 2;
                 tma_load_3d(st, &mapB_hi, &full[s], 0, row0, z0);
                 tma_load_3d(st + kBBytes, &mapB_lo, &full[s], 0, row0, z0);
                 // A: per (hi/lo, plane) the windows of the tile's G variants, back to back
@@ -203,10 +206,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                                             sdesc(aHi + 2 * pitch + ao, 16, 128)};
                     const uint64_t al[3] = {sdesc(aLo + ao, 16, 128), sdesc(aLo + pitch + ao, 16, 128),
                                             sdesc(aLo + 2 * pitch + ao, 16, 128)};
-                    // B planes Re u / Im u: [k-chunk][plane][256 pulses][16 B]; next k-chunk 8 KB, 8 pulses 128 B
-                    const uint32_t bo = (uint32_t)(2 * ks) * 2 * 4096;
-                    const uint64_t bh[2] = {sdesc(bHi + bo, 8192, 128), sdesc(bHi + bo + 4096, 8192, 128)};
-                    const uint64_t bl[2] = {sdesc(bLo + bo, 8192, 128), sdesc(bLo + bo + 4096, 8192, 128)};
+                    // B planes Re u / Im u: [plane][256 pulses][64 B swizzled], 16 KB apart; the K half
+                    // ks is the row's second 32 bytes; 8 pulses 512 B
+                    const uint32_t bo = (uint32_t)ks * 32;
+                    const uint64_t bh[2] = {sdesc_sw64(bHi + bo, 512), sdesc_sw64(bHi + kTN * 64 + bo, 512)};
+                    const uint64_t bl[2] = {sdesc_sw64(bLo + bo, 512), sdesc_sw64(bLo + kTN * 64 + bo, 512)};
                     // (accumulator, A row, B plane): Re += wr ur + wi ui, Im += wr ui + (-wi) ur
                     const int acc_of[4] = {0, 0, 1, 1}, arow[4] = {1, 2, 1, 0}, bpl[4] = {0, 1, 1, 0};
 #pragma unroll
@@ -331,9 +335,9 @@ __global__ void pack_ref32_kernel(const float2 *__restrict__ tree, int64_t tree_
     }
 }
 
-// Received operand of one scale: chunk ((k / 4) * 2 + plane) of row (pulse in
-// grouped order) holds 4 TF32 values u_plane[k .. k + 3] of the concatenated
-// bands (plane 0 Re, 1 Im).  Block: 64 samples x 32 rows.
+// Received operand of one scale: row ((k / 16) * 2 + plane) of 16 TF32 values
+// u_plane[16 (k / 16) .. + 15] per pulse (grouped order) of the concatenated
+// bands (plane 0 Re, 1 Im), 64 bytes a pulse.  Block: 64 samples x 32 rows.
 __global__ void __launch_bounds__(256) pack_rx32_kernel(const float2 *__restrict__ pyr, int64_t pyr_elems, int64_t off,
                                                         const int32_t *__restrict__ perm,
                                                         const int32_t *__restrict__ ntiles, int rows,
@@ -354,7 +358,7 @@ __global__ void __launch_bounds__(256) pack_rx32_kernel(const float2 *__restrict
         const int cp = e >> 5, i = e & 31;
         const int r = r0 + i;
         if (r >= rows) continue;
-        const int kc = cp >> 1, plane = cp & 1;
+        const int kc = cp >> 1, plane = cp & 1;  // kc: 4 samples of the block's 64
         uint4 h, l;
         uint32_t *hp = reinterpret_cast<uint32_t *>(&h), *lp = reinterpret_cast<uint32_t *>(&l);
 #pragma unroll
@@ -362,7 +366,8 @@ __global__ void __launch_bounds__(256) pack_rx32_kernel(const float2 *__restrict
             const float2 v = tile[i][kc * 4 + q];
             split_tf32(plane ? v.y : v.x, hp[q], lp[q]);
         }
-        const int64_t o = (((int64_t)kb * 32 + cp) * rows + r) * 4;
+        const int64_t kq = (int64_t)kb * 4 + (kc >> 2);  // 16-sample row index
+        const int64_t o = ((kq * 2 + plane) * rows + r) * 16 + (kc & 3) * 4;
         *reinterpret_cast<uint4 *>(bhi + o) = h;
         *reinterpret_cast<uint4 *>(blo + o) = l;
     }
@@ -476,12 +481,16 @@ sidwt_status correlate_tc32(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_
             tc32::pack_rx32_kernel<<<g, 256, 0, s>>>(p->pyr_f, p->pyr_elems, 2 * N - 4 * Kp, p->tiles.perm,
                                                      p->tiles.ntiles, (int)B, bhi, blo);
         }
-        // TF32 data is moved as pairs of 16-bit units: a 16-byte chunk is 8 units
+        // TF32 data is moved as pairs of 16-bit units: a 64-byte row is 32 units
         CUtensorMap mA, mBh, mBl;
-        const uint64_t nchunk = (uint64_t)Kj / 4 * 2;
-        if ((st = tc::encode_3d(&mBh, bhi, 8, (uint64_t)B, nchunk, 16, 16 * (uint64_t)B, 8, tc32::kTN, 8)) ||
-            (st = tc::encode_3d(&mBl, blo, 8, (uint64_t)B, nchunk, 16, 16 * (uint64_t)B, 8, tc32::kTN, 8)))
-            return st;
+        {
+            const uint64_t dims[3] = {32, (uint64_t)B, (uint64_t)Kj / 16 * 2};
+            const uint64_t strides[2] = {64, 64 * (uint64_t)B};
+            const uint32_t box[3] = {32, tc32::kTN, 2};
+            if ((st = tc::encode_nd(&mBh, bhi, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B)) ||
+                (st = tc::encode_nd(&mBl, blo, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B)))
+                return st;
+        }
         const int Lc = tc32_lc(Kp);
         const int rpr = tc32_rows_per_ref(p, j);
         int G = 1, cg = tc32::kWinChunks;

@@ -78,6 +78,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
     return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
+// K-major operand in the 64-byte swizzled layout (rows of 64 B, 8-row atoms
+// sbo apart; layout type 4 in bits 61-63).  addr may step through an atom's
+// K extent in 16-byte units; the atoms themselves sit on 512-byte boundaries.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr, uint32_t sbo) {
+    return sdesc(addr, 16, sbo) | (4ull << 61);
+}
 
 // Instruction descriptor, kind::f16: D f32, A and B bf16, A K-major, B MN-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -155,7 +161,7 @@ inline sidwt_status encode_3d(CUtensorMap *m, void *gaddr, uint64_t d0, uint64_t
 
 // Rank-n tiled map (n <= 5): dims[0] innermost, strides in bytes for dims 1..n-1.
 inline sidwt_status encode_nd(CUtensorMap *m, void *gaddr, int n, const uint64_t *dims, const uint64_t *strides,
-                              const uint32_t *box) {
+                              const uint32_t *box, CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_NONE) {
     auto fn = encode_fn();
     if (!fn) {
         set_error("cuTensorMapEncodeTiled is not available from the driver");
@@ -170,7 +176,7 @@ inline sidwt_status encode_nd(CUtensorMap *m, void *gaddr, int n, const uint64_t
         if (i) s[i - 1] = strides[i - 1];
     }
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)n, gaddr, d, s, b, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r));
         return SIDWT_ECUDA;
