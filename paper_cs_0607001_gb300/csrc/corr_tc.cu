@@ -223,6 +223,214 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Short contractions (K_j <= 128 samples, advance tiles <= 128): the received
+// tile of 128 pulses is the same for every variant of the scale, so one CTA
+// keeps it resident (both K-blocks, loaded once) and runs kMultiVar variants
+// in turn, streaming only their stored windows through a 3-stage ring.  The
+// accumulators of consecutive variants rotate through 512 / (2 N_T) TMEM
+// slots, so the epilogue of one variant overlaps the MMAs of the next.
+// ---------------------------------------------------------------------------
+constexpr int kMultiVar = 8;                                 // variants per CTA
+constexpr int kMStagesB = 3;
+constexpr int kMARegion = 2 * kStageA;                       // resident A, K-blocks 0 and 1
+constexpr int kMBarOff = kMARegion + kMStagesB * kStageB;    // 223232
+constexpr int kMSmemBytes = kMBarOff + 256 + 1024;
+static_assert(kMSmemBytes <= 227 * 1024, "shared memory budget");
+
+__global__ void __launch_bounds__(kThreads, 1)
+    corr_tc_multi_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constant__ CUtensorMap mapA_lo,
+                         const __grid_constant__ CUtensorMap mapB, const TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *sA = base;
+    unsigned char *sB = base + kMARegion;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + kMBarOff);
+    // fullA, fullB[3], emptyB[3], accf[4], tfree[4]
+    uint64_t *fullA = bar, *fullB = bar + 1, *emptyB = bar + 4, *accf = bar + 7, *tfree = bar + 11;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 16);
+    // [0] error, [1] B stages issued, [2] B stages consumed, [3] A issued, [4] progress
+    volatile int *sflag = reinterpret_cast<volatile int *>(tmem_slot + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nvg = (a.nv + kMultiVar - 1) / kMultiVar;
+    const int bx = blockIdx.x;
+    const int lt = bx % a.nlt;
+    const int vg = (bx / a.nlt) % nvg;
+    const int pt = bx / (a.nlt * nvg);
+    if (pt >= a.ntiles[0]) return;  // uniform: before any barrier or TMEM use
+    const int row0 = a.tile_start[pt];
+    const int cnt = a.tile_count[pt];
+    const int ref = a.tile_ref[pt];
+    const int p0 = lt * a.ntile_n;
+    const int v0 = vg * kMultiVar;
+    const int nvar = min(kMultiVar, a.nv - v0);
+    const int nslots = 512 / (2 * a.ntile_n);  // 2 (N_T = 128) or 4 (N_T = 64)
+
+    if (threadIdx.x == 0) {
+        mbar_init(fullA, 1);
+        for (int i = 0; i < kMStagesB; ++i) {
+            mbar_init(&fullB[i], 1);
+            mbar_init(&emptyB[i], 1);
+        }
+        for (int i = 0; i < 4; ++i) {
+            mbar_init(&accf[i], 1);
+            mbar_init(&tfree[i], 128);
+        }
+        for (int i = 0; i < 5; ++i) sflag[i] = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            mbar_expect_tx(fullA, (uint32_t)(a.nkb * kStageA));
+            for (int kb = 0; kb < a.nkb; ++kb) {
+                tma_load_3d(sA + kb * kStageA, &mapA_hi, fullA, 0, row0, kb * 16);
+                tma_load_3d(sA + kb * kStageA + kABytes, &mapA_lo, fullA, 0, row0, kb * 16);
+            }
+            sflag[3] = 1;
+            int it = 0;
+            for (int g = 0; g < nvar && !sflag[0]; ++g)
+                for (int kb = 0; kb < a.nkb; ++kb, ++it) {
+                    const int s = it % kMStagesB, use = it / kMStagesB;
+                    if (use > 0 && !mbar_wait(&emptyB[s], (use - 1) & 1)) {
+                        sflag[0] = 1;
+                        break;
+                    }
+                    if (sflag[0]) break;
+                    const int band = kb / a.kb_per_band;
+                    const int kap0 = (kb % a.kb_per_band) * 64;
+                    mbar_expect_tx(&fullB[s], kStageB);
+                    unsigned char *stB = sB + s * kStageB;
+                    const int rowbase = ref * a.rows_per_ref + ((band * a.nv + v0 + g) * 2) * kBRows;
+                    const int chunk0 = (kap0 + p0) >> 3;
+                    tma_load_3d(stB, &mapB, &fullB[s], 0, chunk0, rowbase);
+                    tma_load_3d(stB + kBBytes, &mapB, &fullB[s], 0, chunk0, rowbase + kBRows);
+                    sflag[1] = it + 1;
+                }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(kTM, a.ntile_n);
+            bool okA = mbar_wait(fullA, 0);
+            if (!okA) sflag[0] = 1;
+            tc_fence_after();
+            int it = 0;
+            for (int g = 0; g < nvar && okA && !sflag[0]; ++g) {
+                const int slot = g % nslots, use = g / nslots;
+                if (use > 0) {
+                    if (!mbar_wait(&tfree[slot], (use - 1) & 1)) {
+                        sflag[0] = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                }
+                const uint32_t dre = tmem + (uint32_t)(slot * 2 * a.ntile_n), dim = dre + (uint32_t)a.ntile_n;
+                for (int kb = 0; kb < a.nkb; ++kb, ++it) {
+                    const int s = it % kMStagesB;
+                    if (!mbar_wait(&fullB[s], (it / kMStagesB) & 1)) {
+                        sflag[0] = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t aHi = saddr(sA + kb * kStageA), aLo = aHi + kABytes;
+                    const uint32_t bHi = saddr(sB + s * kStageB), bLo = bHi + kBBytes;
+#pragma unroll 1
+                    for (int c = 0; c < 8; ++c) {
+                        const uint64_t ah = sdesc(aHi + c * 4096, 2048, 128);
+                        const uint64_t al = sdesc(aLo + c * 4096, 2048, 128);
+#pragma unroll
+                        for (int acc = 0; acc < 2; ++acc) {
+                            const uint32_t row = c * 3 + (acc == 0 ? 1 : 0);
+                            const uint64_t bh = sdesc(bHi + row * kWinRowBytes, kWinRowBytes, 16);
+                            const uint64_t bl = sdesc(bLo + row * kWinRowBytes, kWinRowBytes, 16);
+                            const uint32_t d = acc == 0 ? dre : dim;
+                            const uint32_t first = (kb == 0 && c == 0) ? 0u : 1u;
+                            mma_bf16(d, ah, bh, idesc, first);
+                            mma_bf16(d, ah, bl, idesc, 1u);
+                            mma_bf16(d, al, bh, idesc, 1u);
+                        }
+                    }
+                    mma_commit(&emptyB[s]);
+                    sflag[2] = it + 1;
+                    sflag[4] = it + 1;
+                }
+                if (sflag[0]) break;
+                mma_commit(&accf[slot]);  // this variant's MMAs have completed
+            }
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = pulses of the tile
+        const int q4 = warp & 3;
+        const int m = q4 * 32 + lane;
+        const bool valid = m < cnt;
+        const int64_t b = valid ? a.perm[row0 + m] : 0;
+        const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
+        for (int g = 0; g < nvar; ++g) {
+            const int slot = g % nslots, use = g / nslots;
+            uint64_t t0 = now_ns();
+            int last = sflag[4];
+            bool ok = true;
+            while (!mbar_test(&accf[slot], use & 1)) {  // bounded from the MMA thread's last progress
+                const int pr = sflag[4];
+                if (pr != last) {
+                    last = pr;
+                    t0 = now_ns();
+                } else if (now_ns() - t0 > kWaitNs || sflag[0]) {
+                    ok = false;
+                    break;
+                }
+            }
+            tc_fence_after();
+            if (!__all_sync(0xffffffffu, ok && !sflag[0])) {
+                sflag[0] = 1;
+                break;
+            }
+            const int v = v0 + g;
+            unsigned long long best = 0ull;
+            const uint32_t col = (uint32_t)(slot * 2 * a.ntile_n);
+            for (int c0 = 0; c0 < a.ntile_n; c0 += 32) {
+                uint32_t re[32], im[32];
+                TMEM_LD32(tl + col + c0, re);
+                TMEM_LD32(tl + col + a.ntile_n + c0, im);
+                tmem_wait_ld();
+#pragma unroll
+                for (int n = 0; n < 32; ++n) {
+                    const float xr = __uint_as_float(re[n]), xi = __uint_as_float(im[n]);
+                    const float m2 = xr * xr + xi * xi;
+                    const int p = p0 + c0 + n;
+                    const int q = p == 0 ? 0 : a.Kp - p;
+                    const uint32_t D = ((uint32_t)q << a.lev) + (uint32_t)v;
+                    const unsigned long long key =
+                        ((unsigned long long)__float_as_uint(m2) << 32) | (unsigned long long)(0xFFFFFFFFu - D);
+                    best = key > best ? key : best;
+                    if (a.R && valid) a.R[(b * (a.J + 1) + a.j) * a.N + D] = make_float2(xr, xi);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&tfree[slot]);
+            if (valid && best) atomicMax(&a.keys[b * (a.J + 1) + a.j], best);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 0 && sflag[0]) {
+        // let this CTA's own copies land before its shared memory is released
+        if (sflag[3]) mbar_wait(fullA, 0);
+        for (int k = sflag[2]; k < sflag[1]; ++k) mbar_wait(&fullB[k % kMStagesB], (k / kMStagesB) & 1);
+        atomicOr(a.err, 2);
+    }
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---------------------------------------------------------------------------
 // Packing kernels
 // ---------------------------------------------------------------------------
 
@@ -479,12 +687,18 @@ sidwt_status correlate_tc(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t 
         a.keys = p->keys;
         a.R = r_dev;
         a.err = p->err;
-        const int64_t grid = max_pt * a.nv * a.nlt;
+        // short contractions: the received tile stays resident over several variants
+        const bool multi = a.nkb <= 2 && a.ntile_n <= 128;
+        const int64_t grid =
+            max_pt * a.nlt * (multi ? (a.nv + tc::kMultiVar - 1) / tc::kMultiVar : (int64_t)a.nv);
         if (grid > 0x7fffffff) {
             set_error("batch too large for one tensor-core launch");
             return SIDWT_EINVAL;
         }
-        tc::corr_tc_kernel<<<(unsigned)grid, tc::kThreads, tc::kSmemBytes, s>>>(mA_hi, mA_lo, mB, a);
+        if (multi)
+            tc::corr_tc_multi_kernel<<<(unsigned)grid, tc::kThreads, tc::kMSmemBytes, s>>>(mA_hi, mA_lo, mB, a);
+        else
+            tc::corr_tc_kernel<<<(unsigned)grid, tc::kThreads, tc::kSmemBytes, s>>>(mA_hi, mA_lo, mB, a);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "tensor-core correlation launch");
     }
@@ -499,6 +713,9 @@ int tc_group_tile() { return tc::kTM; }
 cudaError_t prepare_tc_kernels() {
     cudaError_t e =
         cudaFuncSetAttribute(tc::corr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc::corr_tc_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc::kMSmemBytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(tc::tc_selftest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  tc::kSelftestSmem);
