@@ -233,7 +233,9 @@ __global__ void __launch_bounds__(1024) group_kernel(const int32_t *__restrict__
     }
 }
 
-__global__ void finalize_kernel(const unsigned long long *__restrict__ keys, const int32_t *__restrict__ ids,
+// Reads each peak key once and resets it to zero, so that the next call on
+// the plan starts from cleared keys without a separate memset.
+__global__ void finalize_kernel(unsigned long long *__restrict__ keys, const int32_t *__restrict__ ids,
                                 int nrefs, const double *__restrict__ xen, int64_t xen_len,
                                 const double *__restrict__ yen, int64_t B, int J, int32_t *__restrict__ lag,
                                 float *__restrict__ mag, double *__restrict__ norm) {
@@ -243,6 +245,7 @@ __global__ void finalize_kernel(const unsigned long long *__restrict__ keys, con
     const int j = (int)(i % (J + 1));
     const int r = ids[b];
     const unsigned long long k = keys[i];
+    keys[i] = 0ull;
     if (r < 0 || r >= nrefs || k == 0ull) {
         lag[i] = -1;
         mag[i] = 0.f;
@@ -309,6 +312,26 @@ sidwt_status finalize_peaks(sidwt_plan *p, int64_t B, cudaStream_t s) {
                                                                 p->yen, B, p->J, p->lag, p->mag, p->norm);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "peak epilogue launch");
+}
+
+namespace {
+__global__ void copy_peaks_kernel(const int32_t *__restrict__ lag, const float *__restrict__ mag,
+                                  const double *__restrict__ norm, int64_t n, int32_t *__restrict__ lag_out,
+                                  float *__restrict__ mag_out, double *__restrict__ norm_out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (lag_out) lag_out[i] = lag[i];
+        if (mag_out) mag_out[i] = mag[i];
+        if (norm_out) norm_out[i] = norm[i];
+    }
+}
+}  // namespace
+
+sidwt_status copy_peaks(const sidwt_plan *p, int64_t n, int32_t *lag, float *mag, double *norm, cudaStream_t s) {
+    if (n == 0 || (!lag && !mag && !norm)) return SIDWT_OK;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    copy_peaks_kernel<<<(unsigned)blocks, 256, 0, s>>>(p->lag, p->mag, p->norm, n, lag, mag, norm);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "peak copy");
 }
 
 int simt_tile_pulses() { return TP; }

@@ -86,6 +86,7 @@ static sidwt_status ensure_batch(sidwt_plan *p, int64_t B) {
     }
     p->cap_batch = cap;
     p->tiles.max_tiles = need_tiles;
+    p->keys_clean = false;
     return SIDWT_OK;
 }
 
@@ -441,8 +442,13 @@ sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const vo
         StageTimer t(p, 2, s, analyze_launch_count(p));
         if ((st = analyze_batch(p, y_dev, B, s))) return st;
     }
-    cudaError_t e = cudaMemsetAsync(p->keys, 0, B * (p->J + 1) * sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    // keys are left zero by the kernel that reads them (finalize); clear them
+    // here only after an interrupted call or a fresh allocation
+    if (!p->keys_clean) {
+        cudaError_t e = cudaMemsetAsync(p->keys, 0, p->cap_batch * (p->J + 1) * sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return cuda_fail(e, "memset");
+    }
+    p->keys_clean = false;
     {
         StageTimer t(p, 3, s, small ? small_launch_count(p) : (tc ? tc_launch_count(p) : (tc32 ? tc32_launch_count(p) : 1)));
         if (small) {
@@ -455,8 +461,12 @@ sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const vo
             return st;
         }
     }
-    StageTimer t(p, 4, s, 1);
-    return finalize_peaks(p, B, s);
+    {
+        StageTimer t(p, 4, s, 1);
+        if ((st = finalize_peaks(p, B, s))) return st;
+    }
+    p->keys_clean = true;
+    return SIDWT_OK;
 }
 
 sidwt_status sidwt_peaks(sidwt_plan *p, int64_t B, int32_t *lag_dev, float *mag_dev, double *norm_dev,
@@ -467,14 +477,7 @@ sidwt_status sidwt_peaks(sidwt_plan *p, int64_t B, int32_t *lag_dev, float *mag_
         return SIDWT_EINVAL;
     }
     if (B == 0) return SIDWT_OK;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const size_t n = (size_t)B * (p->J + 1);
-    cudaError_t e = cudaSuccess;
-    if (lag_dev) e = cudaMemcpyAsync(lag_dev, p->lag, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess && mag_dev) e = cudaMemcpyAsync(mag_dev, p->mag, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess && norm_dev)
-        e = cudaMemcpyAsync(norm_dev, p->norm, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "peak copy");
+    return copy_peaks(p, B * (p->J + 1), lag_dev, mag_dev, norm_dev, reinterpret_cast<cudaStream_t>(stream));
 }
 
 sidwt_status sidwt_correlate_host(sidwt_plan *p, const int32_t *ref_ids_host, const void *y_host, int64_t B,

@@ -135,6 +135,7 @@ struct sidwt_plan {
     int2 *pyr_i = nullptr;         // integer plan only
     double *yen = nullptr;         // [cap_batch][J+1]
     unsigned long long *keys = nullptr;  // [cap_batch][J+1] packed peak keys
+    bool keys_clean = false;             // every key is zero (the kernels that read keys reset them)
     int32_t *lag = nullptr;
     float *mag = nullptr;
     double *norm = nullptr;
@@ -244,6 +245,8 @@ int tc_group_tile();
 int tc_launch_count(const sidwt_plan *p);
 void free_tc(sidwt_plan *p);
 sidwt_status finalize_peaks(sidwt_plan *p, int64_t B, cudaStream_t s);
+// Copy the last batch's n peak entries to the caller's buffers (any may be null) in one launch.
+sidwt_status copy_peaks(const sidwt_plan *p, int64_t n, int32_t *lag, float *mag, double *norm, cudaStream_t s);
 
 // ---- corr_tc32.cu (3xTF32) ----
 sidwt_status correlate_tc32(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t s);
