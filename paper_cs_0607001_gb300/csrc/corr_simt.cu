@@ -239,6 +239,8 @@ __global__ void finalize_kernel(unsigned long long *__restrict__ keys, const int
                                 int nrefs, const double *__restrict__ xen, int64_t xen_len,
                                 const double *__restrict__ yen, int64_t B, int J, int32_t *__restrict__ lag,
                                 float *__restrict__ mag, double *__restrict__ norm) {
+    pdl_wait();  // the correlation kernel's keys
+    pdl_release();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B * (J + 1)) return;
     const int64_t b = i / (J + 1);
@@ -308,9 +310,10 @@ sidwt_status correlate_simt(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_
 sidwt_status finalize_peaks(sidwt_plan *p, int64_t B, cudaStream_t s) {
     const int64_t n = B * (p->J + 1);
     if (n == 0) return SIDWT_OK;
-    finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p->keys, p->ref_ids, p->nrefs, p->xen, p->xen_len,
-                                                                p->yen, B, p->J, p->lag, p->mag, p->norm);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_dependent(finalize_kernel, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, p->keys,
+                                     (const int32_t *)p->ref_ids, p->nrefs, (const double *)p->xen, p->xen_len,
+                                     (const double *)p->yen, B, p->J, p->lag, p->mag, p->norm);
+    if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "peak epilogue launch");
 }
 
@@ -318,6 +321,7 @@ namespace {
 __global__ void copy_peaks_kernel(const int32_t *__restrict__ lag, const float *__restrict__ mag,
                                   const double *__restrict__ norm, int64_t n, int32_t *__restrict__ lag_out,
                                   float *__restrict__ mag_out, double *__restrict__ norm_out) {
+    pdl_wait();  // the peak epilogue's outputs
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (lag_out) lag_out[i] = lag[i];
         if (mag_out) mag_out[i] = mag[i];
@@ -329,8 +333,10 @@ __global__ void copy_peaks_kernel(const int32_t *__restrict__ lag, const float *
 sidwt_status copy_peaks(const sidwt_plan *p, int64_t n, int32_t *lag, float *mag, double *norm, cudaStream_t s) {
     if (n == 0 || (!lag && !mag && !norm)) return SIDWT_OK;
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
-    copy_peaks_kernel<<<(unsigned)blocks, 256, 0, s>>>(p->lag, p->mag, p->norm, n, lag, mag, norm);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_dependent(copy_peaks_kernel, dim3((unsigned)blocks), dim3(256), 0, s,
+                                     (const int32_t *)p->lag, (const float *)p->mag, (const double *)p->norm, n, lag,
+                                     mag, norm);
+    if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "peak copy");
 }
 

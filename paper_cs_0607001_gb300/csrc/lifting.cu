@@ -590,6 +590,7 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
     const int Nh = (int)(N / 2);
     const char *y = reinterpret_cast<const char *>(y_in);
     const int64_t G = gridDim.x;
+    pdl_release();  // the correlation kernel may be scheduled now; it waits for this grid's writes
 
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])) : "memory");

@@ -262,6 +262,8 @@ __global__ void __launch_bounds__(256) corr_latency_kernel(const float2 *__restr
                                                            float2 *__restrict__ R, int32_t *__restrict__ saved,
                                                            int32_t *__restrict__ err) {
     __shared__ float2 part[8][33];
+    pdl_wait();  // the analysis kernel's pyramid and energies
+    pdl_release();
     const int b = blockIdx.y;
     const int ref = ref_ids[b];
     if (blockIdx.x == 0 && threadIdx.x == 0) {  // the ids the peak epilogue reads, and the error record
@@ -855,10 +857,11 @@ sidwt_status correlate_small(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t 
             z.first = total;
             total += z.nv * z.nqb;
         }
-        rg::corr_latency_kernel<<<dim3((unsigned)total, (unsigned)B), 256, 0, s>>>(
-            p->tree_f, p->tree_elems, p->pyr_f, p->pyr_elems, ref_ids_dev, p->nrefs, p->N, p->J, tab, p->keys, R,
-            p->ref_ids, p->err);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_dependent(rg::corr_latency_kernel, dim3((unsigned)total, (unsigned)B), dim3(256), 0, s,
+                                         (const float2 *)p->tree_f, p->tree_elems, (const float2 *)p->pyr_f,
+                                         p->pyr_elems, ref_ids_dev, p->nrefs, p->N, p->J, tab, p->keys, R, p->ref_ids,
+                                         p->err);
+        if (e == cudaSuccess) e = cudaGetLastError();
         return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "small-batch correlation launch");
     }
     PlanSmall *ps = static_cast<PlanSmall *>(p->small);

@@ -438,15 +438,16 @@ sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const vo
         const int gt = tc ? tc_group_tile() : (tc32 ? tc32_group_tile() : simt_tile_pulses());
         if ((st = group_pulses(p, ref_ids_dev, B, gt, s))) return st;
     }
-    {
-        StageTimer t(p, 2, s, analyze_launch_count(p));
-        if ((st = analyze_batch(p, y_dev, B, s))) return st;
-    }
     // keys are left zero by the kernel that reads them (finalize); clear them
-    // here only after an interrupted call or a fresh allocation
+    // only after an interrupted call or a fresh allocation, ahead of the
+    // analysis (the correlation kernels may start before the analysis ends)
     if (!p->keys_clean) {
         cudaError_t e = cudaMemsetAsync(p->keys, 0, p->cap_batch * (p->J + 1) * sizeof(unsigned long long), s);
         if (e != cudaSuccess) return cuda_fail(e, "memset");
+    }
+    {
+        StageTimer t(p, 2, s, analyze_launch_count(p));
+        if ((st = analyze_batch(p, y_dev, B, s))) return st;
     }
     p->keys_clean = false;
     {

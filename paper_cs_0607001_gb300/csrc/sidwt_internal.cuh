@@ -12,6 +12,33 @@
 
 namespace sidwt {
 
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel launched with launch_dependent()
+// may start while the previous kernel on the stream is still running; it
+// calls pdl_wait() before it reads anything that kernel writes (the wait
+// returns once that grid has completed and its writes are visible; launched
+// normally, the wait returns at once).  pdl_release() lets the next such
+// kernel start early.
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... K, typename... A>
+cudaError_t launch_dependent(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<A &&>(args)...);
+}
+#endif
+
 enum Side { SIDE_X = 0, SIDE_Y = 1 };  // x: primal analysis P~(z^-1); y: dual P^T(z^-1)
 
 // ---------------------------------------------------------------------------
