@@ -629,7 +629,6 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
 
         // level-0 energy from the landed input
         {
-            EnAcc en;
             long long eni = 0;
             if constexpr (INT) {
                 const short4 *q = reinterpret_cast<const short4 *>(cur);
