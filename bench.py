@@ -564,7 +564,7 @@ def run_ragged_workload(args):
                                   "peaks_ms": t["peaks_ms"]},
         "tuning_mq_by_log2_band": rg.tuning()[8:16].tolist(),
         "tuning_tc_weights_by_log2_band": {str(S_): [round(float(v), 3) for v in rg.tc_weights()[k, 6:17]]
-                                           for k, S_ in enumerate((256, 128, 64))},
+                                           for k, S_ in enumerate((256, 128, 64, 192))},
         "autotune_s": tune_s,
         "vs_plain": None if plain is None else {
             "plain_correlate_ms": plain["correlate_ms"], "this_correlate_ms": t["correlate_ms"],

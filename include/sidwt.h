@@ -287,7 +287,7 @@ sidwt_status sidwt_ragged_peaks(sidwt_ragged *r, int64_t n_slots, int32_t *lag_d
  * SIDWT_TUNE_CACHE).  CUDA-core tiles: the shifts per thread for band
  * lengths 2^8 .. 2^15, each candidate (1, 2, 4, 8) timed on a synthetic
  * pair.  Tensor-core tiles: for band lengths 2^6 .. 2^14, every tile width S
- * (256, 128, 64 advances) timed on a synthetic pair's tiles replicated over
+ * (256, 192, 128, 64 advances) timed on a synthetic pair's tiles replicated over
  * the SMs; the weight of a width is its time per padded MMA element relative
  * to S = 256, and a reference stored afterwards takes, per scale, the width
  * of least weighted padded work (references stored before keep theirs).
@@ -296,8 +296,8 @@ sidwt_status sidwt_ragged_peaks(sidwt_ragged *r, int64_t n_slots, int32_t *lag_d
 sidwt_status sidwt_ragged_autotune(sidwt_ragged *r, const char *cache_path, sidwt_stream stream);
 
 /* The tensor-core width weights in use: w[k * 25 + b] for width 256 (k = 0),
- * 128 (1), 64 (2) and bands of 2^b .. 2^(b+1) - 1 samples. */
-sidwt_status sidwt_ragged_tc_weights(const sidwt_ragged *r, float *w /* [3 * 25] */);
+ * 128 (1), 64 (2), 192 (3) and bands of 2^b .. 2^(b+1) - 1 samples. */
+sidwt_status sidwt_ragged_tc_weights(const sidwt_ragged *r, float *w /* [4 * 25] */);
 
 /* Stage timing of direct sidwt_ragged_correlate calls (not graph replays),
  * same meaning as sidwt_set_timing / sidwt_read_timing: analyze_ms (lifting),

@@ -753,7 +753,9 @@ void load_tuning(sidwt_ragged *r, const char *path) {
         int lg, mq, S;
         float w;
         if (std::sscanf(line, "tc %d %d %f", &S, &lg, &w) == 3) {
-            const int k = S == 256 ? 0 : (S == 128 ? 1 : (S == 64 ? 2 : -1));
+            int k = -1;
+            for (int q = 0; q < rtc::kTcWidths; ++q)
+                if (rtc::kTcWidth[q] == S) k = q;
             if (k >= 0 && lg >= 0 && lg < rtc::kTcBuckets && w > 0.1f && w < 100.f) r->tcw.w[k][lg] = w;
         } else if (std::sscanf(line, "%d %d", &lg, &mq) == 2) {
             if (lg >= 0 && lg < 32 && (mq == 1 || mq == 2 || mq == 4 || mq == 8)) r->mq_for[lg] = mq;
@@ -1153,10 +1155,11 @@ namespace {
 // element (tiles x 128 rows x S columns x K) relative to width 256.
 sidwt_status tune_tc(sidwt_ragged *r, cudaStream_t s, std::string *report) {
     const int lg_lo = 6, lg_hi = 14;
-    const int widths[3] = {256, 128, 64};
+    const int *widths = rtc::kTcWidth;
     int64_t amax = 0, bmax = 0, tmax = 0;
     for (int lg = lg_lo; lg <= lg_hi; ++lg)
-        for (int S : widths) {
+        for (int k = 0; k < rtc::kTcWidths; ++k) {
+            const int S = widths[k];
             rtc::Shape sh;
             if (!rtc::shape_with(int64_t(16) << lg, 4, 3, S, &sh)) continue;
             amax = std::max(amax, sh.a_elems);
@@ -1207,8 +1210,8 @@ sidwt_status tune_tc(sidwt_ragged *r, cudaStream_t s, std::string *report) {
     rtc::TcWeights w = r->tcw;
     for (int lg = lg_lo; lg <= lg_hi && !st; ++lg) {
         const int64_t Kp = int64_t(1) << lg, N = 16 * Kp;
-        double per[3] = {0, 0, 0};
-        for (int k = 0; k < 3 && !st; ++k) {
+        double per[rtc::kTcWidths] = {};
+        for (int k = 0; k < rtc::kTcWidths && !st; ++k) {
             const int S = widths[k];
             rtc::Shape sh;
             rtc::shape_with(N, 4, 3, S, &sh);
@@ -1257,7 +1260,7 @@ sidwt_status tune_tc(sidwt_ragged *r, cudaStream_t s, std::string *report) {
             per[k] = (double)tot / ((double)n * S * sh.nkb);
         }
         if (st) break;
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < rtc::kTcWidths; ++k) {
             const float v = per[0] > 0 ? (float)(per[k] / per[0]) : w.w[k][lg];
             w.w[k][lg] = std::min(50.f, std::max(0.2f, v));
             *report += "tc " + std::to_string(widths[k]) + " " + std::to_string(lg) + " " + std::to_string(w.w[k][lg]) + "\n";
@@ -1278,9 +1281,9 @@ sidwt_status tune_tc(sidwt_ragged *r, cudaStream_t s, std::string *report) {
     release();
     if (st) return st;
     for (int lg = lg_hi + 1; lg < rtc::kTcBuckets; ++lg)
-        for (int k = 0; k < 3; ++k) w.w[k][lg] = w.w[k][lg_hi];
+        for (int k = 0; k < rtc::kTcWidths; ++k) w.w[k][lg] = w.w[k][lg_hi];
     for (int lg = 0; lg < lg_lo; ++lg)
-        for (int k = 0; k < 3; ++k) w.w[k][lg] = w.w[k][lg_lo];
+        for (int k = 0; k < rtc::kTcWidths; ++k) w.w[k][lg] = w.w[k][lg_lo];
     r->tcw = w;
     return SIDWT_OK;
 }
@@ -1487,7 +1490,7 @@ sidwt_status sidwt_ragged_tc_weights(const sidwt_ragged *r, float *w) {
         set_error("NULL argument");
         return SIDWT_EINVAL;
     }
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < rtc::kTcWidths; ++k)
         for (int b = 0; b < rtc::kTcBuckets; ++b) w[k * rtc::kTcBuckets + b] = r->tcw.w[k][b];
     return SIDWT_OK;
 }

@@ -382,6 +382,7 @@ void default_weights(TcWeights *t) {
         t->w[0][b] = 1.0f;
         t->w[1][b] = 1.15f;
         t->w[2][b] = 1.6f;
+        t->w[3][b] = 1.05f;
     }
 }
 
@@ -409,7 +410,7 @@ static void fill_shape(int64_t N, int J, int j, int S, Shape *sh) {
 bool shape_with(int64_t N, int J, int j, int S, Shape *sh) {
     const int lev = j < J ? j + 1 : J;
     const int64_t Kp = N >> lev;
-    if (Kp < kMinBand || Kp > kMaxBand || (S != 256 && S != 128 && S != 64)) return false;
+    if (Kp < kMinBand || Kp > kMaxBand || (S != 256 && S != 192 && S != 128 && S != 64)) return false;
     fill_shape(N, J, j, S, sh);
     return true;
 }
@@ -430,11 +431,10 @@ bool shape_for(int64_t N, int J, int j, Shape *sh, const TcWeights *w) {
     int b = 0;
     while (b + 1 < kTcBuckets && (int64_t(2) << b) <= Kp) ++b;  // floor(log2 Kp)
     double best = 1e300;
-    const int widths[3] = {256, 128, 64};
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < kTcWidths; ++k) {
         Shape t;
-        fill_shape(N, J, j, widths[k], &t);
-        const double cost = (double)t.tiles * widths[k] * t.nkb * w->w[k][b];
+        fill_shape(N, J, j, kTcWidth[k], &t);
+        const double cost = (double)t.tiles * kTcWidth[k] * t.nkb * w->w[k][b];
         if (cost < best) {
             best = cost;
             *sh = t;

@@ -320,14 +320,17 @@ struct RecvEntry {
 };
 
 // Relative cost per padded MMA element of each tile width (index 0: S = 256,
-// 1: 128, 2: 64) by floor(log2 K'): defaults, or measured by the autotuner.
+// 1: 128, 2: 64, 3: 192) by floor(log2 K'): defaults, or measured by the
+// autotuner.
 constexpr int kTcBuckets = 25;
+constexpr int kTcWidths = 4;
+constexpr int kTcWidth[kTcWidths] = {256, 128, 64, 192};
 struct TcWeights {
-    float w[3][kTcBuckets];
+    float w[kTcWidths][kTcBuckets];
 };
 void default_weights(TcWeights *t);
 // The shape of scale j with tile width S (false: band outside the tensor-core range).
-bool shape_with(int64_t N, int J, int j, int S, Shape *sh);
+bool shape_with(int64_t N, int J, int j, int S, Shape *sh);  // S in kTcWidth
 // The cheapest width under the weights (nullptr: defaults).
 bool shape_for(int64_t N, int J, int j, Shape *sh, const TcWeights *w = nullptr);
 // Tensor-core operand elements (bf16) of one (N, J) pulse: stored side and

@@ -438,8 +438,8 @@ class Ragged:
         return out
 
     def tc_weights(self) -> np.ndarray:
-        """[3, 25]: cost weight of tile width 256 / 128 / 64 by log2 band length."""
-        out = np.zeros((3, 25), np.float32)
+        """[4, 25]: cost weight of tile width 256 / 128 / 64 / 192 by log2 band length."""
+        out = np.zeros((4, 25), np.float32)
         _raise(lib().sidwt_ragged_tc_weights(self._h, out.ctypes.data))
         return out
 

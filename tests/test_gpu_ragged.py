@@ -97,7 +97,7 @@ def test_ragged_autotune_keeps_results(tmp_path, oracle):
         assert set(t[8:16].tolist()) <= {1, 2, 4, 8}
         lines = [l for l in cache.read_text().split("\n") if l.strip()]
         assert len([l for l in lines if not l.startswith("tc ")]) == 8
-        assert len([l for l in lines if l.startswith("tc ")]) == 27  # 3 widths x band buckets 2^6 .. 2^14
+        assert len([l for l in lines if l.startswith("tc ")]) == 36  # 4 widths x band buckets 2^6 .. 2^14
         ids, yd, lag, mag, norm = run_ragged(rg, refs, ypack, offsets)
         first, _ = rg.slots_of(ids)
     exp = oracle_results(oracle, refs, ypack, offsets)

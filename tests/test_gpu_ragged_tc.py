@@ -130,7 +130,7 @@ def test_ragged_bf16x3_tile_widths_autotuned(oracle, tmp_path):
     first, (lag, mag, norm) = run("bf16x3", refs, ypack, offsets, tune_after=len(SPECS) // 2, cache=str(cache))
     check_against_oracle(oracle, refs, ypack, offsets, delays, first, lag, mag, norm)
     tc = [l.split() for l in cache.read_text().split("\n") if l.startswith("tc ")]
-    assert len(tc) == 27
+    assert len(tc) == 36  # 4 widths x band buckets 2^6 .. 2^14
     w = {(int(a), int(b)): float(c) for _, a, b, c in tc}
     assert all(w[(256, lg)] == 1.0 for lg in range(6, 15))
     assert all(0.2 <= v <= 50 for v in w.values())
@@ -138,11 +138,11 @@ def test_ragged_bf16x3_tile_widths_autotuned(oracle, tmp_path):
         np.testing.assert_allclose(rg.tc_weights()[1, 6:15], 1.15)
 
 
-@pytest.mark.parametrize("width", [256, 128, 64])
+@pytest.mark.parametrize("width", [256, 192, 128, 64])
 def test_ragged_bf16x3_each_tile_width(oracle, tmp_path, monkeypatch, width):
-    """Every tile width on its own (a tuning cache that makes the other two
+    """Every tile width on its own (a tuning cache that makes the other
     widths 50x dearer, read by sidwt_ragged_create): same bound."""
-    lines = [f"tc {S} {lg} {1.0 if S == width else 50.0}" for S in (256, 128, 64) for lg in range(25)]
+    lines = [f"tc {S} {lg} {1.0 if S == width else 50.0}" for S in (256, 192, 128, 64) for lg in range(25)]
     cache = tmp_path / "forced.txt"
     cache.write_text("\n".join(lines) + "\n")
     monkeypatch.setenv("SIDWT_TUNE_CACHE", str(cache))
