@@ -475,12 +475,16 @@ __global__ void __launch_bounds__(256) pack_rx_kernel(const float2 *__restrict__
     const int kb = blockIdx.x;
     const int r0 = blockIdx.y * 32;
     const int nvalid = ntiles[1];
-    for (int e = threadIdx.x; e < 32 * 64; e += 256) {
-        const int i = e >> 6, k = e & 63;
+    // 32 rows x 64 samples as 16-byte loads of two samples (rows start on even samples)
+#pragma unroll
+    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+        const int i = e >> 5, k2 = e & 31;
         const int r = r0 + i;
-        float2 v = make_float2(0.f, 0.f);
-        if (r < nvalid) v = pyr[(int64_t)perm[r] * pyr_elems + off + (int64_t)kb * 64 + k];
-        tile[i][k] = v;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < nvalid)
+            v = *reinterpret_cast<const float4 *>(pyr + (int64_t)perm[r] * pyr_elems + off + (int64_t)kb * 64 + 2 * k2);
+        tile[i][2 * k2] = make_float2(v.x, v.y);
+        tile[i][2 * k2 + 1] = make_float2(v.z, v.w);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 16 * 32; e += 256) {
