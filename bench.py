@@ -112,18 +112,38 @@ def measured_peaks() -> dict:
     return {}
 
 
-def source_sha(path: Path) -> str:
-    return hashlib.sha256(path.read_bytes()).hexdigest()[:16]
+def kernel_source(path: Path, kernel: str) -> str:
+    """Text of the __global__ function `kernel` in a CUDA source (from its
+    qualifier line to the brace that closes its body)."""
+    text = path.read_text()
+    i = text.find(f" {kernel}(")
+    if i < 0:
+        return text
+    start = text.rfind("__global__", 0, i)
+    j = text.find("{", i)
+    depth, k = 0, j
+    while k < len(text):
+        depth += {"{": 1, "}": -1}.get(text[k], 0)
+        if depth == 0:
+            break
+        k += 1
+    return text[start:k + 1]
+
+
+def source_sha(path: Path, kernel: str | None = None) -> str:
+    data = kernel_source(path, kernel).encode() if kernel else path.read_bytes()
+    return hashlib.sha256(data).hexdigest()[:16]
 
 
 def committed_traffic(kernel: str, src: Path) -> float | None:
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source."""
+    the current source of that kernel (its own function text, so that edits
+    elsewhere in the file keep the figure)."""
     p = ROOT / "profiles" / "traffic.json"
     if not p.exists():
         return None
     d = json.loads(p.read_text()).get(kernel)
-    if not d or d.get("source_sha") != source_sha(src):
+    if not d or d.get("kernel_sha") != source_sha(src, kernel.split("::")[-1]):
         return None
     return d.get("dram_bytes_per_launch")
 
