@@ -345,30 +345,40 @@ __global__ void __launch_bounds__(256) pack_recv_kernel(const float2 *__restrict
                                                         __nv_bfloat16 *__restrict__ out) {
     const RecvEntry e = ent[blockIdx.x];
     const int Kp = e.Kp;
-    const int per = (e.Lc + kRecvSlices - 1) / kRecvSlices;
-    const int t0 = blockIdx.y * per, t1 = min(e.Lc, t0 + per);
+    // slices of whole 8-sample units (Lc is a multiple of 8): each thread
+    // writes 16-byte rows of 8 bf16 values
+    const int units = e.Lc >> 3;
+    const int per = (units + kRecvSlices - 1) / kRecvSlices;
+    const int g0 = blockIdx.y * per, g1 = min(units, g0 + per);
     for (int b = 0; b < e.nb; ++b) {
         const float2 *u = pyr + e.pyr_off + 2 * (int64_t)e.N - 4 * (int64_t)Kp + (int64_t)b * Kp;
         for (int c = 0; c < 8; ++c) {
             __nv_bfloat16 *hi_row = out + e.out_off + (int64_t)(((2 * b) * 8 + c) * 3) * e.Lc;
             __nv_bfloat16 *lo_row = out + e.out_off + (int64_t)(((2 * b + 1) * 8 + c) * 3) * e.Lc;
-            for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
-                const int idx = t + c + e.k0;
-                float2 x = make_float2(0.f, 0.f);
-                if (e.k0 == 0)
-                    x = u[idx % Kp];  // the window may span several periods when K' < S + 8
-                else if (idx >= 0 && idx < Kp)
-                    x = u[idx];
-                __nv_bfloat16 h0, l0, h1, l1, h2, l2;
-                split_bf16(x.x, h0, l0);
-                split_bf16(x.y, h1, l1);
-                split_bf16(-x.x, h2, l2);
-                hi_row[t] = h0;
-                hi_row[e.Lc + t] = h1;
-                hi_row[2 * (int64_t)e.Lc + t] = h2;
-                lo_row[t] = l0;
-                lo_row[e.Lc + t] = l1;
-                lo_row[2 * (int64_t)e.Lc + t] = l2;
+            for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+                const int t = 8 * g;
+                int idx = t + c + e.k0;
+                if (e.k0 == 0) idx %= Kp;  // circular: the window may span several periods when K' < S + 8
+                __align__(16) __nv_bfloat16 h[3][8], l[3][8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    float2 x = make_float2(0.f, 0.f);
+                    if (e.k0 == 0) {
+                        x = u[idx];
+                        idx = idx + 1 == Kp ? 0 : idx + 1;
+                    } else {
+                        if (idx >= 0 && idx < Kp) x = u[idx];
+                        ++idx;
+                    }
+                    split_bf16(x.x, h[0][q], l[0][q]);
+                    split_bf16(x.y, h[1][q], l[1][q]);
+                    split_bf16(-x.x, h[2][q], l[2][q]);
+                }
+#pragma unroll
+                for (int pl = 0; pl < 3; ++pl) {
+                    *reinterpret_cast<uint4 *>(hi_row + (int64_t)pl * e.Lc + t) = *reinterpret_cast<const uint4 *>(h[pl]);
+                    *reinterpret_cast<uint4 *>(lo_row + (int64_t)pl * e.Lc + t) = *reinterpret_cast<const uint4 *>(l[pl]);
+                }
             }
         }
     }
