@@ -485,9 +485,10 @@ def run_ragged_workload(args):
         r = S.Ragged()
         r.set_precision(precision)
         # tile shapes of both paths tuned on this GPU before the references are stored
-        t0 = time.perf_counter()
-        r.autotune()
-        tune_s[precision] = time.perf_counter() - t0
+        if not args.no_autotune:
+            t0 = time.perf_counter()
+            r.autotune()
+            tune_s[precision] = time.perf_counter() - t0
         r.reserve(int((2 * Js * Ns).sum()), int((2 * Ns - 2 * (Ns >> Js)).sum()), slots)
         return r, [r.store_reference(int(fs[i]), int(Ns[i]), int(Js[i]), refs[off[i]:off[i] + Ns[i]]) for i in range(n)]
 
@@ -1127,6 +1128,8 @@ def main():
     ap.add_argument("--lanes", type=int, default=4)
     ap.add_argument("--pool", type=int, default=256)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="ragged workload: keep the library's untuned tile weights (short profiler captures)")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
