@@ -352,11 +352,10 @@ struct RaggedLayout {  // everything a batch needs on the device, built on the h
     // tensor-core part: one received-operand entry and two tensor maps per
     // (pair, scale), tiles in cost order
     std::vector<rtc::TcTile> tc_tiles;
-    std::vector<rtc::RecvEntry> recv;
+    // one entry per tensor-core (pair, scale): its shape and stored operand
     std::vector<rtc::Shape> recv_shape;
     std::vector<int64_t> recv_a_off;
     std::vector<unsigned char> maps;
-    int64_t recv_elems = 0;
     int64_t pyr_elems = 0, slots = 0;
     int64_t maxN[2][3] = {{0, 0, 0}, {0, 0, 0}};
     int maxJ_long[3] = {0, 0, 0};
@@ -368,11 +367,10 @@ struct DevLayout {  // device copy of a RaggedLayout
     RaggedLift *lift = nullptr;
     int32_t *slot_item = nullptr;
     rtc::TcTile *tc_tiles = nullptr;
-    rtc::RecvEntry *recv = nullptr;
     unsigned char *maps = nullptr;
-    int64_t cap_items = 0, cap_work = 0, cap_lift = 0, cap_slots = 0, cap_tiles = 0, cap_recv = 0, cap_maps = 0;
+    int64_t cap_items = 0, cap_work = 0, cap_lift = 0, cap_slots = 0, cap_tiles = 0, cap_maps = 0;
     RaggedLiftGroups groups;
-    int nwork = 0, n_tc_tiles = 0, n_recv = 0;
+    int nwork = 0, n_tc_tiles = 0;
 };
 
 struct sidwt_ragged {
@@ -380,12 +378,10 @@ struct sidwt_ragged {
     float2 *tree = nullptr;
     int64_t tree_cap = 0, tree_used = 0;
     // tensor-core path (SIDWT_PREC_BF16X3): stored operands of the references
-    // packed at store time, received operands of the current batch, error flag
+    // packed at store time (the received windows are expanded on chip), error flag
     int prec = SIDWT_PREC_FP32;
     __nv_bfloat16 *tc_a = nullptr;
     int64_t tc_a_cap = 0, tc_a_used = 0;
-    __nv_bfloat16 *tc_b = nullptr;
-    int64_t tc_b_cap = 0;
     int32_t *err = nullptr;
     double *xen = nullptr;
     int64_t xen_cap = 0, xen_used = 0;
@@ -493,20 +489,9 @@ sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_i
             rtc::Shape sh;
             if (r->prec == SIDWT_PREC_BF16X3 && j < 16 && ri.tc_off[j] >= 0 &&
                 rtc::shape_with(it.N, it.J, j, ri.tc_S[j], &sh)) {
-                const int e = (int)L.recv.size();
-                rtc::RecvEntry re;
-                re.pyr_off = it.pyr_off;
-                re.out_off = L.recv_elems;
-                re.N = it.N;
-                re.Kp = (int32_t)sh.Kp;
-                re.lev = sh.lev;
-                re.nb = sh.nb;
-                re.Lc = (int32_t)sh.Lc;
-                re.k0 = sh.k0;
-                L.recv.push_back(re);
+                const int e = (int)L.recv_shape.size();
                 L.recv_shape.push_back(sh);
                 L.recv_a_off.push_back(ri.tc_off[j]);
-                L.recv_elems += (sh.b_elems + 63) / 64 * 64;
                 for (int t = 0; t < sh.tiles; ++t) {
                     rtc::TcTile w;
                     w.map = e;
@@ -518,8 +503,9 @@ sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_i
                     w.nb = (int16_t)sh.nb;
                     w.lev = (int16_t)sh.lev;
                     w.S = (int16_t)sh.S;
-                    w.pad = 0;
+                    w.k0 = (int16_t)sh.k0;
                     w.slot = it.slot + j;
+                    w.u_off = it.pyr_off + 2 * (int64_t)it.N - 4 * sh.Kp;
                     tct.push_back({(int64_t)sh.nb * sh.nkb * sh.S, w});
                 }
                 continue;
@@ -555,7 +541,7 @@ sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_i
                                                 const std::pair<int64_t, rtc::TcTile> &b) { return a.first > b.first; });
     L.tc_tiles.reserve(tct.size());
     for (const auto &x : tct) L.tc_tiles.push_back(x.second);
-    if (L.work.size() > 0x7fffffff || L.tc_tiles.size() > 0x7fffffff || L.recv.size() > 0x7fffffff) {
+    if (L.work.size() > 0x7fffffff || L.tc_tiles.size() > 0x7fffffff || L.recv_shape.size() > 0x7fffffff) {
         set_error("too many work items");
         return SIDWT_EINVAL;
     }
@@ -572,7 +558,6 @@ sidwt_status ensure_dev(DevLayout &d, const RaggedLayout &L) {
         (st = grow(&d.lift, &d.cap_lift, nl, 0, "ragged lifting list")) ||
         (st = grow(&d.slot_item, &d.cap_slots, L.slots, 0, "ragged slot map")) ||
         (st = grow(&d.tc_tiles, &d.cap_tiles, (int64_t)L.tc_tiles.size(), 0, "tensor-core tile list")) ||
-        (st = grow(&d.recv, &d.cap_recv, (int64_t)L.recv.size(), 0, "tensor-core operand list")) ||
         (st = grow(&d.maps, &d.cap_maps, (int64_t)L.maps.size(), 0, "tensor maps")))
         return st;
     return SIDWT_OK;
@@ -582,10 +567,10 @@ sidwt_status ensure_dev(DevLayout &d, const RaggedLayout &L) {
 // operand buffers, so after ensure_workspace).
 sidwt_status encode_layout_maps(const sidwt_ragged *r, RaggedLayout &L) {
     const size_t mb = rtc::map_bytes();
-    L.maps.assign(L.recv.size() * 2 * mb, 0);
-    for (size_t e = 0; e < L.recv.size(); ++e) {
-        sidwt_status st = rtc::encode_maps(L.maps.data() + e * 2 * mb, r->tc_a + L.recv_a_off[e],
-                                           r->tc_b + L.recv[e].out_off, L.recv_shape[e]);
+    L.maps.assign(L.recv_shape.size() * 2 * mb, 0);
+    for (size_t e = 0; e < L.recv_shape.size(); ++e) {
+        sidwt_status st = rtc::encode_maps(L.maps.data() + e * 2 * mb, r->tc_a + L.recv_a_off[e], nullptr,
+                                           L.recv_shape[e]);
         if (st) return st;
     }
     return SIDWT_OK;
@@ -617,10 +602,9 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
     d.groups = g;
     d.nwork = (int)L.work.size();
     d.n_tc_tiles = (int)L.tc_tiles.size();
-    d.n_recv = (int)L.recv.size();
     const size_t b1 = L.items.size() * sizeof(rg::Item), b2 = L.work.size() * sizeof(rg::Work);
     const size_t b3 = lift.size() * sizeof(RaggedLift), b4 = L.slot_item.size() * sizeof(int32_t);
-    const size_t b5 = L.tc_tiles.size() * sizeof(rtc::TcTile), b6 = L.recv.size() * sizeof(rtc::RecvEntry);
+    const size_t b5 = L.tc_tiles.size() * sizeof(rtc::TcTile);
     const size_t b7 = L.maps.size();
     cudaError_t e = cudaSuccess;
     if (sync) {
@@ -629,13 +613,12 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
         if (e == cudaSuccess && b3) e = cudaMemcpy(d.lift, lift.data(), b3, cudaMemcpyHostToDevice);
         if (e == cudaSuccess && b4) e = cudaMemcpy(d.slot_item, L.slot_item.data(), b4, cudaMemcpyHostToDevice);
         if (e == cudaSuccess && b5) e = cudaMemcpy(d.tc_tiles, L.tc_tiles.data(), b5, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && b6) e = cudaMemcpy(d.recv, L.recv.data(), b6, cudaMemcpyHostToDevice);
         if (e == cudaSuccess && b7) e = cudaMemcpy(d.maps, L.maps.data(), b7, cudaMemcpyHostToDevice);
         return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "ragged layout upload");
     }
     // asynchronous: through the object's pinned staging buffer (the previous
     // upload has been consumed once the stream reaches this point)
-    const size_t tot = b1 + b2 + b3 + b4 + b5 + b6 + b7 + 7 * 16;
+    const size_t tot = b1 + b2 + b3 + b4 + b5 + b7 + 6 * 16;
     if (tot > r->h_stage_bytes) {
         cudaStreamSynchronize(s);
         if (r->h_stage) cudaFreeHost(r->h_stage);
@@ -663,7 +646,6 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
     put(d.lift, lift.data(), b3);
     put(d.slot_item, L.slot_item.data(), b4);
     put(d.tc_tiles, L.tc_tiles.data(), b5);
-    put(d.recv, L.recv.data(), b6);
     put(d.maps, L.maps.data(), b7);
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "ragged layout upload");
 }
@@ -680,7 +662,6 @@ sidwt_status ensure_workspace(sidwt_ragged *r, const RaggedLayout &L) {
             return st;
         r->slot_cap = c0;
     }
-    if ((st = grow(&r->tc_b, &r->tc_b_cap, L.recv_elems, 0, "received tensor-core operands"))) return st;
     if (!r->counter && cudaMalloc(&r->counter, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         set_error("device allocation failed: work counter");
@@ -710,11 +691,9 @@ sidwt_status enqueue(sidwt_ragged *r, const DevLayout &d, int64_t slots, int64_t
     if (e == cudaSuccess) e = cudaMemsetAsync(r->counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_fail(e, "ragged memset");
     if (timed) cudaEventRecord(ev[1], s);
-    if (d.n_recv > 0) {
-        if ((st = rtc::launch_pack_recv(r->pyr, d.recv, d.n_recv, r->tc_b, s)) ||
-            (st = rtc::launch_corr(d.maps, d.tc_tiles, d.n_tc_tiles, r->keys, r->err, r->sms, s)))
-            return st;
-        nl += 2;
+    if (d.n_tc_tiles > 0) {
+        if ((st = rtc::launch_corr(d.maps, d.tc_tiles, d.n_tc_tiles, r->pyr, r->keys, r->err, r->sms, s))) return st;
+        nl += 1;
     }
     if (d.nwork > 0) {
         rg::corr_ragged_kernel<<<r->sms * 2, rg::kT, 0, s>>>(d.items, d.work, d.nwork, r->counter, r->tree, r->pyr,
@@ -892,10 +871,8 @@ bool sidwt::ragged_room(const sidwt_ragged *r, int64_t tree_elems, int64_t xen_e
            r->tc_a_used + tc_elems <= r->tc_a_cap;
 }
 
-sidwt_status sidwt::ragged_reserve_tc(sidwt_ragged *r, int64_t stored_elems, int64_t received_elems) {
-    sidwt_status st;
-    if ((st = grow(&r->tc_a, &r->tc_a_cap, stored_elems, r->tc_a_used, "stored tensor-core operands"))) return st;
-    return grow(&r->tc_b, &r->tc_b_cap, received_elems, 0, "received tensor-core operands");
+sidwt_status sidwt::ragged_reserve_tc(sidwt_ragged *r, int64_t stored_elems) {
+    return grow(&r->tc_a, &r->tc_a_cap, stored_elems, r->tc_a_used, "stored tensor-core operands");
 }
 
 extern "C" {
@@ -944,11 +921,9 @@ sidwt_status sidwt_ragged_destroy(sidwt_ragged *r) {
         cudaFree(d->lift);
         cudaFree(d->slot_item);
         cudaFree(d->tc_tiles);
-        cudaFree(d->recv);
         cudaFree(d->maps);
     }
     cudaFree(r->tc_a);
-    cudaFree(r->tc_b);
     cudaFree(r->err);
     cudaFree(r->tree);
     cudaFree(r->xen);
@@ -1156,23 +1131,21 @@ namespace {
 sidwt_status tune_tc(sidwt_ragged *r, cudaStream_t s, std::string *report) {
     const int lg_lo = 6, lg_hi = 14;
     const int *widths = rtc::kTcWidth;
-    int64_t amax = 0, bmax = 0, tmax = 0;
+    int64_t amax = 0, tmax = 0;
     for (int lg = lg_lo; lg <= lg_hi; ++lg)
         for (int k = 0; k < rtc::kTcWidths; ++k) {
             const int S = widths[k];
             rtc::Shape sh;
             if (!rtc::shape_with(int64_t(16) << lg, 4, 3, S, &sh)) continue;
             amax = std::max(amax, sh.a_elems);
-            bmax = std::max(bmax, sh.b_elems);
         }
     for (int lg = lg_lo; lg <= lg_hi; ++lg)
         tmax = std::max<int64_t>(tmax, (int64_t)r->sms * std::min(64, std::max(2, 1 << std::max(0, 16 - lg))));
     const int64_t Nmax = int64_t(16) << lg_hi;
     float2 *tree = nullptr, *pyr = nullptr;
-    __nv_bfloat16 *abuf = nullptr, *bbuf = nullptr;
+    __nv_bfloat16 *abuf = nullptr;
     unsigned char *maps = nullptr;
     rtc::TcTile *dt = nullptr;
-    rtc::RecvEntry *dre = nullptr;
     unsigned long long *keys = nullptr;
     int32_t *err = nullptr;
     const size_t mb = rtc::map_bytes();
@@ -1180,19 +1153,15 @@ sidwt_status tune_tc(sidwt_ragged *r, cudaStream_t s, std::string *report) {
         cudaFree(tree);
         cudaFree(pyr);
         cudaFree(abuf);
-        cudaFree(bbuf);
         cudaFree(maps);
         cudaFree(dt);
-        cudaFree(dre);
         cudaFree(keys);
         cudaFree(err);
     };
     if (cudaMalloc(&tree, 8 * Nmax * sizeof(float2)) != cudaSuccess ||  // 2 J N, J = 4
         cudaMalloc(&pyr, 2 * Nmax * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc(&abuf, amax * sizeof(__nv_bfloat16)) != cudaSuccess ||
-        cudaMalloc(&bbuf, bmax * sizeof(__nv_bfloat16)) != cudaSuccess || cudaMalloc(&maps, 2 * mb) != cudaSuccess ||
+        cudaMalloc(&abuf, amax * sizeof(__nv_bfloat16)) != cudaSuccess || cudaMalloc(&maps, 2 * mb) != cudaSuccess ||
         cudaMalloc(&dt, tmax * sizeof(rtc::TcTile)) != cudaSuccess ||
-        cudaMalloc(&dre, sizeof(rtc::RecvEntry)) != cudaSuccess ||
         cudaMalloc(&keys, sizeof(unsigned long long)) != cudaSuccess || cudaMalloc(&err, sizeof(int32_t)) != cudaSuccess) {
         cudaGetLastError();
         release();
@@ -1224,10 +1193,7 @@ sidwt_status tune_tc(sidwt_ragged *r, cudaStream_t s, std::string *report) {
             a_off[3] = 0;
             S_of[3] = (int16_t)S;
             if ((st = rtc::pack_stored(tree, N, 4, a_off, S_of, abuf, s))) break;
-            const rtc::RecvEntry re{0, 0, (int32_t)N, (int32_t)Kp, sh.lev, sh.nb, (int32_t)sh.Lc, sh.k0};
-            cudaMemcpyAsync(dre, &re, sizeof(re), cudaMemcpyHostToDevice, s);
-            if ((st = rtc::launch_pack_recv(pyr, dre, 1, bbuf, s))) break;
-            if ((st = rtc::encode_maps(hmaps.data(), abuf, bbuf, sh))) break;
+            if ((st = rtc::encode_maps(hmaps.data(), abuf, nullptr, sh))) break;
             cudaMemcpyAsync(maps, hmaps.data(), 2 * mb, cudaMemcpyHostToDevice, s);
             const int n = r->sms * std::min(64, std::max(2, 1 << std::max(0, 16 - lg)));
             std::vector<rtc::TcTile> tl((size_t)n);
@@ -1242,15 +1208,16 @@ sidwt_status tune_tc(sidwt_ragged *r, cudaStream_t s, std::string *report) {
                 x.nb = (int16_t)sh.nb;
                 x.lev = (int16_t)sh.lev;
                 x.S = (int16_t)S;
-                x.pad = 0;
+                x.k0 = (int16_t)sh.k0;
                 x.slot = 0;
+                x.u_off = 2 * N - 4 * Kp;  // level sh.lev of the synthetic pyramid
             }
             cudaMemcpyAsync(dt, tl.data(), (size_t)n * sizeof(rtc::TcTile), cudaMemcpyHostToDevice, s);
             cudaStreamSynchronize(s);  // the host staging buffers are reused
             float tot = 0.f;
             for (int rep = 0; rep < 4 && !st; ++rep) {
                 cudaEventRecord(e0, s);
-                st = rtc::launch_corr(maps, dt, n, keys, err, r->sms, s);
+                st = rtc::launch_corr(maps, dt, n, pyr, keys, err, r->sms, s);
                 cudaEventRecord(e1, s);
                 cudaEventSynchronize(e1);
                 float ms = 0.f;

@@ -20,17 +20,23 @@
 //     (residue x Re/Im), 1 variant, hi+lo} fills one 8-row group of the
 //     K-major A tile ([hi/lo][chunk][row][16 B], 4 KB per group);
 //   * received columns: the overlapping MN-major window of the batched kernel
-//     (8 shifted copies U_c[t] = u[t + c + k0], planes Re, Im, -Re).
+//     (8 shifted copies U_c[t] = u[t + c + k0], planes Re, Im, -Re), built
+//     in shared memory for each K-block by four expansion warps straight from
+//     the received pyramid (no packed copy in HBM: the copies and planes are
+//     12x the band's bytes).
 // Band lengths that are a multiple of 64 use the circular form (k0 = 0, the
 // received copies wrap).  Other lengths use the equivalent linear form: the
 // received band is zero outside [0, K'), the contraction runs over
 // k in [-S, ceil(K'/64) 64), and the stored rows stay periodic.
 //
 // Persistent grid, one CTA per SM, tiles in cost order strided over the
-// CTAs.  Roles (192 threads): warp 0 TMA producer (2-stage ring), warp 1
-// TMEM allocation and MMA issue, warps 2-5 epilogue (peak keys).  The
-// producer runs ahead into the next tile; the MMA warp starts a tile once
-// the epilogue has drained the accumulators.  Every wait is bounded.
+// CTAs.  Roles (320 threads): warp 0 TMA producer of the stored operand
+// (2-stage ring), warp 1 TMEM allocation and MMA issue, warps 2-5 epilogue
+// (peak keys), warps 6-9 received-window expansion into the same ring (a
+// stage is full once its copies have landed and the four warps have
+// arrived).  The producer and the expansion warps run ahead into the next
+// tile; the MMA warp starts a tile once the epilogue has drained the
+// accumulators.  Every wait is bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -45,7 +51,7 @@ namespace rtc {
 
 using namespace sidwt::tc;
 
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;
 constexpr int kGroupBytes = 4096;             // [hi/lo][16 chunks][8 rows][16 B]
 constexpr int kStageA = 16 * kGroupBytes;     // 65536
 constexpr int kMaxBRow = (256 + 64) * 2;      // 640 bytes per window row at S = 256
@@ -66,14 +72,6 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const void *map, uint64_t
         "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
         "%6}], [%7];" ::"r"(saddr(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(saddr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_load_3d_g(void *dst, const void *map, uint64_t *bar, int c0, int c1, int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(saddr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(saddr(bar))
         : "memory");
 }
 
@@ -109,9 +107,48 @@ __device__ __forceinline__ int valid_groups(const TcTile &w) {
     return max(0, min(16, total - g0));
 }
 
+// The received operand of one K-block: for the 8 residues c the window
+// U_c[64 kb + t] = u[64 kb + t + c + k0], t < S + 64 (wrapped mod K' in the
+// circular form, zero outside [0, K') in the padded one), as bf16 hi and lo
+// of the planes Re, Im, -Re: rows (hi/lo) * 24 + 3 c + plane of S + 64
+// samples.  Written by the four expansion warps straight from the received
+// pyramid (8 samples and 16-byte stores per work item).
+__device__ __forceinline__ void expand_window(unsigned char *stB, const float2 *__restrict__ u, int Kp, int k0, int S,
+                                              int kb, int tw, int nthreads) {
+    const int rowlen = S + 64, ngrp = rowlen >> 3;
+    const uint32_t bRow = (uint32_t)rowlen * 2;
+    for (int item = tw; item < 8 * ngrp; item += nthreads) {
+        const int c = item / ngrp, g = item - c * ngrp;
+        int idx = 64 * kb + 8 * g + c + k0;
+        if (k0 == 0) idx %= Kp;
+        __align__(16) __nv_bfloat16 h[3][8], l[3][8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            float2 x = make_float2(0.f, 0.f);
+            if (k0 == 0) {
+                x = u[idx];
+                idx = idx + 1 == Kp ? 0 : idx + 1;
+            } else {
+                if (idx >= 0 && idx < Kp) x = u[idx];
+                ++idx;
+            }
+            split_bf16(x.x, h[0][q], l[0][q]);
+            split_bf16(x.y, h[1][q], l[1][q]);
+            split_bf16(-x.x, h[2][q], l[2][q]);
+        }
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl) {
+            const uint32_t off = (uint32_t)(3 * c + pl) * bRow + 16u * (uint32_t)g;
+            *reinterpret_cast<uint4 *>(stB + off) = *reinterpret_cast<const uint4 *>(h[pl]);
+            *reinterpret_cast<uint4 *>(stB + 24 * bRow + off) = *reinterpret_cast<const uint4 *>(l[pl]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     corr_pair_tc_kernel(const CUtensorMap *__restrict__ maps, const TcTile *__restrict__ tiles, int ntiles,
-                        unsigned long long *__restrict__ keys, int32_t *__restrict__ err) {
+                        const float2 *__restrict__ pyr, unsigned long long *__restrict__ keys,
+                        int32_t *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *sB = base;
@@ -127,7 +164,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&full[i], 1);
+            mbar_init(&full[i], 1 + 4);  // the producer's expect_tx and one arrival per expansion warp
             mbar_init(&empty[i], 1);
         }
         mbar_init(accf, 1);
@@ -151,13 +188,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int t = blockIdx.x; t < ntiles && !sflag[0]; t += gridDim.x) {
                 const TcTile w = tiles[t];
                 const CUtensorMap *mA = maps + 2 * (int64_t)w.map;
-                const CUtensorMap *mB = mA + 1;
                 const int Lr = w.S >> 3;
-                const int bRow = (w.S + 64) * 2;
                 const int ng = valid_groups(w);
                 tensormap_acquire(mA);
-                tensormap_acquire(mB);
-                const uint32_t tx = (uint32_t)(ng * kGroupBytes + 48 * bRow);
+                const uint32_t tx = (uint32_t)(ng * kGroupBytes);
                 for (int b = 0; b < w.nb && !sflag[0]; ++b)
                     for (int kb = 0; kb < w.nkb; ++kb) {
                         const int s = it & 1;
@@ -168,19 +202,38 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (sflag[0]) break;
                         mbar_expect_tx(&full[s], tx);
                         unsigned char *stA = sA + s * kStageA;
-                        unsigned char *stB = sB + s * kStageB;
                         const int col = (8 * kb) % Lr, rsh = (8 * kb) / Lr;
                         for (int g = 0; g < ng; ++g) {
                             const int G = 16 * w.tile + g;
                             const int v = G / w.gv, i0 = 8 * (G % w.gv);
                             tma_load_5d(stA + g * kGroupBytes, mA, &full[s], col, i0 + rsh, 0, v, 2 * b);
                         }
-                        tma_load_3d_g(stB, mB, &full[s], 0, 8 * kb, (2 * b) * 24);
-                        tma_load_3d_g(stB + 24 * bRow, mB, &full[s], 0, 8 * kb, (2 * b + 1) * 24);
                         ++it;
                     }
             }
             sflag[1] = it;
+        }
+    } else if (warp >= 6) {
+        // expansion warps: the received windows of the same K-blocks, in the same order
+        const int tw = threadIdx.x - 6 * 32;
+        int it = 0;
+        for (int t = blockIdx.x; t < ntiles && !sflag[0]; t += gridDim.x) {
+            const TcTile w = tiles[t];
+            for (int b = 0; b < w.nb && !sflag[0]; ++b)
+                for (int kb = 0; kb < w.nkb; ++kb) {
+                    const int s = it & 1;
+                    if (it >= 2 && !mbar_wait(&empty[s], ((it >> 1) - 1) & 1)) {
+                        sflag[0] = 1;
+                        break;
+                    }
+                    if (sflag[0]) break;
+                    expand_window(sB + s * kStageB, pyr + w.u_off + (int64_t)b * w.Kp, w.Kp, w.k0, w.S, kb, tw, 128);
+                    // the tensor cores read these stores through the async proxy
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&full[s]);
+                    ++it;
+                }
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -237,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_commit(drain);  // every MMA issued by this CTA has completed
             if (!mbar_wait(drain, 0)) sflag[0] = 1;
         }
-    } else {
+    } else if (warp >= 2 && warp < 6) {
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = tile rows
         const int q4 = warp & 3;
         const int m = q4 * 32 + lane;
@@ -335,54 +388,6 @@ __global__ void pack_stored_kernel(const float2 *__restrict__ tree, int64_t N, S
     }
 }
 
-// Received windows of one (pulse, scale): row ((2 b + h) 8 + c) 3 + plane
-// holds Lc samples U_c[t] = plane(u_b[t + c + k0]), plane 0 Re, 1 Im, 2 -Re,
-// u_b periodic (k0 = 0) or zero outside [0, K') (k0 < 0); hi or lo part.
-// Block (entry, slice of t): all 8 residues of a slice, so that the band is
-// read from DRAM about once (the 8 shifted reads of a sample hit L1).
-constexpr int kRecvSlices = 8;
-__global__ void __launch_bounds__(256) pack_recv_kernel(const float2 *__restrict__ pyr, const RecvEntry *__restrict__ ent,
-                                                        __nv_bfloat16 *__restrict__ out) {
-    const RecvEntry e = ent[blockIdx.x];
-    const int Kp = e.Kp;
-    // slices of whole 8-sample units (Lc is a multiple of 8): each thread
-    // writes 16-byte rows of 8 bf16 values
-    const int units = e.Lc >> 3;
-    const int per = (units + kRecvSlices - 1) / kRecvSlices;
-    const int g0 = blockIdx.y * per, g1 = min(units, g0 + per);
-    for (int b = 0; b < e.nb; ++b) {
-        const float2 *u = pyr + e.pyr_off + 2 * (int64_t)e.N - 4 * (int64_t)Kp + (int64_t)b * Kp;
-        for (int c = 0; c < 8; ++c) {
-            __nv_bfloat16 *hi_row = out + e.out_off + (int64_t)(((2 * b) * 8 + c) * 3) * e.Lc;
-            __nv_bfloat16 *lo_row = out + e.out_off + (int64_t)(((2 * b + 1) * 8 + c) * 3) * e.Lc;
-            for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
-                const int t = 8 * g;
-                int idx = t + c + e.k0;
-                if (e.k0 == 0) idx %= Kp;  // circular: the window may span several periods when K' < S + 8
-                __align__(16) __nv_bfloat16 h[3][8], l[3][8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    float2 x = make_float2(0.f, 0.f);
-                    if (e.k0 == 0) {
-                        x = u[idx];
-                        idx = idx + 1 == Kp ? 0 : idx + 1;
-                    } else {
-                        if (idx >= 0 && idx < Kp) x = u[idx];
-                        ++idx;
-                    }
-                    split_bf16(x.x, h[0][q], l[0][q]);
-                    split_bf16(x.y, h[1][q], l[1][q]);
-                    split_bf16(-x.x, h[2][q], l[2][q]);
-                }
-#pragma unroll
-                for (int pl = 0; pl < 3; ++pl) {
-                    *reinterpret_cast<uint4 *>(hi_row + (int64_t)pl * e.Lc + t) = *reinterpret_cast<const uint4 *>(h[pl]);
-                    *reinterpret_cast<uint4 *>(lo_row + (int64_t)pl * e.Lc + t) = *reinterpret_cast<const uint4 *>(l[pl]);
-                }
-            }
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Host side
@@ -416,8 +421,6 @@ static void fill_shape(int64_t N, int J, int j, int S, Shape *sh) {
     sh->tiles = (int)((groups + 15) / 16);
     sh->Rs = sh->gv * 8 + (8 * sh->nkb + sh->Lr - 1) / sh->Lr;
     sh->a_elems = (int64_t)2 * sh->nb * sh->nv * 16 * sh->Rs * sh->Lr;
-    sh->Lc = (int64_t)64 * sh->nkb + S;
-    sh->b_elems = (int64_t)48 * sh->nb * sh->Lc;
 }
 
 bool shape_with(int64_t N, int J, int j, int S, Shape *sh) {
@@ -456,16 +459,14 @@ bool shape_for(int64_t N, int J, int j, Shape *sh, const TcWeights *w) {
     return true;
 }
 
-void operand_elems(int64_t N, int J, int64_t *stored, int64_t *received) {
-    int64_t a = 0, b = 0;
+int64_t operand_elems(int64_t N, int J) {
+    int64_t a = 0;
     for (int j = 0; j <= J && j < 16; ++j) {
         Shape sh;
         if (!shape_for(N, J, j, &sh)) continue;
         a += (sh.a_elems + 63) / 64 * 64;
-        b += (sh.b_elems + 63) / 64 * 64;
     }
-    *stored = a;
-    *received = b;
+    return a;
 }
 
 sidwt_status pack_stored(const float2 *tree, int64_t N, int J, const int64_t *a_off, const int16_t *S_of, void *abuf,
@@ -502,27 +503,18 @@ sidwt_status encode_maps(void *two_maps, const void *a_base, const void *b_base,
     const uint64_t da[5] = {(uint64_t)sh.Lr, (uint64_t)sh.Rs, 16, (uint64_t)sh.nv, (uint64_t)(2 * sh.nb)};
     const uint64_t sa[4] = {lr2, lr2 * sh.Rs, lr2 * sh.Rs * 16, lr2 * sh.Rs * 16 * sh.nv};
     const uint32_t ba[5] = {8, 8, 16, 1, 2};
-    sidwt_status st = encode_nd(&m[0], const_cast<void *>(a_base), 5, da, sa, ba);
-    if (st) return st;
-    const uint64_t db[3] = {8, (uint64_t)sh.Lc / 8, (uint64_t)(48 * sh.nb)};
-    const uint64_t sb[2] = {16, (uint64_t)sh.Lc * 2};
-    const uint32_t bb[3] = {8, (uint32_t)(sh.S / 8 + 8), 24};
-    return encode_nd(&m[1], const_cast<void *>(b_base), 3, db, sb, bb);
+    (void)b_base;  // the received windows are expanded in shared memory by the kernel
+    std::memset(&m[1], 0, sizeof(CUtensorMap));
+    return encode_nd(&m[0], const_cast<void *>(a_base), 5, da, sa, ba);
 }
 
-sidwt_status launch_pack_recv(const float2 *pyr, const RecvEntry *e, int n, void *out, cudaStream_t s) {
-    if (n <= 0) return SIDWT_OK;
-    pack_recv_kernel<<<dim3((unsigned)n, kRecvSlices), 256, 0, s>>>(pyr, e, static_cast<__nv_bfloat16 *>(out));
-    cudaError_t er = cudaGetLastError();
-    return er == cudaSuccess ? SIDWT_OK : cuda_fail(er, "received tensor-core operand packing");
-}
 
-sidwt_status launch_corr(const void *maps, const TcTile *tiles, int ntiles, unsigned long long *keys, int32_t *err,
-                         int sms, cudaStream_t s) {
+sidwt_status launch_corr(const void *maps, const TcTile *tiles, int ntiles, const float2 *pyr, unsigned long long *keys,
+                         int32_t *err, int sms, cudaStream_t s) {
     if (ntiles <= 0) return SIDWT_OK;
     const int grid = std::min(sms, ntiles);
-    corr_pair_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(static_cast<const CUtensorMap *>(maps), tiles, ntiles, keys,
-                                                            err);
+    corr_pair_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(static_cast<const CUtensorMap *>(maps), tiles, ntiles, pyr,
+                                                            keys, err);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "tensor-core pair correlation launch");
 }

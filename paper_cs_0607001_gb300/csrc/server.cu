@@ -50,11 +50,7 @@ struct Request {
 int64_t footprint(int64_t N, int J, int precision) {
     // pulse, padded reference, SIDWT tree, pyramid, peak slots
     int64_t b = 8 * N + 8 * N + 16 * (int64_t)J * N + 16 * N + 64 * (J + 1);
-    if (precision == SIDWT_PREC_BF16X3) {  // packed tensor-core operands (bf16)
-        int64_t a = 0, r = 0;
-        rtc::operand_elems(N, J, &a, &r);
-        b += 2 * (a + r);
-    }
+    if (precision == SIDWT_PREC_BF16X3) b += 2 * rtc::operand_elems(N, J);  // packed stored operand (bf16)
     return b;
 }
 
@@ -159,9 +155,7 @@ void fail_lane(sidwt_server *s, Lane &L, sidwt_status st) {
 void store_needs(const sidwt_server *s, int64_t N, int J, int64_t *tree, int64_t *xen, int64_t *tc) {
     *tree = 2 * (int64_t)J * N;
     *xen = (int64_t(2) << J) - 1;
-    int64_t a = 0, b = 0;
-    if (s->cfg.precision == SIDWT_PREC_BF16X3) rtc::operand_elems(N, J, &a, &b);
-    *tc = a;
+    *tc = s->cfg.precision == SIDWT_PREC_BF16X3 ? rtc::operand_elems(N, J) : 0;
 }
 
 // Enqueue a formed batch on a lane (server thread only).
@@ -331,9 +325,8 @@ sidwt_status sidwt_server_create(const sidwt_server_config *cfg, sidwt_server **
         if (!st) st = sidwt_ragged_reserve(L.rg, 2 * (int64_t)cfg->max_j * cap, 2 * cap, slots);
         if (!st) st = sidwt_ragged_set_precision(L.rg, (sidwt_precision)cfg->precision);
         if (!st && cfg->precision == SIDWT_PREC_BF16X3) {
-            int64_t a = 0, r = 0;
-            rtc::operand_elems(cap - cap % (int64_t(1) << cfg->max_j), cfg->max_j, &a, &r);
-            st = ragged_reserve_tc(L.rg, a + a / 2, r + r / 2);
+            const int64_t a = rtc::operand_elems(cap - cap % (int64_t(1) << cfg->max_j), cfg->max_j);
+            st = ragged_reserve_tc(L.rg, a + a / 2);
         }
         if (st || cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess ||

@@ -301,23 +301,17 @@ struct Shape {
     int Rs;       // stored rows of Lr samples per (band, hi/lo, variant, chunk)
     int tiles;    // 128-row tiles of this (pair, scale)
     int64_t a_elems;  // stored operand, bf16 elements
-    int64_t Lc;       // received window row length
-    int64_t b_elems;  // received operand, bf16 elements
 };
 
 struct TcTile {
-    int32_t map;   // maps[2 map]: stored operand, maps[2 map + 1]: received window
+    int32_t map;   // maps[2 map]: stored operand (maps[2 map + 1] unused)
     int32_t tile;  // first 8-row group = 16 tile
     int32_t nkb, Kp, gv, nv;
-    int16_t nb, lev, S, pad;
-    int64_t slot;  // peak key of this (pair, scale)
+    int16_t nb, lev, S, k0;  // k0: first contraction index (0 circular, -S zero-padded)
+    int64_t slot;   // peak key of this (pair, scale)
+    int64_t u_off;  // received band 0 of this scale in the pyramid buffer (band 1 follows at + Kp)
 };
 
-struct RecvEntry {
-    int64_t pyr_off;  // received pyramid of the pulse (float2 elements)
-    int64_t out_off;  // received window rows (bf16 elements)
-    int32_t N, Kp, lev, nb, Lc, k0;
-};
 
 // Relative cost per padded MMA element of each tile width (index 0: S = 256,
 // 1: 128, 2: 64, 3: 192) by floor(log2 K'): defaults, or measured by the
@@ -333,9 +327,9 @@ void default_weights(TcWeights *t);
 bool shape_with(int64_t N, int J, int j, int S, Shape *sh);  // S in kTcWidth
 // The cheapest width under the weights (nullptr: defaults).
 bool shape_for(int64_t N, int J, int j, Shape *sh, const TcWeights *w = nullptr);
-// Tensor-core operand elements (bf16) of one (N, J) pulse: stored side and
-// received side, each rounded up per scale as the ragged object lays them out.
-void operand_elems(int64_t N, int J, int64_t *stored, int64_t *received);
+// Stored tensor-core operand elements (bf16) of one (N, J) signal, rounded up
+// per scale as the ragged object lays them out.
+int64_t operand_elems(int64_t N, int J);
 // Stored operand of every tensor-core scale of one signal whose SIDWT tree
 // starts at tree; a_off[j] = element offset in abuf (-1: scale not packed),
 // S_of[j] its tile width.
@@ -343,15 +337,14 @@ sidwt_status pack_stored(const float2 *tree, int64_t N, int J, const int64_t *a_
                          cudaStream_t s);
 sidwt_status encode_maps(void *two_maps, const void *a_base, const void *b_base, const Shape &sh);
 size_t map_bytes();
-sidwt_status launch_pack_recv(const float2 *pyr, const RecvEntry *e, int n, void *out, cudaStream_t s);
-sidwt_status launch_corr(const void *maps, const TcTile *tiles, int ntiles, unsigned long long *keys, int32_t *err,
-                         int sms, cudaStream_t s);
+sidwt_status launch_corr(const void *maps, const TcTile *tiles, int ntiles, const float2 *pyr, unsigned long long *keys,
+                         int32_t *err, int sms, cudaStream_t s);
 cudaError_t prepare_kernels();
 
 }  // namespace rtc
 
 // ---- ragged.cu: pre-size a ragged object's tensor-core operand buffers ----
-sidwt_status ragged_reserve_tc(sidwt_ragged *r, int64_t stored_elems, int64_t received_elems);
+sidwt_status ragged_reserve_tc(sidwt_ragged *r, int64_t stored_elems);
 // whether the reserved stores hold that many more elements without growing
 bool ragged_room(const sidwt_ragged *r, int64_t tree_elems, int64_t xen_elems, int64_t tc_elems);
 }  // namespace sidwt
