@@ -22,6 +22,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 from pathlib import Path
 
@@ -63,8 +64,9 @@ class ClockSampler:
 
     def start(self):
         try:
-            out = ROOT / "gpurun_out"
-            out.mkdir(exist_ok=True)
+            # the raw samples go to SIDWT_CLOCKS_DIR (default: the temporary directory)
+            out = Path(os.environ.get("SIDWT_CLOCKS_DIR", tempfile.gettempdir()))
+            out.mkdir(parents=True, exist_ok=True)
             self.path = out / f"clocks_{os.getpid()}.csv"
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={CLOCK_FIELDS}",
