@@ -644,8 +644,9 @@ def ragged_roofline(prec, achieved, flops, ms):
                 "flops_per_launch": flops, "launch_ms": ms,
                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz"}
     pk = measured_peaks().get("bf16_tflops", 1900.0) / 3.0
+    traffic = committed_traffic("corr_pair_tc_kernel", ROOT / "paper_cs_0607001_gb300" / "csrc" / "ragged_tc.cu")
     return {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
-            "traffic": None, "kernel": "corr_pair_tc_kernel (+ its operand packing and the CUDA-core tail)",
+            "traffic": traffic, "kernel": "corr_pair_tc_kernel (+ the CUDA-core tail for bands under 64 samples)",
             "flops_per_launch": flops, "launch_ms": ms,
             "peak_source": "measured bf16 dense (burst) / 3 products; achieved = all scales' algorithmic flops "
                            "over the whole correlation stage"}
