@@ -16,9 +16,14 @@
 //   * stored rows: for each residue c of k mod 8 the polyphase sequence
 //     P_c[s] = w[(k0 + c + 8 s) mod K'] is cut into rows of S/8 samples, so
 //     that row r of a K-block starting at sample 8 kb is row i + (8 kb)/(S/8)
-//     of that reshaped array; a 5-D TMA box {8 samples, 8 rows, 16 chunks
-//     (residue x Re/Im), 1 variant, hi+lo} fills one 8-row group of the
-//     K-major A tile ([hi/lo][chunk][row][16 B], 4 KB per group);
+//     of that reshaped array.  The packed operand keeps, for every reshaped
+//     row and block of 8 samples, its 16 chunks (residue x Re/Im) of 8
+//     samples together (256 bytes), so that two 5-D TMA boxes {64 elements,
+//     1 block, 8 rows, hi+lo, 1} per 8-row group move whole 128-byte rows
+//     into the K-major A tile, in the 128-byte swizzled layout
+//     [chunk half][group][hi/lo][8 rows][128 B] (4 KB per group; with
+//     16-byte rows the copies were bound by their row count, 4096 per
+//     K-block, which set a floor under the narrower widths);
 //   * received columns: the overlapping MN-major window of the batched kernel
 //     (8 shifted copies U_c[t] = u[t + c + k0], planes Re, Im, -Re), built
 //     in shared memory for each K-block by four expansion warps straight from
@@ -52,13 +57,16 @@ namespace rtc {
 using namespace sidwt::tc;
 
 constexpr int kThreads = 320;
-constexpr int kGroupBytes = 4096;             // [hi/lo][16 chunks][8 rows][16 B]
+constexpr int kGroupBytes = 4096;             // per 8-row group: 2 chunk halves x hi/lo x 8 rows x 128 B
 constexpr int kStageA = 16 * kGroupBytes;     // 65536
+constexpr int kHalfBytes = kStageA / 2;       // chunks 0-7 (residues 0-3), then 8-15: [group][hi/lo][8][128 B]
+static_assert(kHalfBytes % 1024 == 0, "128-byte swizzle atoms on 1 KB boundaries");
 constexpr int kMaxBRow = (256 + 64) * 2;      // 640 bytes per window row at S = 256
 constexpr int kStageB = 2 * 24 * kMaxBRow;    // 30720
 constexpr int kBRegion = 2 * kStageB;
 constexpr int kARegion = 2 * kStageA;
 constexpr int kBarOff = kBRegion + kARegion;  // 192512
+static_assert(kBRegion % 1024 == 0, "the stored-operand ring starts on a 1 KB boundary");
 // what the kernel uses (rings, barriers, 1 KB alignment slack), so that a
 // CUDA-core CTA of the ragged kernel (about 20 KB) fits beside it on an SM
 constexpr int kSmemBytes = kBarOff + 128 + 1024;
@@ -206,7 +214,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int g = 0; g < ng; ++g) {
                             const int G = 16 * w.tile + g;
                             const int v = G / w.gv, i0 = 8 * (G % w.gv);
-                            tma_load_5d(stA + g * kGroupBytes, mA, &full[s], col, i0 + rsh, 0, v, 2 * b);
+                            // chunk halves h: elements 64 h .. 64 h + 63 of the (row, block) record
+                            for (int h = 0; h < 2; ++h)
+                                tma_load_5d(stA + h * kHalfBytes + g * 2048, mA, &full[s], 64 * h, col >> 3, i0 + rsh,
+                                            0, b * w.nv + v);
                         }
                         ++it;
                     }
@@ -258,13 +269,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t aHi = saddr(sA + s * kStageA), aLo = aHi + 2048;
+                        const uint32_t aHi = saddr(sA + s * kStageA), aLo = aHi + 1024;
                         const uint32_t bHi = saddr(sB + s * kStageB), bLo = bHi + 24 * bRow;
 #pragma unroll 1
                         for (int c = 0; c < 8; ++c) {
-                            // A: chunks (c, Re) and (c, Im) 128 B apart along K; 8-row groups 4 KB apart
-                            const uint64_t ah = sdesc(aHi + c * 256, 128, kGroupBytes);
-                            const uint64_t al = sdesc(aLo + c * 256, 128, kGroupBytes);
+                            // A: chunks (c, Re), (c, Im) are the 32 bytes at 32 (c % 4) of the 128-byte
+                            // rows of chunk half c / 4; 8-row atoms 2 KB apart (hi and lo interleaved)
+                            const uint32_t ao = (uint32_t)(c >> 2) * kHalfBytes + (uint32_t)(c & 3) * 32u;
+                            const uint64_t ah = sdesc_sw128(aHi + ao, 2048);
+                            const uint64_t al = sdesc_sw128(aLo + ao, 2048);
 #pragma unroll
                             for (int acc = 0; acc < 2; ++acc) {
                                 // window rows c*3 + {0: Re u, 1: Im u, 2: -Re u}; Re uses (Re u, Im u),
@@ -355,15 +368,16 @@ struct StoreScale {
     int64_t first;     // first flat index of this scale in the launch
     int64_t count;     // elements of this scale
     int64_t level_off; // 2 N (lev - 1): level lev in the SIDWT tree
-    int32_t Kp, nv, row, k0;  // row = Rs * Lr samples per (band, hi/lo, variant, chunk)
+    int32_t Kp, nv, Lr, Rs, k0;  // Rs reshaped rows of Lr polyphase samples
 };
 struct StoreScales {
     StoreScale s[16];
     int n;
 };
 
-// Stored operand of one signal: element [(2 b + h)][v][2 c + plane][s] =
-// hi or lo part of plane(w_{v,b}[(k0 + c + 8 s) mod K']), plane 0 Re, 1 Im.
+// Stored operand of one signal: element [b nv + v][h][row][blk][2 c + plane][e]
+// = hi (h = 0) or lo part of plane(w_{v,b}[(k0 + c + 8 s) mod K']), plane 0
+// Re, 1 Im, at polyphase sample s = row Lr + 8 blk + e.
 __global__ void pack_stored_kernel(const float2 *__restrict__ tree, int64_t N, StoreScales sc, int64_t total,
                                    __nv_bfloat16 *__restrict__ out) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -371,14 +385,19 @@ __global__ void pack_stored_kernel(const float2 *__restrict__ tree, int64_t N, S
         while (k + 1 < sc.n && e >= sc.s[k + 1].first) ++k;
         const StoreScale &z = sc.s[k];
         const int64_t local = e - z.first;
-        const int64_t s = local % z.row;
-        int64_t rest = local / z.row;
-        const int ch = (int)(rest % 16);
-        rest /= 16;
-        const int v = (int)(rest % z.nv);
-        const int bh = (int)(rest / z.nv);
-        const int h = bh & 1, b = bh >> 1;
+        const int ee = (int)(local & 7);
+        const int ch = (int)((local >> 3) & 15);
+        const int nblk = z.Lr >> 3;
+        int64_t rest = local >> 7;
+        const int blk = (int)(rest % nblk);
+        rest /= nblk;
+        const int64_t row = rest % z.Rs;
+        rest /= z.Rs;
+        const int h = (int)(rest & 1);
+        const int vb = (int)(rest >> 1);
+        const int b = vb / z.nv, v = vb - b * z.nv;
         const int c = ch >> 1, plane = ch & 1;
+        const int64_t s = row * z.Lr + 8 * blk + ee;
         int64_t idx = ((int64_t)z.k0 + c + 8 * s) % z.Kp;
         if (idx < 0) idx += z.Kp;
         const float2 x = tree[z.level_off + (int64_t)b * N + (int64_t)v * z.Kp + idx];
@@ -484,7 +503,8 @@ sidwt_status pack_stored(const float2 *tree, int64_t N, int J, const int64_t *a_
         z.level_off = 2 * N * (int64_t)(sh.lev - 1);
         z.Kp = (int32_t)sh.Kp;
         z.nv = sh.nv;
-        z.row = sh.Rs * sh.Lr;
+        z.Lr = sh.Lr;
+        z.Rs = sh.Rs;
         z.k0 = sh.k0;
         total += sh.a_elems;
     }
@@ -499,13 +519,15 @@ size_t map_bytes() { return sizeof(CUtensorMap); }
 
 sidwt_status encode_maps(void *two_maps, const void *a_base, const void *b_base, const Shape &sh) {
     CUtensorMap *m = static_cast<CUtensorMap *>(two_maps);
-    const uint64_t lr2 = (uint64_t)sh.Lr * 2;
-    const uint64_t da[5] = {(uint64_t)sh.Lr, (uint64_t)sh.Rs, 16, (uint64_t)sh.nv, (uint64_t)(2 * sh.nb)};
-    const uint64_t sa[4] = {lr2, lr2 * sh.Rs, lr2 * sh.Rs * 16, lr2 * sh.Rs * 16 * sh.nv};
-    const uint32_t ba[5] = {8, 8, 16, 1, 2};
+    // dims: 128 elements of a (row, block) record, Lr / 8 blocks, Rs rows,
+    // hi/lo, band x variant; a box is one chunk half of 8 rows, hi and lo
+    const uint64_t blk = (uint64_t)sh.Lr / 8;
+    const uint64_t da[5] = {128, blk, (uint64_t)sh.Rs, 2, (uint64_t)sh.nv * sh.nb};
+    const uint64_t sa[4] = {256, 256 * blk, 256 * blk * sh.Rs, 512 * blk * sh.Rs};
+    const uint32_t ba[5] = {64, 1, 8, 2, 1};
     (void)b_base;  // the received windows are expanded in shared memory by the kernel
     std::memset(&m[1], 0, sizeof(CUtensorMap));
-    return encode_nd(&m[0], const_cast<void *>(a_base), 5, da, sa, ba);
+    return encode_nd(&m[0], const_cast<void *>(a_base), 5, da, sa, ba, CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
 

@@ -84,6 +84,13 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr, uint32_t sbo) {
     return sdesc(addr, 16, sbo) | (4ull << 61);
 }
+// K-major operand in the 128-byte swizzled layout (rows of 128 B, 8-row
+// atoms of 1 KB sbo apart; layout type 2).  addr steps through an atom's
+// 128-byte K extent in 32-byte units (one K = 16 step of bf16); the atoms
+// themselves sit on 1024-byte boundaries.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr, uint32_t sbo) {
+    return sdesc(addr, 16, sbo) | (2ull << 61);
+}
 
 // Instruction descriptor, kind::f16: D f32, A and B bf16, A K-major, B MN-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
