@@ -314,8 +314,8 @@ sidwt_status sidwt_ragged_reset_references(sidwt_ragged *r);
  * signal also keeps, for every scale whose band K' is at least 64 samples,
  * its variants packed for the tensor cores (bf16 hi and lo, about 32 N bytes
  * per such scale), and correlations run those scales as GEMMs on tcgen05:
- * rows are the stored variants advanced by multiples of S (S = 64, 128 or 256
- * chosen per scale), columns the received band advanced by 0..S-1, so that
+ * rows are the stored variants advanced by multiples of S (S = 64, 128, 192
+ * or 256 chosen per scale), columns the received band advanced by 0..S-1, so that
  * one received pulse fills whole tiles (eq. 20 / 20a unchanged; bands that
  * are not a multiple of 64 use the equivalent zero-padded linear form).
  * Shorter bands, and signals stored before the switch, stay on the CUDA

@@ -21,9 +21,9 @@
 //     samples together (256 bytes), so that two 5-D TMA boxes {64 elements,
 //     1 block, 8 rows, hi+lo, 1} per 8-row group move whole 128-byte rows
 //     into the K-major A tile, in the 128-byte swizzled layout
-//     [chunk half][group][hi/lo][8 rows][128 B] (4 KB per group; with
-//     16-byte rows the copies were bound by their row count, 4096 per
-//     K-block, which set a floor under the narrower widths);
+//     [chunk half][group][hi/lo][8 rows][128 B] (4 KB per group: 512
+//     copy rows per K-block where 16-byte rows took 4096, a quarter of the
+//     L2 throughput);
 //   * received columns: the overlapping MN-major window of the batched kernel
 //     (8 shifted copies U_c[t] = u[t + c + k0], planes Re, Im, -Re), built
 //     in shared memory for each K-block by four expansion warps straight from
@@ -451,7 +451,7 @@ bool shape_with(int64_t N, int J, int j, int S, Shape *sh) {
 }
 
 // Tensor-core shape of scale j, or false when the band is too short (it
-// stays on the CUDA cores).  S (256, 128 or 64) minimises the padded MMA
+// stays on the CUDA cores).  S (256, 192, 128 or 64) minimises the padded MMA
 // work, weighted by each width's cost per padded element in the band's
 // log2 bucket (defaults, or measured by the autotuner).
 bool shape_for(int64_t N, int J, int j, Shape *sh, const TcWeights *w) {
