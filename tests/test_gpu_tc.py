@@ -148,6 +148,47 @@ def test_bf16x3_many_reference_batch_sampled(oracle):
         U.check_peak_lags(lag[b], ro[i], 3 * 2.0 ** -16, what=f"pulse {b}")
 
 
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3", "fp32"])
+def test_precision_sweep_launch_sampled(oracle, precision):
+    """The precision sweep's own launch: one correlate call of all 16384
+    pulses (N = 4096, J = 6, CDF 9/7) against one of the 64 stored
+    references; sampled pairs against the oracle, each precision at its own
+    bound (the bf16 split at u = 2^-16, 3xTF32 at u = 2^-22, FP32 within
+    1e-5 of the peak), peak lags per scale."""
+    from paper_cs_0607001_gb300 import sidwt
+    w = inputs.many_ref_batch(n_refs=64, B=16384, N=4096, J=6)
+    k = 5
+    with sidwt.Plan("cdf97", 4096, 6) as p:
+        for x in w["refs"]:
+            p.store_reference(U.to_dev_c64(x))
+        ids = torch.full((16384,), k, dtype=torch.int32, device=U.dev())
+        r = p.correlate(ids, U.to_dev_c64(w["y"]), precision=precision, want_r=True)
+        lag, mag, norm = p.peaks(16384)
+        p.check()
+        sample = np.array([0, 5, 69, 4097, 9000, 16383])
+        rs = r[torch.from_numpy(sample).to(U.dev())].cpu().numpy().astype(np.complex128)
+        lag = lag.cpu().numpy()
+        del r
+    # pulses echoing reference k peak at their delays
+    own = np.nonzero(w["ref_ids"] == k)[0]
+    assert np.mean(lag[own, 0] == w["delays"][own]) > 0.99
+    X = np.repeat(w["refs"][k:k + 1].astype(np.complex128), len(sample), axis=0)
+    Y = w["y"][sample].astype(np.complex128)
+    lo, mo, no, ro, _ = oracle.correlate_batch(2, X, Y, 6, want_r=True)
+    tree = oracle.tree_x(2, w["refs"][k].astype(np.complex128), 6)[0]
+    u = {"bf16x3": 2.0 ** -16, "tf32x3": 2.0 ** -22}.get(precision)
+    for i, b in enumerate(sample):
+        pyr, _ = oracle.pyramid_y(2, Y[i], 6)
+        for j in range(7):
+            err = np.abs(rs[i, j] - ro[i, j]).max()
+            if u is None:
+                bound = 1e-5 * np.abs(ro[i, j]).max()
+            else:
+                bound = stated_bound(tree, pyr, 4096, 6, j, 4096 >> j, u=u)
+            assert err <= bound, (precision, b, j, err, bound)
+        U.check_peak_lags(lag[b], ro[i], 3 * u if u else 1e-5, what=f"{precision} pulse {b}")
+
+
 @pytest.mark.parametrize("fname,fid", list(U.FLOAT_FILTERS.items()))
 @pytest.mark.parametrize("N,J,B,nrefs", [(1024, 4, 300, 3), (256, 2, 130, 2), (4096, 6, 40, 1), (512, 3, 257, 2)])
 def test_tf32x3_matches_oracle_within_stated_bound(oracle, fname, fid, N, J, B, nrefs):
