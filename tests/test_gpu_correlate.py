@@ -159,7 +159,8 @@ def test_empty_batch_and_argument_errors():
                         torch.zeros((1, 128), dtype=torch.complex64, device=U.dev()), precision=7)
 
 
-def test_host_entry_point_matches_device_entry_point():
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_host_entry_point_matches_device_entry_point(precision):
     w = inputs.random_batch(n_refs=2, B=64, N=1024, J=4, seed=12)
     from paper_cs_0607001_gb300 import sidwt
     with sidwt.Plan("legall53", 1024, 4) as p:
@@ -167,9 +168,9 @@ def test_host_entry_point_matches_device_entry_point():
             p.store_reference(U.to_dev_c64(x))
         ids = torch.from_numpy(w["ref_ids"].astype(np.int32))
         y = torch.from_numpy(w["y"])
-        lh, mh, nh = p.correlate_host(ids, y)  # pageable
-        lp, mp, np_ = p.correlate_host(ids.pin_memory(), y.pin_memory())  # pinned
-        p.correlate(ids.to(U.dev()), y.to(U.dev()))
+        lh, mh, nh = p.correlate_host(ids, y, precision=precision)  # pageable
+        lp, mp, np_ = p.correlate_host(ids.pin_memory(), y.pin_memory(), precision=precision)  # pinned
+        p.correlate(ids.to(U.dev()), y.to(U.dev()), precision=precision)
         ld, md, nd = p.peaks(64)
         torch.cuda.synchronize()
         for a, b in ((lh, ld), (mh, md), (nh, nd), (lp, ld)):
