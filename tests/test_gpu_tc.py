@@ -74,7 +74,8 @@ def run(fname, N, J, refs, y, ids, precision, want_r=True):
 
 
 @pytest.mark.parametrize("fname,fid", list(U.FLOAT_FILTERS.items()))
-@pytest.mark.parametrize("N,J,B,nrefs", [(1024, 4, 150, 3), (256, 2, 130, 2), (4096, 6, 40, 1), (512, 3, 129, 2)])
+@pytest.mark.parametrize("N,J,B,nrefs", [(1024, 4, 150, 3), (256, 2, 130, 2), (4096, 6, 40, 1), (512, 3, 129, 2),
+                                         (128, 1, 140, 2)])
 def test_bf16x3_matches_oracle_within_stated_bound(oracle, fname, fid, N, J, B, nrefs):
     w = U.small_batch(nrefs, B, N, J, seed=1000 + N + B + fid)
     r, lag, mag, norm = run(fname, N, J, w["refs"], w["y"], w["ref_ids"], "bf16x3")
