@@ -63,7 +63,7 @@ def test_full_depth_parseval(oracle, f, N, J):
 
 
 @pytest.mark.parametrize("f", FILTERS)
-@pytest.mark.parametrize("N,J", [(16, 1), (32, 5), (128, 3), (96, 5)])
+@pytest.mark.parametrize("N,J", [(16, 1), (32, 5), (128, 3), (96, 5), (2, 1), (128, 1)])
 def test_correlation_forms_agree_and_scale0_is_brute_force(oracle, f, N, J):
     g = np.random.default_rng(7 * N + f)
     x = signal_for(f, g, N)
