@@ -74,8 +74,12 @@ def test_correlation_forms_agree_and_scale0_is_brute_force(oracle, f, N, J):
     if f in (3, 4):
         # integer bands: the level-(j+1) form pairs integer details whose
         # scalings cancel, but the floor rounding makes the two forms differ
-        # by a rounding-sized amount
-        assert np.abs(r0 - r1).max() <= 1e-3 * scale
+        # by a rounding-sized amount.  Each rounded step moves a coefficient
+        # by less than one unit (at most four steps a level), so the forms
+        # differ by about 4 J sqrt(N) (|x| + |y|) at most; for all but the
+        # shortest signals that is well under 1e-3 |x| |y|
+        tol = 1e-3 * scale if N >= 16 else 4 * J * np.sqrt(N) * (np.linalg.norm(x) + np.linalg.norm(y))
+        assert np.abs(r0 - r1).max() <= tol
     else:
         assert np.abs(r0 - r1).max() <= 1e-12 * scale
     br = oracle.brute_xcorr(x, y)
