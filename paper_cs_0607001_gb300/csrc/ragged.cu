@@ -485,7 +485,12 @@ sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_i
     for (int64_t i = 0; i < n; ++i) {
         const rg::Item &it = L.items[(size_t)i];
         const RefInfo &ri = r->refs[(size_t)it.ref];
+        // scale J (eq. 20a) is band 0 of scale J - 1 (eq. 20) at the same level: its
+        // peak is formed by the scale J - 1 tiles before they add band 1
+        const bool mergeJ = r->prec == SIDWT_PREC_BF16X3 && it.J >= 1 && it.J < 16 && ri.tc_off[it.J] >= 0 &&
+                            ri.tc_off[it.J - 1] >= 0 && ri.tc_S[it.J] == ri.tc_S[it.J - 1];
         for (int j = 0; j <= it.J; ++j) {
+            if (j == it.J && mergeJ) continue;
             rtc::Shape sh;
             if (r->prec == SIDWT_PREC_BF16X3 && j < 16 && ri.tc_off[j] >= 0 &&
                 rtc::shape_with(it.N, it.J, j, ri.tc_S[j], &sh)) {
@@ -506,6 +511,7 @@ sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_i
                     w.k0 = (int16_t)sh.k0;
                     w.slot = it.slot + j;
                     w.u_off = it.pyr_off + 2 * (int64_t)it.N - 4 * sh.Kp;
+                    w.slot_mid = (mergeJ && j == it.J - 1) ? it.slot + it.J : -1;
                     tct.push_back({(int64_t)sh.nb * sh.nkb * sh.S, w});
                 }
                 continue;
@@ -1211,6 +1217,7 @@ sidwt_status tune_tc(sidwt_ragged *r, cudaStream_t s, std::string *report) {
                 x.k0 = (int16_t)sh.k0;
                 x.slot = 0;
                 x.u_off = 2 * N - 4 * Kp;  // level sh.lev of the synthetic pyramid
+                x.slot_mid = -1;
             }
             cudaMemcpyAsync(dt, tl.data(), (size_t)n * sizeof(rtc::TcTile), cudaMemcpyHostToDevice, s);
             cudaStreamSynchronize(s);  // the host staging buffers are reused

@@ -248,11 +248,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            int it = 0, tc = 0;
-            for (int t = blockIdx.x; t < ntiles && !sflag[0]; t += gridDim.x, ++tc) {
+            int it = 0, ec = 0;  // ec: accumulator hand-overs to the epilogue so far
+            for (int t = blockIdx.x; t < ntiles && !sflag[0]; t += gridDim.x) {
                 const TcTile w = tiles[t];
-                if (tc > 0) {
-                    if (!mbar_wait(tfree, (tc - 1) & 1)) {
+                if (ec > 0) {
+                    if (!mbar_wait(tfree, (ec - 1) & 1)) {
                         sflag[0] = 1;
                         break;
                     }
@@ -261,7 +261,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t idesc = idesc_bf16(128, w.S);
                 const uint32_t bRow = (uint32_t)(w.S + 64) * 2;
                 bool first = true;
-                for (int b = 0; b < w.nb && !sflag[0]; ++b)
+                for (int b = 0; b < w.nb && !sflag[0]; ++b) {
+                    if (b == 1 && w.slot_mid >= 0) {
+                        // band 0 alone is the coarser scale's product: hand it to the
+                        // epilogue and add band 1 once the epilogue has read it
+                        mma_commit(accf);
+                        ++ec;
+                        if (!mbar_wait(tfree, (ec - 1) & 1)) {
+                            sflag[0] = 1;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
                     for (int kb = 0; kb < w.nkb; ++kb) {
                         const int s = it & 1;
                         if (!mbar_wait(&full[s], (it >> 1) & 1)) {
@@ -296,8 +307,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ++it;
                         sflag[3] = it;
                     }
+                }
                 if (sflag[0]) break;
                 mma_commit(accf);  // arrives once every MMA of this tile has completed
+                ++ec;
             }
             sflag[2] = it;
             mma_commit(drain);  // every MMA issued by this CTA has completed
@@ -307,13 +320,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = tile rows
         const int q4 = warp & 3;
         const int m = q4 * 32 + lane;
-        int tc = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tc) {
+        int ec = 0;  // accumulator hand-overs read so far
+        bool stop = false;
+        for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x)
+          for (int pass = tiles[t].slot_mid >= 0 ? 0 : 1; pass < 2; ++pass, ++ec) {
+            // pass 0: band 0 alone (peak of slot_mid); pass 1: the whole product (slot)
             const TcTile w = tiles[t];
-            const bool ok = mbar_wait_progress(accf, tc & 1, &sflag[3]);
+            const bool ok = mbar_wait_progress(accf, ec & 1, &sflag[3]);
             tc_fence_after();
             if (!__all_sync(0xffffffffu, ok && !sflag[0])) {  // warp-uniform before the aligned TMEM loads
                 sflag[0] = 1;
+                stop = true;
                 break;
             }
             const int G = 16 * w.tile + (m >> 3);
@@ -344,8 +361,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_before();
             mbar_arrive(tfree);
-            if (valid && best) atomicMax(&keys[w.slot], best);
-        }
+            if (valid && best) atomicMax(&keys[pass ? w.slot : w.slot_mid], best);
+          }
     }
 
     tc_fence_before();

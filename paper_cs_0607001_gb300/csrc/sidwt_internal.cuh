@@ -310,6 +310,9 @@ struct TcTile {
     int16_t nb, lev, S, k0;  // k0: first contraction index (0 circular, -S zero-padded)
     int64_t slot;   // peak key of this (pair, scale)
     int64_t u_off;  // received band 0 of this scale in the pyramid buffer (band 1 follows at + Kp)
+    // peak key formed from band 0 alone before band 1 is added (scale J, whose
+    // eq. 20a product is band 0 of scale J - 1's eq. 20 product), or -1
+    int64_t slot_mid;
 };
 
 
