@@ -41,7 +41,11 @@
 // stage is full once its copies have landed and the four warps have
 // arrived).  The producer and the expansion warps run ahead into the next
 // tile; the MMA warp starts a tile once the epilogue has drained the
-// accumulators.  Every wait is bounded.
+// accumulators.  Scale J has no tiles of its own: its product (eq. 20a) is
+// band 0 of scale J - 1's (eq. 20) at the same level, so a scale J - 1 tile
+// with a slot_mid hands its accumulators to the epilogue after band 0 (peak
+// of scale J) and adds band 1 once they have been read.  Every wait is
+// bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
