@@ -62,6 +62,7 @@ struct TcArgs {
     int nlt;         // advance tiles per variant
     int nkb;         // K-blocks of 64
     int kb_per_band; // Kp / 64
+    int fold;        // 1: j = J - 1 also forms scale J (eq. 20a) from band 0 before adding band 1
     int rows_per_ref;
     const int32_t *perm;
     const int32_t *tile_ref;
@@ -80,8 +81,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *sB = base;
     unsigned char *sA = base + kBRegion;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(base + kBarOff);  // full[2], empty[2], accf
-    uint64_t *full = bar, *empty = bar + 2, *accf = bar + 4;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + kBarOff);  // full[2], empty[2], accf, tfree
+    uint64_t *full = bar, *empty = bar + 2, *accf = bar + 4, *tfree = bar + 5;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 8);
     volatile int *sflag = reinterpret_cast<volatile int *>(tmem_slot + 4);  // [0] error, [1] issued, [2] consumed
 
@@ -102,6 +103,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&empty[i], 1);
         }
         mbar_init(accf, 1);
+        mbar_init(tfree, 128);
         sflag[0] = 0;
         sflag[1] = 0;
         sflag[2] = 0;
@@ -144,6 +146,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             int consumed = 0;
             for (int kb = 0; kb < a.nkb; ++kb) {
                 const int s = kb & 1;
+                if (a.fold && kb == a.kb_per_band) {
+                    // band 0 alone is scale J's product (eq. 20a): hand it to the epilogue,
+                    // add band 1 once the epilogue has read it
+                    mma_commit(accf);
+                    if (!mbar_wait(tfree, 0)) {
+                        sflag[0] = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                }
                 if (!mbar_wait(&full[s], (kb >> 1) & 1)) {
                     sflag[0] = 1;
                     break;
@@ -177,12 +189,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_commit(accf);  // arrives once every MMA issued above has completed
         }
     } else {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
-        const bool ok = mbar_wait(accf, 0);
-        tc_fence_after();
-        if (!ok) sflag[0] = 1;
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31; with a.fold
+        // first band 0 alone (scale J = a.j + 1), then the whole product (a.j)
         const int q4 = warp & 3;
         const int m = q4 * 32 + lane;
+        for (int pass = a.fold ? 0 : 1; pass < 2; ++pass) {
+        const int jo = pass ? a.j : a.j + 1;
+        const bool ok = mbar_wait(accf, a.fold ? (uint32_t)pass : 0u);
+        tc_fence_after();
+        if (!ok) sflag[0] = 1;
         if (ok && !sflag[0]) {
             const bool valid = m < cnt;
             const int64_t b = valid ? a.perm[row0 + m] : 0;
@@ -203,10 +218,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const unsigned long long key =
                         ((unsigned long long)__float_as_uint(m2) << 32) | (unsigned long long)(0xFFFFFFFFu - D);
                     best = key > best ? key : best;
-                    if (a.R && valid) a.R[(b * (a.J + 1) + a.j) * a.N + D] = make_float2(xr, xi);
+                    if (a.R && valid) a.R[(b * (a.J + 1) + jo) * a.N + D] = make_float2(xr, xi);
                 }
             }
-            if (valid && best) atomicMax(&a.keys[b * (a.J + 1) + a.j], best);
+            if (valid && best) atomicMax(&a.keys[b * (a.J + 1) + jo], best);
+        }
+        if (pass == 0) {
+            tc_fence_before();
+            mbar_arrive(tfree);
+        }
         }
     }
 
@@ -579,6 +599,15 @@ uint32_t tc_scale_mask(const sidwt_plan *p) {
 }
 
 static int tc_ntile(int64_t Kp) { return Kp % 256 == 0 ? 256 : (Kp % 128 == 0 ? 128 : 64); }
+
+// Scale J (eq. 20a) is band 0 of scale J - 1 (eq. 20), both at level J: the
+// scale J - 1 launch forms both when both are tensor-core scales and it runs
+// the one-tile kernel (K' >= 128; K' = 64 takes the short-contraction kernel).
+static bool tc_fold_last(const sidwt_plan *p, uint32_t mask) {
+    const int J = p->J;
+    if (J < 1 || !(mask & (1u << J)) || !(mask & (1u << (J - 1)))) return false;
+    return (p->N >> J) >= 128;
+}
 static int tc_lc(int64_t Kp) { return (int)(2 * Kp + 320); }
 static int tc_rows_per_ref(const sidwt_plan *p, int j) {
     const int lev = j < p->J ? j + 1 : p->J;
@@ -647,8 +676,10 @@ sidwt_status correlate_tc(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t 
         p->tc_packed = p->nrefs;
     }
     const int64_t max_pt = (B + tc::kTM - 1) / tc::kTM + std::min<int64_t>(p->nrefs, B);
+    const bool fold = tc_fold_last(p, mask);
     for (int j = 0; j <= J; ++j) {
         if (!(mask & (1u << j))) continue;
+        if (fold && j == J) continue;  // formed by the scale J - 1 launch
         const int lev = j < J ? j + 1 : J;
         const int64_t Kp = N >> lev;
         const int nb = j < J ? 2 : 1;
@@ -682,6 +713,7 @@ sidwt_status correlate_tc(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t 
         a.nlt = (int)(Kp / a.ntile_n);
         a.nkb = (int)(Kj / 64);
         a.kb_per_band = (int)(Kp / 64);
+        a.fold = (fold && j == J - 1) ? 1 : 0;
         a.rows_per_ref = rpr;
         a.perm = p->tiles.perm;
         a.tile_ref = p->tiles.tile_ref;
@@ -693,6 +725,10 @@ sidwt_status correlate_tc(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t 
         a.err = p->err;
         // short contractions: the received tile stays resident over several variants
         const bool multi = a.nkb <= 2 && a.ntile_n <= 128;
+        if (multi && a.fold) {
+            set_error("internal: scale J folded into a short-contraction launch");
+            return SIDWT_EINVAL;
+        }
         const int64_t grid =
             max_pt * a.nlt * (multi ? (a.nv + tc::kMultiVar - 1) / tc::kMultiVar : (int64_t)a.nv);
         if (grid > 0x7fffffff) {
@@ -732,6 +768,7 @@ int tc_launch_count(const sidwt_plan *p) {
     int n = 0;
     for (int j = 0; j <= p->J; ++j)
         if (mask & (1u << j)) n += pack_refs ? 3 : 2;  // (reference pack) + received pack + correlation
+    if (tc_fold_last(p, mask)) n -= 2;                 // scale J: no received pack, no launch of its own
     if (((1u << (p->J + 1)) - 1u) & ~mask) n += 1;
     return n;
 }
