@@ -22,8 +22,12 @@
 //
 // Roles (192 threads): warp 0 issues TMA loads into a 2-stage ring, warp 1
 // allocates TMEM and issues the MMAs, warps 2-5 read the accumulators and
-// reduce the peaks.  Every wait is bounded; on a timeout the CTA records an
-// error, drains its own copies and frees TMEM.
+// reduce the peaks.  Scales J - 1 and J share level J, and scale J's product
+// (eq. 20a) is band 0 of scale J - 1's (eq. 20): with TcArgs::fold the scale
+// J - 1 launch hands its accumulators to the epilogue after band 0 (scale J's
+// peaks), waits on `tfree` until they have been read, then adds band 1.
+// Every wait is bounded; on a timeout the CTA records an error, drains its
+// own copies and frees TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
