@@ -6,7 +6,8 @@ CPU-baseline leg of ``bench.py``; the library itself never imports it.
 
 Complex vectors cross this boundary as numpy ``complex128`` arrays (interleaved
 re/im doubles).  Filter ids: 0 causal Daubechies-4 (eq. 17), 1 LeGall 5/3,
-2 CDF 9/7 (Table I), 3 reversible integer LeGall 5/3.  Sides: 0 = stored signal
+2 CDF 9/7 (Table I), 3 reversible integer LeGall 5/3, 4 integer CDF 9/7 (Table I's
+steps as dyadic fractions, rounded updates).  Sides: 0 = stored signal
 x (primal analysis), 1 = received signal y (dual analysis).
 """
 from __future__ import annotations
