@@ -216,10 +216,27 @@ sidwt_status sidwt_read_timing(sidwt_plan *p, sidwt_timing *out, int reset);
 
 /* Synchronise `stream` and report device-side errors recorded by earlier
  * calls on this plan: SIDWT_EINVAL for an out-of-range reference id,
- * SIDWT_ETIMEOUT if a tensor-core CTA gave up on one of its bounded waits
- * (its results are then incomplete); SIDWT_OK otherwise.  The record is
- * cleared. */
+ * SIDWT_ETIMEOUT if a tensor-core CTA or the pipelined received analysis
+ * gave up on one of its bounded waits (the message says which; the results
+ * are then incomplete); SIDWT_OK otherwise.  The record is cleared. */
 sidwt_status sidwt_check(sidwt_plan *p, sidwt_stream stream);
+
+/* Test hook (the paper has no counterpart): makes a bounded device wait run
+ * out on purpose, so that a caller can test its handling of SIDWT_ETIMEOUT
+ * without faulting the GPU.  Process-wide; read at each later launch of the
+ * kernels it names; what = 0 restores normal operation.
+ *   SIDWT_STALL_ANALYSIS: the pipelined received analysis (pulses that fit
+ *     its shared memory, y_dev 16-byte aligned) issues no input copy, so its
+ *     first wait gives up after 200 ms; it records the timeout (sidwt_check:
+ *     SIDWT_ETIMEOUT; sidwt_correlate_static: every peak record of the call
+ *     is lag -1, |r| 0, norm 0) and returns with nothing in flight.
+ *   SIDWT_STALL_TC_SELFTEST: sidwt_tc_selftest issues neither its MMA nor
+ *     the commit, so its wait gives up after 200 ms and sets bit 4 of its err
+ *     word; the kernel still releases its tensor memory.
+ * EINVAL for unknown bits. */
+#define SIDWT_STALL_ANALYSIS 1u
+#define SIDWT_STALL_TC_SELFTEST 2u
+sidwt_status sidwt_debug_stall(uint32_t what);
 
 /* ---------------------------------------------------------------------------
  * Ragged batches: pulses of uneven length N, depth J and filter, each against
@@ -473,9 +490,15 @@ sidwt_status sidwt_tc_selftest(float *out_dev, int32_t *err_dev, sidwt_stream st
  * (roughly 16 N (B + J) bytes, twice that for the integer filter) returns
  * SIDWT_EINVAL with the size in the message; 1 <= B <= 65535.  The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Every call reuses the
- * same array, so calls that overlap on the GPU (other streams, other host
- * threads) race and corrupt each other: serialise them on one stream. */
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process: after cudaDeviceReset (or anything else that
+ * replaces the device's primary context) this entry point must not be called
+ * again on that device.  Every call reuses the same array, so calls that
+ * overlap on the GPU (other streams, other host threads) race and corrupt
+ * each other: serialise them on one stream.  The call's own device error
+ * record lives in the array too: if the received analysis gave up on its
+ * bounded wait for an input copy, every peak record of the call is written as
+ * lag -1, |r| 0, norm 0 (see sidwt_debug_stall). */
 sidwt_status sidwt_correlate_static(sidwt_filter f, int64_t N, int J, const void *x_dev, const void *y_dev,
                                     int64_t B, int32_t *lag_dev, float *mag_dev, double *norm_dev,
                                     sidwt_stream stream);

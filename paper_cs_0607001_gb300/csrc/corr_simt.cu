@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(1024) group_kernel(const int32_t *__restrict__
         const int r = ref_ids[b];
         saved[b] = r;
         if (r >= 0 && r < nrefs) atomicAdd(&cursor[r], 1);
-        else atomicOr(err, 1);
+        else atomicOr(err, kErrBadRefId);
     }
     __syncthreads();
     for (int base = 0; base < nrefs; base += blockDim.x) {
@@ -238,7 +238,8 @@ __global__ void __launch_bounds__(1024) group_kernel(const int32_t *__restrict__
 __global__ void finalize_kernel(unsigned long long *__restrict__ keys, const int32_t *__restrict__ ids,
                                 int nrefs, const double *__restrict__ xen, int64_t xen_len,
                                 const double *__restrict__ yen, int64_t B, int J, int32_t *__restrict__ lag,
-                                float *__restrict__ mag, double *__restrict__ norm) {
+                                float *__restrict__ mag, double *__restrict__ norm,
+                                const int32_t *__restrict__ fail) {
     pdl_wait();  // the correlation kernel's keys
     pdl_release();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -248,7 +249,7 @@ __global__ void finalize_kernel(unsigned long long *__restrict__ keys, const int
     const int r = ids[b];
     const unsigned long long k = keys[i];
     keys[i] = 0ull;
-    if (r < 0 || r >= nrefs || k == 0ull) {
+    if (r < 0 || r >= nrefs || k == 0ull || (fail && *fail)) {
         lag[i] = -1;
         mag[i] = 0.f;
         norm[i] = 0.0;
@@ -307,12 +308,13 @@ sidwt_status correlate_simt(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "FP32 correlation launch");
 }
 
-sidwt_status finalize_peaks(sidwt_plan *p, int64_t B, cudaStream_t s) {
+sidwt_status finalize_peaks(sidwt_plan *p, int64_t B, cudaStream_t s, bool invalidate_on_error) {
     const int64_t n = B * (p->J + 1);
     if (n == 0) return SIDWT_OK;
     cudaError_t e = launch_dependent(finalize_kernel, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, p->keys,
                                      (const int32_t *)p->ref_ids, p->nrefs, (const double *)p->xen, p->xen_len,
-                                     (const double *)p->yen, B, p->J, p->lag, p->mag, p->norm);
+                                     (const double *)p->yen, B, p->J, p->lag, p->mag, p->norm,
+                                     (const int32_t *)(invalidate_on_error ? p->err : nullptr));
     if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "peak epilogue launch");
 }

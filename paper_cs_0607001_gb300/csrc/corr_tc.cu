@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0 && sflag[0]) {
         // let this CTA's own copies land before its shared memory is released
         for (int kb = sflag[2]; kb < sflag[1]; ++kb) mbar_wait(&full[kb & 1], (kb >> 1) & 1);
-        atomicOr(a.err, 2);
+        atomicOr(a.err, kErrTcWait);
     }
     __syncthreads();
     if (warp == 1) tmem_dealloc(tmem, kTmemCols);
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // let this CTA's own copies land before its shared memory is released
         if (sflag[3]) mbar_wait(fullA, 0);
         for (int k = sflag[2]; k < sflag[1]; ++k) mbar_wait(&fullB[k % kMStagesB], (k / kMStagesB) & 1);
-        atomicOr(a.err, 2);
+        atomicOr(a.err, kErrTcWait);
     }
     __syncthreads();
     if (warp == 1) tmem_dealloc(tmem, kTmemCols);
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(256) pack_rx_kernel(const float2 *__restrict__
 // ---------------------------------------------------------------------------
 constexpr int kSelftestSmem = 64 * 1024;
 
-__global__ void __launch_bounds__(128, 1) tc_selftest_kernel(float *out, int32_t *err) {
+__global__ void __launch_bounds__(128, 1) tc_selftest_kernel(float *out, int32_t *err, int stall) {
     extern __shared__ __align__(1024) unsigned char sm[];  // 64 KB: every reading of the strides stays inside
     __shared__ uint64_t bar;
     __shared__ uint32_t slot;
@@ -564,7 +564,10 @@ __global__ void __launch_bounds__(128, 1) tc_selftest_kernel(float *out, int32_t
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = slot;
-    if (threadIdx.x == 0) {
+    // stall (test hook, sidwt_debug_stall): neither the MMA nor its commit is
+    // issued, so the wait below runs out with nothing in flight, and TMEM is
+    // still released at the end
+    if (threadIdx.x == 0 && !stall) {
         const uint64_t ad = sdesc(saddr(sa), 2048, 128);
         const uint64_t bd = sdesc(saddr(sb + 640), 640, 16);  // planes 1 and 2
         mma_bf16(tmem, ad, bd, idesc_bf16(128, 64), 0u);
@@ -572,7 +575,7 @@ __global__ void __launch_bounds__(128, 1) tc_selftest_kernel(float *out, int32_t
     }
     const bool ok = mbar_wait(&bar, 0);
     tc_fence_after();
-    if (!ok && threadIdx.x == 0) atomicOr(err, 4);
+    if (!ok && threadIdx.x == 0) atomicOr(err, kErrSelftestWait);
     if (ok) {
         const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
         for (int c0 = 0; c0 < 64; c0 += 32) {
@@ -787,7 +790,9 @@ extern "C" sidwt_status sidwt_tc_selftest(float *out_dev, int32_t *err_dev, sidw
     }
     sidwt_status st = prepare_kernels();
     if (st) return st;
-    tc::tc_selftest_kernel<<<1, 128, tc::kSelftestSmem, reinterpret_cast<cudaStream_t>(stream)>>>(out_dev, err_dev);
+    const int stall = (debug_stall_flags() & SIDWT_STALL_TC_SELFTEST) ? 1 : 0;
+    tc::tc_selftest_kernel<<<1, 128, tc::kSelftestSmem, reinterpret_cast<cudaStream_t>(stream)>>>(out_dev, err_dev,
+                                                                                                 stall);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "self-test launch");
 }

@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     if (threadIdx.x == 0 && sflag[0]) {
         for (int kb = sflag[2]; kb < sflag[1]; ++kb) mbar_wait(&full[kb & 1], (kb >> 1) & 1);
-        atomicOr(a.err, 2);
+        atomicOr(a.err, kErrTcWait);
     }
     __syncthreads();
     if (warp == 1) tmem_dealloc(tmem, kTmemCols);

@@ -574,7 +574,8 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
                                                                        int64_t B, float2 *__restrict__ pyr_f,
                                                                        int2 *__restrict__ pyr_i, int64_t pyr_elems,
                                                                        double *__restrict__ yen, LiftCoef c,
-                                                                       int32_t *__restrict__ err, int nbuf) {
+                                                                       int32_t *__restrict__ err, int nbuf,
+                                                                       int stall) {
     constexpr bool INT = is_int_filter(F);
     constexpr int IN_BYTES = INT ? 4 : 8;
     extern __shared__ __align__(16) unsigned char smraw[];  // 16-byte aligned: enough for the bulk copies
@@ -599,16 +600,18 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
         sfail = 0;
     }
     __syncthreads();
-    if (tid == 0) pipe_load(buf0, y + (int64_t)blockIdx.x * bytes, bytes, &bar[0]);
+    // stall (test hook, sidwt_debug_stall): no copy is issued, so the first
+    // wait runs out and the CTA records the timeout with nothing in flight
+    if (tid == 0 && !stall) pipe_load(buf0, y + (int64_t)blockIdx.x * bytes, bytes, &bar[0]);
     int i = 0;
-    int64_t issued = 1, landed = 0;  // copies issued / waited for (thread 0's bookkeeping)
+    int64_t issued = stall ? 0 : 1, landed = 0;  // copies issued / waited for (thread 0's bookkeeping)
     for (int64_t b = blockIdx.x; b < B; b += G, ++i) {
         // two buffers: pulse i in buffer i % 2, the next one loading meanwhile;
         // one buffer: pulse i loads once pulse i - 1 is done (other CTAs on the
         // SM overlap it)
         const int s = nbuf == 2 ? (i & 1) : 0;
         unsigned char *const cur = s ? buf1 : buf0;
-        if (tid == 0) {
+        if (tid == 0 && !stall) {
             // the buffer written next held a finished pulse, whose accesses ended at the last barrier
             if (nbuf == 2 && b + G < B) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -752,7 +755,7 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
         // let this CTA's own copies land before its shared memory is released
         for (int64_t k = landed; k < issued; ++k)
             pipe_wait(&bar[nbuf == 2 ? (k & 1) : 0], (uint32_t)(nbuf == 2 ? ((k >> 1) & 1) : (k & 1)));
-        atomicOr(err, 2);
+        atomicOr(err, kErrAnalysisWait);
     }
 }
 
@@ -971,26 +974,27 @@ sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStre
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int per_sm = std::max(1, std::min(2048 / kPipeThreads, (int)((size_t)(228 * 1024) / (pipe_smem + 9 * 1024))));
         const int64_t grid = std::min<int64_t>(B, (int64_t)sms * per_sm);
+        const int stall = (debug_stall_flags() & SIDWT_STALL_ANALYSIS) ? 1 : 0;
         switch (p->filter) {
         case SIDWT_D4:
             analyze_pipe_kernel<SIDWT_D4, float2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
-                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf);
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf, stall);
             break;
         case SIDWT_LEGALL53:
             analyze_pipe_kernel<SIDWT_LEGALL53, float2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
-                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf);
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf, stall);
             break;
         case SIDWT_CDF97:
             analyze_pipe_kernel<SIDWT_CDF97, float2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
-                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf);
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf, stall);
             break;
         case SIDWT_CDF97_INT:
             analyze_pipe_kernel<SIDWT_CDF97_INT, int2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
-                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf);
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf, stall);
             break;
         default:
             analyze_pipe_kernel<SIDWT_LEGALL53_INT, int2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
-                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf);
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf, stall);
             break;
         }
         e = cudaGetLastError();

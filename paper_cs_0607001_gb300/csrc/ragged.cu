@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(256) corr_latency_kernel(const float2 *__restr
     const int ref = ref_ids[b];
     if (blockIdx.x == 0 && threadIdx.x == 0) {  // the ids the peak epilogue reads, and the error record
         saved[b] = ref;
-        if (ref < 0 || ref >= nrefs) atomicOr(err, 1);
+        if (ref < 0 || ref >= nrefs) atomicOr(err, kErrBadRefId);
     }
     if (ref < 0 || ref >= nrefs) return;  // invalid pulse: its keys stay 0 (lag -1)
     const int task = blockIdx.x;
@@ -1443,7 +1443,7 @@ sidwt_status sidwt_ragged_check(sidwt_ragged *r, sidwt_stream stream) {
     if (e == cudaSuccess) e = cudaMemcpy(&h, r->err, sizeof(h), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(r->err, 0, sizeof(int32_t));
     if (e != cudaSuccess) return cuda_fail(e, "ragged check");
-    if (h & 2) {
+    if (h & kErrTcWait) {
         set_error("a tensor-core CTA gave up on a bounded wait; results are incomplete");
         return SIDWT_ETIMEOUT;
     }

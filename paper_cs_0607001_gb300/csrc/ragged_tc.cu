@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0 && sflag[0]) {
         // let this CTA's own copies land before its shared memory is released
         for (int k = sflag[2]; k < sflag[1]; ++k) mbar_wait(&full[k & 1], (k >> 1) & 1);
-        atomicOr(err, 2);
+        atomicOr(err, kErrTcWait);
     }
     __syncthreads();
     if (warp == 1) tmem_dealloc(tmem, kTmemCols);

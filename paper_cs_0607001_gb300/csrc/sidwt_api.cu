@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <atomic>
 #include <new>
 #include <string>
 
@@ -17,6 +18,10 @@ namespace sidwt {
 static thread_local std::string g_last_error;
 
 void set_error(const std::string &msg) { g_last_error = msg; }
+
+static std::atomic<uint32_t> g_debug_stall{0};
+
+uint32_t debug_stall_flags() { return g_debug_stall.load(std::memory_order_relaxed); }
 
 sidwt_status cuda_fail(cudaError_t e, const char *what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
@@ -211,6 +216,15 @@ extern "C" {
 const char *sidwt_version(void) { return "libsidwt 0.1 sm_103a"; }
 
 const char *sidwt_last_error(void) { return g_last_error.c_str(); }
+
+sidwt_status sidwt_debug_stall(uint32_t what) {
+    if (what & ~(SIDWT_STALL_ANALYSIS | SIDWT_STALL_TC_SELFTEST)) {
+        set_error("sidwt_debug_stall: unknown flag");
+        return SIDWT_EINVAL;
+    }
+    g_debug_stall.store(what, std::memory_order_relaxed);
+    return SIDWT_OK;
+}
 
 sidwt_status sidwt_plan_create(sidwt_filter f, int64_t N, int J, sidwt_plan **out) {
     if (!out) {
@@ -599,8 +613,12 @@ sidwt_status sidwt_check(sidwt_plan *p, sidwt_stream stream) {
     if (h) {
         cudaMemsetAsync(p->err, 0, sizeof(int32_t), s);
         cudaStreamSynchronize(s);
-        if (h & 2) {
+        if (h & kErrTcWait) {
             set_error("a tensor-core correlation CTA gave up on a bounded wait; its results are incomplete");
+            return SIDWT_ETIMEOUT;
+        }
+        if (h & kErrAnalysisWait) {
+            set_error("the received analysis gave up waiting for an input copy; the pyramid and the peaks are incomplete");
             return SIDWT_ETIMEOUT;
         }
         set_error("a correlate call received a reference id outside [0, num_refs)");

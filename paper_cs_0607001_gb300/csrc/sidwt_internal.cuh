@@ -230,6 +230,15 @@ sidwt_status check_plan_pulses(sidwt_plan *p, const void *y_dev, int64_t B);
 void set_error(const std::string &msg);
 sidwt_status cuda_fail(cudaError_t e, const char *what);
 
+// bits of a plan's device error record
+constexpr int32_t kErrBadRefId = 1;       // a pulse named a reference outside [0, num_refs)
+constexpr int32_t kErrTcWait = 2;         // a tensor-core correlation CTA gave up on a bounded wait
+constexpr int32_t kErrSelftestWait = 4;   // sidwt_tc_selftest's wait for its MMA gave up
+constexpr int32_t kErrAnalysisWait = 8;   // the pipelined received analysis gave up waiting for an input copy
+
+// sidwt_debug_stall's flags, read at each launch of a kernel they apply to
+uint32_t debug_stall_flags();
+
 // ---- lifting.cu ----
 // SIDWT tree of one stored pulse (x_dev: complex64[N] or int16x2[N]) into
 // reference slot ref of the plan, plus its energies.
@@ -271,7 +280,10 @@ uint32_t tc_scale_mask(const sidwt_plan *p);
 int tc_group_tile();
 int tc_launch_count(const sidwt_plan *p);
 void free_tc(sidwt_plan *p);
-sidwt_status finalize_peaks(sidwt_plan *p, int64_t B, cudaStream_t s);
+// Peak records from the keys.  With invalidate_on_error, every record of the
+// batch is written as no peak (lag -1, |r| 0, norm 0) if the plan's error
+// record is set when the epilogue runs (callers that have no sidwt_check).
+sidwt_status finalize_peaks(sidwt_plan *p, int64_t B, cudaStream_t s, bool invalidate_on_error = false);
 // Copy the last batch's n peak entries to the caller's buffers (any may be null) in one launch.
 sidwt_status copy_peaks(const sidwt_plan *p, int64_t n, int32_t *lag, float *mag, double *norm, cudaStream_t s);
 

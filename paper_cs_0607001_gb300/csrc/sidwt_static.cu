@@ -24,7 +24,9 @@ void *g_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  The symbol's
 // host-side name is only a stand-in, so the address is looked up once per
-// device (with that device current) and cached.
+// device (with that device current) and cached.  A device reset
+// (cudaDeviceReset) or a new primary context leaves the cached address stale:
+// calls after one would write to memory that no longer exists.
 sidwt_status scratch_address(unsigned char **out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -119,6 +121,7 @@ extern "C" sidwt_status sidwt_correlate_static(sidwt_filter f, int64_t N, int J,
     }
     sidwt_status st = prepare_kernels();
     if (st) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     unsigned char *base = nullptr;
     st = scratch_address(&base);
     if (st) return st;
@@ -130,7 +133,6 @@ extern "C" sidwt_status sidwt_correlate_static(sidwt_filter f, int64_t N, int J,
     p.mag = mag_dev;
     p.norm = norm_dev;
     p.last_B = B;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // the array keeps the previous call's contents: zero what must start at zero
     cudaError_t e = cudaMemsetAsync(ids_in, 0, (size_t)B * sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p.keys, 0, (size_t)B * (J + 1) * sizeof(unsigned long long), s);
@@ -140,5 +142,7 @@ extern "C" sidwt_status sidwt_correlate_static(sidwt_filter f, int64_t N, int J,
     if ((st = group_pulses(&p, ids_in, B, simt_tile_pulses(), s))) return st;
     if ((st = analyze_batch(&p, y_dev, B, s))) return st;
     if ((st = correlate_simt(&p, B, nullptr, s))) return st;
-    return finalize_peaks(&p, B, s);
+    // no sidwt_check reaches this scratch: a recorded error (the analysis gave
+    // up on a bounded wait) turns every record of the call into "no peak"
+    return finalize_peaks(&p, B, s, true);
 }

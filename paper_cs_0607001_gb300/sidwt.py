@@ -88,6 +88,7 @@ def lib():
     L.sidwt_read_timing.argtypes = [_vp, ctypes.POINTER(Timing), ctypes.c_int]
     L.sidwt_correlate_static.argtypes = [ctypes.c_int, _i64, ctypes.c_int, _vp, _vp, _i64, _vp, _vp, _vp, _vp]
     L.sidwt_tc_selftest.argtypes = [_vp, _vp, _vp]
+    L.sidwt_debug_stall.argtypes = [ctypes.c_uint32]
     L.sidwt_synthesize.argtypes = [ctypes.c_int, _i64, _i64, _vp, _vp, _i64, _vp, _vp]
     L.sidwt_correlate_c2f.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp]
     L.sidwt_plan_set_cdf97_t.argtypes = [_vp, ctypes.c_double]
@@ -123,7 +124,7 @@ def lib():
     for name in ("sidwt_plan_create", "sidwt_plan_destroy", "sidwt_plan_reserve", "sidwt_store_reference",
                  "sidwt_reference_tree", "sidwt_analyze", "sidwt_correlate", "sidwt_peaks",
                  "sidwt_correlate_host", "sidwt_check", "sidwt_reset_references", "sidwt_set_timing",
-                 "sidwt_read_timing", "sidwt_correlate_static", "sidwt_tc_selftest", "sidwt_ragged_create",
+                 "sidwt_read_timing", "sidwt_correlate_static", "sidwt_tc_selftest", "sidwt_debug_stall", "sidwt_ragged_create",
                  "sidwt_ragged_destroy", "sidwt_ragged_reserve", "sidwt_ragged_store_reference",
                  "sidwt_ragged_correlate", "sidwt_ragged_graph_create", "sidwt_ragged_graph_launch",
                  "sidwt_ragged_peaks", "sidwt_ragged_autotune", "sidwt_ragged_tuning", "sidwt_ragged_set_timing",
@@ -537,6 +538,16 @@ def tc_selftest(stream=None):
     err = torch.zeros(1, dtype=torch.int32, device=dev)
     _raise(lib().sidwt_tc_selftest(_ptr(out), _ptr(err), _stream(stream)))
     return out, err
+
+
+STALL_ANALYSIS = 1      # the pipelined received analysis issues no input copy
+STALL_TC_SELFTEST = 2   # sidwt_tc_selftest issues no MMA
+
+
+def debug_stall(what: int):
+    """Test hook (sidwt_debug_stall): make the named bounded device waits run
+    out on purpose (0 restores normal operation).  Process-wide."""
+    _raise(lib().sidwt_debug_stall(int(what)))
 
 
 def level_slices(N: int, J: int, l: int) -> tuple[slice, slice]:

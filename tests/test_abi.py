@@ -65,3 +65,12 @@ def test_binding_refuses_to_run_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(build, "LIB", tmp_path / "missing.so")
     with pytest.raises(RuntimeError, match="not built"):
         sidwt.lib()
+
+
+def test_debug_stall_takes_only_known_flags(lib):
+    """The test hook that makes bounded device waits run out is host state
+    only: unknown bits are rejected, 0 restores normal operation."""
+    assert lib.sidwt_debug_stall(4) == 1
+    assert b"unknown flag" in lib.sidwt_last_error()
+    assert lib.sidwt_debug_stall(3) == 0
+    assert lib.sidwt_debug_stall(0) == 0
