@@ -284,6 +284,17 @@ sidwt_status sidwt_ragged_correlate(sidwt_ragged *r, int64_t n_items, const int3
                                     const int64_t *y_offsets_host, const void *y_dev, int64_t y_elems,
                                     sidwt_stream stream);
 
+/* sidwt_ragged_correlate that also writes the correlation at every lag and
+ * every scale, r_j[D] for D = 0..N_i-1 (eq. 20 for j < J_i, eq. 20a for
+ * j = J_i), of every item: item i's rows start at complex64 element
+ * sum_{i' < i} (J_i' + 1) N_i' of r_dev, scale j's row at + j N_i.  r_dev
+ * (caller-owned, 8-byte aligned) must hold r_elems >= that sum over the
+ * batch, else SIDWT_EINVAL; r_dev = NULL is sidwt_ragged_correlate.  The
+ * writes are scattered (meant for checking, not for the bulk path). */
+sidwt_status sidwt_ragged_correlate_r(sidwt_ragged *r, int64_t n_items, const int32_t *ref_ids_host,
+                                      const int64_t *y_offsets_host, const void *y_dev, int64_t y_elems, void *r_dev,
+                                      int64_t r_elems, sidwt_stream stream);
+
 /* Build and instantiate a CUDA graph of the whole batch (lifting, the
  * persistent correlation, peaks) for this item layout and pulse buffer; the
  * layout is copied to device memory owned by the graph.  Replay with

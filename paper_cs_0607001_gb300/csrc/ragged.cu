@@ -39,6 +39,7 @@ struct Item {
     int64_t xen_off;   // stored energies start
     int64_t slot;      // first of the J+1 peak slots (and received energies)
     int32_t N, J, ref, pad;
+    int64_t r_off;     // complex64 offset of this pulse's J+1 rows of N lags in the optional r output
 };
 
 struct Work {
@@ -129,7 +130,7 @@ __device__ __forceinline__ void large_tile(const Item &it, const Work &wk, int l
             const uint32_t D = ((uint32_t)q << lev) + (uint32_t)v;
             const unsigned long long k = peak_key(acc[l], D);
             best = k > best ? k : best;
-            if (R) R[(it.slot + wk.j) * (int64_t)N + D] = acc[l];
+            if (R) R[it.r_off + (int64_t)wk.j * N + D] = acc[l];
         }
     }
     best = block_max_key(best, red);
@@ -171,7 +172,7 @@ __device__ __forceinline__ void small_tile(const Item &it, const Work &wk, int l
         }
         const uint32_t D = ((uint32_t)q << lev) + (uint32_t)(wk.v0 + vi);
         best = peak_key(acc, D);
-        if (R) R[(it.slot + wk.j) * (int64_t)N + D] = acc;
+        if (R) R[it.r_off + (int64_t)wk.j * N + D] = acc;
     }
     best = block_max_key(best, red);
     if (threadIdx.x == 0 && best) atomicMax(&keys[it.slot + wk.j], best);
@@ -238,7 +239,7 @@ __global__ void plan_items_kernel(const int32_t *__restrict__ ref_ids, int B, in
     const int r = ref_ids[b];
     const bool ok = r >= 0 && r < nrefs;
     items[b] = Item{(int64_t)b * pyr_elems, ok ? (int64_t)r * tree_elems : 0, ok ? (int64_t)r * xen_len : 0,
-                    (int64_t)b * (J + 1), ok ? N : 0, J, r, 0};
+                    (int64_t)b * (J + 1), ok ? N : 0, J, r, 0, (int64_t)b * (J + 1) * N};
 }
 
 // Latency path for a few short pulses of a plan: every (pulse, scale,
@@ -357,6 +358,7 @@ struct RaggedLayout {  // everything a batch needs on the device, built on the h
     std::vector<int64_t> recv_a_off;
     std::vector<unsigned char> maps;
     int64_t pyr_elems = 0, slots = 0;
+    int64_t r_elems = 0;  // complex64 elements of the optional r output: sum of (J_i + 1) N_i
     int64_t maxN[2][3] = {{0, 0, 0}, {0, 0, 0}};
     int maxJ_long[3] = {0, 0, 0};
 };
@@ -470,6 +472,8 @@ sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_i
         it.J = ri.J;
         it.ref = rid;
         it.pad = 0;
+        it.r_off = L.r_elems;
+        L.r_elems += (int64_t)(ri.J + 1) * ri.N;
         RaggedLift lf{y_off[i], L.pyr_elems, L.slots, (int32_t)ri.N, ri.J};
         const int path = ri.N <= smem_max ? 0 : 1;
         L.lift[path][ri.filter].push_back(lf);
@@ -512,6 +516,8 @@ sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_i
                     w.slot = it.slot + j;
                     w.u_off = it.pyr_off + 2 * (int64_t)it.N - 4 * sh.Kp;
                     w.slot_mid = (mergeJ && j == it.J - 1) ? it.slot + it.J : -1;
+                    w.r_at = it.r_off + (int64_t)j * it.N;
+                    w.r_mid = it.r_off + (int64_t)it.J * it.N;
                     tct.push_back({(int64_t)sh.nb * sh.nkb * sh.S, w});
                 }
                 continue;
@@ -678,7 +684,7 @@ sidwt_status ensure_workspace(sidwt_ragged *r, const RaggedLayout &L) {
 
 // The launches of one batch (all capturable; events only outside capture).
 sidwt_status enqueue(sidwt_ragged *r, const DevLayout &d, int64_t slots, int64_t nitems, const float2 *y, cudaStream_t s,
-                     int *launches) {
+                     int *launches, float2 *R = nullptr) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cap);
     const bool timed = r->timing && cap == cudaStreamCaptureStatusNone;
@@ -698,12 +704,12 @@ sidwt_status enqueue(sidwt_ragged *r, const DevLayout &d, int64_t slots, int64_t
     if (e != cudaSuccess) return cuda_fail(e, "ragged memset");
     if (timed) cudaEventRecord(ev[1], s);
     if (d.n_tc_tiles > 0) {
-        if ((st = rtc::launch_corr(d.maps, d.tc_tiles, d.n_tc_tiles, r->pyr, r->keys, r->err, r->sms, s))) return st;
+        if ((st = rtc::launch_corr(d.maps, d.tc_tiles, d.n_tc_tiles, r->pyr, r->keys, r->err, r->sms, s, R))) return st;
         nl += 1;
     }
     if (d.nwork > 0) {
         rg::corr_ragged_kernel<<<r->sms * 2, rg::kT, 0, s>>>(d.items, d.work, d.nwork, r->counter, r->tree, r->pyr,
-                                                              r->keys, nullptr);
+                                                              r->keys, R);
         ++nl;
     }
     if (timed) cudaEventRecord(ev[2], s);
@@ -1028,25 +1034,37 @@ sidwt_status sidwt_ragged_store_reference(sidwt_ragged *r, sidwt_filter f, int64
     return SIDWT_OK;
 }
 
-sidwt_status sidwt_ragged_correlate(sidwt_ragged *r, int64_t n_items, const int32_t *ref_ids_host,
-                                    const int64_t *y_offsets_host, const void *y_dev, int64_t y_elems,
-                                    sidwt_stream stream) {
+sidwt_status sidwt_ragged_correlate_r(sidwt_ragged *r, int64_t n_items, const int32_t *ref_ids_host,
+                                      const int64_t *y_offsets_host, const void *y_dev, int64_t y_elems, void *r_dev,
+                                      int64_t r_elems, sidwt_stream stream) {
     if (!r || n_items < 0 || (n_items > 0 && (!ref_ids_host || !y_offsets_host || !y_dev))) {
         set_error("bad arguments");
         return SIDWT_EINVAL;
     }
-    if (reinterpret_cast<uintptr_t>(y_dev) % 16) {
-        set_error("y_dev must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(y_dev) % 16 || reinterpret_cast<uintptr_t>(r_dev) % 8) {
+        set_error("y_dev must be 16-byte aligned (r_dev 8-byte aligned)");
         return SIDWT_EINVAL;
     }
     RaggedLayout L;
     sidwt_status st = build_layout(r, n_items, ref_ids_host, y_offsets_host, y_elems, L);
     if (st) return st;
+    if (r_dev && r_elems < L.r_elems) {
+        set_error("r_dev holds " + std::to_string(r_elems) + " elements; this batch writes " +
+                  std::to_string(L.r_elems) + " (the sum of (J_i + 1) N_i)");
+        return SIDWT_EINVAL;
+    }
     if ((st = ensure_workspace(r, L)) || (st = encode_layout_maps(r, L))) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if ((st = upload(r, r->dl, L, s, false))) return st;
     r->last_slots = L.slots;
-    return enqueue(r, r->dl, L.slots, n_items, static_cast<const float2 *>(y_dev), s, nullptr);
+    return enqueue(r, r->dl, L.slots, n_items, static_cast<const float2 *>(y_dev), s, nullptr,
+                   static_cast<float2 *>(r_dev));
+}
+
+sidwt_status sidwt_ragged_correlate(sidwt_ragged *r, int64_t n_items, const int32_t *ref_ids_host,
+                                    const int64_t *y_offsets_host, const void *y_dev, int64_t y_elems,
+                                    sidwt_stream stream) {
+    return sidwt_ragged_correlate_r(r, n_items, ref_ids_host, y_offsets_host, y_dev, y_elems, nullptr, 0, stream);
 }
 
 sidwt_status sidwt_ragged_graph_create(sidwt_ragged *r, int64_t n_items, const int32_t *ref_ids_host,
@@ -1304,7 +1322,7 @@ sidwt_status sidwt_ragged_autotune(sidwt_ragged *r, const char *cache_path, sidw
     std::string report;
     for (int lg = lg_lo; lg <= lg_hi; ++lg) {
         const int64_t Kp = int64_t(1) << lg, N = 2 * Kp;
-        rg::Item it{0, 0, 0, 0, (int32_t)N, 1, 0, 0};
+        rg::Item it{0, 0, 0, 0, (int32_t)N, 1, 0, 0, 0};
         cudaMemcpyAsync(ditem, &it, sizeof(it), cudaMemcpyHostToDevice, s);
         float best_ms = 1e30f;
         int best_mq = default_mq(lg);

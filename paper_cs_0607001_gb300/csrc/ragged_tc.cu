@@ -157,10 +157,13 @@ __device__ __forceinline__ void expand_window(unsigned char *stB, const float2 *
     }
 }
 
+// WITH_R: also write r at every lag (a separate instance, so that the bulk
+// path's epilogue is unchanged)
+template <bool WITH_R>
 __global__ void __launch_bounds__(kThreads, 1)
     corr_pair_tc_kernel(const CUtensorMap *__restrict__ maps, const TcTile *__restrict__ tiles, int ntiles,
                         const float2 *__restrict__ pyr, unsigned long long *__restrict__ keys,
-                        int32_t *__restrict__ err) {
+                        int32_t *__restrict__ err, float2 *__restrict__ R) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *sB = base;
@@ -345,6 +348,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             // advance of column n: p = S i - n (mod K'); delay q = -p mod K'
             int pm = (int)(((int64_t)w.S * i) % Kp);
             unsigned long long best = 0ull;
+            // optional r output (every (row, column) is a correct advance; rows past
+            // ceil(K'/S) and the wrapped columns repeat advances already written)
+            float2 *Rrow = (WITH_R && valid) ? R + (pass ? w.r_at : w.r_mid) : nullptr;
             const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
             for (int c0 = 0; c0 < w.S; c0 += 32) {
                 uint32_t re[32], im[32];
@@ -360,6 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const unsigned long long key =
                         ((unsigned long long)__float_as_uint(m2) << 32) | (unsigned long long)(0xFFFFFFFFu - D);
                     best = key > best ? key : best;
+                    if (WITH_R && Rrow) Rrow[D] = make_float2(xr, xi);
                     pm = pm == 0 ? Kp - 1 : pm - 1;
                 }
             }
@@ -553,17 +560,25 @@ sidwt_status encode_maps(void *two_maps, const void *a_base, const void *b_base,
 
 
 sidwt_status launch_corr(const void *maps, const TcTile *tiles, int ntiles, const float2 *pyr, unsigned long long *keys,
-                         int32_t *err, int sms, cudaStream_t s) {
+                         int32_t *err, int sms, cudaStream_t s, float2 *R) {
     if (ntiles <= 0) return SIDWT_OK;
     const int grid = std::min(sms, ntiles);
-    corr_pair_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(static_cast<const CUtensorMap *>(maps), tiles, ntiles, pyr,
-                                                            keys, err);
+    if (R)
+        corr_pair_tc_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(static_cast<const CUtensorMap *>(maps), tiles,
+                                                                      ntiles, pyr, keys, err, R);
+    else
+        corr_pair_tc_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(static_cast<const CUtensorMap *>(maps), tiles,
+                                                                       ntiles, pyr, keys, err, nullptr);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "tensor-core pair correlation launch");
 }
 
 cudaError_t prepare_kernels() {
-    return cudaFuncSetAttribute(corr_pair_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(corr_pair_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(corr_pair_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    return e;
 }
 
 }  // namespace rtc

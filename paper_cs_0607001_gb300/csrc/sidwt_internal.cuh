@@ -325,6 +325,8 @@ struct TcTile {
     // peak key formed from band 0 alone before band 1 is added (scale J, whose
     // eq. 20a product is band 0 of scale J - 1's eq. 20 product), or -1
     int64_t slot_mid;
+    // optional r output: complex64 offsets of the N-lag rows of slot and slot_mid
+    int64_t r_at = -1, r_mid = -1;
 };
 
 
@@ -352,8 +354,9 @@ sidwt_status pack_stored(const float2 *tree, int64_t N, int J, const int64_t *a_
                          cudaStream_t s);
 sidwt_status encode_maps(void *two_maps, const void *a_base, const void *b_base, const Shape &sh);
 size_t map_bytes();
+// R: optional complex64 r output (each tile writes its rows at r_at / r_mid), or null
 sidwt_status launch_corr(const void *maps, const TcTile *tiles, int ntiles, const float2 *pyr, unsigned long long *keys,
-                         int32_t *err, int sms, cudaStream_t s);
+                         int32_t *err, int sms, cudaStream_t s, float2 *R = nullptr);
 cudaError_t prepare_kernels();
 
 }  // namespace rtc

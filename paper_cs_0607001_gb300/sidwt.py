@@ -100,6 +100,7 @@ def lib():
     L.sidwt_ragged_num_refs.restype = _i32
     L.sidwt_ragged_store_reference.argtypes = [_vp, ctypes.c_int, _i64, ctypes.c_int, _vp, ctypes.POINTER(_i32), _vp]
     L.sidwt_ragged_correlate.argtypes = [_vp, _i64, _vp, _vp, _vp, _i64, _vp]
+    L.sidwt_ragged_correlate_r.argtypes = [_vp, _i64, _vp, _vp, _vp, _i64, _vp, _i64, _vp]
     L.sidwt_ragged_graph_create.argtypes = [_vp, _i64, _vp, _vp, _vp, _i64, ctypes.POINTER(_i32)]
     L.sidwt_ragged_graph_launch.argtypes = [_vp, _vp]
     L.sidwt_ragged_peaks.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp]
@@ -126,7 +127,7 @@ def lib():
                  "sidwt_correlate_host", "sidwt_check", "sidwt_reset_references", "sidwt_set_timing",
                  "sidwt_read_timing", "sidwt_correlate_static", "sidwt_tc_selftest", "sidwt_debug_stall", "sidwt_ragged_create",
                  "sidwt_ragged_destroy", "sidwt_ragged_reserve", "sidwt_ragged_store_reference",
-                 "sidwt_ragged_correlate", "sidwt_ragged_graph_create", "sidwt_ragged_graph_launch",
+                 "sidwt_ragged_correlate", "sidwt_ragged_correlate_r", "sidwt_ragged_graph_create", "sidwt_ragged_graph_launch",
                  "sidwt_ragged_peaks", "sidwt_ragged_autotune", "sidwt_ragged_tuning", "sidwt_ragged_set_timing",
                  "sidwt_ragged_read_timing", "sidwt_ragged_reset_references", "sidwt_server_create",
                  "sidwt_server_add_waveform", "sidwt_server_start", "sidwt_server_submit", "sidwt_server_wait",
@@ -405,6 +406,24 @@ class Ragged:
                                             y.numel(), _stream(stream)))
         self._layout = ids
         return self.slots_of(ids)[1]
+
+    def r_rows_of(self, ref_ids) -> tuple[np.ndarray, int]:
+        """First element of every item's J + 1 rows of N lags in the r output, and the total."""
+        sz = np.array([(self.refs[int(r)][2] + 1) * self.refs[int(r)][1] for r in ref_ids], dtype=np.int64)
+        first = np.concatenate([[0], np.cumsum(sz)[:-1]]) if len(sz) else np.zeros(0, np.int64)
+        return first, int(sz.sum())
+
+    def correlate_r(self, ref_ids, offsets, y: torch.Tensor, stream=None):
+        """As correlate, and the correlation at every lag and scale
+        (sidwt_ragged_correlate_r): returns (slots, r) with r a packed complex64
+        tensor; item i's scale j is r[first[i] + j N_i : + N_i] (r_rows_of)."""
+        ids, off = self._args(ref_ids, offsets)
+        _, total = self.r_rows_of(ids)
+        r = torch.zeros(max(1, total), dtype=torch.complex64, device=y.device)
+        _raise(lib().sidwt_ragged_correlate_r(self._h, ids.size, ids.ctypes.data, off.ctypes.data, _ptr(y),
+                                              y.numel(), _ptr(r), r.numel(), _stream(stream)))
+        self._layout = ids
+        return self.slots_of(ids)[1], r[:total]
 
     def graph_create(self, ref_ids, offsets, y: torch.Tensor) -> int:
         ids, off = self._args(ref_ids, offsets)

@@ -59,3 +59,46 @@ def check_peak_lags(lag_gpu: np.ndarray, r_or: np.ndarray, bound: float, what=""
 
 def small_batch(n_refs, B, N, J, seed):
     return inputs.random_batch(n_refs=n_refs, B=B, N=N, J=J, seed=seed)
+
+
+# Bounds of the split tensor-core products (bf16 hi+lo: u = 2^-16, 16 products
+# per MMA; 3xTF32: u = 2^-22, 8 per MMA), per (pair, scale), on
+# max_D |r_gpu - r_oracle|.  With a_k the stored coefficients of one variant band
+# (advanced by D) and b_k the received ones, each kept product hi*hi + hi*lo +
+# lo*hi is off by |e_k| <= 3 u |a_k||b_k| (the dropped lo*lo and the roundings
+# of the lo parts); the sums are accumulated in FP32.
+#   worst case: (3 u + K 2^-24) max_v ||w_v|| ||u||
+#     (FP32 summation of K terms, every rounding at its bound and of one sign;
+#     Cauchy-Schwarz over the band);
+#   per MMA step: (3 u + s 2^-23) max_v ||w_v|| ||u||, s = 3 ceil(K / k_mma)
+#     (the tensor cores add each MMA's products to the running sum in TMEM
+#     once; each such step loses at most one unit in the last place of the
+#     running sum, whose size is at most sum_k |a_k b_k|).  The loss is a bias,
+#     not a random walk: at a matched peak all products have one phase and the
+#     measured error grows linearly with K, about half a unit per step (0.42 of
+#     this bound on dense random pulses, 0.2 on the LFM / Barker batch, where
+#     only the steps that hold the pulse's samples add anything).
+def split_bounds(tree, pyr, N, J, j, u, k_mma=None):
+    """(worst-case, per-MMA-step) bound for scale j; tree and pyr from the
+    oracle (tree_x, pyramid_y); k_mma: products per MMA (16 for bf16, 8 for
+    TF32; default from u)."""
+    if k_mma is None:
+        k_mma = 16 if u >= 2.0 ** -16 else 8
+    lev = j + 1 if j < J else J
+    Kp = N >> lev
+    base = 2 * N * (lev - 1)
+    A = tree[base:base + N].reshape(1 << lev, Kp)
+    Bb = tree[base + N:base + 2 * N].reshape(1 << lev, Kp)
+    off = 2 * N - 4 * Kp
+    if j < J:
+        wn = np.sqrt((np.abs(A) ** 2).sum(1) + (np.abs(Bb) ** 2).sum(1)).max()
+        un = np.linalg.norm(pyr[off:off + 2 * Kp])
+        K = 2 * Kp
+    else:
+        wn = np.sqrt((np.abs(A) ** 2).sum(1)).max()
+        un = np.linalg.norm(pyr[off:off + Kp])
+        K = Kp
+    steps = 3 * -(-K // k_mma)
+    worst = (3 * u + K * 2.0 ** -24) * wn * un
+    step = (3 * u + steps * 2.0 ** -23) * wn * un
+    return worst, step

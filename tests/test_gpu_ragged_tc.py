@@ -7,9 +7,11 @@ zero-padded linear form otherwise); shorter bands stay on the CUDA cores.
 
 Error bound, stated a priori as for the batched tensor-core path: per (pair,
 scale) every |r_j[D]| is off by at most
-    (3 * 2^-16 + K_j 2^-24) * max_v ||w_v|| * ||u||
-(bf16 hi+lo split without the lo*lo term, FP32 accumulation over K_j terms,
-Cauchy-Schwarz over the band).  The padded terms of the linear form are
+    (3 * 2^-16 + s 2^-23) * max_v ||w_v|| * ||u||
+(bf16 hi+lo split without the lo*lo term; s = 3 K_j / 16 accumulation steps
+of the tensor cores, each losing at most one unit in the last place of the
+running sum; Cauchy-Schwarz over the band), which is below the worst-case
+FP32-summation bound with K_j 2^-24.  The padded terms of the linear form are
 exact zeros and add nothing."""
 import numpy as np
 import pytest
@@ -41,26 +43,11 @@ def build_batch(seed):
 
 
 def stated_bounds(oracle, f, N, J, x, y):
+    """Per scale, the split's per-MMA-step bound (tests/gpu_util.py), the
+    tighter of its two stated bounds."""
     tree, _ = oracle.tree_x(f, x.astype(np.complex128), J)
     pyr, _ = oracle.pyramid_y(f, y.astype(np.complex128), J)
-    out = []
-    for j in range(J + 1):
-        lev = j + 1 if j < J else J
-        Kp = N >> lev
-        base = 2 * N * (lev - 1)
-        A = tree[base:base + N].reshape(1 << lev, Kp)
-        Bb = tree[base + N:base + 2 * N].reshape(1 << lev, Kp)
-        off = 2 * N - 4 * Kp
-        if j < J:
-            wn = np.sqrt((np.abs(A) ** 2).sum(1) + (np.abs(Bb) ** 2).sum(1)).max()
-            un = np.linalg.norm(pyr[off:off + 2 * Kp])
-            Kj = 2 * Kp
-        else:
-            wn = np.sqrt((np.abs(A) ** 2).sum(1)).max()
-            un = np.linalg.norm(pyr[off:off + Kp])
-            Kj = Kp
-        out.append((3 * 2.0 ** -16 + Kj * 2.0 ** -24) * wn * un)
-    return np.array(out)
+    return np.array([U.split_bounds(tree, pyr, N, J, j, 2.0 ** -16)[1] for j in range(J + 1)])
 
 
 def run(precision, refs, ypack, offsets, graph=False, tune_after=None, cache=None):

@@ -1,12 +1,16 @@
 """GPU parity of the tcgen05 bf16 hi+lo correlation (SIDWT_PREC_BF16X3).
 
-Error bound stated a priori: splitting a = a_h + a_l + e (bf16 round to
-nearest, unit roundoff 2^-8) and keeping a_h b_h + a_h b_l + a_l b_h leaves
-|a b - kept| <= 3 * 2^-16 |a| |b| per product; FP32 accumulation of K terms
-adds at most K * 2^-24 sum |a b|.  Per (pair, scale):
-    max_D |r_tc - r_oracle| <= (3 * 2^-16 + K_j 2^-24) max_v ||w_v|| ||u||
-with w_v the stored variant's bands and u the received bands (Cauchy-Schwarz).
-The tests also report the measured error relative to the peak."""
+Error bounds stated a priori (tests/gpu_util.py split_bounds): splitting
+a = a_h + a_l + e (bf16 round to nearest, unit roundoff 2^-8) and keeping
+a_h b_h + a_h b_l + a_l b_h leaves |a b - kept| <= 3 * 2^-16 |a| |b| per
+product.  Per (pair, scale), with w_v the stored variant's bands and u the
+received bands (Cauchy-Schwarz):
+  worst case     max_D |r_tc - r_oracle| <= (3 * 2^-16 + K_j 2^-24) max_v ||w_v|| ||u||
+  per MMA step   max_D |r_tc - r_oracle| <= (3 * 2^-16 + s 2^-23) max_v ||w_v|| ||u||,
+                 s = 3 K_j / 16 accumulation steps of the tensor cores, each
+                 losing at most one unit in the last place of the running sum.
+Both are checked; the tests also report the measured error relative to the
+peak."""
 import numpy as np
 import pytest
 import torch
@@ -42,22 +46,11 @@ def test_tc_operand_layouts_selftest():
                     f"expected[1,:8]={exp[1, :8]}")
 
 
-def stated_bound(tree, pyr, N, J, j, Kj, u=2.0 ** -16):
-    """(3 u + K 2^-24) max_v ||w_v|| ||u|| for scale j (tree and pyr from the
-    oracle); u = 2^-16 for the bf16 split, 2^-22 for 3xTF32."""
-    lev = j + 1 if j < J else J
-    Kp = N >> lev
-    base = 2 * N * (lev - 1)
-    A = tree[base:base + N].reshape(1 << lev, Kp)
-    Bb = tree[base + N:base + 2 * N].reshape(1 << lev, Kp)
-    off = 2 * N - 4 * Kp
-    if j < J:
-        wn = np.sqrt((np.abs(A) ** 2).sum(1) + (np.abs(Bb) ** 2).sum(1)).max()
-        un = np.linalg.norm(pyr[off:off + 2 * Kp])
-    else:
-        wn = np.sqrt((np.abs(A) ** 2).sum(1)).max()
-        un = np.linalg.norm(pyr[off:off + Kp])
-    return (3 * u + Kj * 2.0 ** -24) * wn * un
+def check_bounds(err, tree, pyr, N, J, j, u, what):
+    """err against both stated bounds of scale j (worst case, per MMA step)."""
+    worst, step = U.split_bounds(tree, pyr, N, J, j, u)
+    assert err <= worst, f"{what} scale {j}: error {err:.3e} > worst-case bound {worst:.3e}"
+    assert err <= step, f"{what} scale {j}: error {err:.3e} > per-MMA-step bound {step:.3e}"
 
 
 def run(fname, N, J, refs, y, ids, precision, want_r=True):
@@ -88,10 +81,8 @@ def test_bf16x3_matches_oracle_within_stated_bound(oracle, fname, fid, N, J, B, 
         rb = r[b].cpu().numpy().astype(np.complex128)
         pyr, _ = oracle.pyramid_y(fid, Y[b], J)
         for j in range(J + 1):
-            Kj = N >> j
             err = np.abs(rb[j] - ro[b, j]).max()
-            bound = stated_bound(trees[w["ref_ids"][b]], pyr, N, J, j, Kj)
-            assert err <= bound, f"pulse {b} scale {j}: error {err:.3e} > stated bound {bound:.3e}"
+            check_bounds(err, trees[w["ref_ids"][b]], pyr, N, J, j, 2.0 ** -16, f"pulse {b}")
             worst_rel = max(worst_rel, err / np.abs(ro[b, j]).max())
         U.check_peak_lags(lag[b], ro[b], 3 * 2.0 ** -16, what=f"{fname} pulse {b}")
     assert worst_rel < 1e-4, worst_rel
@@ -111,11 +102,15 @@ def test_bf16x3_full_size_two_reference_batch_sampled(oracle, fname):
     X = w["refs"][w["ref_ids"][sample]].astype(np.complex128)
     Y = w["y"][sample].astype(np.complex128)
     lo, mo, no, ro, _ = oracle.correlate_batch(fid, X, Y, 5, want_r=True)
+    trees = {k: oracle.tree_x(fid, w["refs"][k].astype(np.complex128), 5)[0] for k in (0, 1)}
     for i, b in enumerate(sample):
         rb = r[b].cpu().numpy().astype(np.complex128)
+        pyr, _ = oracle.pyramid_y(fid, Y[i], 5)
         for j in range(6):
-            rel = np.abs(rb[j] - ro[i, j]).max() / np.abs(ro[i, j]).max()
-            assert rel < 1e-4, (b, j, rel)
+            err = np.abs(rb[j] - ro[i, j]).max()
+            check_bounds(err, trees[int(w["ref_ids"][b])], pyr, 8192, 5, j, 2.0 ** -16, f"{fname} pulse {b}")
+            # on this batch the split also meets the FP32 path's target (measured up to 8.5e-6)
+            assert err <= 1e-5 * np.abs(ro[i, j]).max(), (b, j, err / np.abs(ro[i, j]).max())
         U.check_peak_lags(lag[b], ro[i], 3 * 2.0 ** -16, what=f"{fname} pulse {b}")
 
 
@@ -144,8 +139,7 @@ def test_bf16x3_many_reference_batch_sampled(oracle):
         pyr, _ = oracle.pyramid_y(2, Y[i], 6)
         for j in range(7):
             err = np.abs(rs[i, j] - ro[i, j]).max()
-            bound = stated_bound(trees[int(w["ref_ids"][b])], pyr, 4096, 6, j, 4096 >> j)
-            assert err <= bound, (b, j, err, bound)
+            check_bounds(err, trees[int(w["ref_ids"][b])], pyr, 4096, 6, j, 2.0 ** -16, f"pulse {b}")
         U.check_peak_lags(lag[b], ro[i], 3 * 2.0 ** -16, what=f"pulse {b}")
 
 
@@ -183,10 +177,9 @@ def test_precision_sweep_launch_sampled(oracle, precision):
         for j in range(7):
             err = np.abs(rs[i, j] - ro[i, j]).max()
             if u is None:
-                bound = 1e-5 * np.abs(ro[i, j]).max()
+                assert err <= 1e-5 * np.abs(ro[i, j]).max(), (precision, b, j, err)
             else:
-                bound = stated_bound(tree, pyr, 4096, 6, j, 4096 >> j, u=u)
-            assert err <= bound, (precision, b, j, err, bound)
+                check_bounds(err, tree, pyr, 4096, 6, j, u, f"{precision} pulse {b}")
         U.check_peak_lags(lag[b], ro[i], 3 * u if u else 1e-5, what=f"{precision} pulse {b}")
 
 
@@ -195,8 +188,9 @@ def test_precision_sweep_launch_sampled(oracle, precision):
 def test_tf32x3_matches_oracle_within_stated_bound(oracle, fname, fid, N, J, B, nrefs):
     """3xTF32: a = a_hi + a_lo, both rounded to TF32 (unit roundoff 2^-11);
     dropping lo*lo and the two lo roundings leave <= 3 * 2^-22 |a||b| per
-    product, FP32 accumulation adds K 2^-24: the FP32 path's own a-priori
-    bound."""
+    product; FP32 accumulation adds K 2^-24 (worst case, the FP32 path's own
+    a-priori bound) or one unit in the last place per MMA step (8 products per
+    kind::tf32 MMA, 3 K / 8 steps)."""
     w = U.small_batch(nrefs, B, N, J, seed=2000 + N + B + fid)
     r, lag, mag, norm = run(fname, N, J, w["refs"], w["y"], w["ref_ids"], "tf32x3")
     X = w["refs"][w["ref_ids"]].astype(np.complex128)
@@ -209,8 +203,7 @@ def test_tf32x3_matches_oracle_within_stated_bound(oracle, fname, fid, N, J, B, 
         pyr, _ = oracle.pyramid_y(fid, Y[b], J)
         for j in range(J + 1):
             err = np.abs(rb[j] - ro[b, j]).max()
-            bound = stated_bound(trees[w["ref_ids"][b]], pyr, N, J, j, N >> j, u=2.0 ** -22)
-            assert err <= bound, f"pulse {b} scale {j}: error {err:.3e} > stated bound {bound:.3e}"
+            check_bounds(err, trees[w["ref_ids"][b]], pyr, N, J, j, 2.0 ** -22, f"pulse {b}")
             worst_rel = max(worst_rel, err / np.abs(ro[b, j]).max())
         U.check_peak_lags(lag[b], ro[b], 3 * 2.0 ** -16, what=f"{fname} pulse {b}")
     # measured: about 2e-5 of the peak at K ~ 1e3, set by the tensor cores'
