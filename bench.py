@@ -177,6 +177,31 @@ def cpu_oracle_sample(w, seconds: float = 12.0, max_pairs: int = 4096):
     return {"pairs": pairs, "seconds": el, "cores": used, "value": pairs * N / el / 1e9}
 
 
+def accuracy_sample(w, plans, ids, y_c, torch, precisions, sample=(0, 7, 100, 2047, 2048, 3000, 4095)):
+    """Per precision and filter, per scale: max over the sampled pulses of
+    max_D |r_gpu - r_oracle| / max_D |r_oracle|, the GPU r taken from a
+    correlate call over the whole batch (the timed launch configuration)."""
+    from oracle import oracle as O
+    sample = np.array(sample)
+    X = w["refs"][w["ref_ids"][sample]].astype(np.complex128)
+    Y = w["y"][sample].astype(np.complex128)
+    idx = torch.from_numpy(sample).to(y_c.device)
+    out = {"what": f"per scale j = 0..{J}: max over pulses {sample.tolist()} of max_D |r_gpu - r_oracle| / "
+                   "max_D |r_oracle|", "target_fp32": 1e-5}
+    for fname, p in plans.items():
+        ro = O.correlate_batch(FILTER_IDS[fname], X, Y, J, want_r=True)[3]
+        for pr in precisions:
+            R = p.correlate(ids, y_c, precision=pr, want_r=True)
+            rg = R[idx].cpu().numpy().astype(np.complex128)
+            del R
+            errs = [max(float(np.abs(rg[i, j] - ro[i, j]).max() / np.abs(ro[i, j]).max()) for i in range(len(sample)))
+                    for j in range(J + 1)]
+            out.setdefault(pr, {})[fname] = errs
+    for pr in precisions:
+        out[pr]["max"] = max(max(v) for k, v in out[pr].items())
+    return out
+
+
 def run_reference(args):
     from paper_cs_0607001_gb300 import inputs
     from paper_cs_0607001_gb300 import multigpu as M
@@ -352,6 +377,27 @@ def run_ours(args):
         plain = {"value": world * pairs_n(B) * N / (pms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": pms,
                  "path": "FP32 CUDA cores (correlation only, same batch and peaks)", "steps": kp}
 
+    # the 3xTF32 split on the same batch (FP32-grade accuracy on the tensor cores)
+    tf32 = None
+    if prec != "fp32" and not args.no_plain:
+        def tf32_step():
+            for k, p in plans.items():
+                p.correlate(ids, y_c, precision="tf32x3")
+                p.peaks_into(B, *outs[k])
+        tf32_step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        kt = max(2, min(args.steps, 5))
+        e0.record(stream)
+        for _ in range(kt):
+            tf32_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tms = M.max_over_ranks(e0.elapsed_time(e1) / kt)
+        tf32 = {"value": world * pairs_n(B) * N / (tms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": tms, "steps": kt,
+                "path": "tcgen05 kind::tf32, 3xTF32 split (correlation only, same batch and peaks)"}
+
     # end to end through the host-buffer C-ABI call: pinned y in, peaks out
     e2e = None
     if not args.no_e2e:
@@ -361,55 +407,60 @@ def run_ours(args):
                     torch.empty((B, J + 1), dtype=torch.float32).pin_memory(),
                     torch.empty((B, J + 1), dtype=torch.float64).pin_memory()) for k in plans}
 
-        from concurrent.futures import ThreadPoolExecutor
-        streams = {k: torch.cuda.Stream() for k in plans}
-
-        def one(k):
-            plans[k].correlate_host(ids_pin, y_pin, precision=prec, lag=hout[k][0], mag=hout[k][1],
-                                    norm=hout[k][2], stream=streams[k])
+        stream_e2e = torch.cuda.Stream()
+        # one set of pinned peak outputs per step in flight (two steps alternate)
+        hout2 = [hout, {k: tuple(t.clone().pin_memory() for t in v) for k, v in hout.items()}]
 
         def e2e_seq():
+            # the blocking host call per filter: copy in, correlate, copy the peaks out, wait
             for k in plans:
-                one(k)
+                plans[k].correlate_host(ids_pin, y_pin, precision=prec, lag=hout[k][0], mag=hout[k][1],
+                                        norm=hout[k][2], stream=stream_e2e)
 
-        pool = ThreadPoolExecutor(max_workers=len(plans))
-
-        def e2e_par():
-            # one host thread per filter, each call on its own stream: one call's input copy runs
-            # while the other's kernels do
-            for f in [pool.submit(one, k) for k in plans]:
-                f.result()
+        def e2e_pipe(step_i):
+            # the asynchronous host call per filter on one stream: each plan's input copy runs on
+            # its own copy stream beside the previous call's correlation; the correlations stay in
+            # stream order; the peaks come back on the same stream
+            o = hout2[step_i & 1]
+            for k in plans:
+                plans[k].correlate_host_async(ids_pin, y_pin, *o[k], precision=prec, stream=stream_e2e)
 
         def timed(fn):
-            for _ in range(2):
-                fn()
+            for i in range(2):
+                fn(i)
+            stream_e2e.synchronize()
             torch.cuda.synchronize()
             M.barrier()
             t0 = time.perf_counter()
             k_e2e = max(1, args.steps)
-            for _ in range(k_e2e):
-                fn()
-            torch.cuda.synchronize()
+            for i in range(k_e2e):
+                fn(i)
+            stream_e2e.synchronize()
             return M.max_over_ranks((time.perf_counter() - t0) / k_e2e)
 
-        el_seq = timed(e2e_seq)
-        el = timed(e2e_par)
-        pool.shutdown()
+        el_seq = timed(lambda i: e2e_seq())
+        el = timed(e2e_pipe)
+        lag_back = hout2[(max(1, args.steps) - 1) & 1]["cdf97"][0].numpy()[:, 0]
         h2d = 2 * (y_pin.numel() * 8 + ids_pin.numel() * 4)
         d2h = 2 * B * (J + 1) * (4 + 4 + 8)
         e2e = {"value": world * pairs * N / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": el * 1e3,
-               "path": "sidwt_correlate_host per filter from two host threads, each on its own stream "
-                       "(pinned host y -> device, peaks -> host)",
+               "path": "sidwt_correlate_host_async per filter from one host thread on one stream (pinned host y "
+                       "-> device on each plan's copy stream, overlapping the previous call's correlation; "
+                       "peaks -> pinned host)",
+               "peak_at_injected_delay_scale0": float(np.mean(lag_back == w["delays"])),
                "sequential": {"value": world * pairs * N / el_seq / 1e9, "ms_per_step": el_seq * 1e3,
-                              "path": "the two host calls one after the other on one thread"}}
+                              "path": "sidwt_correlate_host (blocking) per filter, one after the other"}}
 
     cpu = None
+    acc = None
     if rank == 0 and world == 1 and not args.no_cpu:
         r = cpu_oracle_sample(w, seconds=args.cpu_seconds)
         cpu = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                "sample": f"{r['pairs']} whole (pulse, filter) pairs of this workload (N={N}, J={J}, all lags and "
                          f"scales, peaks), {r['seconds']:.1f} s wall"}
+        # the same leg's oracle results at every lag for a few pairs, against each GPU precision
+        acc = accuracy_sample(w, plans, ids, y_c, torch, ["fp32", "tf32x3", "bf16x3"] if prec != "fp32" else ["fp32"])
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -430,8 +481,11 @@ def run_ours(args):
         "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99)),
                        "what": "per step (whole batch), CUDA events"},
         "vs_plain": ({"plain_fp32": plain, "speedup_correlation": plain["ms_per_step"] / corr_step_ms,
+                      "tf32x3": tf32,
+                      "speedup_tf32x3_over_plain": (plain["ms_per_step"] / tf32["ms_per_step"]) if tf32 else None,
                       "what": "plain FP32 correlate calls per step / this precision's correlate calls per step"}
                      if plain else None),
+        "accuracy_vs_oracle": acc,
         "peak_at_injected_delay_scale0": hit,
     }
     if rank == 0:

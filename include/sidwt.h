@@ -189,6 +189,21 @@ sidwt_status sidwt_correlate_host(sidwt_plan *p, const int32_t *ref_ids_host, co
                                   sidwt_precision prec, int32_t *lag_host, float *mag_host, double *norm_host,
                                   sidwt_stream stream);
 
+/* Asynchronous form of sidwt_correlate_host for page-locked host buffers
+ * (every non-NULL host pointer must be pinned, else SIDWT_EINVAL): the input
+ * copies run on a copy stream owned by the plan, ordered after the previous
+ * call's compute on this plan has read the plan's device copy of the inputs;
+ * the correlation and the peak copies to the host run on `stream`, after the
+ * input copies.  Returns once everything is enqueued: the outputs are valid,
+ * and the host inputs may be reused, after `stream` has been synchronised.
+ * Calls on different plans that share one stream overlap one call's input
+ * copy with the previous call's correlation, while the correlations
+ * themselves stay in stream order (they do not compete for the SMs).  Same
+ * layouts as sidwt_correlate / sidwt_peaks. */
+sidwt_status sidwt_correlate_host_async(sidwt_plan *p, const int32_t *ref_ids_host, const void *y_host, int64_t B,
+                                        sidwt_precision prec, int32_t *lag_host, float *mag_host, double *norm_host,
+                                        sidwt_stream stream);
+
 /* Forget every stored reference (ids restart at 0); the store's capacity is
  * kept, so storing again allocates nothing. */
 sidwt_status sidwt_reset_references(sidwt_plan *p);

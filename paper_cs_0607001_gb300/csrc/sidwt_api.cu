@@ -190,6 +190,23 @@ sidwt_status prepare_kernels() {
     return SIDWT_OK;
 }
 
+// Device buffer for the inputs of the host-buffer entry points, owned by the
+// plan; growing it waits for the device (the old buffer may still be read).
+static sidwt_status ensure_host_inputs(sidwt_plan *p, size_t need) {
+    if (need <= p->d_in_bytes) return SIDWT_OK;
+    cudaDeviceSynchronize();
+    if (p->d_in) cudaFree(p->d_in);
+    p->d_in = nullptr;
+    p->d_in_bytes = 0;
+    if (cudaMalloc(&p->d_in, need) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("device allocation failed for host-call inputs");
+        return SIDWT_ENOMEM;
+    }
+    p->d_in_bytes = need;
+    return SIDWT_OK;
+}
+
 static bool is_pinned_host(const void *ptr) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
@@ -284,6 +301,9 @@ sidwt_status sidwt_plan_destroy(sidwt_plan *p) {
     dfree(p->err);
     if (p->h_stage) cudaFreeHost(p->h_stage);
     if (p->d_in) cudaFree(p->d_in);
+    if (p->in_ready) cudaEventDestroy(p->in_ready);
+    if (p->in_free) cudaEventDestroy(p->in_free);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     for (auto &m : p->marks) {
         cudaEventDestroy(m.a);
         cudaEventDestroy(m.b);
@@ -495,6 +515,53 @@ sidwt_status sidwt_peaks(sidwt_plan *p, int64_t B, int32_t *lag_dev, float *mag_
     return copy_peaks(p, B * (p->J + 1), lag_dev, mag_dev, norm_dev, reinterpret_cast<cudaStream_t>(stream));
 }
 
+sidwt_status sidwt_correlate_host_async(sidwt_plan *p, const int32_t *ref_ids_host, const void *y_host, int64_t B,
+                                        sidwt_precision prec, int32_t *lag_host, float *mag_host, double *norm_host,
+                                        sidwt_stream stream) {
+    CHECK_PLAN(p);
+    if (B < 0 || (B > 0 && (!ref_ids_host || !y_host))) {
+        set_error("bad host buffers");
+        return SIDWT_EINVAL;
+    }
+    if (B > 0 && (!is_pinned_host(y_host) || !is_pinned_host(ref_ids_host) ||
+                  (lag_host && !is_pinned_host(lag_host)) || (mag_host && !is_pinned_host(mag_host)) ||
+                  (norm_host && !is_pinned_host(norm_host)))) {
+        set_error("sidwt_correlate_host_async needs page-locked host buffers (cudaMallocHost / cudaHostRegister)");
+        return SIDWT_EINVAL;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t ybytes = (size_t)B * p->N * (p->is_int ? 4 : 8);
+    const size_t ibytes = (size_t)B * sizeof(int32_t);
+    sidwt_status st = ensure_host_inputs(p, ybytes + ibytes + 256);
+    if (st) return st;
+    if (!p->copy_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->in_ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->in_free, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "copy stream / events");
+    }
+    char *dy = static_cast<char *>(p->d_in);
+    int32_t *dids = reinterpret_cast<int32_t *>(dy + ((ybytes + 255) / 256) * 256);
+    // the copies wait for the compute of the previous call on this plan to have
+    // read d_in (an event never recorded lets them start at once), then run
+    // beside whatever the compute stream is doing
+    cudaError_t e = cudaStreamWaitEvent(p->copy_stream, p->in_free, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y_host, ybytes, cudaMemcpyHostToDevice, p->copy_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dids, ref_ids_host, ibytes, cudaMemcpyHostToDevice, p->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(p->in_ready, p->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->in_ready, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    st = sidwt_correlate(p, dids, dy, B, prec, nullptr, stream);
+    if (st) return st;
+    e = cudaEventRecord(p->in_free, s);
+    const size_t n = (size_t)B * (p->J + 1);
+    if (e == cudaSuccess && lag_host) e = cudaMemcpyAsync(lag_host, p->lag, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && mag_host) e = cudaMemcpyAsync(mag_host, p->mag, n * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && norm_host)
+        e = cudaMemcpyAsync(norm_host, p->norm, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "device-to-host copy");
+}
+
 sidwt_status sidwt_correlate_host(sidwt_plan *p, const int32_t *ref_ids_host, const void *y_host, int64_t B,
                                   sidwt_precision prec, int32_t *lag_host, float *mag_host, double *norm_host,
                                   sidwt_stream stream) {
@@ -506,20 +573,8 @@ sidwt_status sidwt_correlate_host(sidwt_plan *p, const int32_t *ref_ids_host, co
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const size_t ybytes = (size_t)B * p->N * (p->is_int ? 4 : 8);
     const size_t ibytes = (size_t)B * sizeof(int32_t);
-    // device copies of the inputs, owned by the plan
-    const size_t need = ybytes + ibytes + 256;
-    if (need > p->d_in_bytes) {
-        cudaDeviceSynchronize();
-        if (p->d_in) cudaFree(p->d_in);
-        p->d_in = nullptr;
-        p->d_in_bytes = 0;
-        if (cudaMalloc(&p->d_in, need) != cudaSuccess) {
-            cudaGetLastError();
-            set_error("device allocation failed for host-call inputs");
-            return SIDWT_ENOMEM;
-        }
-        p->d_in_bytes = need;
-    }
+    sidwt_status st0 = ensure_host_inputs(p, ybytes + ibytes + 256);
+    if (st0) return st0;
     char *dy = static_cast<char *>(p->d_in);
     int32_t *dids = reinterpret_cast<int32_t *>(dy + ((ybytes + 255) / 256) * 256);
     const void *ysrc = y_host;

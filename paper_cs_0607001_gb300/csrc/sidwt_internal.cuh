@@ -176,6 +176,11 @@ struct sidwt_plan {
     size_t h_stage_bytes = 0;
     void *d_in = nullptr;
     size_t d_in_bytes = 0;
+    // sidwt_correlate_host_async: the input copies run on the plan's own copy
+    // stream; in_ready orders the compute after them, in_free the next call's
+    // copies after the compute that read d_in
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t in_ready = nullptr, in_free = nullptr;
 
     // tensor-core operands (per scale j): packed reference windows and the
     // received bf16 hi/lo planes in grouped order

@@ -82,6 +82,7 @@ def lib():
     L.sidwt_correlate.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, _vp, _vp]
     L.sidwt_peaks.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp]
     L.sidwt_correlate_host.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp, _vp]
+    L.sidwt_correlate_host_async.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp, _vp]
     L.sidwt_check.argtypes = [_vp, _vp]
     L.sidwt_reset_references.argtypes = [_vp]
     L.sidwt_set_timing.argtypes = [_vp, ctypes.c_int]
@@ -124,7 +125,7 @@ def lib():
     L.sidwt_server_destroy.argtypes = [_vp]
     for name in ("sidwt_plan_create", "sidwt_plan_destroy", "sidwt_plan_reserve", "sidwt_store_reference",
                  "sidwt_reference_tree", "sidwt_analyze", "sidwt_correlate", "sidwt_peaks",
-                 "sidwt_correlate_host", "sidwt_check", "sidwt_reset_references", "sidwt_set_timing",
+                 "sidwt_correlate_host", "sidwt_correlate_host_async", "sidwt_check", "sidwt_reset_references", "sidwt_set_timing",
                  "sidwt_read_timing", "sidwt_correlate_static", "sidwt_tc_selftest", "sidwt_debug_stall", "sidwt_ragged_create",
                  "sidwt_ragged_destroy", "sidwt_ragged_reserve", "sidwt_ragged_store_reference",
                  "sidwt_ragged_correlate", "sidwt_ragged_correlate_r", "sidwt_ragged_graph_create", "sidwt_ragged_graph_launch",
@@ -299,6 +300,18 @@ class Plan:
         _raise(lib().sidwt_correlate_host(self._h, _ptr(ref_ids), _ptr(y), B, _prec_id(precision), _ptr(lag),
                                           _ptr(mag), _ptr(norm), _stream(stream)))
         return lag, mag, norm
+
+    def correlate_host_async(self, ref_ids: torch.Tensor, y: torch.Tensor, lag: torch.Tensor, mag: torch.Tensor,
+                             norm: torch.Tensor, precision="fp32", stream=None):
+        """Asynchronous end-to-end call on pinned host tensors
+        (sidwt_correlate_host_async): the peaks land in lag / mag / norm once
+        `stream` has been synchronised."""
+        B = y.shape[0]
+        for t in (ref_ids, y, lag, mag, norm):
+            if t.is_cuda or not t.is_pinned():
+                raise ValueError("correlate_host_async takes pinned host tensors")
+        _raise(lib().sidwt_correlate_host_async(self._h, _ptr(ref_ids), _ptr(y), B, _prec_id(precision), _ptr(lag),
+                                                _ptr(mag), _ptr(norm), _stream(stream)))
 
     def check(self, stream=None):
         _raise(lib().sidwt_check(self._h, _stream(stream)))

@@ -175,3 +175,41 @@ def test_host_entry_point_matches_device_entry_point(precision):
         torch.cuda.synchronize()
         for a, b in ((lh, ld), (mh, md), (nh, nd), (lp, ld)):
             np.testing.assert_array_equal(a.numpy(), b.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_async_host_entry_point_pipeline(precision):
+    """Two plans on one stream, three rounds enqueued back to back with
+    different pulses each round (the plan's device copy of the inputs is
+    reused every round), one synchronisation at the end: every round's peaks
+    equal the device entry point's on the same pulses."""
+    from paper_cs_0607001_gb300 import sidwt
+    N, J, B = 2048, 4, 96
+    w3 = inputs.random_batch(n_refs=2, B=3 * B, N=N, J=J, seed=40)
+    refs = w3["refs"]
+    ws = [{key: w3[key][k * B:(k + 1) * B] for key in ("ref_ids", "y", "delays")} for k in range(3)]
+    s = torch.cuda.Stream()
+    with sidwt.Plan("legall53", N, J) as pa, sidwt.Plan("cdf97", N, J) as pb:
+        for p in (pa, pb):
+            for x in refs:
+                p.store_reference(U.to_dev_c64(x))
+        outs = []
+        hin = [(torch.from_numpy(w["ref_ids"].astype(np.int32)).pin_memory(), torch.from_numpy(w["y"]).pin_memory())
+               for w in ws]
+        for k in range(3):
+            for p in (pa, pb):
+                o = tuple(torch.empty((B, J + 1), dtype=dt).pin_memory()
+                          for dt in (torch.int32, torch.float32, torch.float64))
+                p.correlate_host_async(hin[k][0], hin[k][1], *o, precision=precision, stream=s)
+                outs.append((k, p, o))
+        s.synchronize()
+        with pytest.raises(ValueError, match="pinned"):
+            pa.correlate_host_async(hin[0][0], torch.from_numpy(ws[0]["y"]), *outs[0][2], stream=s)
+        for k, p, (lag, mag, norm) in outs:
+            p.correlate(hin[k][0].to(U.dev()), hin[k][1].to(U.dev()), precision=precision)
+            ld, md, nd = p.peaks(B)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(lag.numpy(), ld.cpu().numpy())
+            np.testing.assert_array_equal(mag.numpy(), md.cpu().numpy())
+            np.testing.assert_array_equal(norm.numpy(), nd.cpu().numpy())
+            assert (lag.numpy()[:, 0] == ws[k]["delays"]).all()
