@@ -1,13 +1,17 @@
 """Host-side helpers for running the correlation on several GPUs of one node.
 
 Pairs of (received pulse, stored reference) are independent, so a multi-GPU
-run shards or replicates batches across ranks with no collective on the data
-path; the only exchanges are host-level: a barrier, the maximum of the
-per-rank step times, and an optional gather of the peak records.
+run splits one batch across ranks: every rank stores the same references,
+correlates its share of the pulses, and the peak records are gathered back in
+batch order.  There is no collective on the data path; the only exchanges are
+host-level: a barrier, the maximum of the per-rank step times, and the gather
+of the peak records (about 16 bytes per pulse and scale).
 """
 from __future__ import annotations
 
 import os
+
+import numpy as np
 
 import torch
 import torch.distributed as dist
@@ -71,3 +75,60 @@ def gather_rows(rows, world: int):
     out = [None] * world
     dist.all_gather_object(out, rows)
     return out
+
+
+def shard_by_cost(costs, world: int) -> list[np.ndarray]:
+    """Split items of uneven cost over `world` ranks: largest first, each to
+    the rank with the least total so far (ties to the lower rank).  Returns
+    each rank's item indices in increasing order."""
+    costs = np.asarray(costs, dtype=np.float64)
+    load = np.zeros(world)
+    owner = np.empty(len(costs), dtype=np.int64)
+    for i in np.argsort(-costs, kind="stable"):
+        r = int(np.argmin(load))
+        owner[i] = r
+        load[r] += costs[i]
+    return [np.nonzero(owner == r)[0] for r in range(world)]
+
+
+def pair_cost(N, J) -> np.ndarray:
+    """Algorithmic flops of the all-lag, all-scale correlation of one pair:
+    8 N^2 (2 - 2^-J) (N lags at each of the J + 1 scales)."""
+    N = np.asarray(N, dtype=np.float64)
+    J = np.asarray(J, dtype=np.float64)
+    return 8.0 * N * N * (2.0 - 2.0 ** -J)
+
+
+def gather_slots(index, counts, lag, mag, norm, n_items: int, world: int):
+    """Gather the peak records of a split batch in batch order.
+
+    This rank correlated the items `index` (positions in the whole batch, in
+    the order its records are packed); item index[k] has counts[k] records
+    (J + 1, one per scale).  Returns (lag, mag, norm) for all n_items items,
+    packed by slot as a single-rank call would pack them (item i's scales at
+    sum_{i' < i} (J_i' + 1)), on every rank."""
+    index = np.asarray(index, dtype=np.int64)
+    counts = np.asarray(counts, dtype=np.int64)
+    mine = (index, counts, np.asarray(lag), np.asarray(mag), np.asarray(norm))
+    parts = gather_rows(mine, world)
+    cnt = np.zeros(n_items, dtype=np.int64)
+    for idx, c, *_ in parts:
+        cnt[idx] = c
+    first = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+    total = int(cnt.sum())
+    out_lag = np.full(total, -1, dtype=np.int32)
+    out_mag = np.zeros(total, dtype=np.float32)
+    out_norm = np.zeros(total, dtype=np.float64)
+    seen = np.zeros(n_items, dtype=bool)
+    for idx, c, lg, mg, nm in parts:
+        src = np.concatenate([[0], np.cumsum(c)[:-1]]) if len(c) else np.zeros(0, np.int64)
+        for k, i in enumerate(idx):
+            if seen[i]:
+                raise ValueError(f"item {int(i)} was correlated by two ranks")
+            seen[i] = True
+            out_lag[first[i]:first[i] + c[k]] = lg.reshape(-1)[src[k]:src[k] + c[k]]
+            out_mag[first[i]:first[i] + c[k]] = mg.reshape(-1)[src[k]:src[k] + c[k]]
+            out_norm[first[i]:first[i] + c[k]] = nm.reshape(-1)[src[k]:src[k] + c[k]]
+    if not seen.all():
+        raise ValueError(f"{int((~seen).sum())} items were correlated by no rank")
+    return out_lag, out_mag, out_norm
