@@ -288,6 +288,20 @@ int32_t sidwt_ragged_num_refs(const sidwt_ragged *r);
 sidwt_status sidwt_ragged_store_reference(sidwt_ragged *r, sidwt_filter f, int64_t N, int J, const void *x_dev,
                                           int32_t *ref_id_out, sidwt_stream stream);
 
+/* Store n signals at once (same rules per item as
+ * sidwt_ragged_store_reference): item i is the complex64 signal of N_host[i]
+ * samples at element x_offsets_host[i] of x_dev (x_elems elements; x_dev
+ * 8-byte aligned), stored for filter filters_host[i] and depth J_host[i]
+ * (Sec. II: the even and odd children at every level, Fig. 1 and 5).  All
+ * the items' trees are built together, one launch per level and filter for
+ * every 64 items, instead of one per level per item.  ref_ids_out[i]
+ * receives item i's reference id.  The host arrays are read before the call
+ * returns; x_dev must stay valid until the stream reaches the call. */
+sidwt_status sidwt_ragged_store_references(sidwt_ragged *r, int64_t n, const int32_t *filters_host,
+                                           const int64_t *N_host, const int32_t *J_host, const void *x_dev,
+                                           const int64_t *x_offsets_host, int64_t x_elems, int32_t *ref_ids_out,
+                                           sidwt_stream stream);
+
 /* Correlate n_items pulses: item i is the complex64 pulse starting at element
  * y_offsets_host[i] of y_dev (even offsets: 16-byte aligned pulses), whose
  * length, depth and filter are those of reference ref_ids_host[i]; y_dev

@@ -15,7 +15,9 @@
 // 11-sample window of its input (the lifting steps have support <= 9), so a
 // level is one fully parallel launch.  The same window kernel is the
 // received-side path for pulses too long for shared memory.
+#include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "sidwt_internal.cuh"
 
@@ -271,16 +273,12 @@ constexpr int WR = 5;  // window radius
 // Row r (of nrows) of `in` has K samples at in + r * in_stride; child 1 reads
 // the row delayed by one sample.  Output row (r + child * nrows) of length
 // K/2 goes to lo/hi at row stride out_stride.
+// Output pair n of one analysis level of the periodic row v (K samples),
+// delayed by `child` samples: the window of 2 WR + 1 phase pairs around n,
+// lifted in registers.
 template <int F, int S, typename TIn>
-__global__ void level_window_f(const TIn *__restrict__ in, int64_t in_stride, int nrows, int nchild, int64_t K,
-                               float2 *__restrict__ lo, float2 *__restrict__ hi, int64_t out_stride, LiftCoef c) {
-    const int64_t H = K / 2;
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= H) return;
-    const int rc = blockIdx.y;
-    const int row = rc % nrows, child = rc / nrows;
-    if (child >= nchild) return;
-    const TIn *v = in + (int64_t)row * in_stride;
+__device__ __forceinline__ void window_pair(const TIn *__restrict__ v, int64_t K, int64_t n, int child,
+                                            const LiftCoef &c, float2 &l, float2 &h) {
     using Sh = LiftShape<F, S>;
     float2 E[2 * WR + 1], O[2 * WR + 1];
 #pragma unroll
@@ -290,13 +288,82 @@ __global__ void level_window_f(const TIn *__restrict__ in, int64_t in_stride, in
         O[i] = to_f2(v[wrapi(Sh::d4 ? 2 * m - 1 - child : 2 * m + 1 - child, K)]);
     }
     lift_window<F, S, WR>(E, O, c);
-    const float2 l = scale2(c.ce, E[WR]);
-    float2 h;
+    l = scale2(c.ce, E[WR]);
     if (Sh::d4) h = scale2(c.co, make_float2(E[WR].x + O[WR - 1].x, E[WR].y + O[WR - 1].y));
     else h = scale2(c.co, O[WR]);
+}
+
+template <int F, int S, typename TIn>
+__global__ void level_window_f(const TIn *__restrict__ in, int64_t in_stride, int nrows, int nchild, int64_t K,
+                               float2 *__restrict__ lo, float2 *__restrict__ hi, int64_t out_stride, LiftCoef c) {
+    const int64_t H = K / 2;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= H) return;
+    const int rc = blockIdx.y;
+    const int row = rc % nrows, child = rc / nrows;
+    if (child >= nchild) return;
+    float2 l, h;
+    window_pair<F, S>(in + (int64_t)row * in_stride, K, n, child, c, l, h);
     const int64_t orow = (int64_t)(row + child * nrows) * out_stride;
     lo[orow + n] = l;
     hi[orow + n] = h;
+}
+
+// Stored SIDWT trees of many signals at once (x side, float filters): one
+// launch per level for every tree of the batch.  Item k's level j + 1 is
+// N_k outputs (2^(j+1) variant rows of N_k / 2^(j+1), in the A and the B
+// band), one thread each; the items are sorted by decreasing J, so the
+// items still lifting at level j are the first n_active, and a thread finds
+// its item by binary search in the prefix sums of N.
+template <int F>
+__global__ void tree_level_batch_kernel(const float2 *__restrict__ x, float2 *__restrict__ tree,
+                                        const __grid_constant__ TreeBatch b, int j, int n_active, LiftCoef c) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= b.nprefix[n_active]) return;
+    int lo_k = 0, hi_k = n_active - 1;
+    while (lo_k < hi_k) {  // last k with nprefix[k] <= t
+        const int mid = (lo_k + hi_k + 1) >> 1;
+        if (b.nprefix[mid] <= t) lo_k = mid;
+        else hi_k = mid - 1;
+    }
+    const TreeItem it = b.it[lo_k];
+    const int64_t N = it.N, local = t - b.nprefix[lo_k];
+    const int64_t K = N >> j, H = K / 2;
+    const int nrows = 1 << j;
+    const int64_t orow = local / H, n = local - orow * H;
+    const int row = (int)(orow % nrows), child = (int)(orow / nrows);
+    const float2 *v = j == 0 ? x + it.x_off : tree + it.tree_off + 2 * N * (int64_t)(j - 1) + (int64_t)row * K;
+    float2 l, h;
+    window_pair<F, SIDE_X>(v, K, n, child, c, l, h);
+    float2 *A = tree + it.tree_off + 2 * N * (int64_t)j;
+    A[orow * H + n] = l;
+    A[N + orow * H + n] = h;
+}
+
+// Energies of the batch's trees: block e -> item k (prefix sums of
+// 2^(J+1) - 1 blocks per item) and (level l, variant v) as in
+// ref_energy_kernel.
+__global__ void tree_energy_batch_kernel(const float2 *__restrict__ x, const float2 *__restrict__ tree,
+                                         double *__restrict__ xen, const __grid_constant__ TreeBatch b) {
+    __shared__ float2 red[32];
+    const int64_t e = blockIdx.x;
+    int lo_k = 0, hi_k = b.n - 1;
+    while (lo_k < hi_k) {
+        const int mid = (lo_k + hi_k + 1) >> 1;
+        if (b.eprefix[mid] <= e) lo_k = mid;
+        else hi_k = mid - 1;
+    }
+    const TreeItem it = b.it[lo_k];
+    const int bl = (int)(e - b.eprefix[lo_k]);
+    int l = 0;
+    while ((2 << l) - 1 <= bl) ++l;
+    const int v = bl - ((1 << l) - 1);
+    const int64_t N = it.N, K = N >> l;
+    const float2 *X = l == 0 ? x + it.x_off : tree + it.tree_off + 2 * N * (int64_t)(l - 1) + (int64_t)v * K;
+    EnAcc acc;
+    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) acc.add(sq2(X[k]));
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) xen[it.xen_off + bl] = tot;
 }
 
 template <int F, int S, typename TIn>
@@ -899,6 +966,53 @@ sidwt_status build_reference_tree(sidwt_plan *p, const void *x_dev, int32_t ref,
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "reference tree launch");
+}
+
+template <int F>
+static cudaError_t launch_tree_batch(const float2 *x, float2 *tree, double *xen, const TreeBatch &b, int maxJ,
+                                     cudaStream_t s) {
+    const LiftCoef c = lift_coef(F, SIDE_X);
+    int active = b.n;
+    for (int j = 0; j < maxJ; ++j) {
+        while (active > 0 && b.it[active - 1].J <= j) --active;  // sorted by decreasing J
+        const int64_t total = b.nprefix[active];
+        if (total == 0) break;
+        tree_level_batch_kernel<F><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(x, tree, b, j, active, c);
+    }
+    tree_energy_batch_kernel<<<(unsigned)b.eprefix[b.n], 256, 0, s>>>(x, tree, xen, b);
+    return cudaGetLastError();
+}
+
+sidwt_status build_reference_trees(int filter, const float2 *x, float2 *tree, double *xen, const TreeItem *items,
+                                   int n, cudaStream_t s, int *launches) {
+    int nl = 0;
+    for (int k0 = 0; k0 < n; k0 += kTreeBatch) {
+        TreeBatch b;
+        std::memset(&b, 0, sizeof(b));
+        b.n = std::min(kTreeBatch, n - k0);
+        for (int k = 0; k < b.n; ++k) b.it[k] = items[k0 + k];
+        std::stable_sort(b.it, b.it + b.n, [](const TreeItem &a, const TreeItem &c) { return a.J > c.J; });
+        for (int k = 0; k < b.n; ++k) {
+            b.nprefix[k + 1] = b.nprefix[k] + b.it[k].N;
+            b.eprefix[k + 1] = b.eprefix[k] + ((int64_t(2) << b.it[k].J) - 1);
+        }
+        const int maxJ = b.it[0].J;
+        if (b.eprefix[b.n] > 0x7fffffff || (b.nprefix[b.n] + 255) / 256 > 0x7fffffff) {
+            set_error("tree batch too large for one launch");
+            return SIDWT_EINVAL;
+        }
+        cudaError_t e;
+        switch (filter) {
+        case SIDWT_D4: e = launch_tree_batch<SIDWT_D4>(x, tree, xen, b, maxJ, s); break;
+        case SIDWT_LEGALL53: e = launch_tree_batch<SIDWT_LEGALL53>(x, tree, xen, b, maxJ, s); break;
+        case SIDWT_CDF97: e = launch_tree_batch<SIDWT_CDF97>(x, tree, xen, b, maxJ, s); break;
+        default: set_error("batched trees take the float filters"); return SIDWT_EINVAL;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "batched reference trees");
+        nl += maxJ + 1;
+    }
+    if (launches) *launches = nl;
+    return SIDWT_OK;
 }
 
 template <int F, typename T>

@@ -401,6 +401,7 @@ struct sidwt_ragged {
     DevLayout gl;       // layout owned by the captured graph
     void *h_stage = nullptr;
     size_t h_stage_bytes = 0;
+    cudaEvent_t stage_done = nullptr;  // recorded after the last upload's copies from h_stage
     int64_t last_slots = -1;
     // graph
     cudaGraph_t graph = nullptr;
@@ -642,8 +643,10 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
             return SIDWT_ENOMEM;
         }
         r->h_stage_bytes = tot * 2;
-    } else {
-        cudaStreamSynchronize(s);  // the staging buffer may still feed the previous call's copies
+    } else if (r->stage_done) {
+        // the staging buffer may still feed the previous upload's copies: wait
+        // for those alone, not for the rest of the stream
+        cudaEventSynchronize(r->stage_done);
     }
     char *h = static_cast<char *>(r->h_stage);
     size_t o = 0;
@@ -659,6 +662,8 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
     put(d.slot_item, L.slot_item.data(), b4);
     put(d.tc_tiles, L.tc_tiles.data(), b5);
     put(d.maps, L.maps.data(), b7);
+    if (e == cudaSuccess && !r->stage_done) e = cudaEventCreateWithFlags(&r->stage_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(r->stage_done, s);
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "ragged layout upload");
 }
 
@@ -947,6 +952,7 @@ sidwt_status sidwt_ragged_destroy(sidwt_ragged *r) {
     cudaFree(r->norm);
     cudaFree(r->counter);
     for (auto e : r->ev) cudaEventDestroy(e);
+    if (r->stage_done) cudaEventDestroy(r->stage_done);
     if (r->h_stage) cudaFreeHost(r->h_stage);
     delete r;
     return SIDWT_OK;
@@ -1031,6 +1037,95 @@ sidwt_status sidwt_ragged_store_reference(sidwt_ragged *r, sidwt_filter f, int64
     r->tree_used += te;
     r->xen_used += xe;
     *ref_id_out = (int32_t)r->refs.size() - 1;
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_ragged_store_references(sidwt_ragged *r, int64_t n, const int32_t *filters_host,
+                                           const int64_t *N_host, const int32_t *J_host, const void *x_dev,
+                                           const int64_t *x_offsets_host, int64_t x_elems, int32_t *ref_ids_out,
+                                           sidwt_stream stream) {
+    if (!r || n < 0 || (n > 0 && (!filters_host || !N_host || !J_host || !x_dev || !x_offsets_host || !ref_ids_out))) {
+        set_error("NULL argument");
+        return SIDWT_EINVAL;
+    }
+    if (reinterpret_cast<uintptr_t>(x_dev) % 8) {
+        set_error("x_dev is misaligned");
+        return SIDWT_EINVAL;
+    }
+    int64_t te_all = 0, xe_all = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int f = filters_host[i], J = J_host[i];
+        const int64_t N = N_host[i];
+        if (f < 0 || f > 2) {
+            set_error("item " + std::to_string(i) + ": ragged batches take the float filters (D4, LeGall 5/3, CDF 9/7)");
+            return (f == 3 || f == 4) ? SIDWT_EUNSUPPORTED : SIDWT_EINVAL;
+        }
+        if (J < 1 || J > 15 || N < 2 || N > (int64_t(1) << 26) || N % (int64_t(1) << J) != 0) {
+            set_error("item " + std::to_string(i) + ": need 1 <= J <= 15, N a multiple of 2^J, N <= 2^26");
+            return SIDWT_EINVAL;
+        }
+        if (x_offsets_host[i] < 0 || x_offsets_host[i] + N > x_elems) {
+            set_error("item " + std::to_string(i) + " runs past the end of the signal buffer");
+            return SIDWT_EINVAL;
+        }
+        te_all += 2 * (int64_t)J * N;
+        xe_all += (int64_t(2) << J) - 1;
+    }
+    if (n == 0) return SIDWT_OK;
+    if (r->tree_used + te_all > r->tree_cap || r->xen_used + xe_all > r->xen_cap) cudaDeviceSynchronize();
+    sidwt_status st;
+    if ((st = grow(&r->tree, &r->tree_cap, r->tree_used + te_all, r->tree_used, "ragged reference store")) ||
+        (st = grow(&r->xen, &r->xen_cap, r->xen_used + xe_all, r->xen_used, "ragged reference energies")))
+        return st;
+    // offsets of every tree, energy row and stored tensor-core operand
+    std::vector<RefInfo> infos((size_t)n);
+    std::vector<TreeItem> by_filter[3];
+    int64_t tree_at = r->tree_used, xen_at = r->xen_used, tc_at = r->tc_a_used;
+    for (int64_t i = 0; i < n; ++i) {
+        const int f = filters_host[i], J = J_host[i];
+        const int64_t N = N_host[i];
+        RefInfo &ri = infos[(size_t)i];
+        ri = RefInfo{f, N, J, tree_at, xen_at, {}, {}};
+        for (int j = 0; j < 16; ++j) {
+            ri.tc_off[j] = -1;
+            ri.tc_S[j] = 0;
+        }
+        if (r->prec == SIDWT_PREC_BF16X3)
+            for (int j = 0; j <= J && j < 16; ++j) {
+                rtc::Shape sh;
+                if (!rtc::shape_for(N, J, j, &sh, &r->tcw)) continue;
+                ri.tc_off[j] = tc_at;
+                ri.tc_S[j] = (int16_t)sh.S;
+                tc_at += (sh.a_elems + 63) / 64 * 64;
+            }
+        by_filter[f].push_back(TreeItem{x_offsets_host[i], tree_at, xen_at, (int32_t)N, J});
+        tree_at += 2 * (int64_t)J * N;
+        xen_at += (int64_t(2) << J) - 1;
+    }
+    if (tc_at > r->tc_a_used) {
+        if (tc_at > r->tc_a_cap) cudaDeviceSynchronize();
+        if ((st = grow(&r->tc_a, &r->tc_a_cap, tc_at, r->tc_a_used, "stored tensor-core operands"))) return st;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const float2 *x = static_cast<const float2 *>(x_dev);
+    for (int f = 0; f < 3; ++f)
+        if (!by_filter[f].empty() &&
+            (st = build_reference_trees(f, x, r->tree, r->xen, by_filter[f].data(), (int)by_filter[f].size(), s,
+                                        nullptr)))
+            return st;
+    if (tc_at > r->tc_a_used) {
+        std::vector<rtc::PackItem> pk;
+        pk.reserve((size_t)n);
+        for (const RefInfo &ri : infos) pk.push_back(rtc::PackItem{ri.tree_off, ri.N, ri.J, ri.tc_off, ri.tc_S});
+        if ((st = rtc::pack_stored_batch(r->tree, pk.data(), (int)pk.size(), r->tc_a, s, nullptr))) return st;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        ref_ids_out[i] = (int32_t)r->refs.size();
+        r->refs.push_back(infos[(size_t)i]);
+    }
+    r->tree_used = tree_at;
+    r->xen_used = xen_at;
+    r->tc_a_used = tc_at;
     return SIDWT_OK;
 }
 

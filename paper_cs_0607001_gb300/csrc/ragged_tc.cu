@@ -403,6 +403,11 @@ struct StoreScales {
     int n;
 };
 
+// Element `local` of one scale's packed stored operand; the bands of the
+// scale's level start at tree[z.level_off] and are N elements apart.
+__device__ __forceinline__ __nv_bfloat16 stored_element(const float2 *__restrict__ tree, int64_t N,
+                                                        const StoreScale &z, int64_t local);
+
 // Stored operand of one signal: element [b nv + v][h][row][blk][2 c + plane][e]
 // = hi (h = 0) or lo part of plane(w_{v,b}[(k0 + c + 8 s) mod K']), plane 0
 // Re, 1 Im, at polyphase sample s = row Lr + 8 blk + e.
@@ -412,27 +417,58 @@ __global__ void pack_stored_kernel(const float2 *__restrict__ tree, int64_t N, S
         int k = 0;
         while (k + 1 < sc.n && e >= sc.s[k + 1].first) ++k;
         const StoreScale &z = sc.s[k];
-        const int64_t local = e - z.first;
-        const int ee = (int)(local & 7);
-        const int ch = (int)((local >> 3) & 15);
-        const int nblk = z.Lr >> 3;
-        int64_t rest = local >> 7;
-        const int blk = (int)(rest % nblk);
-        rest /= nblk;
-        const int64_t row = rest % z.Rs;
-        rest /= z.Rs;
-        const int h = (int)(rest & 1);
-        const int vb = (int)(rest >> 1);
-        const int b = vb / z.nv, v = vb - b * z.nv;
-        const int c = ch >> 1, plane = ch & 1;
-        const int64_t s = row * z.Lr + 8 * blk + ee;
-        int64_t idx = ((int64_t)z.k0 + c + 8 * s) % z.Kp;
-        if (idx < 0) idx += z.Kp;
-        const float2 x = tree[z.level_off + (int64_t)b * N + (int64_t)v * z.Kp + idx];
-        __nv_bfloat16 hi, lo;
-        split_bf16(plane ? x.y : x.x, hi, lo);
-        out[z.out_off + local] = h ? lo : hi;
+        out[z.out_off + e - z.first] = stored_element(tree, N, z, e - z.first);
     }
+}
+
+// The stored operands of many signals in one launch: entry k is one scale
+// of one signal (level_off absolute in the tree buffer, N its band stride);
+// entries ordered by `first`, found by binary search.
+constexpr int kPackBatch = 240;
+struct StoreScaleB {
+    StoreScale z;
+    int64_t N;
+};
+struct PackBatch {
+    int32_t n, pad;
+    StoreScaleB s[kPackBatch];
+};
+
+__global__ void pack_stored_batch_kernel(const float2 *__restrict__ tree, const __grid_constant__ PackBatch b,
+                                         int64_t total, __nv_bfloat16 *__restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = b.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.s[mid].z.first <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        const StoreScale &z = b.s[lo].z;
+        out[z.out_off + e - z.first] = stored_element(tree, b.s[lo].N, z, e - z.first);
+    }
+}
+
+__device__ __forceinline__ __nv_bfloat16 stored_element(const float2 *__restrict__ tree, int64_t N,
+                                                    const StoreScale &z, int64_t local) {
+    const int ee = (int)(local & 7);
+    const int ch = (int)((local >> 3) & 15);
+    const int nblk = z.Lr >> 3;
+    int64_t rest = local >> 7;
+    const int blk = (int)(rest % nblk);
+    rest /= nblk;
+    const int64_t row = rest % z.Rs;
+    rest /= z.Rs;
+    const int h = (int)(rest & 1);
+    const int vb = (int)(rest >> 1);
+    const int b = vb / z.nv, v = vb - b * z.nv;
+    const int c = ch >> 1, plane = ch & 1;
+    const int64_t s = row * z.Lr + 8 * blk + ee;
+    int64_t idx = ((int64_t)z.k0 + c + 8 * s) % z.Kp;
+    if (idx < 0) idx += z.Kp;
+    const float2 x = tree[z.level_off + (int64_t)b * N + (int64_t)v * z.Kp + idx];
+    __nv_bfloat16 hi, lo;
+    split_bf16(plane ? x.y : x.x, hi, lo);
+    return h ? lo : hi;
 }
 
 
@@ -541,6 +577,52 @@ sidwt_status pack_stored(const float2 *tree, int64_t N, int J, const int64_t *a_
     pack_stored_kernel<<<(unsigned)blocks, 256, 0, s>>>(tree, N, sc, total, static_cast<__nv_bfloat16 *>(abuf));
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "stored tensor-core operand packing");
+}
+
+sidwt_status pack_stored_batch(const float2 *tree, const PackItem *items, int n, void *abuf, cudaStream_t s,
+                               int *launches) {
+    PackBatch b;
+    std::memset(&b, 0, sizeof(b));
+    int64_t total = 0;
+    int nl = 0;
+    auto flush = [&]() -> sidwt_status {
+        if (b.n == 0) return SIDWT_OK;
+        const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
+        pack_stored_batch_kernel<<<(unsigned)blocks, 256, 0, s>>>(tree, b, total,
+                                                                   static_cast<__nv_bfloat16 *>(abuf));
+        cudaError_t e = cudaGetLastError();
+        ++nl;
+        b.n = 0;
+        total = 0;
+        return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "batched stored tensor-core operand packing");
+    };
+    for (int k = 0; k < n; ++k) {
+        const PackItem &it = items[k];
+        for (int j = 0; j <= it.J && j < 16; ++j) {
+            Shape sh;
+            if (it.a_off[j] < 0 || !shape_with(it.N, it.J, j, it.S_of[j], &sh)) continue;
+            if (b.n == kPackBatch) {
+                sidwt_status st = flush();
+                if (st) return st;
+            }
+            StoreScaleB &e = b.s[b.n++];
+            e.N = it.N;
+            StoreScale &z = e.z;
+            z.out_off = it.a_off[j];
+            z.first = total;
+            z.count = sh.a_elems;
+            z.level_off = it.tree_off + 2 * it.N * (int64_t)(sh.lev - 1);
+            z.Kp = (int32_t)sh.Kp;
+            z.nv = sh.nv;
+            z.Lr = sh.Lr;
+            z.Rs = sh.Rs;
+            z.k0 = sh.k0;
+            total += sh.a_elems;
+        }
+    }
+    sidwt_status st = flush();
+    if (launches) *launches = nl;
+    return st;
 }
 
 size_t map_bytes() { return sizeof(CUtensorMap); }

@@ -54,9 +54,21 @@ int64_t footprint(int64_t N, int J, int precision) {
     return b;
 }
 
-__global__ void pad_kernel(const float2 *__restrict__ wave, int64_t wlen, float2 *__restrict__ x, int64_t N) {
+// The waveforms of a batch's new stored signals, each zero-padded to its
+// request's N at its offset of the lane's signal buffer: grid.y = item.
+constexpr int kPadBatch = 64;
+struct PadBatch {
+    const float2 *wave[kPadBatch];
+    int64_t wlen[kPadBatch], off[kPadBatch], N[kPadBatch];
+};
+
+__global__ void pad_batch_kernel(const __grid_constant__ PadBatch b, float2 *__restrict__ x) {
+    const int k = blockIdx.y;
+    const float2 *w = b.wave[k];
+    const int64_t wl = b.wlen[k], N = b.N[k];
+    float2 *o = x + b.off[k];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = i < wlen ? wave[i] : make_float2(0.f, 0.f);
+        o[i] = i < wl ? w[i] : make_float2(0.f, 0.f);
 }
 
 struct Lane {
@@ -184,6 +196,16 @@ sidwt_status launch_lane(sidwt_server *s, Lane &L) {
     }
     std::vector<int32_t> ids;
     std::vector<int64_t> offs;
+    // signals not yet resident: padded into the lane's signal buffer at the
+    // request's offset and stored together (one batched tree build)
+    std::vector<int32_t> nf, nJ;
+    std::vector<int64_t> nN, noff;
+    std::vector<uint64_t> nkey;
+    std::unordered_map<uint64_t, int> pending;  // key -> index in the new signals
+    std::vector<int> wait_new;                  // per request: index of the new signal it waits for, or -1
+    PadBatch pb;
+    int npad = 0;
+    int64_t maxN = 0;
     int64_t off = 0, slots = 0, hits = 0, misses = 0;
     for (Request *r : L.batch) {
         cudaError_t e = cudaMemcpyAsync(L.y + off, r->y_host, (size_t)r->N * 8, cudaMemcpyHostToDevice, st);
@@ -191,23 +213,53 @@ sidwt_status launch_lane(sidwt_server *s, Lane &L) {
         const uint64_t key = ref_key(r->wave, r->filter, r->N, r->J);
         auto it = L.cache.find(key);
         int32_t rid = -1;
+        int wn = -1;
         if (it != L.cache.end()) {
             rid = it->second;
             ++hits;
+        } else if (pending.count(key)) {
+            wn = pending[key];
+            ++hits;
         } else {
-            const int64_t wl = std::min<int64_t>(s->wave_len[(size_t)r->wave], r->N);
-            pad_kernel<<<(unsigned)std::min<int64_t>(1024, (r->N + 255) / 256), 256, 0, st>>>(
-                s->waves[(size_t)r->wave], wl, L.x + off, r->N);
-            sidwt_status ss = sidwt_ragged_store_reference(L.rg, (sidwt_filter)r->filter, r->N, r->J, L.x + off, &rid,
-                                                           reinterpret_cast<sidwt_stream>(st));
-            if (ss) return ss;
-            L.cache[key] = rid;
+            wn = (int)nkey.size();
+            pending[key] = wn;
+            nkey.push_back(key);
+            nf.push_back(r->filter);
+            nN.push_back(r->N);
+            nJ.push_back(r->J);
+            noff.push_back(off);
+            pb.wave[npad] = s->waves[(size_t)r->wave];
+            pb.wlen[npad] = std::min<int64_t>(s->wave_len[(size_t)r->wave], r->N);
+            pb.off[npad] = off;
+            pb.N[npad] = r->N;
+            maxN = std::max(maxN, r->N);
+            ++npad;
             ++misses;
+            if (npad == kPadBatch) {
+                pad_batch_kernel<<<dim3((unsigned)std::min<int64_t>(64, (maxN + 255) / 256), (unsigned)npad), 256, 0,
+                                   st>>>(pb, L.x);
+                npad = 0;
+                maxN = 0;
+            }
         }
         ids.push_back(rid);
+        wait_new.push_back(wn);
         offs.push_back(off);
         off += r->N;
         slots += r->J + 1;
+    }
+    if (npad > 0)
+        pad_batch_kernel<<<dim3((unsigned)std::min<int64_t>(64, (maxN + 255) / 256), (unsigned)npad), 256, 0, st>>>(
+            pb, L.x);
+    if (!nkey.empty()) {
+        std::vector<int32_t> nid(nkey.size());
+        sidwt_status ss = sidwt_ragged_store_references(L.rg, (int64_t)nkey.size(), nf.data(), nN.data(), nJ.data(),
+                                                        L.x, noff.data(), off, nid.data(),
+                                                        reinterpret_cast<sidwt_stream>(st));
+        if (ss) return ss;
+        for (size_t k = 0; k < nkey.size(); ++k) L.cache[nkey[k]] = nid[k];
+        for (size_t b = 0; b < ids.size(); ++b)
+            if (wait_new[b] >= 0) ids[b] = nid[(size_t)wait_new[b]];
     }
     {
         std::lock_guard<std::mutex> lock(s->mu);

@@ -248,6 +248,23 @@ uint32_t debug_stall_flags();
 // SIDWT tree of one stored pulse (x_dev: complex64[N] or int16x2[N]) into
 // reference slot ref of the plan, plus its energies.
 sidwt_status build_reference_tree(sidwt_plan *p, const void *x_dev, int32_t ref, cudaStream_t s);
+// Stored trees of up to kTreeBatch float signals of one filter in one pass
+// (kernel parameters carry the descriptors): item k's pulse at x + x_off,
+// its tree (2 J N elements) at tree + tree_off, its energies at
+// xen + xen_off.  J from 1 to 15.
+struct TreeItem {
+    int64_t x_off, tree_off, xen_off;
+    int32_t N, J;
+};
+constexpr int kTreeBatch = 64;
+struct TreeBatch {
+    int32_t n, pad;
+    TreeItem it[kTreeBatch];           // sorted by decreasing J
+    int64_t nprefix[kTreeBatch + 1];   // sum of N over the items before k
+    int64_t eprefix[kTreeBatch + 1];   // sum of 2^(J+1) - 1 (energy blocks) before k
+};
+sidwt_status build_reference_trees(int filter, const float2 *x, float2 *tree, double *xen, const TreeItem *items,
+                                   int n, cudaStream_t s, int *launches);
 // Received analysis of B pulses into the plan's pyramid workspace (+ energies).
 sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStream_t s);
 int analyze_launch_count(const sidwt_plan *p);
@@ -357,6 +374,16 @@ int64_t operand_elems(int64_t N, int J);
 // S_of[j] its tile width.
 sidwt_status pack_stored(const float2 *tree, int64_t N, int J, const int64_t *a_off, const int16_t *S_of, void *abuf,
                          cudaStream_t s);
+// The same for many signals whose trees start at tree + tree_off, in as few
+// launches as the kernel-parameter tables allow.
+struct PackItem {
+    int64_t tree_off, N;
+    int J;
+    const int64_t *a_off;
+    const int16_t *S_of;
+};
+sidwt_status pack_stored_batch(const float2 *tree, const PackItem *items, int n, void *abuf, cudaStream_t s,
+                               int *launches);
 sidwt_status encode_maps(void *two_maps, const void *a_base, const void *b_base, const Shape &sh);
 size_t map_bytes();
 // R: optional complex64 r output (each tile writes its rows at r_at / r_mid), or null

@@ -100,6 +100,7 @@ def lib():
     L.sidwt_ragged_num_refs.argtypes = [_vp]
     L.sidwt_ragged_num_refs.restype = _i32
     L.sidwt_ragged_store_reference.argtypes = [_vp, ctypes.c_int, _i64, ctypes.c_int, _vp, ctypes.POINTER(_i32), _vp]
+    L.sidwt_ragged_store_references.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]
     L.sidwt_ragged_correlate.argtypes = [_vp, _i64, _vp, _vp, _vp, _i64, _vp]
     L.sidwt_ragged_correlate_r.argtypes = [_vp, _i64, _vp, _vp, _vp, _i64, _vp, _i64, _vp]
     L.sidwt_ragged_graph_create.argtypes = [_vp, _i64, _vp, _vp, _vp, _i64, ctypes.POINTER(_i32)]
@@ -128,6 +129,7 @@ def lib():
                  "sidwt_correlate_host", "sidwt_correlate_host_async", "sidwt_check", "sidwt_reset_references", "sidwt_set_timing",
                  "sidwt_read_timing", "sidwt_correlate_static", "sidwt_tc_selftest", "sidwt_debug_stall", "sidwt_ragged_create",
                  "sidwt_ragged_destroy", "sidwt_ragged_reserve", "sidwt_ragged_store_reference",
+                 "sidwt_ragged_store_references",
                  "sidwt_ragged_correlate", "sidwt_ragged_correlate_r", "sidwt_ragged_graph_create", "sidwt_ragged_graph_launch",
                  "sidwt_ragged_peaks", "sidwt_ragged_autotune", "sidwt_ragged_tuning", "sidwt_ragged_set_timing",
                  "sidwt_ragged_read_timing", "sidwt_ragged_reset_references", "sidwt_server_create",
@@ -398,6 +400,24 @@ class Ragged:
                                                   ctypes.byref(rid), _stream(stream)))
         self.refs.append((_filter_id(filter), int(N), int(J)))
         return rid.value
+
+    def store_references(self, filters, Ns, Js, x: torch.Tensor, offsets, stream=None) -> list[int]:
+        """Store many signals at once (sidwt_ragged_store_references): item i
+        is x[offsets[i]:offsets[i] + Ns[i]] (x a packed CUDA complex64 buffer)."""
+        if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("signals must be a contiguous CUDA complex64 buffer")
+        f = np.ascontiguousarray([_filter_id(v) for v in filters], dtype=np.int32)
+        n = np.ascontiguousarray(Ns, dtype=np.int64)
+        j = np.ascontiguousarray(Js, dtype=np.int32)
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        if not (f.shape == n.shape == j.shape == off.shape):
+            raise ValueError("one filter, N, J and offset per item")
+        ids = np.zeros(f.shape, dtype=np.int32)
+        _raise(lib().sidwt_ragged_store_references(self._h, f.size, f.ctypes.data, n.ctypes.data, j.ctypes.data,
+                                                   _ptr(x), off.ctypes.data, x.numel(), ids.ctypes.data,
+                                                   _stream(stream)))
+        self.refs.extend((int(a), int(b), int(c)) for a, b, c in zip(f, n, j))
+        return ids.tolist()
 
     def slots_of(self, ref_ids) -> tuple[np.ndarray, int]:
         """First peak slot of every item and the total slot count."""

@@ -143,3 +143,38 @@ def test_ragged_r_output_too_small_is_rejected():
         st = L.sidwt_ragged_correlate_r(rg._h, 1, ids.ctypes.data, off.ctypes.data, x.data_ptr(), 256,
                                         r.data_ptr(), r.numel(), torch.cuda.current_stream().cuda_stream)
         assert st == 1 and b"r_dev holds" in L.sidwt_last_error()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_batched_store_equals_one_by_one_store(batch, precision):
+    """sidwt_ragged_store_references (all trees of a batch built together)
+    gives the same stored trees, energies and packed operands as storing the
+    signals one at a time: the same batch's peaks are bit-identical, and so is
+    r up to which of the tensor-core tiles' repeated advances (each summed in
+    its own order) lands last."""
+    from paper_cs_0607001_gb300 import sidwt
+    refs, ypack, offsets, delays, ref_r, bounds = batch
+    xpack = U.to_dev_c64(np.concatenate(refs))
+    yd = U.to_dev_c64(ypack)
+    out = []
+    for batched in (False, True):
+        with sidwt.Ragged() as rg:
+            rg.set_precision(precision)
+            if batched:
+                ids = rg.store_references([s[0] for s in SPECS], [s[1] for s in SPECS], [s[2] for s in SPECS], xpack,
+                                          offsets)
+            else:
+                ids = [rg.store_reference(f, N, J, xpack[o:o + N]) for (f, N, J), o in zip(SPECS, offsets)]
+            n, r = rg.correlate_r(ids, offsets, yd)
+            lag, mag, norm = rg.peaks(n)
+            rg.check()
+            torch.cuda.synchronize()
+            out.append((r.cpu().numpy(), lag.cpu().numpy(), mag.cpu().numpy(), norm.cpu().numpy()))
+    for a, b in zip(out[0][1:], out[1][1:]):
+        np.testing.assert_array_equal(a, b)
+    r0, r1 = out[0][0], out[1][0]
+    if precision == "fp32":
+        np.testing.assert_array_equal(r0, r1)
+    else:
+        assert np.abs(r0 - r1).max() <= 1e-6 * np.abs(r0).max()
