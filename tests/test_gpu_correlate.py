@@ -49,11 +49,21 @@ def test_correlation_matches_oracle(oracle, fname, fid, N, J, B, nrefs):
     X = w["refs"][w["ref_ids"]].astype(np.complex128)
     Y = w["y"].astype(np.complex128)
     lo, mo, no, ro, _ = oracle.correlate_batch(fid, X, Y, J, form=1, want_r=True)
+    ex = [oracle.tree_x(fid, x.astype(np.complex128), J)[1] for x in w["refs"]]
     for b in range(B):
         U.check_r(r[b], ro[b], what=f"{fname} pulse {b}")
         U.check_peak_lags(lag[b], ro[b], U.RTOL_FP32, what=f"{fname} pulse {b}")
         np.testing.assert_allclose(mag[b], np.abs(ro[b][np.arange(J + 1), lag[b]]), rtol=2e-5)
         np.testing.assert_allclose(norm[b], no[b], rtol=5e-5, atol=1e-6)
+        # the normalisation alone: the GPU's |r| at its lag over the oracle's FP64
+        # energies (eq. 1), so that only the GPU energies' error is left, held to
+        # the energies' own tolerance (2e-6 J, as in the lifting tests)
+        ey = oracle.pyramid_y(fid, Y[b], J)[1]
+        for j in range(J + 1):
+            D = int(lag[b][j])
+            e_x = ex[w["ref_ids"][b]][(1 << j) - 1 + (D & ((1 << j) - 1))]
+            want = float(mag[b][j]) / np.sqrt(e_x * ey[j])
+            assert abs(norm[b][j] - want) <= 2e-6 * J * want + 1e-12, (b, j, norm[b][j], want)
 
 
 @pytest.mark.parametrize("fname,fid", [("legall53_int", 3), ("cdf97_int", 4)])
