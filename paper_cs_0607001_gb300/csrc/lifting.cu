@@ -636,13 +636,14 @@ __device__ __forceinline__ void out_pair_i16(const short2 *in, int H, int n, int
 constexpr int kPipeMaxLevels = 16;
 constexpr int kPipeThreads = 512;
 
-template <int F, typename T>
+template <int F, typename T, bool RAGGED = false>
 __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *__restrict__ y_in, int64_t N, int J,
                                                                        int64_t B, float2 *__restrict__ pyr_f,
                                                                        int2 *__restrict__ pyr_i, int64_t pyr_elems,
                                                                        double *__restrict__ yen, LiftCoef c,
                                                                        int32_t *__restrict__ err, int nbuf,
-                                                                       int stall) {
+                                                                       int stall,
+                                                                       const RaggedLift *__restrict__ items) {
     constexpr bool INT = is_int_filter(F);
     constexpr int IN_BYTES = INT ? 4 : 8;
     extern __shared__ __align__(16) unsigned char smraw[];  // 16-byte aligned: enough for the bulk copies
@@ -650,12 +651,13 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
     __shared__ float2 redf[kPipeMaxLevels][kPipeThreads / 32];
     __shared__ long long redi[kPipeMaxLevels][kPipeThreads / 32];
     __shared__ int sfail;
+    // RAGGED: item b of `items` has its own N, J and places (pulse, pyramid
+    // row, energies); the shared buffers are sized for N, the longest of them
     const uint32_t bytes = (uint32_t)(N * IN_BYTES);
     const size_t inb = ((size_t)bytes + 127) & ~(size_t)127;
     unsigned char *const buf0 = smraw, *const buf1 = smraw + inb;
     T *W = reinterpret_cast<T *>(smraw + nbuf * inb);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int Nh = (int)(N / 2);
     const char *y = reinterpret_cast<const char *>(y_in);
     const int64_t G = gridDim.x;
     pdl_release();  // the correlation kernel may be scheduled now; it waits for this grid's writes
@@ -669,7 +671,9 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
     __syncthreads();
     // stall (test hook, sidwt_debug_stall): no copy is issued, so the first
     // wait runs out and the CTA records the timeout with nothing in flight
-    if (tid == 0 && !stall) pipe_load(buf0, y + (int64_t)blockIdx.x * bytes, bytes, &bar[0]);
+    auto src = [&](int64_t q) { return RAGGED ? y + items[q].y_off * IN_BYTES : y + q * (int64_t)bytes; };
+    auto len = [&](int64_t q) { return RAGGED ? (uint32_t)(items[q].N * IN_BYTES) : bytes; };
+    if (tid == 0 && !stall) pipe_load(buf0, src(blockIdx.x), len(blockIdx.x), &bar[0]);
     int i = 0;
     int64_t issued = stall ? 0 : 1, landed = 0;  // copies issued / waited for (thread 0's bookkeeping)
     for (int64_t b = blockIdx.x; b < B; b += G, ++i) {
@@ -682,11 +686,11 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
             // the buffer written next held a finished pulse, whose accesses ended at the last barrier
             if (nbuf == 2 && b + G < B) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                pipe_load(s ? buf0 : buf1, y + (b + G) * (int64_t)bytes, bytes, &bar[s ^ 1]);
+                pipe_load(s ? buf0 : buf1, src(b + G), len(b + G), &bar[s ^ 1]);
                 ++issued;
             } else if (nbuf == 1 && i > 0) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                pipe_load(buf0, y + b * (int64_t)bytes, bytes, &bar[0]);
+                pipe_load(buf0, src(b), len(b), &bar[0]);
                 ++issued;
             }
         }
@@ -694,15 +698,19 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
         __syncthreads();
         if (sfail) break;
         if (tid == 0) ++landed;
-        float2 *pf = pyr_f + b * pyr_elems;
+        const int64_t Nb = RAGGED ? (int64_t)items[b].N : N;
+        const int Jb = RAGGED ? items[b].J : J;
+        const int Nhb = (int)(Nb / 2);
+        float2 *pf = RAGGED ? pyr_f + items[b].pyr_off : pyr_f + b * pyr_elems;
         int2 *pi = INT ? pyr_i + b * pyr_elems : nullptr;
+        double *yb = RAGGED ? yen + items[b].yen_off : yen + b * (J + 1);
 
         // level-0 energy from the landed input
         {
             long long eni = 0;
             if constexpr (INT) {
                 const short4 *q = reinterpret_cast<const short4 *>(cur);
-                for (int n = tid; n < Nh; n += blockDim.x) {
+                for (int n = tid; n < Nhb; n += blockDim.x) {
                     const short4 v = q[n];
                     eni += sq2i(make_int2(v.x, v.y)) + sq2i(make_int2(v.z, v.w));
                 }
@@ -711,7 +719,7 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
             } else {
                 const float4 *q = reinterpret_cast<const float4 *>(cur);
                 float ens = 0.f;
-                for (int n = tid; n < Nh; n += blockDim.x) {
+                for (int n = tid; n < Nhb; n += blockDim.x) {
                     const float4 v = q[n];
                     ens = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, ens))));
                 }
@@ -722,9 +730,9 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
                 if (lane == 0) redf[0][warp] = make_float2(ens, 0.f);
             }
         }
-        for (int l = 1; l <= J; ++l) {
-            const int H = (int)(N >> l);
-            const int64_t off = 2 * N - 4 * (int64_t)H;
+        for (int l = 1; l <= Jb; ++l) {
+            const int H = (int)(Nb >> l);
+            const int64_t off = 2 * Nb - 4 * (int64_t)H;
             T *out = (l & 1) ? W : reinterpret_cast<T *>(cur);
             const T *in = (l & 1) ? reinterpret_cast<const T *>(cur) : W;
             EnAcc en;
@@ -799,11 +807,11 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
             }
             __syncthreads();
         }
-        if (tid <= J) {
+        if (tid <= Jb) {
             if constexpr (INT) {
                 long long t = 0;
                 for (int w = 0; w < nw; ++w) t += redi[tid][w];
-                yen[b * (J + 1) + tid] = (double)t;
+                yb[tid] = (double)t;
             } else {
                 EnAcc t;
                 for (int w = 0; w < nw; ++w) {
@@ -812,7 +820,7 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
                     u.lo = redf[tid][w].y;
                     t.add(u);
                 }
-                yen[b * (J + 1) + tid] = t.total();
+                yb[tid] = t.total();
             }
         }
         // J = 0 cannot happen (J >= 1): the level loop's last barrier orders
@@ -1092,23 +1100,23 @@ sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStre
         switch (p->filter) {
         case SIDWT_D4:
             analyze_pipe_kernel<SIDWT_D4, float2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
-                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf, stall);
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf, stall, nullptr);
             break;
         case SIDWT_LEGALL53:
             analyze_pipe_kernel<SIDWT_LEGALL53, float2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
-                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf, stall);
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf, stall, nullptr);
             break;
         case SIDWT_CDF97:
             analyze_pipe_kernel<SIDWT_CDF97, float2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
-                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf, stall);
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf, stall, nullptr);
             break;
         case SIDWT_CDF97_INT:
             analyze_pipe_kernel<SIDWT_CDF97_INT, int2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
-                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf, stall);
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf, stall, nullptr);
             break;
         default:
             analyze_pipe_kernel<SIDWT_LEGALL53_INT, int2><<<(unsigned)grid, kPipeThreads, pipe_smem, s>>>(
-                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf, stall);
+                y_dev, N, J, B, p->pyr_f, p->pyr_i, p->pyr_elems, p->yen, c, p->err, nbuf, stall, nullptr);
             break;
         }
         e = cudaGetLastError();
@@ -1154,6 +1162,10 @@ sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStre
 // Ragged batches
 // ---------------------------------------------------------------------------
 int64_t analyze_smem_max_n() { return (int64_t)kSmemLimit / 12; }
+// two input buffers of N complex64 and the level-1 buffer of N / 2
+int64_t analyze_pipe_max_n() { return (int64_t)kPipeSmemLimit / 20 / 128 * 128; }
+// up to 2048 samples four CTAs fit an SM, up to 5120 two
+int64_t analyze_pipe_class_max(int k) { return k == 0 ? 2048 : (k == 1 ? 5120 : analyze_pipe_max_n()); }
 
 // Per-level window lifting of long pulses: block (x, item) computes outputs
 // x*128.. of item's level l from its level l-1 approximation (y at l = 1).
@@ -1200,6 +1212,136 @@ __global__ void ragged_energy_kernel(const float2 *__restrict__ y, const RaggedL
     if (threadIdx.x == 0) yen[it.yen_off + l] = t;
 }
 
+
+// Long pulses of a ragged batch, in tiles of kTileSamples samples: the CTA
+// loads its samples and a periodic halo of kTileHalo on each side with
+// 128-bit loads, lifts levels 1..L in shared memory (each level's valid range
+// shrinks by the windows' reach; the halo keeps the tile's own range valid
+// down to level 5), writes the tile's own part of every level to the pyramid
+// and leaves per-level energy partials.  Output pair n of a level reads the
+// input pairs n - 3 .. n + 2; the level's buffer holds pairs [p0, p1) and the
+// outputs [n0, n1) = [p0 + 3, p1 - 3) rounded inwards to even n.
+constexpr int kTileThreads = 512;
+constexpr int kTileSmem = (kTileSamples + 2 * kTileHalo) * 8 * 3 / 2;
+
+template <int F>
+__global__ void __launch_bounds__(kTileThreads, 3) ragged_tile_kernel(const float2 *__restrict__ y,
+                                                                   const RaggedTile *__restrict__ tiles,
+                                                                   float2 *__restrict__ pyr, double *__restrict__ part,
+                                                                   LiftCoef c) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ float2 red[32];
+    constexpr bool D4 = (F == SIDWT_D4);
+    const RaggedTile t = tiles[blockIdx.x];
+    const int64_t N = t.N;
+    float2 *in = reinterpret_cast<float2 *>(smraw);
+    float2 *out = in + (kTileSamples + 2 * kTileHalo);
+    int64_t s0 = (int64_t)t.t0 - kTileHalo;  // first sample of the level held in `in`
+    int cnt = t.Tc + 2 * kTileHalo;
+    {
+        const float4 *y4 = reinterpret_cast<const float4 *>(y + t.y_off);
+        float4 *d4 = reinterpret_cast<float4 *>(in);
+        // periodic; N and s0 are even, so a pair never straddles the wrap, and
+        // the halo is shorter than the pulse (N > kTileSamples + 2 kTileHalo on
+        // this path), so one wrap at most
+        for (int k = threadIdx.x; k < cnt / 2; k += blockDim.x) {
+            int64_t a = s0 + 2 * k;
+            a += a < 0 ? N : 0;
+            a -= a >= N ? N : 0;
+            d4[k] = y4[a / 2];
+        }
+    }
+    __syncthreads();
+    {
+        EnAcc acc;
+        for (int k = threadIdx.x; k < t.Tc; k += blockDim.x) acc.add(sq2(in[kTileHalo + k]));
+        const double e0 = block_sum(acc, red);
+        if (threadIdx.x == 0) part[t.part_off] = e0;
+    }
+    for (int l = 1; l <= t.L; ++l) {
+        const int64_t p0 = s0 / 2, p1 = (s0 + cnt) / 2;
+        int64_t n0 = p0 + 3, n1 = p1 - 3;
+        n0 += n0 & 1;
+        n1 -= n1 & 1;
+        const int64_t K = N >> l, core0 = (int64_t)t.t0 >> l;
+        // outputs are indexed from n0 in 32 bits (a tile level holds at most kTileSamples + 2 kTileHalo)
+        const int m_end = (int)(n1 - n0), kofs = (int)(n0 - p0);
+        const int c0 = (int)(core0 - n0), c1 = c0 + (t.Tc >> l);
+        float2 *pl = pyr + t.pyr_off + 2 * N - 4 * K + n0, *ph = pl + K;
+        const float4 *q = reinterpret_cast<const float4 *>(in) + kofs;
+        EnAcc acc;
+        for (int m = threadIdx.x; m < m_end; m += blockDim.x) {
+            const int k = m;
+            float2 E[5], O[5];
+            float4 prev = D4 ? q[k - 3] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                const float4 cur = q[k - 2 + i];
+                E[i] = make_float2(cur.x, cur.y);
+                O[i] = D4 ? make_float2(prev.z, prev.w) : make_float2(cur.z, cur.w);  // D4 odd phase: v[2m-1]
+                prev = cur;
+            }
+            lift_window<F, SIDE_Y, 2>(E, O, c);
+            const float2 lo = scale2(c.ce, E[2]);
+            const float2 hi = D4 ? scale2(c.co, make_float2(E[2].x + O[1].x, E[2].y + O[1].y)) : scale2(c.co, O[2]);
+            out[m] = lo;
+            if (m >= c0 && m < c1) {
+                pl[m] = lo;
+                ph[m] = hi;
+                acc.add(sq2(lo));
+            }
+        }
+        const double el = block_sum(acc, red);  // its barriers also end this level's reads of `in`
+        if (threadIdx.x == 0) part[t.part_off + l] = el;
+        float2 *tmp = in;
+        in = out;
+        out = tmp;
+        s0 = n0;
+        cnt = (int)(n1 - n0);
+        __syncthreads();
+    }
+}
+
+// The tails of the tiled pulses: the energies of levels 0..L from the tiles'
+// partials (summed in tile order), then levels L + 1..J from c_L in shared
+// memory (the pyramid and energy pointers shifted so that its level l lands
+// at level L + l).
+template <int F>
+__global__ void __launch_bounds__(kAnalyzeThreads) ragged_tail_kernel(const RaggedTail *__restrict__ tails,
+                                                                      const double *__restrict__ part,
+                                                                      float2 *__restrict__ pyr,
+                                                                      double *__restrict__ yen, LiftCoef c) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ float2 red[32];
+    __shared__ long long redi[32];
+    const RaggedTail tl = tails[blockIdx.x];
+    const int L = tl.L, J = tl.it.J;
+    const int last = J > L ? L - 1 : L;  // level L's energy comes from the lifting below when it goes on
+    if ((int)threadIdx.x <= last) {
+        double e = 0.0;
+        for (int k = 0; k < tl.ntiles; ++k) e += part[tl.part_off + (int64_t)k * (kTileLevels + 1) + threadIdx.x];
+        yen[tl.it.yen_off + threadIdx.x] = e;
+    }
+    if (J > L) {
+        const int64_t N = tl.it.N, N2 = N >> L;
+        float2 *base = pyr + tl.it.pyr_off;
+        analyze_one<F, float2>(base + 2 * N - 4 * N2, N2, J - L, base + 2 * N - 2 * N2, nullptr,
+                               yen + tl.it.yen_off + L, c, reinterpret_cast<float2 *>(smraw), red, redi);
+    }
+}
+
+template <int F>
+static cudaError_t launch_ragged_tiles(const RaggedTile *tiles, int ntiles, const RaggedTail *tails, int ntails,
+                                       int64_t maxN2, const float2 *y, float2 *pyr, double *yen, double *part,
+                                       cudaStream_t s) {
+    const LiftCoef c = lift_coef(F, SIDE_Y);
+    ragged_tile_kernel<F><<<ntiles, kTileThreads, kTileSmem, s>>>(y, tiles, pyr, part, c);
+    ragged_tail_kernel<F><<<ntails, kAnalyzeThreads, (size_t)(maxN2 + maxN2 / 2) * 8, s>>>(tails, part, pyr, yen, c);
+    return cudaGetLastError();
+}
+
+int64_t tile_tail_max_n() { return (int64_t)kSmemLimit / 12; }
+
 // The ragged kernels get the whole shared-memory budget once, outside any
 // stream capture, so that launching them needs no attribute call.
 cudaError_t prepare_ragged_kernels() {
@@ -1211,7 +1353,47 @@ cudaError_t prepare_ragged_kernels() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(analyze_ragged_kernel<SIDWT_CDF97>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSmemLimit);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ragged_tile_kernel<SIDWT_D4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ragged_tile_kernel<SIDWT_LEGALL53>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ragged_tile_kernel<SIDWT_CDF97>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ragged_tail_kernel<SIDWT_D4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ragged_tail_kernel<SIDWT_LEGALL53>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ragged_tail_kernel<SIDWT_CDF97>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(analyze_pipe_kernel<SIDWT_D4, float2, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(analyze_pipe_kernel<SIDWT_LEGALL53, float2, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(analyze_pipe_kernel<SIDWT_CDF97, float2, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmemLimit);
     return e;
+}
+
+// Pulses of a ragged batch whose double buffer fits: the pipelined kernel
+// over the item list (persistent CTAs, the next pulse bulk-copied while the
+// current one lifts), its shared buffers sized for the longest of them.
+template <int F>
+static cudaError_t launch_ragged_pipe(const float2 *y, const RaggedLift *items, int n, int64_t maxN, float2 *pyr,
+                                      double *yen, int32_t *err, cudaStream_t s) {
+    const size_t inb = ((size_t)maxN * 8 + 127) & ~(size_t)127;
+    const size_t smem = 2 * inb + (size_t)(maxN / 2) * 8;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = std::max(1, std::min(2048 / kPipeThreads, (int)((size_t)(228 * 1024) / (smem + 9 * 1024))));
+    const int grid = (int)std::min<int64_t>(n, (int64_t)sms * per_sm);
+    const int stall = (debug_stall_flags() & SIDWT_STALL_ANALYSIS) ? 1 : 0;
+    analyze_pipe_kernel<F, float2, true><<<grid, kPipeThreads, smem, s>>>(
+        y, maxN, 15, n, pyr, nullptr, 0, yen, lift_coef(F, SIDE_Y), err, 2, stall, items);
+    return cudaGetLastError();
 }
 
 template <int F>
@@ -1239,12 +1421,40 @@ static cudaError_t launch_ragged_window(const float2 *y, const RaggedLift *items
 // Items grouped by filter and path: groups[f] (shared-memory path) and
 // long_groups[f] (window path) are device item lists with their counts and
 // the largest N / J in each.
-sidwt_status analyze_ragged(const float2 *y, const RaggedLiftGroups &g, float2 *pyr, double *yen, cudaStream_t s,
-                            int *launches) {
+sidwt_status analyze_ragged(const float2 *y, const RaggedLiftGroups &g, float2 *pyr, double *yen, double *part,
+                            int32_t *err, cudaStream_t s, int *launches) {
     cudaError_t e = cudaSuccess;
     int nl = 0;
     for (int f = 0; f < 3 && e == cudaSuccess; ++f) {
-        if (g.n_smem[f] > 0) {
+        if (g.n_tiles[f] > 0) {
+            switch (f) {
+            case SIDWT_D4:
+                e = launch_ragged_tiles<SIDWT_D4>(g.tiles[f], g.n_tiles[f], g.tails[f], g.n_tails[f], g.maxN_tail[f], y,
+                                                  pyr, yen, part, s);
+                break;
+            case SIDWT_LEGALL53:
+                e = launch_ragged_tiles<SIDWT_LEGALL53>(g.tiles[f], g.n_tiles[f], g.tails[f], g.n_tails[f],
+                                                        g.maxN_tail[f], y, pyr, yen, part, s);
+                break;
+            default:
+                e = launch_ragged_tiles<SIDWT_CDF97>(g.tiles[f], g.n_tiles[f], g.tails[f], g.n_tails[f], g.maxN_tail[f],
+                                                     y, pyr, yen, part, s);
+            }
+            nl += 2;
+        }
+        for (int k = 0; k < kPipeClasses && e == cudaSuccess; ++k) {
+            if (g.n_pipe[k][f] == 0) continue;
+            const RaggedLift *it = g.pipe[k][f];
+            const int n = g.n_pipe[k][f];
+            const int64_t mx = g.maxN_pipe[k][f];
+            switch (f) {
+            case SIDWT_D4: e = launch_ragged_pipe<SIDWT_D4>(y, it, n, mx, pyr, yen, err, s); break;
+            case SIDWT_LEGALL53: e = launch_ragged_pipe<SIDWT_LEGALL53>(y, it, n, mx, pyr, yen, err, s); break;
+            default: e = launch_ragged_pipe<SIDWT_CDF97>(y, it, n, mx, pyr, yen, err, s);
+            }
+            ++nl;
+        }
+        if (e == cudaSuccess && g.n_smem[f] > 0) {
             switch (f) {
             case SIDWT_D4: e = launch_ragged_smem<SIDWT_D4>(y, g.smem[f], g.n_smem[f], g.maxN_smem[f], pyr, yen, s); break;
             case SIDWT_LEGALL53:

@@ -348,7 +348,11 @@ struct RefInfo {
 struct RaggedLayout {  // everything a batch needs on the device, built on the host
     std::vector<rg::Item> items;
     std::vector<rg::Work> work;
-    std::vector<RaggedLift> lift[2][3];  // [path: smem, long][filter]
+    std::vector<RaggedLift> lift[2 + kPipeClasses][3];  // [path: smem, long, pipelined by size class][filter]
+    std::vector<RaggedTile> tiles[3];    // tiled long pulses, by filter
+    std::vector<RaggedTail> tails[3];
+    int64_t maxN_tail[3] = {0, 0, 0};
+    int64_t part_elems = 0;
     std::vector<int32_t> slot_item;
     // tensor-core part: one received-operand entry and two tensor maps per
     // (pair, scale), tiles in cost order
@@ -359,7 +363,7 @@ struct RaggedLayout {  // everything a batch needs on the device, built on the h
     std::vector<unsigned char> maps;
     int64_t pyr_elems = 0, slots = 0;
     int64_t r_elems = 0;  // complex64 elements of the optional r output: sum of (J_i + 1) N_i
-    int64_t maxN[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    int64_t maxN[2 + kPipeClasses][3] = {};
     int maxJ_long[3] = {0, 0, 0};
 };
 
@@ -370,7 +374,10 @@ struct DevLayout {  // device copy of a RaggedLayout
     int32_t *slot_item = nullptr;
     rtc::TcTile *tc_tiles = nullptr;
     unsigned char *maps = nullptr;
-    int64_t cap_items = 0, cap_work = 0, cap_lift = 0, cap_slots = 0, cap_tiles = 0, cap_maps = 0;
+    RaggedTile *lt = nullptr;   // tiled long pulses (all filters, filter-major)
+    RaggedTail *ltail = nullptr;
+    int64_t cap_items = 0, cap_work = 0, cap_lift = 0, cap_slots = 0, cap_tiles = 0, cap_maps = 0, cap_lt = 0,
+            cap_ltail = 0;
     RaggedLiftGroups groups;
     int nwork = 0, n_tc_tiles = 0;
 };
@@ -391,6 +398,8 @@ struct sidwt_ragged {
     float2 *pyr = nullptr;
     int64_t pyr_cap = 0;
     double *yen = nullptr;
+    double *part = nullptr;  // energy partials of the tiled long pulses
+    int64_t part_cap = 0;
     unsigned long long *keys = nullptr;
     int32_t *lag = nullptr;
     float *mag = nullptr;
@@ -448,7 +457,7 @@ sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_i
                           int64_t y_elems, RaggedLayout &L) {
     L = RaggedLayout();
     L.items.resize((size_t)n);
-    const int64_t smem_max = analyze_smem_max_n();
+    const int64_t smem_max = analyze_smem_max_n(), pipe_max = analyze_pipe_max_n();
     for (int64_t i = 0; i < n; ++i) {
         const int32_t rid = ref_ids[i];
         if (rid < 0 || rid >= (int32_t)r->refs.size()) {
@@ -476,14 +485,37 @@ sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_i
         it.r_off = L.r_elems;
         L.r_elems += (int64_t)(ri.J + 1) * ri.N;
         RaggedLift lf{y_off[i], L.pyr_elems, L.slots, (int32_t)ri.N, ri.J};
-        const int path = ri.N <= smem_max ? 0 : 1;
-        L.lift[path][ri.filter].push_back(lf);
-        L.maxN[path][ri.filter] = std::max<int64_t>(L.maxN[path][ri.filter], ri.N);
-        if (path) L.maxJ_long[ri.filter] = std::max(L.maxJ_long[ri.filter], ri.J);
+        const int Lv = std::min(ri.J, kTileLevels);
+        const bool tiled = ri.N > pipe_max && (ri.J == Lv || (ri.N >> Lv) <= tile_tail_max_n());
+        if (tiled) {
+            const int nt = (int)((ri.N + kTileSamples - 1) / kTileSamples);
+            for (int k = 0; k < nt; ++k) {
+                const int64_t t0 = (int64_t)k * kTileSamples;
+                L.tiles[ri.filter].push_back(RaggedTile{y_off[i], L.pyr_elems, L.part_elems + (int64_t)k * (kTileLevels + 1),
+                                                        (int32_t)ri.N, Lv, (int32_t)t0,
+                                                        (int32_t)std::min<int64_t>(kTileSamples, ri.N - t0)});
+            }
+            L.tails[ri.filter].push_back(RaggedTail{lf, L.part_elems, nt, Lv});
+            if (ri.J > Lv) L.maxN_tail[ri.filter] = std::max<int64_t>(L.maxN_tail[ri.filter], ri.N >> Lv);
+            L.part_elems += (int64_t)nt * (kTileLevels + 1);
+        }
+        int path = ri.N <= smem_max ? 0 : 1;
+        for (int k = kPipeClasses - 1; k >= 0; --k)
+            if (ri.N <= analyze_pipe_class_max(k)) path = 2 + k;
+        if (!tiled) L.lift[path][ri.filter].push_back(lf);
+        if (!tiled) {
+            L.maxN[path][ri.filter] = std::max<int64_t>(L.maxN[path][ri.filter], ri.N);
+            if (path == 1) L.maxJ_long[ri.filter] = std::max(L.maxJ_long[ri.filter], ri.J);
+        }
         for (int j = 0; j <= ri.J; ++j) L.slot_item.push_back((int32_t)i);
         L.pyr_elems += 2 * ri.N - 2 * (ri.N >> ri.J);
         L.slots += ri.J + 1;
     }
+    // the pipelined kernel's persistent CTAs take the pulses in list order: longest first
+    for (int k = 2; k < 2 + kPipeClasses; ++k)
+        for (int f = 0; f < 3; ++f)
+            std::stable_sort(L.lift[k][f].begin(), L.lift[k][f].end(),
+                             [](const RaggedLift &a, const RaggedLift &b) { return a.N > b.N; });
     // work items, bucketed by log2 of their cost, largest first
     std::vector<std::vector<rg::Work>> buckets(64);
     std::vector<std::pair<int64_t, rtc::TcTile>> tct;  // (cost, tile)
@@ -563,7 +595,7 @@ sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_i
 
 sidwt_status ensure_dev(DevLayout &d, const RaggedLayout &L) {
     int64_t nl = 0;
-    for (int p = 0; p < 2; ++p)
+    for (int p = 0; p < 2 + kPipeClasses; ++p)
         for (int f = 0; f < 3; ++f) nl += (int64_t)L.lift[p][f].size();
     sidwt_status st;
     if ((st = grow(&d.items, &d.cap_items, (int64_t)L.items.size(), 0, "ragged items")) ||
@@ -572,6 +604,14 @@ sidwt_status ensure_dev(DevLayout &d, const RaggedLayout &L) {
         (st = grow(&d.slot_item, &d.cap_slots, L.slots, 0, "ragged slot map")) ||
         (st = grow(&d.tc_tiles, &d.cap_tiles, (int64_t)L.tc_tiles.size(), 0, "tensor-core tile list")) ||
         (st = grow(&d.maps, &d.cap_maps, (int64_t)L.maps.size(), 0, "tensor maps")))
+        return st;
+    int64_t nt = 0, ntl = 0;
+    for (int f = 0; f < 3; ++f) {
+        nt += (int64_t)L.tiles[f].size();
+        ntl += (int64_t)L.tails[f].size();
+    }
+    if ((st = grow(&d.lt, &d.cap_lt, nt, 0, "ragged analysis tiles")) ||
+        (st = grow(&d.ltail, &d.cap_ltail, ntl, 0, "ragged analysis tails")))
         return st;
     return SIDWT_OK;
 }
@@ -596,10 +636,14 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
     std::vector<RaggedLift> lift;
     int64_t base = 0;
     RaggedLiftGroups g;
-    for (int p = 0; p < 2; ++p)
+    for (int p = 0; p < 2 + kPipeClasses; ++p)
         for (int f = 0; f < 3; ++f) {
             const auto &v = L.lift[p][f];
-            if (p == 0) {
+            if (p >= 2) {
+                g.pipe[p - 2][f] = d.lift + base;
+                g.n_pipe[p - 2][f] = (int)v.size();
+                g.maxN_pipe[p - 2][f] = L.maxN[p][f];
+            } else if (p == 0) {
                 g.smem[f] = d.lift + base;
                 g.n_smem[f] = (int)v.size();
                 g.maxN_smem[f] = L.maxN[0][f];
@@ -612,6 +656,17 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
             lift.insert(lift.end(), v.begin(), v.end());
             base += (int64_t)v.size();
         }
+    std::vector<RaggedTile> tiles;
+    std::vector<RaggedTail> tails;
+    for (int f = 0; f < 3; ++f) {
+        g.tiles[f] = d.lt + tiles.size();
+        g.n_tiles[f] = (int)L.tiles[f].size();
+        g.tails[f] = d.ltail + tails.size();
+        g.n_tails[f] = (int)L.tails[f].size();
+        g.maxN_tail[f] = L.maxN_tail[f];
+        tiles.insert(tiles.end(), L.tiles[f].begin(), L.tiles[f].end());
+        tails.insert(tails.end(), L.tails[f].begin(), L.tails[f].end());
+    }
     d.groups = g;
     d.nwork = (int)L.work.size();
     d.n_tc_tiles = (int)L.tc_tiles.size();
@@ -619,6 +674,7 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
     const size_t b3 = lift.size() * sizeof(RaggedLift), b4 = L.slot_item.size() * sizeof(int32_t);
     const size_t b5 = L.tc_tiles.size() * sizeof(rtc::TcTile);
     const size_t b7 = L.maps.size();
+    const size_t b8 = tiles.size() * sizeof(RaggedTile), b9 = tails.size() * sizeof(RaggedTail);
     cudaError_t e = cudaSuccess;
     if (sync) {
         if (b1) e = cudaMemcpy(d.items, L.items.data(), b1, cudaMemcpyHostToDevice);
@@ -627,11 +683,13 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
         if (e == cudaSuccess && b4) e = cudaMemcpy(d.slot_item, L.slot_item.data(), b4, cudaMemcpyHostToDevice);
         if (e == cudaSuccess && b5) e = cudaMemcpy(d.tc_tiles, L.tc_tiles.data(), b5, cudaMemcpyHostToDevice);
         if (e == cudaSuccess && b7) e = cudaMemcpy(d.maps, L.maps.data(), b7, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && b8) e = cudaMemcpy(d.lt, tiles.data(), b8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && b9) e = cudaMemcpy(d.ltail, tails.data(), b9, cudaMemcpyHostToDevice);
         return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "ragged layout upload");
     }
     // asynchronous: through the object's pinned staging buffer (the previous
     // upload has been consumed once the stream reaches this point)
-    const size_t tot = b1 + b2 + b3 + b4 + b5 + b7 + 6 * 16;
+    const size_t tot = b1 + b2 + b3 + b4 + b5 + b7 + b8 + b9 + 8 * 16;
     if (tot > r->h_stage_bytes) {
         cudaStreamSynchronize(s);
         if (r->h_stage) cudaFreeHost(r->h_stage);
@@ -662,6 +720,8 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
     put(d.slot_item, L.slot_item.data(), b4);
     put(d.tc_tiles, L.tc_tiles.data(), b5);
     put(d.maps, L.maps.data(), b7);
+    put(d.lt, tiles.data(), b8);
+    put(d.ltail, tails.data(), b9);
     if (e == cudaSuccess && !r->stage_done) e = cudaEventCreateWithFlags(&r->stage_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(r->stage_done, s);
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "ragged layout upload");
@@ -670,6 +730,7 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
 sidwt_status ensure_workspace(sidwt_ragged *r, const RaggedLayout &L) {
     sidwt_status st;
     if ((st = grow(&r->pyr, &r->pyr_cap, L.pyr_elems, 0, "ragged pyramid"))) return st;
+    if ((st = grow(&r->part, &r->part_cap, L.part_elems, 0, "ragged analysis partials"))) return st;
     if (L.slots > r->slot_cap) {
         int64_t c0 = r->slot_cap, c1 = r->slot_cap, c2 = r->slot_cap, c3 = r->slot_cap, c4 = r->slot_cap;
         if ((st = grow(&r->yen, &c0, L.slots, 0, "ragged energies")) ||
@@ -702,7 +763,7 @@ sidwt_status enqueue(sidwt_ragged *r, const DevLayout &d, int64_t slots, int64_t
             }
     if (timed) cudaEventRecord(ev[0], s);
     int nl = 0;
-    sidwt_status st = analyze_ragged(y, d.groups, r->pyr, r->yen, s, &nl);
+    sidwt_status st = analyze_ragged(y, d.groups, r->pyr, r->yen, r->part, r->err, s, &nl);
     if (st) return st;
     cudaError_t e = cudaMemsetAsync(r->keys, 0, (size_t)slots * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->counter, 0, sizeof(int), s);
@@ -939,6 +1000,8 @@ sidwt_status sidwt_ragged_destroy(sidwt_ragged *r) {
         cudaFree(d->slot_item);
         cudaFree(d->tc_tiles);
         cudaFree(d->maps);
+        cudaFree(d->lt);
+        cudaFree(d->ltail);
     }
     cudaFree(r->tc_a);
     cudaFree(r->err);
@@ -946,6 +1009,7 @@ sidwt_status sidwt_ragged_destroy(sidwt_ragged *r) {
     cudaFree(r->xen);
     cudaFree(r->pyr);
     cudaFree(r->yen);
+    cudaFree(r->part);
     cudaFree(r->keys);
     cudaFree(r->lag);
     cudaFree(r->mag);
@@ -971,6 +1035,9 @@ sidwt_status sidwt_ragged_reserve(sidwt_ragged *r, int64_t tree_elems, int64_t p
     RaggedLayout L;
     L.pyr_elems = pyr_elems;
     L.slots = slots;
+    // the tiled analysis keeps kTileLevels + 1 partials per tile: at most one tile per
+    // kTileSamples samples plus one per pulse (a pyramid row holds about 2 N elements)
+    L.part_elems = (kTileLevels + 1) * (pyr_elems / (2 * kTileSamples) + slots + 1);
     return ensure_workspace(r, L);
 }
 

@@ -114,8 +114,36 @@ struct RaggedLift {
     int32_t N, J;
 };
 
+// Long pulses of a ragged batch, in tiles: tile k lifts levels 1..L of
+// samples [t0, t0 + Tc) of its pulse (with a periodic halo) and leaves the
+// energy partials of levels 0..L at part[part_off ..]; the pulse's tail then
+// sums them and lifts levels L + 1..J from c_L.
+constexpr int kTileSamples = 4096;
+constexpr int kTileHalo = 256;   // samples each side: covers 5 levels of the 5-pair windows
+constexpr int kTileLevels = 5;
+struct RaggedTile {
+    int64_t y_off, pyr_off, part_off;
+    int32_t N, L, t0, Tc;
+};
+struct RaggedTail {
+    RaggedLift it;
+    int64_t part_off;  // the pulse's first tile's partials
+    int32_t ntiles, L;
+};
+
 // Device item lists of a ragged batch by filter (0 D4, 1 5/3, 2 9/7) and path.
 struct RaggedLiftGroups {
+    const RaggedTile *tiles[3] = {nullptr, nullptr, nullptr};
+    int n_tiles[3] = {0, 0, 0};
+    const RaggedTail *tails[3] = {nullptr, nullptr, nullptr};
+    int n_tails[3] = {0, 0, 0};
+    int64_t maxN_tail[3] = {0, 0, 0};  // the longest c_L a tail lifts
+    // pipelined persistent kernel (double buffer fits), [size class][filter]:
+    // the shared buffers follow the class's longest pulse, so short pulses run
+    // more CTAs per SM
+    const RaggedLift *pipe[3][3] = {};
+    int n_pipe[3][3] = {};
+    int64_t maxN_pipe[3][3] = {};
     const RaggedLift *smem[3] = {nullptr, nullptr, nullptr};
     int n_smem[3] = {0, 0, 0};
     int64_t maxN_smem[3] = {0, 0, 0};
@@ -269,9 +297,17 @@ sidwt_status build_reference_trees(int filter, const float2 *x, float2 *tree, do
 sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStream_t s);
 int analyze_launch_count(const sidwt_plan *p);
 // Ragged batch: all listed pulses, each with its own N, J and filter.
-sidwt_status analyze_ragged(const float2 *y, const RaggedLiftGroups &g, float2 *pyr, double *yen, cudaStream_t s,
-                            int *launches);
+// part: the tiles' energy partials (kTileLevels + 1 per tile); err: the
+// object's device error record (the pipelined kernel's bounded waits)
+sidwt_status analyze_ragged(const float2 *y, const RaggedLiftGroups &g, float2 *pyr, double *yen, double *part,
+                            int32_t *err, cudaStream_t s, int *launches);
+int64_t tile_tail_max_n();
 int64_t analyze_smem_max_n();
+// Longest float pulse the pipelined analysis takes with two input buffers,
+// and the upper ends of its size classes (the last one is that maximum).
+int64_t analyze_pipe_max_n();
+constexpr int kPipeClasses = 3;
+int64_t analyze_pipe_class_max(int k);
 cudaError_t prepare_ragged_kernels();
 cudaError_t prepare_analysis_kernels();
 cudaError_t prepare_tc_kernels();
