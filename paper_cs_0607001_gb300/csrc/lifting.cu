@@ -834,21 +834,6 @@ __global__ void __launch_bounds__(kPipeThreads) analyze_pipe_kernel(const void *
     }
 }
 
-// One CTA per listed pulse of a ragged batch (float filters): item k has its
-// own N and J; its pulse, pyramid row and energies sit at the given offsets.
-template <int F>
-__global__ void __launch_bounds__(kAnalyzeThreads) analyze_ragged_kernel(const float2 *__restrict__ y,
-                                                                         const RaggedLift *__restrict__ items,
-                                                                         float2 *__restrict__ pyr,
-                                                                         double *__restrict__ yen, LiftCoef c) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ float2 red[32];
-    __shared__ long long redi[32];
-    const RaggedLift it = items[blockIdx.x];
-    analyze_one<F, float2>(y + it.y_off, it.N, it.J, pyr + it.pyr_off, nullptr, yen + it.yen_off, c,
-                           reinterpret_cast<float2 *>(smraw), red, redi);
-}
-
 // Energies of the received pyramid for the window path (c_l read back).
 __global__ void pyr_energy_kernel(const float2 *__restrict__ y, const float2 *__restrict__ pyr_f,
                                   const int2 *__restrict__ pyr_i, const short2 *__restrict__ y_i, int64_t N, int J,
@@ -1161,7 +1146,6 @@ sidwt_status analyze_batch(sidwt_plan *p, const void *y_dev, int64_t B, cudaStre
 // ---------------------------------------------------------------------------
 // Ragged batches
 // ---------------------------------------------------------------------------
-int64_t analyze_smem_max_n() { return (int64_t)kSmemLimit / 12; }
 // two input buffers of N complex64 and the level-1 buffer of N / 2
 int64_t analyze_pipe_max_n() { return (int64_t)kPipeSmemLimit / 20 / 128 * 128; }
 // up to 2048 samples four CTAs fit an SM, up to 5120 two
@@ -1345,15 +1329,7 @@ int64_t tile_tail_max_n() { return (int64_t)kSmemLimit / 12; }
 // The ragged kernels get the whole shared-memory budget once, outside any
 // stream capture, so that launching them needs no attribute call.
 cudaError_t prepare_ragged_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(analyze_ragged_kernel<SIDWT_D4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemLimit);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(analyze_ragged_kernel<SIDWT_LEGALL53>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kSmemLimit);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(analyze_ragged_kernel<SIDWT_CDF97>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kSmemLimit);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(ragged_tile_kernel<SIDWT_D4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmem);
+    cudaError_t e = cudaFuncSetAttribute(ragged_tile_kernel<SIDWT_D4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(ragged_tile_kernel<SIDWT_LEGALL53>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmem);
     if (e == cudaSuccess)
@@ -1397,14 +1373,6 @@ static cudaError_t launch_ragged_pipe(const float2 *y, const RaggedLift *items, 
 }
 
 template <int F>
-static cudaError_t launch_ragged_smem(const float2 *y, const RaggedLift *items, int n, int64_t maxN, float2 *pyr,
-                                      double *yen, cudaStream_t s) {
-    const size_t smem = (size_t)(maxN + maxN / 2) * 8;
-    analyze_ragged_kernel<F><<<n, kAnalyzeThreads, smem, s>>>(y, items, pyr, yen, lift_coef(F, SIDE_Y));
-    return cudaGetLastError();
-}
-
-template <int F>
 static cudaError_t launch_ragged_window(const float2 *y, const RaggedLift *items, int n, int64_t maxN, int maxJ,
                                         float2 *pyr, double *yen, cudaStream_t s) {
     const LiftCoef c = lift_coef(F, SIDE_Y);
@@ -1418,9 +1386,11 @@ static cudaError_t launch_ragged_window(const float2 *y, const RaggedLift *items
     return cudaGetLastError();
 }
 
-// Items grouped by filter and path: groups[f] (shared-memory path) and
-// long_groups[f] (window path) are device item lists with their counts and
-// the largest N / J in each.
+// The received analysis of a ragged batch, by filter: pulses up to
+// analyze_pipe_max_n() on the pipelined kernel (one launch per size class),
+// longer ones in tiles plus a tail per pulse, and pulses too long for a
+// tail's shared memory (N >> 5 above tile_tail_max_n(), J > 5) one launch per
+// level (window path).
 sidwt_status analyze_ragged(const float2 *y, const RaggedLiftGroups &g, float2 *pyr, double *yen, double *part,
                             int32_t *err, cudaStream_t s, int *launches) {
     cudaError_t e = cudaSuccess;
@@ -1451,16 +1421,6 @@ sidwt_status analyze_ragged(const float2 *y, const RaggedLiftGroups &g, float2 *
             case SIDWT_D4: e = launch_ragged_pipe<SIDWT_D4>(y, it, n, mx, pyr, yen, err, s); break;
             case SIDWT_LEGALL53: e = launch_ragged_pipe<SIDWT_LEGALL53>(y, it, n, mx, pyr, yen, err, s); break;
             default: e = launch_ragged_pipe<SIDWT_CDF97>(y, it, n, mx, pyr, yen, err, s);
-            }
-            ++nl;
-        }
-        if (e == cudaSuccess && g.n_smem[f] > 0) {
-            switch (f) {
-            case SIDWT_D4: e = launch_ragged_smem<SIDWT_D4>(y, g.smem[f], g.n_smem[f], g.maxN_smem[f], pyr, yen, s); break;
-            case SIDWT_LEGALL53:
-                e = launch_ragged_smem<SIDWT_LEGALL53>(y, g.smem[f], g.n_smem[f], g.maxN_smem[f], pyr, yen, s);
-                break;
-            default: e = launch_ragged_smem<SIDWT_CDF97>(y, g.smem[f], g.n_smem[f], g.maxN_smem[f], pyr, yen, s);
             }
             ++nl;
         }

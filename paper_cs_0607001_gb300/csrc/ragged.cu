@@ -348,7 +348,7 @@ struct RefInfo {
 struct RaggedLayout {  // everything a batch needs on the device, built on the host
     std::vector<rg::Item> items;
     std::vector<rg::Work> work;
-    std::vector<RaggedLift> lift[2 + kPipeClasses][3];  // [path: smem, long, pipelined by size class][filter]
+    std::vector<RaggedLift> lift[2 + kPipeClasses][3];  // [path: unused, long, pipelined by size class][filter]
     std::vector<RaggedTile> tiles[3];    // tiled long pulses, by filter
     std::vector<RaggedTail> tails[3];
     int64_t maxN_tail[3] = {0, 0, 0};
@@ -457,7 +457,7 @@ sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_i
                           int64_t y_elems, RaggedLayout &L) {
     L = RaggedLayout();
     L.items.resize((size_t)n);
-    const int64_t smem_max = analyze_smem_max_n(), pipe_max = analyze_pipe_max_n();
+    const int64_t pipe_max = analyze_pipe_max_n();
     for (int64_t i = 0; i < n; ++i) {
         const int32_t rid = ref_ids[i];
         if (rid < 0 || rid >= (int32_t)r->refs.size()) {
@@ -499,7 +499,7 @@ sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_i
             if (ri.J > Lv) L.maxN_tail[ri.filter] = std::max<int64_t>(L.maxN_tail[ri.filter], ri.N >> Lv);
             L.part_elems += (int64_t)nt * (kTileLevels + 1);
         }
-        int path = ri.N <= smem_max ? 0 : 1;
+        int path = 1;  // per-level windows: pulses too long for the tiles' tail
         for (int k = kPipeClasses - 1; k >= 0; --k)
             if (ri.N <= analyze_pipe_class_max(k)) path = 2 + k;
         if (!tiled) L.lift[path][ri.filter].push_back(lf);
@@ -643,11 +643,7 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
                 g.pipe[p - 2][f] = d.lift + base;
                 g.n_pipe[p - 2][f] = (int)v.size();
                 g.maxN_pipe[p - 2][f] = L.maxN[p][f];
-            } else if (p == 0) {
-                g.smem[f] = d.lift + base;
-                g.n_smem[f] = (int)v.size();
-                g.maxN_smem[f] = L.maxN[0][f];
-            } else {
+            } else if (p == 1) {
                 g.lng[f] = d.lift + base;
                 g.n_long[f] = (int)v.size();
                 g.maxN_long[f] = L.maxN[1][f];

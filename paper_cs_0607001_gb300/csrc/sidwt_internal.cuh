@@ -144,9 +144,6 @@ struct RaggedLiftGroups {
     const RaggedLift *pipe[3][3] = {};
     int n_pipe[3][3] = {};
     int64_t maxN_pipe[3][3] = {};
-    const RaggedLift *smem[3] = {nullptr, nullptr, nullptr};
-    int n_smem[3] = {0, 0, 0};
-    int64_t maxN_smem[3] = {0, 0, 0};
     const RaggedLift *lng[3] = {nullptr, nullptr, nullptr};
     int n_long[3] = {0, 0, 0};
     int64_t maxN_long[3] = {0, 0, 0};
@@ -302,7 +299,6 @@ int analyze_launch_count(const sidwt_plan *p);
 sidwt_status analyze_ragged(const float2 *y, const RaggedLiftGroups &g, float2 *pyr, double *yen, double *part,
                             int32_t *err, cudaStream_t s, int *launches);
 int64_t tile_tail_max_n();
-int64_t analyze_smem_max_n();
 // Longest float pulse the pipelined analysis takes with two input buffers,
 // and the upper ends of its size classes (the last one is that maximum).
 int64_t analyze_pipe_max_n();
