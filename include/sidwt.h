@@ -313,6 +313,18 @@ sidwt_status sidwt_ragged_correlate(sidwt_ragged *r, int64_t n_items, const int3
                                     const int64_t *y_offsets_host, const void *y_dev, int64_t y_elems,
                                     sidwt_stream stream);
 
+/* How the tensor-core tiles' contractions are scheduled (not in the paper:
+ * a latency measure).  mode 0 (default): a tile whose contraction is more
+ * than twice the batch's total divided by twice the SM count is cut into
+ * parts of about that share, at least 8 K-blocks of 64 samples each (never
+ * across the two bands of eq. 20), each run by its own CTA; their
+ * accumulators are summed in a fixed order by a second kernel that then
+ * forms the peaks (and r), so a lone long pulse spreads over the GPU while a
+ * large batch of short tiles is left as it is.  mode 1: never; mode 2: every tile long enough (for
+ * tests).  Results agree within the stated bounds (the parts are summed in
+ * FP32 outside the tensor cores).  EINVAL for another mode. */
+sidwt_status sidwt_ragged_set_split(sidwt_ragged *r, int mode);
+
 /* sidwt_ragged_correlate that also writes the correlation at every lag and
  * every scale, r_j[D] for D = 0..N_i-1 (eq. 20 for j < J_i, eq. 20a for
  * j = J_i), of every item: item i's rows start at complex64 element

@@ -357,6 +357,9 @@ struct RaggedLayout {  // everything a batch needs on the device, built on the h
     // tensor-core part: one received-operand entry and two tensor maps per
     // (pair, scale), tiles in cost order
     std::vector<rtc::TcTile> tc_tiles;
+    std::vector<rtc::TcSplit> tc_splits;  // tiles whose contraction runs as several parts
+    int64_t tc_part_elems = 0;            // complex64 elements of those parts' accumulators
+    int tc_split_maxS = 0;
     // one entry per tensor-core (pair, scale): its shape and stored operand
     std::vector<rtc::Shape> recv_shape;
     std::vector<int64_t> recv_a_off;
@@ -376,8 +379,10 @@ struct DevLayout {  // device copy of a RaggedLayout
     unsigned char *maps = nullptr;
     RaggedTile *lt = nullptr;   // tiled long pulses (all filters, filter-major)
     RaggedTail *ltail = nullptr;
+    rtc::TcSplit *splits = nullptr;
     int64_t cap_items = 0, cap_work = 0, cap_lift = 0, cap_slots = 0, cap_tiles = 0, cap_maps = 0, cap_lt = 0,
-            cap_ltail = 0;
+            cap_ltail = 0, cap_splits = 0;
+    int n_splits = 0, split_maxS = 0;
     RaggedLiftGroups groups;
     int nwork = 0, n_tc_tiles = 0;
 };
@@ -389,6 +394,11 @@ struct sidwt_ragged {
     // tensor-core path (SIDWT_PREC_BF16X3): stored operands of the references
     // packed at store time (the received windows are expanded on chip), error flag
     int prec = SIDWT_PREC_FP32;
+    // split contractions (sidwt_ragged_set_split): 0 when a batch has too few
+    // tiles to fill the GPU, 1 never, 2 every tile long enough (tests)
+    int split_mode = 0;
+    float2 *tcpart = nullptr;
+    int64_t tcpart_cap = 0;
     __nv_bfloat16 *tc_a = nullptr;
     int64_t tc_a_cap = 0, tc_a_used = 0;
     int32_t *err = nullptr;
@@ -451,6 +461,66 @@ sidwt_status grow(T **p, int64_t *cap, int64_t need, int64_t keep, const char *w
 }
 
 int default_mq(int lg) { return lg >= 11 ? 8 : (lg >= 10 ? 4 : (lg >= 9 ? 2 : 1)); }
+
+// A tile whose contraction (2 K' samples at the long scales) is long against
+// the batch's whole work keeps its SM busy after the others have finished:
+// such tiles are cut into parts of at least kMinPartKB K-blocks, never across the
+// band boundary, each a work item of its own whose accumulators go to the
+// partials buffer; tc_split_reduce then sums them and forms the peaks.
+constexpr int kMinPartKB = 8;
+constexpr int kMaxParts = 64;
+
+void split_long_tiles(const sidwt_ragged *r, std::vector<std::pair<int64_t, rtc::TcTile>> &tct, RaggedLayout &L) {
+    if (tct.empty() || r->split_mode == 1) return;
+    int64_t total_kb = 0;
+    for (const auto &x : tct) total_kb += (int64_t)x.second.nb * x.second.nkb;
+    const int64_t items = 2 * (int64_t)std::max(1, r->sms);
+    // K-blocks per work item that would spread the batch over about `items`
+    // items; a tile with more than twice that is cut (a large batch, whose
+    // tiles are many and short against the batch, cuts none)
+    const int64_t target = std::max<int64_t>(kMinPartKB, (total_kb + items - 1) / items);
+    std::vector<std::pair<int64_t, rtc::TcTile>> out;
+    out.reserve(tct.size());
+    for (const auto &x : tct) {
+        const rtc::TcTile &w = x.second;
+        const int nb = w.nb, nkb = w.nkb, F = nb * nkb;
+        int P = r->split_mode == 2 ? F / kMinPartKB : (F >= 2 * target ? (int)((F + target - 1) / target) : 1);
+        P = std::min(P, kMaxParts);
+        const int per_band = (P + nb - 1) / nb;  // parts per band
+        if (P < 2 || nkb / per_band < kMinPartKB) {
+            out.push_back(x);
+            continue;
+        }
+        rtc::TcSplit sp;
+        sp.slot = w.slot;
+        sp.slot_mid = w.slot_mid;
+        sp.r_at = w.r_at;
+        sp.r_mid = w.r_mid;
+        sp.part_first = L.tc_part_elems;
+        sp.nparts = per_band * nb;
+        sp.nparts0 = per_band;  // band 0's parts come first
+        sp.tile = w.tile;
+        sp.gv = w.gv;
+        sp.nv = w.nv;
+        sp.Kp = w.Kp;
+        sp.lev = w.lev;
+        sp.S = w.S;
+        for (int b = 0; b < nb; ++b)
+            for (int k = 0; k < per_band; ++k) {
+                const int k0 = (int)((int64_t)nkb * k / per_band), k1 = (int)((int64_t)nkb * (k + 1) / per_band);
+                rtc::TcTile part = w;
+                part.slot_mid = -1;
+                part.f0 = b * nkb + k0;
+                part.fcnt = k1 - k0;
+                part.part_off = L.tc_part_elems;
+                L.tc_part_elems += (int64_t)w.S * 128;
+                out.push_back({(int64_t)part.fcnt * w.S, part});
+            }
+        L.tc_splits.push_back(sp);
+        L.tc_split_maxS = std::max<int>(L.tc_split_maxS, w.S);
+    }
+    tct.swap(out);
+}
 
 // Builds the device-side description of a batch on the host.
 sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_ids, const int64_t *y_off,
@@ -582,6 +652,7 @@ sidwt_status build_layout(const sidwt_ragged *r, int64_t n, const int32_t *ref_i
         }
     }
     for (int b = 63; b >= 0; --b) L.work.insert(L.work.end(), buckets[b].begin(), buckets[b].end());
+    split_long_tiles(r, tct, L);
     std::stable_sort(tct.begin(), tct.end(), [](const std::pair<int64_t, rtc::TcTile> &a,
                                                 const std::pair<int64_t, rtc::TcTile> &b) { return a.first > b.first; });
     L.tc_tiles.reserve(tct.size());
@@ -611,7 +682,8 @@ sidwt_status ensure_dev(DevLayout &d, const RaggedLayout &L) {
         ntl += (int64_t)L.tails[f].size();
     }
     if ((st = grow(&d.lt, &d.cap_lt, nt, 0, "ragged analysis tiles")) ||
-        (st = grow(&d.ltail, &d.cap_ltail, ntl, 0, "ragged analysis tails")))
+        (st = grow(&d.ltail, &d.cap_ltail, ntl, 0, "ragged analysis tails")) ||
+        (st = grow(&d.splits, &d.cap_splits, (int64_t)L.tc_splits.size(), 0, "split tensor-core tiles")))
         return st;
     return SIDWT_OK;
 }
@@ -664,6 +736,8 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
         tails.insert(tails.end(), L.tails[f].begin(), L.tails[f].end());
     }
     d.groups = g;
+    d.n_splits = (int)L.tc_splits.size();
+    d.split_maxS = L.tc_split_maxS;
     d.nwork = (int)L.work.size();
     d.n_tc_tiles = (int)L.tc_tiles.size();
     const size_t b1 = L.items.size() * sizeof(rg::Item), b2 = L.work.size() * sizeof(rg::Work);
@@ -671,6 +745,7 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
     const size_t b5 = L.tc_tiles.size() * sizeof(rtc::TcTile);
     const size_t b7 = L.maps.size();
     const size_t b8 = tiles.size() * sizeof(RaggedTile), b9 = tails.size() * sizeof(RaggedTail);
+    const size_t b10 = L.tc_splits.size() * sizeof(rtc::TcSplit);
     cudaError_t e = cudaSuccess;
     if (sync) {
         if (b1) e = cudaMemcpy(d.items, L.items.data(), b1, cudaMemcpyHostToDevice);
@@ -681,11 +756,12 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
         if (e == cudaSuccess && b7) e = cudaMemcpy(d.maps, L.maps.data(), b7, cudaMemcpyHostToDevice);
         if (e == cudaSuccess && b8) e = cudaMemcpy(d.lt, tiles.data(), b8, cudaMemcpyHostToDevice);
         if (e == cudaSuccess && b9) e = cudaMemcpy(d.ltail, tails.data(), b9, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && b10) e = cudaMemcpy(d.splits, L.tc_splits.data(), b10, cudaMemcpyHostToDevice);
         return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "ragged layout upload");
     }
     // asynchronous: through the object's pinned staging buffer (the previous
     // upload has been consumed once the stream reaches this point)
-    const size_t tot = b1 + b2 + b3 + b4 + b5 + b7 + b8 + b9 + 8 * 16;
+    const size_t tot = b1 + b2 + b3 + b4 + b5 + b7 + b8 + b9 + b10 + 9 * 16;
     if (tot > r->h_stage_bytes) {
         cudaStreamSynchronize(s);
         if (r->h_stage) cudaFreeHost(r->h_stage);
@@ -718,6 +794,7 @@ sidwt_status upload(sidwt_ragged *r, DevLayout &d, const RaggedLayout &L, cudaSt
     put(d.maps, L.maps.data(), b7);
     put(d.lt, tiles.data(), b8);
     put(d.ltail, tails.data(), b9);
+    put(d.splits, L.tc_splits.data(), b10);
     if (e == cudaSuccess && !r->stage_done) e = cudaEventCreateWithFlags(&r->stage_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(r->stage_done, s);
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "ragged layout upload");
@@ -727,6 +804,7 @@ sidwt_status ensure_workspace(sidwt_ragged *r, const RaggedLayout &L) {
     sidwt_status st;
     if ((st = grow(&r->pyr, &r->pyr_cap, L.pyr_elems, 0, "ragged pyramid"))) return st;
     if ((st = grow(&r->part, &r->part_cap, L.part_elems, 0, "ragged analysis partials"))) return st;
+    if ((st = grow(&r->tcpart, &r->tcpart_cap, L.tc_part_elems, 0, "split-contraction partials"))) return st;
     if (L.slots > r->slot_cap) {
         int64_t c0 = r->slot_cap, c1 = r->slot_cap, c2 = r->slot_cap, c3 = r->slot_cap, c4 = r->slot_cap;
         if ((st = grow(&r->yen, &c0, L.slots, 0, "ragged energies")) ||
@@ -766,8 +844,15 @@ sidwt_status enqueue(sidwt_ragged *r, const DevLayout &d, int64_t slots, int64_t
     if (e != cudaSuccess) return cuda_fail(e, "ragged memset");
     if (timed) cudaEventRecord(ev[1], s);
     if (d.n_tc_tiles > 0) {
-        if ((st = rtc::launch_corr(d.maps, d.tc_tiles, d.n_tc_tiles, r->pyr, r->keys, r->err, r->sms, s, R))) return st;
+        if ((st = rtc::launch_corr(d.maps, d.tc_tiles, d.n_tc_tiles, r->pyr, r->keys, r->err, r->sms, s, R,
+                                   d.n_splits > 0 ? r->tcpart : nullptr)))
+            return st;
         nl += 1;
+        if (d.n_splits > 0) {
+            if ((st = rtc::launch_split_reduce(d.splits, d.n_splits, d.split_maxS, r->tcpart, r->keys, R, s)))
+                return st;
+            nl += 1;
+        }
     }
     if (d.nwork > 0) {
         rg::corr_ragged_kernel<<<r->sms * 2, rg::kT, 0, s>>>(d.items, d.work, d.nwork, r->counter, r->tree, r->pyr,
@@ -998,6 +1083,7 @@ sidwt_status sidwt_ragged_destroy(sidwt_ragged *r) {
         cudaFree(d->maps);
         cudaFree(d->lt);
         cudaFree(d->ltail);
+        cudaFree(d->splits);
     }
     cudaFree(r->tc_a);
     cudaFree(r->err);
@@ -1006,6 +1092,7 @@ sidwt_status sidwt_ragged_destroy(sidwt_ragged *r) {
     cudaFree(r->pyr);
     cudaFree(r->yen);
     cudaFree(r->part);
+    cudaFree(r->tcpart);
     cudaFree(r->keys);
     cudaFree(r->lag);
     cudaFree(r->mag);
@@ -1189,6 +1276,15 @@ sidwt_status sidwt_ragged_store_references(sidwt_ragged *r, int64_t n, const int
     r->tree_used = tree_at;
     r->xen_used = xen_at;
     r->tc_a_used = tc_at;
+    return SIDWT_OK;
+}
+
+sidwt_status sidwt_ragged_set_split(sidwt_ragged *r, int mode) {
+    if (!r || mode < 0 || mode > 2) {
+        set_error("need a ragged object and mode 0 (automatic), 1 (never) or 2 (always)");
+        return SIDWT_EINVAL;
+    }
+    r->split_mode = mode;
     return SIDWT_OK;
 }
 

@@ -157,13 +157,31 @@ __device__ __forceinline__ void expand_window(unsigned char *stB, const float2 *
     }
 }
 
-// WITH_R: also write r at every lag (a separate instance, so that the bulk
-// path's epilogue is unchanged)
-template <bool WITH_R>
+// The (band b, K-block kb) steps of a work item: all nb x nkb of a whole tile,
+// or, for one part of a split contraction, the contiguous run f0 .. f0 + fcnt - 1
+// of f = nkb b + kb.  Bands b0 .. b1; band b0 starts at kb0, band b1 ends
+// before kb1.
+struct StepRange {
+    int b0, b1, kb0, kb1;
+    __device__ __forceinline__ int kb_begin(int b) const { return b == b0 ? kb0 : 0; }
+    __device__ __forceinline__ int kb_end(int b, int nkb) const { return b == b1 ? kb1 : nkb; }
+};
+
+template <bool PARTS>
+__device__ __forceinline__ StepRange step_range(const TcTile &w) {
+    if (!PARTS || w.fcnt < 0) return {0, w.nb - 1, 0, w.nkb};
+    const int fe = w.f0 + w.fcnt, b1 = (fe - 1) / w.nkb, b0 = w.f0 / w.nkb;
+    return {b0, b1, w.f0 - b0 * w.nkb, fe - b1 * w.nkb};
+}
+
+// WITH_R: also write r at every lag; PARTS: some work items are parts of a
+// split contraction (separate instances, so that the bulk path's epilogue is
+// unchanged)
+template <bool WITH_R, bool PARTS>
 __global__ void __launch_bounds__(kThreads, 1)
     corr_pair_tc_kernel(const CUtensorMap *__restrict__ maps, const TcTile *__restrict__ tiles, int ntiles,
                         const float2 *__restrict__ pyr, unsigned long long *__restrict__ keys,
-                        int32_t *__restrict__ err, float2 *__restrict__ R) {
+                        int32_t *__restrict__ err, float2 *__restrict__ R, float2 *__restrict__ part) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *sB = base;
@@ -207,8 +225,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int ng = valid_groups(w);
                 tensormap_acquire(mA);
                 const uint32_t tx = (uint32_t)(ng * kGroupBytes);
-                for (int b = 0; b < w.nb && !sflag[0]; ++b)
-                    for (int kb = 0; kb < w.nkb; ++kb) {
+                const StepRange sr = step_range<PARTS>(w);
+                for (int b = sr.b0; b <= sr.b1 && !sflag[0]; ++b)
+                    for (int kb = sr.kb_begin(b); kb < sr.kb_end(b, w.nkb); ++kb) {
                         const int s = it & 1;
                         if (it >= 2 && !mbar_wait(&empty[s], ((it >> 1) - 1) & 1)) {
                             sflag[0] = 1;
@@ -237,8 +256,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         int it = 0;
         for (int t = blockIdx.x; t < ntiles && !sflag[0]; t += gridDim.x) {
             const TcTile w = tiles[t];
-            for (int b = 0; b < w.nb && !sflag[0]; ++b)
-                for (int kb = 0; kb < w.nkb; ++kb) {
+            const StepRange sr = step_range<PARTS>(w);
+            for (int b = sr.b0; b <= sr.b1 && !sflag[0]; ++b)
+                for (int kb = sr.kb_begin(b); kb < sr.kb_end(b, w.nkb); ++kb) {
                     const int s = it & 1;
                     if (it >= 2 && !mbar_wait(&empty[s], ((it >> 1) - 1) & 1)) {
                         sflag[0] = 1;
@@ -268,8 +288,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t idesc = idesc_bf16(128, w.S);
                 const uint32_t bRow = (uint32_t)(w.S + 64) * 2;
                 bool first = true;
-                for (int b = 0; b < w.nb && !sflag[0]; ++b) {
-                    if (b == 1 && w.slot_mid >= 0) {
+                const StepRange sr = step_range<PARTS>(w);
+                for (int b = sr.b0; b <= sr.b1 && !sflag[0]; ++b) {
+                    if (b == 1 && b > sr.b0 && w.slot_mid >= 0) {
                         // band 0 alone is the coarser scale's product: hand it to the
                         // epilogue and add band 1 once the epilogue has read it
                         mma_commit(accf);
@@ -280,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                         tc_fence_after();
                     }
-                    for (int kb = 0; kb < w.nkb; ++kb) {
+                    for (int kb = sr.kb_begin(b); kb < sr.kb_end(b, w.nkb); ++kb) {
                         const int s = it & 1;
                         if (!mbar_wait(&full[s], (it >> 1) & 1)) {
                             sflag[0] = 1;
@@ -352,6 +373,23 @@ __global__ void __launch_bounds__(kThreads, 1)
             // ceil(K'/S) and the wrapped columns repeat advances already written)
             float2 *Rrow = (WITH_R && valid) ? R + (pass ? w.r_at : w.r_mid) : nullptr;
             const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
+            if (PARTS && w.part_off >= 0) {
+                // one part of a split contraction: the raw accumulators, column-major
+                // [S][128], for tc_split_reduce (which forms the peaks)
+                float2 *P = part + w.part_off + m;
+                for (int c0 = 0; c0 < w.S; c0 += 32) {
+                    uint32_t re[32], im[32];
+                    TMEM_LD32(tl + c0, re);
+                    TMEM_LD32(tl + 256 + c0, im);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int n = 0; n < 32; ++n)
+                        P[(int64_t)(c0 + n) * 128] = make_float2(__uint_as_float(re[n]), __uint_as_float(im[n]));
+                }
+                tc_fence_before();
+                mbar_arrive(tfree);
+                continue;
+            }
             for (int c0 = 0; c0 < w.S; c0 += 32) {
                 uint32_t re[32], im[32];
                 TMEM_LD32(tl + c0, re);
@@ -386,6 +424,64 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
     if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---------------------------------------------------------------------------
+// Split contractions: block (x = split tile, y = pair of columns) sums the
+// tile's parts for its 2 x 128 elements in a fixed order (band-0 parts
+// first; their partial sum is scale J's product when slot_mid >= 0) and forms
+// the peak keys exactly as the epilogue does (one atomicMax per warp).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) tc_split_reduce_kernel(const TcSplit *__restrict__ splits,
+                                                              const float2 *__restrict__ part,
+                                                              unsigned long long *__restrict__ keys,
+                                                              float2 *__restrict__ R) {
+    const TcSplit sp = splits[blockIdx.x];
+    const int n = 2 * blockIdx.y + (threadIdx.x >> 7);  // column (advance offset within the tile)
+    const int m = threadIdx.x & 127;                    // row
+    if (n >= sp.S) return;                               // warp-uniform: a warp holds one column
+    const int G = 16 * sp.tile + (m >> 3);
+    const int v = G / sp.gv;
+    const int i = 8 * (G % sp.gv) + (m & 7);
+    const bool valid = v < sp.nv;
+    const int64_t stride = (int64_t)sp.S * 128;
+    const float2 *p = part + sp.part_first + (int64_t)n * 128 + m;
+    float2 mid = make_float2(0.f, 0.f);
+    for (int k = 0; k < sp.nparts0; ++k) {
+        const float2 x = p[k * stride];
+        mid.x += x.x;
+        mid.y += x.y;
+    }
+    float2 all = mid;
+    for (int k = sp.nparts0; k < sp.nparts; ++k) {
+        const float2 x = p[k * stride];
+        all.x += x.x;
+        all.y += x.y;
+    }
+    // advance of column n: p = S i - n (mod K'); delay q = -p mod K'
+    int pm = (int)((((int64_t)sp.S * i - n) % sp.Kp + sp.Kp) % sp.Kp);
+    const int q = pm == 0 ? 0 : sp.Kp - pm;
+    const uint32_t D = ((uint32_t)q << sp.lev) + (uint32_t)v;
+    auto key_of = [&](float2 a) {
+        const float m2 = a.x * a.x + a.y * a.y;
+        return ((unsigned long long)__float_as_uint(m2) << 32) | (unsigned long long)(0xFFFFFFFFu - D);
+    };
+    unsigned long long kall = valid ? key_of(all) : 0ull;
+    unsigned long long kmid = (valid && sp.slot_mid >= 0) ? key_of(mid) : 0ull;
+    if (R && valid) {
+        R[sp.r_at + D] = all;
+        if (sp.slot_mid >= 0) R[sp.r_mid + D] = mid;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, kall, o);
+        const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmid, o);
+        kall = a > kall ? a : kall;
+        kmid = b > kmid ? b : kmid;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (kall) atomicMax(&keys[sp.slot], kall);
+        if (kmid) atomicMax(&keys[sp.slot_mid], kmid);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -642,24 +738,42 @@ sidwt_status encode_maps(void *two_maps, const void *a_base, const void *b_base,
 
 
 sidwt_status launch_corr(const void *maps, const TcTile *tiles, int ntiles, const float2 *pyr, unsigned long long *keys,
-                         int32_t *err, int sms, cudaStream_t s, float2 *R) {
+                         int32_t *err, int sms, cudaStream_t s, float2 *R, float2 *part) {
     if (ntiles <= 0) return SIDWT_OK;
     const int grid = std::min(sms, ntiles);
-    if (R)
-        corr_pair_tc_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(static_cast<const CUtensorMap *>(maps), tiles,
-                                                                      ntiles, pyr, keys, err, R);
+    const CUtensorMap *m = static_cast<const CUtensorMap *>(maps);
+    if (R && part)
+        corr_pair_tc_kernel<true, true><<<grid, kThreads, kSmemBytes, s>>>(m, tiles, ntiles, pyr, keys, err, R, part);
+    else if (R)
+        corr_pair_tc_kernel<true, false><<<grid, kThreads, kSmemBytes, s>>>(m, tiles, ntiles, pyr, keys, err, R, part);
+    else if (part)
+        corr_pair_tc_kernel<false, true><<<grid, kThreads, kSmemBytes, s>>>(m, tiles, ntiles, pyr, keys, err, R, part);
     else
-        corr_pair_tc_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(static_cast<const CUtensorMap *>(maps), tiles,
-                                                                       ntiles, pyr, keys, err, nullptr);
+        corr_pair_tc_kernel<false, false><<<grid, kThreads, kSmemBytes, s>>>(m, tiles, ntiles, pyr, keys, err, R, part);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "tensor-core pair correlation launch");
 }
 
+sidwt_status launch_split_reduce(const TcSplit *splits, int nsplits, int maxS, const float2 *part,
+                                 unsigned long long *keys, float2 *R, cudaStream_t s) {
+    if (nsplits <= 0) return SIDWT_OK;
+    tc_split_reduce_kernel<<<dim3((unsigned)nsplits, (unsigned)((maxS + 1) / 2)), 256, 0, s>>>(splits, part, keys, R);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "split-contraction reduction launch");
+}
+
 cudaError_t prepare_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(corr_pair_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(corr_pair_tc_kernel<false, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(corr_pair_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        e = cudaFuncSetAttribute(corr_pair_tc_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(corr_pair_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(corr_pair_tc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemBytes);
     return e;
 }
 

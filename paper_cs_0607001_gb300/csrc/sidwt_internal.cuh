@@ -381,6 +381,21 @@ struct TcTile {
     int64_t slot_mid;
     // optional r output: complex64 offsets of the N-lag rows of slot and slot_mid
     int64_t r_at = -1, r_mid = -1;
+    // split contraction: this work item runs the K-blocks f0 .. f0 + fcnt - 1
+    // of the flattened (band, K-block) sequence (fcnt < 0: all of them); with
+    // part_off >= 0 its accumulators go to the partials buffer ([S][128]
+    // complex64 at part_off) for tc_split_reduce instead of peak keys
+    int32_t f0 = 0, fcnt = -1;
+    int64_t part_off = -1;
+};
+
+// A tile whose contraction was split into parts: the reduction sums its
+// parts (the band-0 ones first: their sum alone is scale J's product when
+// slot_mid >= 0) and forms the peaks as the epilogue would.
+struct TcSplit {
+    int64_t slot, slot_mid, r_at, r_mid, part_first;
+    int32_t nparts, nparts0;  // all parts, and those of band 0 (the first nparts0)
+    int32_t tile, gv, nv, Kp, lev, S;
 };
 
 
@@ -418,9 +433,13 @@ sidwt_status pack_stored_batch(const float2 *tree, const PackItem *items, int n,
                                int *launches);
 sidwt_status encode_maps(void *two_maps, const void *a_base, const void *b_base, const Shape &sh);
 size_t map_bytes();
-// R: optional complex64 r output (each tile writes its rows at r_at / r_mid), or null
+// R: optional complex64 r output (each tile writes its rows at r_at / r_mid), or null;
+// part: the partials buffer of split tiles (null when none is split)
 sidwt_status launch_corr(const void *maps, const TcTile *tiles, int ntiles, const float2 *pyr, unsigned long long *keys,
-                         int32_t *err, int sms, cudaStream_t s, float2 *R = nullptr);
+                         int32_t *err, int sms, cudaStream_t s, float2 *R = nullptr, float2 *part = nullptr);
+// Peaks (and r) of the split tiles from their parts.
+sidwt_status launch_split_reduce(const TcSplit *splits, int nsplits, int maxS, const float2 *part,
+                                 unsigned long long *keys, float2 *R, cudaStream_t s);
 cudaError_t prepare_kernels();
 
 }  // namespace rtc

@@ -103,6 +103,7 @@ def lib():
     L.sidwt_ragged_store_references.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]
     L.sidwt_ragged_correlate.argtypes = [_vp, _i64, _vp, _vp, _vp, _i64, _vp]
     L.sidwt_ragged_correlate_r.argtypes = [_vp, _i64, _vp, _vp, _vp, _i64, _vp, _i64, _vp]
+    L.sidwt_ragged_set_split.argtypes = [_vp, ctypes.c_int]
     L.sidwt_ragged_graph_create.argtypes = [_vp, _i64, _vp, _vp, _vp, _i64, ctypes.POINTER(_i32)]
     L.sidwt_ragged_graph_launch.argtypes = [_vp, _vp]
     L.sidwt_ragged_peaks.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp]
@@ -130,7 +131,7 @@ def lib():
                  "sidwt_read_timing", "sidwt_correlate_static", "sidwt_tc_selftest", "sidwt_debug_stall", "sidwt_ragged_create",
                  "sidwt_ragged_destroy", "sidwt_ragged_reserve", "sidwt_ragged_store_reference",
                  "sidwt_ragged_store_references",
-                 "sidwt_ragged_correlate", "sidwt_ragged_correlate_r", "sidwt_ragged_graph_create", "sidwt_ragged_graph_launch",
+                 "sidwt_ragged_correlate", "sidwt_ragged_correlate_r", "sidwt_ragged_set_split", "sidwt_ragged_graph_create", "sidwt_ragged_graph_launch",
                  "sidwt_ragged_peaks", "sidwt_ragged_autotune", "sidwt_ragged_tuning", "sidwt_ragged_set_timing",
                  "sidwt_ragged_read_timing", "sidwt_ragged_reset_references", "sidwt_server_create",
                  "sidwt_server_add_waveform", "sidwt_server_start", "sidwt_server_submit", "sidwt_server_wait",
@@ -439,6 +440,12 @@ class Ragged:
                                             y.numel(), _stream(stream)))
         self._layout = ids
         return self.slots_of(ids)[1]
+
+    def set_split(self, mode):
+        """Contraction splitting of the tensor-core tiles (sidwt_ragged_set_split):
+        "auto" (0), "never" (1) or "always" (2)."""
+        m = {"auto": 0, "never": 1, "always": 2}.get(mode, mode)
+        _raise(lib().sidwt_ragged_set_split(self._h, int(m)))
 
     def r_rows_of(self, ref_ids) -> tuple[np.ndarray, int]:
         """First element of every item's J + 1 rows of N lags in the r output, and the total."""

@@ -68,10 +68,11 @@ def batch(oracle):
     return refs, np.concatenate(ys), offsets, delays, ref_r, bounds
 
 
-def run_r(precision, refs, ypack, offsets):
+def run_r(precision, refs, ypack, offsets, split="auto"):
     from paper_cs_0607001_gb300 import sidwt
     with sidwt.Ragged() as rg:
         rg.set_precision(precision)
+        rg.set_split(split)
         ids = [rg.store_reference(f, N, J, U.to_dev_c64(x)) for (f, N, J), x in zip(SPECS, refs)]
         n, r = rg.correlate_r(ids, offsets, U.to_dev_c64(ypack))
         lag, mag, _ = rg.peaks(n)
@@ -82,9 +83,9 @@ def run_r(precision, refs, ypack, offsets):
         return (first_slot, first_r, r.cpu().numpy().astype(np.complex128), lag.cpu().numpy(), mag.cpu().numpy())
 
 
-def check(precision, batch):
+def check(precision, batch, split="auto"):
     refs, ypack, offsets, delays, ref_r, bounds = batch
-    first_slot, first_r, r, lag, mag = run_r(precision, refs, ypack, offsets)
+    first_slot, first_r, r, lag, mag = run_r(precision, refs, ypack, offsets, split)
     worst_ratio = 0.0
     for i, (f, N, J) in enumerate(SPECS):
         for j in range(J + 1):
@@ -123,6 +124,17 @@ def test_ragged_bf16x3_full_r_each_tile_width(batch, tmp_path, monkeypatch, widt
 @pytest.mark.gpu
 def test_ragged_bf16x3_full_r_default_widths(batch):
     check("bf16x3", batch)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("split", ["always", "never"])
+def test_ragged_bf16x3_full_r_split_contractions(batch, split):
+    """Every tensor-core tile long enough cut into parts of its contraction
+    (each part's accumulators summed by the reduction kernel, band-0 parts
+    alone for the folded scale J), and no tile cut: the same bounds, peaks
+    consistent with the call's own r.  (This 22-pulse batch has fewer tiles
+    than SMs, so the default already splits.)"""
+    check("bf16x3", batch, split)
 
 
 @pytest.mark.gpu
