@@ -65,7 +65,9 @@ class ClockSampler:
         self.proc = None
         self.path = None
 
-    def start(self):
+    def start(self, wait_first: bool = False):
+        """wait_first: return once the first sample is written (up to 3 s), for
+        timed regions shorter than the 200 ms sampling period."""
         try:
             # the raw samples go to SIDWT_CLOCKS_DIR (default: the temporary directory)
             out = Path(os.environ.get("SIDWT_CLOCKS_DIR", tempfile.gettempdir()))
@@ -77,6 +79,12 @@ class ClockSampler:
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while wait_first and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+            if self.path.stat().st_size > 0:
+                break
+            time.sleep(0.01)
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -1068,6 +1076,8 @@ def run_single_workload(args):
     torch.cuda.synchronize()
     reps = max(1000, args.steps)
     stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start(wait_first=True)
     ms, per = _timed_steps(g.replay, reps, stream, torch)
     host = []
     for _ in range(min(reps, 1000)):
@@ -1075,6 +1085,7 @@ def run_single_workload(args):
         g.replay()
         torch.cuda.synchronize()
         host.append((time.perf_counter() - t0) * 1e3)
+    clk = clocks.stop()
     host = np.array(host)
     ok = int(lag[0, 0].item()) == int(w["delays"][0])
     cpu = None
@@ -1100,7 +1111,7 @@ def run_single_workload(args):
                        "host_p50": float(np.percentile(host, 50)), "host_p99": float(np.percentile(host, 99)),
                        "what": "device time per replay (events) and host launch-to-sync time"},
         "peak_at_injected_delay": ok,
-        "cpu_baseline": cpu,
+        "cpu_baseline": cpu, "clocks": clk,
     }
     print(json.dumps(line))
     p.close()
@@ -1165,6 +1176,8 @@ def run_serve_workload(args):
         gaps = g.exponential(1.0 / rate, size=n_req)
         t_sched = np.cumsum(gaps)
         pick = g.integers(0, len(pool), size=n_req)
+        clocks = ClockSampler(0)
+        clocks.start()
         t0 = time.perf_counter()
         ids = []
         for k in range(n_req):
@@ -1174,6 +1187,7 @@ def run_serve_workload(args):
             ids.append((srv.submit(*p[:5]), p[5]))
         offered = n_req / max(time.perf_counter() - t0, 1e-9)  # what the submit loop achieved
         srv.drain(600.0)
+        clk = clocks.stop()
         st = srv.stats(reset=True)
         for rid, D in ids[:64]:
             hits.append(int(srv.result(rid)[0][0] == D))
@@ -1185,7 +1199,7 @@ def run_serve_workload(args):
                          "req_s": st["completed"] / max(st["span_s"], 1e-9), "batches": st["batches"],
                          "max_batch": st["max_batch"], "ref_hits": st["ref_hits"], "ref_stores": st["ref_stores"],
                          "stored_tree_hit_rate": st["ref_hits"] / max(1, st["ref_hits"] + st["ref_stores"]),
-                         "window_s": st["span_s"]})
+                         "window_s": st["span_s"], "clocks": clk})
     srv.close()
     cpu = None
     if not args.no_cpu:
@@ -1223,6 +1237,7 @@ def run_serve_workload(args):
         "latency_ms": {"p50": lat["p50_ms"], "p99": lat["p99_ms"], "rate_req_s": lat["rate_req_s"],
                        "what": "submit to completion at the highest offered rate the loop keeps up with"},
         "saturated_latency_ms": {"p50": best["p50_ms"], "p99": best["p99_ms"], "rate_req_s": best["rate_req_s"]},
+        "clocks": dict(best["clocks"], what="sampled at the saturated rate (each rate's own in per_rate)"),
         "per_rate": per_rate,
         "cpu_baseline": cpu,
         "peak_at_injected_delay_scale0": float(np.mean(hits)) if hits else None,
