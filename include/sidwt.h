@@ -240,11 +240,13 @@ sidwt_status sidwt_check(sidwt_plan *p, sidwt_stream stream);
  * out on purpose, so that a caller can test its handling of SIDWT_ETIMEOUT
  * without faulting the GPU.  Process-wide; read at each later launch of the
  * kernels it names; what = 0 restores normal operation.
- *   SIDWT_STALL_ANALYSIS: the pipelined received analysis (pulses that fit
- *     its shared memory, y_dev 16-byte aligned) issues no input copy, so its
- *     first wait gives up after 200 ms; it records the timeout (sidwt_check:
- *     SIDWT_ETIMEOUT; sidwt_correlate_static: every peak record of the call
- *     is lag -1, |r| 0, norm 0) and returns with nothing in flight.
+ *   SIDWT_STALL_ANALYSIS: the pipelined received analysis (plan pulses that
+ *     fit its shared memory, y_dev 16-byte aligned; ragged pulses of every
+ *     length but those too long for a tail's shared memory) issues no input
+ *     copy, so its first wait gives up after 200 ms; it records the timeout
+ *     (sidwt_check / sidwt_ragged_check: SIDWT_ETIMEOUT; a serving request:
+ *     status SIDWT_ETIMEOUT; sidwt_correlate_static: every peak record of the
+ *     call is lag -1, |r| 0, norm 0) and returns with nothing in flight.
  *   SIDWT_STALL_TC_SELFTEST: sidwt_tc_selftest issues neither its MMA nor
  *     the commit, so its wait gives up after 200 ms and sets bit 4 of its err
  *     word; the kernel still releases its tensor memory.
@@ -393,8 +395,9 @@ sidwt_status sidwt_ragged_reset_references(sidwt_ragged *r);
 sidwt_status sidwt_ragged_set_precision(sidwt_ragged *r, sidwt_precision prec);
 
 /* Synchronise `stream` and report device-side failures of earlier batches:
- * SIDWT_ETIMEOUT if a tensor-core CTA gave up on a bounded wait (its results
- * are incomplete), SIDWT_OK otherwise.  The record is cleared. */
+ * SIDWT_ETIMEOUT if a tensor-core CTA or the received analysis gave up on a
+ * bounded wait (the message says which; the results are incomplete),
+ * SIDWT_OK otherwise.  The record is cleared. */
 sidwt_status sidwt_ragged_check(sidwt_ragged *r, sidwt_stream stream);
 
 /* The current choice: mq_by_log2_band[k] shifts per thread for bands of
@@ -454,7 +457,9 @@ sidwt_status sidwt_server_submit(sidwt_server *s, int32_t wave_id, sidwt_filter 
                                  const void *y_host, int64_t *request_id);
 
 /* Bounded waits: SIDWT_ETIMEOUT if not finished within timeout_s; otherwise
- * the request's own status (SIDWT_ENOMEM if it was rejected). */
+ * the request's own status (SIDWT_ENOMEM if it was rejected, SIDWT_ETIMEOUT
+ * if a bounded device wait of its batch ran out: every request of that batch
+ * fails, and the lane's stored signals are rebuilt for later batches). */
 sidwt_status sidwt_server_wait(sidwt_server *s, int64_t request_id, double timeout_s);
 sidwt_status sidwt_server_drain(sidwt_server *s, double timeout_s);
 

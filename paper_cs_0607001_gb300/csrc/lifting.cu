@@ -1197,92 +1197,156 @@ __global__ void ragged_energy_kernel(const float2 *__restrict__ y, const RaggedL
 }
 
 
-// Long pulses of a ragged batch, in tiles of kTileSamples samples: the CTA
-// loads its samples and a periodic halo of kTileHalo on each side with
-// 128-bit loads, lifts levels 1..L in shared memory (each level's valid range
-// shrinks by the windows' reach; the halo keeps the tile's own range valid
-// down to level 5), writes the tile's own part of every level to the pyramid
-// and leaves per-level energy partials.  Output pair n of a level reads the
-// input pairs n - 3 .. n + 2; the level's buffer holds pairs [p0, p1) and the
-// outputs [n0, n1) = [p0 + 3, p1 - 3) rounded inwards to even n.
+// Long pulses of a ragged batch, in tiles of kTileSamples samples.  A
+// persistent CTA walks the tiles b, b + G, ...: while the levels of one tile
+// run, bulk copies (cp.async.bulk) bring the next tile's samples and a
+// periodic halo of kTileHalo on each side into the other of two input
+// buffers, so the HBM reads stay in flight across the kernel.  Levels 1..L
+// run in shared memory: each level's valid range shrinks by the windows'
+// reach, and the halo keeps the tile's own range valid down to level 5.
+// Each level writes the tile's own part to the pyramid.  Output pair n of a level
+// reads the input pairs n - 3 .. n + 2; the level's buffer holds pairs
+// [p0, p1) and the outputs are [n0, n1) = [p0 + 3, p1 - 3) rounded inwards to
+// even n.  Level 1 writes the work buffer W, level 2 the current input buffer
+// (free once level 1 has read it), and so on alternately.  Energies: a plain
+// FP32 partial per thread (a few terms) summed per warp for each level, and
+// the warps' sums added (compensated) once per tile into the tile's partials.
 constexpr int kTileThreads = 512;
-constexpr int kTileSmem = (kTileSamples + 2 * kTileHalo) * 8 * 3 / 2;
+constexpr int kTileIn = kTileSamples + 2 * kTileHalo;     // samples of one input buffer
+constexpr int kTileSmem = (2 * kTileIn + kTileIn / 2) * 8;  // two input buffers and W
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Samples [s0, s0 + cnt) of the periodic pulse (N samples) into dst.  N > cnt,
+// so the range wraps once at most: one or two copies.  s0, N and cnt are even
+// and the pulse starts 16-byte aligned, so every copy starts on a 16-byte
+// boundary and moves a multiple of 16 bytes.
+__device__ __forceinline__ void tile_load(float2 *dst, const float2 *pulse, int64_t N, int64_t s0, int cnt,
+                                          uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"((uint32_t)cnt * 8u)
+                 : "memory");
+    const int64_t a = s0 < 0 ? s0 + N : s0;
+    const int first = N - a < cnt ? (int)(N - a) : cnt;  // samples before the wrap
+    bulk_copy_g2s(dst, pulse + a, (uint32_t)first * 8u, bar);
+    if (first < cnt) bulk_copy_g2s(dst + first, pulse, (uint32_t)(cnt - first) * 8u, bar);
+}
 
 template <int F>
-__global__ void __launch_bounds__(kTileThreads, 3) ragged_tile_kernel(const float2 *__restrict__ y,
-                                                                   const RaggedTile *__restrict__ tiles,
+__global__ void __launch_bounds__(kTileThreads, 2) ragged_tile_kernel(const float2 *__restrict__ y,
+                                                                   const RaggedTile *__restrict__ tiles, int ntiles,
                                                                    float2 *__restrict__ pyr, double *__restrict__ part,
-                                                                   LiftCoef c) {
+                                                                   LiftCoef c, int32_t *__restrict__ err, int stall) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ float2 red[32];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float redf[kTileLevels + 1][kTileThreads / 32];
+    __shared__ int sfail;
     constexpr bool D4 = (F == SIDWT_D4);
-    const RaggedTile t = tiles[blockIdx.x];
-    const int64_t N = t.N;
-    float2 *in = reinterpret_cast<float2 *>(smraw);
-    float2 *out = in + (kTileSamples + 2 * kTileHalo);
-    int64_t s0 = (int64_t)t.t0 - kTileHalo;  // first sample of the level held in `in`
-    int cnt = t.Tc + 2 * kTileHalo;
-    {
-        const float4 *y4 = reinterpret_cast<const float4 *>(y + t.y_off);
-        float4 *d4 = reinterpret_cast<float4 *>(in);
-        // periodic; N and s0 are even, so a pair never straddles the wrap, and
-        // the halo is shorter than the pulse (N > kTileSamples + 2 kTileHalo on
-        // this path), so one wrap at most
-        for (int k = threadIdx.x; k < cnt / 2; k += blockDim.x) {
-            int64_t a = s0 + 2 * k;
-            a += a < 0 ? N : 0;
-            a -= a >= N ? N : 0;
-            d4[k] = y4[a / 2];
-        }
+    float2 *const buf0 = reinterpret_cast<float2 *>(smraw), *const buf1 = buf0 + kTileIn, *const W = buf1 + kTileIn;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sfail = 0;
     }
     __syncthreads();
-    {
-        EnAcc acc;
-        for (int k = threadIdx.x; k < t.Tc; k += blockDim.x) acc.add(sq2(in[kTileHalo + k]));
-        const double e0 = block_sum(acc, red);
-        if (threadIdx.x == 0) part[t.part_off] = e0;
-    }
-    for (int l = 1; l <= t.L; ++l) {
-        const int64_t p0 = s0 / 2, p1 = (s0 + cnt) / 2;
-        int64_t n0 = p0 + 3, n1 = p1 - 3;
-        n0 += n0 & 1;
-        n1 -= n1 & 1;
-        const int64_t K = N >> l, core0 = (int64_t)t.t0 >> l;
-        // outputs are indexed from n0 in 32 bits (a tile level holds at most kTileSamples + 2 kTileHalo)
-        const int m_end = (int)(n1 - n0), kofs = (int)(n0 - p0);
-        const int c0 = (int)(core0 - n0), c1 = c0 + (t.Tc >> l);
-        float2 *pl = pyr + t.pyr_off + 2 * N - 4 * K + n0, *ph = pl + K;
-        const float4 *q = reinterpret_cast<const float4 *>(in) + kofs;
-        EnAcc acc;
-        for (int m = threadIdx.x; m < m_end; m += blockDim.x) {
-            const int k = m;
-            float2 E[5], O[5];
-            float4 prev = D4 ? q[k - 3] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                const float4 cur = q[k - 2 + i];
-                E[i] = make_float2(cur.x, cur.y);
-                O[i] = D4 ? make_float2(prev.z, prev.w) : make_float2(cur.z, cur.w);  // D4 odd phase: v[2m-1]
-                prev = cur;
-            }
-            lift_window<F, SIDE_Y, 2>(E, O, c);
-            const float2 lo = scale2(c.ce, E[2]);
-            const float2 hi = D4 ? scale2(c.co, make_float2(E[2].x + O[1].x, E[2].y + O[1].y)) : scale2(c.co, O[2]);
-            out[m] = lo;
-            if (m >= c0 && m < c1) {
-                pl[m] = lo;
-                ph[m] = hi;
-                acc.add(sq2(lo));
-            }
+    // stall (test hook, sidwt_debug_stall): no copy is issued, so the first
+    // wait runs out and the CTA records the timeout with nothing in flight
+    auto load = [&](int b, float2 *dst, uint64_t *br) {
+        const RaggedTile w = tiles[b];
+        tile_load(dst, y + w.y_off, w.N, (int64_t)w.t0 - kTileHalo, w.Tc + 2 * kTileHalo, br);
+    };
+    if (tid == 0 && !stall) load(blockIdx.x, buf0, &bar[0]);  // the grid has at most ntiles CTAs
+    int issued = stall ? 0 : 1, landed = 0;  // copies issued / waited for (thread 0's bookkeeping)
+    int i = 0;
+    for (int b = blockIdx.x; b < ntiles; b += G, ++i) {
+        const int s = i & 1;
+        float2 *const cur = s ? buf1 : buf0;
+        if (tid == 0 && !stall && b + G < ntiles) {
+            // the other buffer held tile i - 1, whose accesses ended at its last barrier
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            load(b + G, s ? buf0 : buf1, &bar[s ^ 1]);
+            ++issued;
         }
-        const double el = block_sum(acc, red);  // its barriers also end this level's reads of `in`
-        if (threadIdx.x == 0) part[t.part_off + l] = el;
-        float2 *tmp = in;
-        in = out;
-        out = tmp;
-        s0 = n0;
-        cnt = (int)(n1 - n0);
+        if (!pipe_wait(&bar[s], (uint32_t)((i >> 1) & 1))) sfail = 1;
         __syncthreads();
+        if (sfail) break;
+        if (tid == 0) ++landed;
+        const RaggedTile t = tiles[b];
+        const int64_t N = t.N;
+        // level 0: the energy of the tile's own samples
+        {
+            const float4 *q = reinterpret_cast<const float4 *>(cur + kTileHalo);
+            float e = 0.f;
+            for (int k = tid; k < t.Tc / 2; k += kTileThreads) {
+                const float4 v = q[k];
+                e = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, e))));
+            }
+            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+            if (lane == 0) redf[0][warp] = e;
+        }
+        float2 *in = cur, *out = W;
+        int64_t s0 = (int64_t)t.t0 - kTileHalo;  // first sample of the level held in `in`
+        int cnt = t.Tc + 2 * kTileHalo;
+        for (int l = 1; l <= t.L; ++l) {
+            const int64_t p0 = s0 / 2, p1 = (s0 + cnt) / 2;
+            int64_t n0 = p0 + 3, n1 = p1 - 3;
+            n0 += n0 & 1;
+            n1 -= n1 & 1;
+            const int64_t K = N >> l, core0 = (int64_t)t.t0 >> l;
+            // outputs are indexed from n0 in 32 bits (a tile level holds at most kTileIn samples)
+            const int m_end = (int)(n1 - n0), kofs = (int)(n0 - p0);
+            const int c0 = (int)(core0 - n0), c1 = c0 + (t.Tc >> l);
+            float2 *pl = pyr + t.pyr_off + 2 * N - 4 * K + n0, *ph = pl + K;
+            const float4 *q = reinterpret_cast<const float4 *>(in) + kofs;
+            float e = 0.f;
+            for (int m = tid; m < m_end; m += kTileThreads) {
+                float2 E[5], O[5];
+                float4 prev = D4 ? q[m - 3] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const float4 cv = q[m - 2 + k];
+                    E[k] = make_float2(cv.x, cv.y);
+                    O[k] = D4 ? make_float2(prev.z, prev.w) : make_float2(cv.z, cv.w);  // D4 odd phase: v[2m-1]
+                    prev = cv;
+                }
+                lift_window<F, SIDE_Y, 2>(E, O, c);
+                const float2 lo = scale2(c.ce, E[2]);
+                const float2 hi = D4 ? scale2(c.co, make_float2(E[2].x + O[1].x, E[2].y + O[1].y)) : scale2(c.co, O[2]);
+                out[m] = lo;
+                if (m >= c0 && m < c1) {
+                    pl[m] = lo;
+                    ph[m] = hi;
+                    e = fmaf(lo.x, lo.x, fmaf(lo.y, lo.y, e));
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+            if (lane == 0) redf[l][warp] = e;
+            float2 *tmp = in;
+            in = out;
+            out = tmp;
+            s0 = n0;
+            cnt = m_end;
+            __syncthreads();  // this level's reads of `in` end before the next level overwrites it
+        }
+        if (tid <= t.L) {
+            EnAcc a;
+            for (int w = 0; w < kTileThreads / 32; ++w) a.add(redf[tid][w]);
+            part[t.part_off + tid] = a.total();
+        }
+        // the next iteration's wait and barrier order these reads of redf
+        // before its level-0 writes
+    }
+    if (tid == 0 && sfail) {
+        // let this CTA's own copies land before its shared memory is released
+        for (int k = landed; k < issued; ++k) pipe_wait(&bar[k & 1], (uint32_t)((k >> 1) & 1));
+        atomicOr(err, kErrAnalysisWait);
     }
 }
 
@@ -1317,9 +1381,14 @@ __global__ void __launch_bounds__(kAnalyzeThreads) ragged_tail_kernel(const Ragg
 template <int F>
 static cudaError_t launch_ragged_tiles(const RaggedTile *tiles, int ntiles, const RaggedTail *tails, int ntails,
                                        int64_t maxN2, const float2 *y, float2 *pyr, double *yen, double *part,
-                                       cudaStream_t s) {
+                                       int32_t *err, cudaStream_t s) {
     const LiftCoef c = lift_coef(F, SIDE_Y);
-    ragged_tile_kernel<F><<<ntiles, kTileThreads, kTileSmem, s>>>(y, tiles, pyr, part, c);
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::min(ntiles, 2 * sms);  // persistent: two CTAs per SM
+    const int stall = (debug_stall_flags() & SIDWT_STALL_ANALYSIS) ? 1 : 0;
+    ragged_tile_kernel<F><<<grid, kTileThreads, kTileSmem, s>>>(y, tiles, ntiles, pyr, part, c, err, stall);
     ragged_tail_kernel<F><<<ntails, kAnalyzeThreads, (size_t)(maxN2 + maxN2 / 2) * 8, s>>>(tails, part, pyr, yen, c);
     return cudaGetLastError();
 }
@@ -1400,15 +1469,15 @@ sidwt_status analyze_ragged(const float2 *y, const RaggedLiftGroups &g, float2 *
             switch (f) {
             case SIDWT_D4:
                 e = launch_ragged_tiles<SIDWT_D4>(g.tiles[f], g.n_tiles[f], g.tails[f], g.n_tails[f], g.maxN_tail[f], y,
-                                                  pyr, yen, part, s);
+                                                  pyr, yen, part, err, s);
                 break;
             case SIDWT_LEGALL53:
                 e = launch_ragged_tiles<SIDWT_LEGALL53>(g.tiles[f], g.n_tiles[f], g.tails[f], g.n_tails[f],
-                                                        g.maxN_tail[f], y, pyr, yen, part, s);
+                                                        g.maxN_tail[f], y, pyr, yen, part, err, s);
                 break;
             default:
                 e = launch_ragged_tiles<SIDWT_CDF97>(g.tiles[f], g.n_tiles[f], g.tails[f], g.n_tails[f], g.maxN_tail[f],
-                                                     y, pyr, yen, part, s);
+                                                     y, pyr, yen, part, err, s);
             }
             nl += 2;
         }

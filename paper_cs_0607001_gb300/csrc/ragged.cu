@@ -1719,6 +1719,10 @@ sidwt_status sidwt_ragged_check(sidwt_ragged *r, sidwt_stream stream) {
         set_error("a tensor-core CTA gave up on a bounded wait; results are incomplete");
         return SIDWT_ETIMEOUT;
     }
+    if (h & kErrAnalysisWait) {
+        set_error("the received analysis gave up waiting for an input copy; the pyramids and the peaks are incomplete");
+        return SIDWT_ETIMEOUT;
+    }
     return SIDWT_OK;
 }
 
@@ -1742,3 +1746,5 @@ sidwt_status sidwt_ragged_tc_weights(const sidwt_ragged *r, float *w) {
 }
 
 }  // extern "C"
+
+int32_t *sidwt::ragged_error_record(sidwt_ragged *r) { return r->err; }

@@ -83,6 +83,7 @@ struct Lane {
     int32_t *lag_h = nullptr;
     float *mag_h = nullptr;
     double *norm_h = nullptr;
+    int32_t *err_h = nullptr;  // the ragged object's device error record, copied out with each batch
     int64_t cap_slots = 0;
     bool busy = false;
     std::vector<Request *> batch;
@@ -274,6 +275,10 @@ sidwt_status launch_lane(sidwt_server *s, Lane &L) {
     cudaError_t e = cudaMemcpyAsync(L.lag_h, L.lag_d, slots * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(L.mag_h, L.mag_d, slots * sizeof(float), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(L.norm_h, L.norm_d, slots * sizeof(double), cudaMemcpyDeviceToHost, st);
+    // a bounded device wait that ran out (bits of the record) fails the batch
+    int32_t *rec = ragged_error_record(L.rg);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.err_h, rec, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(rec, 0, sizeof(int32_t), st);
     if (e == cudaSuccess) e = cudaEventRecord(L.done, st);
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "request result copy");
 }
@@ -285,7 +290,10 @@ void serve(sidwt_server *s) {
         for (Lane &L : s->lanes) {
             if (L.busy) {
                 cudaError_t q = cudaEventQuery(L.done);
-                if (q == cudaSuccess) {
+                if (q == cudaSuccess && *L.err_h) {
+                    fail_lane(s, L, SIDWT_ETIMEOUT);
+                    progressed = true;
+                } else if (q == cudaSuccess) {
                     complete_lane(s, L);
                     progressed = true;
                 } else if (q != cudaErrorNotReady) {
@@ -388,7 +396,8 @@ sidwt_status sidwt_server_create(const sidwt_server_config *cfg, sidwt_server **
             cudaMalloc(&L.norm_d, slots * sizeof(double)) != cudaSuccess ||
             cudaMallocHost(&L.lag_h, slots * sizeof(int32_t)) != cudaSuccess ||
             cudaMallocHost(&L.mag_h, slots * sizeof(float)) != cudaSuccess ||
-            cudaMallocHost(&L.norm_h, slots * sizeof(double)) != cudaSuccess) {
+            cudaMallocHost(&L.norm_h, slots * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&L.err_h, sizeof(int32_t)) != cudaSuccess) {
             cudaGetLastError();
             sidwt_server_destroy(s);
             if (!st) set_error("server allocation failed");
@@ -525,8 +534,9 @@ sidwt_status sidwt_server_result(sidwt_server *s, int64_t request_id, int32_t *l
         return SIDWT_EBUSY;
     }
     if (r->status) {
-        set_error(r->status == SIDWT_ENOMEM ? "request rejected: larger than a lane's share of the memory cap"
-                                            : "request failed");
+        set_error(r->status == SIDWT_ENOMEM     ? "request rejected: larger than a lane's share of the memory cap"
+                  : r->status == SIDWT_ETIMEOUT ? "request failed: a bounded device wait of its batch ran out"
+                                                : "request failed");
         return r->status;
     }
     const size_t n = r->lag.size();
@@ -632,6 +642,7 @@ sidwt_status sidwt_server_destroy(sidwt_server *s) {
         if (L.lag_h) cudaFreeHost(L.lag_h);
         if (L.mag_h) cudaFreeHost(L.mag_h);
         if (L.norm_h) cudaFreeHost(L.norm_h);
+        if (L.err_h) cudaFreeHost(L.err_h);
     }
     for (float2 *w : s->waves) cudaFree(w);
     for (auto &kv : s->reqs) delete kv.second;

@@ -448,4 +448,7 @@ cudaError_t prepare_kernels();
 sidwt_status ragged_reserve_tc(sidwt_ragged *r, int64_t stored_elems);
 // whether the reserved stores hold that many more elements without growing
 bool ragged_room(const sidwt_ragged *r, int64_t tree_elems, int64_t xen_elems, int64_t tc_elems);
+// the device error record of a ragged object (kErr* bits; the serving loop
+// copies it out with each batch's results)
+int32_t *ragged_error_record(sidwt_ragged *r);
 }  // namespace sidwt
