@@ -1280,17 +1280,6 @@ __global__ void __launch_bounds__(kTileThreads, 2) ragged_tile_kernel(const floa
         if (tid == 0) ++landed;
         const RaggedTile t = tiles[b];
         const int64_t N = t.N;
-        // level 0: the energy of the tile's own samples
-        {
-            const float4 *q = reinterpret_cast<const float4 *>(cur + kTileHalo);
-            float e = 0.f;
-            for (int k = tid; k < t.Tc / 2; k += kTileThreads) {
-                const float4 v = q[k];
-                e = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, e))));
-            }
-            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-            if (lane == 0) redf[0][warp] = e;
-        }
         float2 *in = cur, *out = W;
         int64_t s0 = (int64_t)t.t0 - kTileHalo;  // first sample of the level held in `in`
         int cnt = t.Tc + 2 * kTileHalo;
@@ -1305,16 +1294,20 @@ __global__ void __launch_bounds__(kTileThreads, 2) ragged_tile_kernel(const floa
             const int c0 = (int)(core0 - n0), c1 = c0 + (t.Tc >> l);
             float2 *pl = pyr + t.pyr_off + 2 * N - 4 * K + n0, *ph = pl + K;
             const float4 *q = reinterpret_cast<const float4 *>(in) + kofs;
-            float e = 0.f;
+            // e0: the energy of the tile's own samples (level 0), from level 1's
+            // windows: the centre pair of output m is the input pair n0 + m, so
+            // the core outputs' centres are exactly the tile's own pairs
+            float e = 0.f, e0 = 0.f;
             for (int m = tid; m < m_end; m += kTileThreads) {
                 float2 E[5], O[5];
-                float4 prev = D4 ? q[m - 3] : make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 prev = D4 ? q[m - 3] : make_float4(0.f, 0.f, 0.f, 0.f), ctr;
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
                     const float4 cv = q[m - 2 + k];
                     E[k] = make_float2(cv.x, cv.y);
                     O[k] = D4 ? make_float2(prev.z, prev.w) : make_float2(cv.z, cv.w);  // D4 odd phase: v[2m-1]
                     prev = cv;
+                    if (k == 2) ctr = cv;
                 }
                 lift_window<F, SIDE_Y, 2>(E, O, c);
                 const float2 lo = scale2(c.ce, E[2]);
@@ -1324,10 +1317,15 @@ __global__ void __launch_bounds__(kTileThreads, 2) ragged_tile_kernel(const floa
                     pl[m] = lo;
                     ph[m] = hi;
                     e = fmaf(lo.x, lo.x, fmaf(lo.y, lo.y, e));
+                    if (l == 1) e0 = fmaf(ctr.x, ctr.x, fmaf(ctr.y, ctr.y, fmaf(ctr.z, ctr.z, fmaf(ctr.w, ctr.w, e0))));
                 }
             }
             for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
             if (lane == 0) redf[l][warp] = e;
+            if (l == 1) {
+                for (int o = 16; o > 0; o >>= 1) e0 += __shfl_xor_sync(0xffffffffu, e0, o);
+                if (lane == 0) redf[0][warp] = e0;
+            }
             float2 *tmp = in;
             in = out;
             out = tmp;
