@@ -218,7 +218,7 @@ def run_reference(args):
     from paper_cs_0607001_gb300 import multigpu as M
     rank, world, _ = M.dist_env()
     if rank != 0:
-        return 0
+        return None
     w = inputs.two_ref_batch(B=B, N=N, J=J)
     cores = os.cpu_count() or 1
     step_seconds = min(10.0, max(2.0, 150.0 / max(1, args.steps + args.warmup)))
@@ -241,8 +241,7 @@ def run_reference(args):
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line))
-    return 0
+    return line
 
 
 # --------------------------------------------------------------------------
@@ -513,11 +512,11 @@ def run_ours(args):
         "accuracy_vs_oracle": acc,
         "peak_at_injected_delay_scale0": hit,
     }
-    if rank == 0:
-        print(json.dumps(line))
     for p in list(plans.values()) + [pint]:
         p.close()
-    return 0
+    if world == 1 and not args.no_extra:
+        line["other_configs"] = other_configs(args)
+    return line if rank == 0 else None
 
 
 
@@ -710,10 +709,8 @@ def run_ragged_workload(args):
             "what": "correlation stage of one direct call, plain FP32 CUDA-core path / this precision"},
         "peak_at_injected_delay_scale0": hit,
     }
-    if rank == 0:
-        print(json.dumps(line))
     rg.close()
-    return 0
+    return line if rank == 0 else None
 
 
 def ragged_roofline(prec, achieved, flops, ms):
@@ -760,19 +757,21 @@ def run_sweep_workload(args):
     norm = torch.empty((B, Js + 1), dtype=torch.float64, device=dev)
     flops = float(nref) * B * 8.0 * Ns * Ns * (2.0 - 2.0 ** -Js)
     # sampled pairs for the error: pulses 0..47 against references 0 and 33
+    # (the CPU leg, which also gives the errors; skipped with --no-cpu)
     sample_p = np.arange(48)
-    sample_r = [0, 33]
-    from oracle import oracle as O
-    t0 = time.perf_counter()
-    r_or = {}
-    for r in sample_r:
-        X = np.repeat(w["refs"][r:r + 1].astype(np.complex128), len(sample_p), axis=0)
-        out = O.correlate_batch(2, X, w["y"][sample_p].astype(np.complex128), Js, want_r=True)
-        r_or[r] = out[3]
-    cpu_s = time.perf_counter() - t0
-    cpu = {"value": len(sample_r) * len(sample_p) * Ns / cpu_s / 1e9, "unit": UNIT, "cores": os.cpu_count(),
-           "kind": "oracle", "sample": f"{len(sample_r) * len(sample_p)} pairs (pulses 0-47 x references 0, 33), "
-                                       f"all lags and scales, {cpu_s:.1f} s wall"}
+    sample_r = [0, 33] if not args.no_cpu else []
+    r_or, cpu = {}, None
+    if sample_r:
+        from oracle import oracle as O
+        t0 = time.perf_counter()
+        for r in sample_r:
+            X = np.repeat(w["refs"][r:r + 1].astype(np.complex128), len(sample_p), axis=0)
+            out = O.correlate_batch(2, X, w["y"][sample_p].astype(np.complex128), Js, want_r=True)
+            r_or[r] = out[3]
+        cpu_s = time.perf_counter() - t0
+        cpu = {"value": len(sample_r) * len(sample_p) * Ns / cpu_s / 1e9, "unit": UNIT, "cores": os.cpu_count(),
+               "kind": "oracle", "sample": f"{len(sample_r) * len(sample_p)} pairs (pulses 0-47 x references 0, 33), "
+                                           f"all lags and scales, {cpu_s:.1f} s wall"}
     stream = torch.cuda.current_stream()
     precisions = ["bf16x3", "tf32x3", "fp32"] if args.no_plain is False else ["bf16x3", "tf32x3"]
     res = {}
@@ -795,8 +794,7 @@ def run_sweep_workload(args):
         plan.set_timing(False)
         t = plan.read_timing(reset=True)
         # error on the sampled pairs
-        errs = np.zeros(Js + 1)
-        bound_ratio = 0.0
+        errs = np.zeros(Js + 1) if sample_r else None
         for r in sample_r:
             R = plan.correlate(ids_all[r][:len(sample_p)], y[:len(sample_p)].contiguous(), precision=prec,
                                want_r=True)
@@ -816,7 +814,7 @@ def run_sweep_workload(args):
         res[prec] = {"gsamples_s": nref * B * Ns / (ms * 1e-3) / 1e9, "ms_per_step": ms, "steps": steps,
                      "correlate_ms_per_call": t["correlate_ms"] / max(1, t["correlate_calls"]),
                      "achieved_tflops": flops / nref / (t["correlate_ms"] / max(1, t["correlate_calls"]) * 1e-3) / 1e12,
-                     "max_err_rel_peak_by_scale": errs.tolist(),
+                     "max_err_rel_peak_by_scale": errs.tolist() if errs is not None else None,
                      "peak_lags_equal_to_first_precision": same}
     clk = clocks.stop()
     bf = res["bf16x3"]
@@ -835,8 +833,7 @@ def run_sweep_workload(args):
         "per_precision": res,
         "error_what": "per scale, max over 96 sampled (pulse, reference) pairs of max_D |r - r_oracle| / max_D |r_oracle|",
     }
-    print(json.dumps(line))
-    return 0
+    return line
 
 
 def run_c2f_workload(args):
@@ -899,8 +896,7 @@ def run_c2f_workload(args):
                                 "scale0_lag_at_injected_delay": float(np.mean(lag_c2f[:, 0] == w["delays"]))},
         "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
     }
-    print(json.dumps(line))
-    return 0
+    return line
 
 
 def run_multitarget_workload(args):
@@ -960,8 +956,7 @@ def run_multitarget_workload(args):
         "detections_mean_by_scale": count.mean(axis=0).tolist(),
         "strongest_target_detected_at_scale0": hit0,
     }
-    print(json.dumps(line))
-    return 0
+    return line
 
 
 def run_t97_workload(args):
@@ -1035,8 +1030,7 @@ def run_t97_workload(args):
                                "correlate call per t", "l2": "inputs larger than L2"},
         "cpu_baseline": cpu, "clocks": clk, "per_t": rows,
     }
-    print(json.dumps(line))
-    return 0
+    return line
 
 
 def run_single_workload(args):
@@ -1113,9 +1107,8 @@ def run_single_workload(args):
         "peak_at_injected_delay": ok,
         "cpu_baseline": cpu, "clocks": clk,
     }
-    print(json.dumps(line))
     p.close()
-    return 0
+    return line
 
 
 def run_serve_workload(args):
@@ -1242,8 +1235,49 @@ def run_serve_workload(args):
         "cpu_baseline": cpu,
         "peak_at_injected_delay_scale0": float(np.mean(hits)) if hits else None,
     }
-    print(json.dumps(line))
-    return 0
+    return line
+
+def other_configs(args) -> dict:
+    """Short legs of the other configurations, run after the default line's
+    timing so that one run records them all:
+      * the precision sweep (64 references x 16384 pulses, N = 4096, J = 6):
+        BF16x3 and 3xTF32; the plain FP32 path and the errors against the
+        oracle are left to --workload sweep;
+      * the 10000-pulse ragged batch: the library's default tile weights,
+        end to end included, no plain FP32 leg;
+      * the serving loop at 1000 and 20000 requests/s offered, 3 s or 6000
+        requests each.
+    Each leg keeps its own workload's timing rules (warm-up, CUDA events,
+    clocks sampled during its timed region).  A leg that fails is recorded
+    in its entry rather than raised."""
+    import copy
+
+    out = {}
+    common = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "roofline", "clocks")
+
+    def leg(name, fn, keep, **over):
+        a = copy.copy(args)
+        for k, v in over.items():
+            setattr(a, k, v)
+        t0 = time.perf_counter()
+        try:
+            line = fn(a)
+            d = {k: line[k] for k in keep if k in line}
+        except Exception as e:
+            d = {"error": f"{type(e).__name__}: {e}"}
+        d["wall_s"] = round(time.perf_counter() - t0, 1)
+        out[name] = d
+
+    leg("c3_precision_sweep", run_sweep_workload, common + ("per_precision",),
+        no_plain=True, no_cpu=True, steps=3, warmup=3, pulses=4096)
+    leg("c4_ragged_batch", run_ragged_workload,
+        common + ("e2e", "stages_ms_direct_call", "gpu_launches", "peak_at_injected_delay_scale0"),
+        no_plain=True, no_cpu=True, no_autotune=True, steps=3, warmup=3, items=10000)
+    leg("c5_serving", run_serve_workload,
+        ("metric", "value", "unit", "dtype", "config", "latency_ms", "saturated_latency_ms", "per_rate", "clocks"),
+        no_cpu=True, rates="1000,20000", seconds=3.0, max_requests=6000, pool=2048, lanes=4)
+    return out
+
 
 def main():
     ap = argparse.ArgumentParser()
@@ -1266,24 +1300,17 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="ragged workload: keep the library's untuned tile weights (short profiler captures)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default workload: skip the short legs of the other configurations")
     args = ap.parse_args()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload == "ragged":
-        return run_ragged_workload(args)
-    if args.workload == "single":
-        return run_single_workload(args)
-    if args.workload == "serve":
-        return run_serve_workload(args)
-    if args.workload == "sweep":
-        return run_sweep_workload(args)
-    if args.workload == "c2f":
-        return run_c2f_workload(args)
-    if args.workload == "multitarget":
-        return run_multitarget_workload(args)
-    if args.workload == "t97":
-        return run_t97_workload(args)
-    return run_ours(args)
+    fn = run_reference if args.impl == "reference" else {
+        "ragged": run_ragged_workload, "single": run_single_workload, "serve": run_serve_workload,
+        "sweep": run_sweep_workload, "c2f": run_c2f_workload, "multitarget": run_multitarget_workload,
+        "t97": run_t97_workload}.get(args.workload, run_ours)
+    line = fn(args)
+    if isinstance(line, dict):
+        print(json.dumps(line))
+    return 0
 
 
 if __name__ == "__main__":
