@@ -148,14 +148,15 @@ def source_sha(path: Path, kernel: str | None = None) -> str:
     return hashlib.sha256(data).hexdigest()[:16]
 
 
-def committed_traffic(kernel: str, src: Path) -> float | None:
+def committed_traffic(kernel: str, src: Path, key: str | None = None) -> float | None:
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current source of that kernel (its own function text, so that edits
-    elsewhere in the file keep the figure)."""
+    elsewhere in the file keep the figure).  key: the entry, when one kernel
+    has figures for several workloads (default: the kernel's name)."""
     p = ROOT / "profiles" / "traffic.json"
     if not p.exists():
         return None
-    d = json.loads(p.read_text()).get(kernel)
+    d = json.loads(p.read_text()).get(key or kernel)
     if not d or d.get("kernel_sha") != source_sha(src, kernel.split("::")[-1]):
         return None
     return d.get("dram_bytes_per_launch")
@@ -827,7 +828,12 @@ def run_sweep_workload(args):
                                "CDF 9/7; one correlate call per reference",
                    "pairs_per_step": nref * B, "l2": "inputs larger than L2 (537 MB complex64 pulses)"},
         "roofline": {"bound": "tensor", "achieved": bf["achieved_tflops"], "peak": pk, "unit": "TFLOP/s",
-                     "frac": bf["achieved_tflops"] / pk, "traffic": None, "kernel": "corr_tc_kernel",
+                     "frac": bf["achieved_tflops"] / pk,
+                     "traffic": committed_traffic("corr_tc_kernel",
+                                                  ROOT / "paper_cs_0607001_gb300" / "csrc" / "corr_tc.cu",
+                                                  key="corr_tc_kernel@precision_sweep"),
+                     "traffic_unit": "bytes per correlate call (one reference against the 16384 pulses, all scales)",
+                     "kernel": "corr_tc_kernel",
                      "peak_source": "measured bf16 dense (burst) / 3 products"},
         "cpu_baseline": cpu, "clocks": clk,
         "per_precision": res,
