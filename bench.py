@@ -1243,6 +1243,61 @@ def run_serve_workload(args):
     }
     return line
 
+def run_store_workload(args):
+    """Stored-signal SIDWT trees (a3) built in batches: each step stores 256
+    signals of N = 65536, J = 8, CDF 9/7 through sidwt_ragged_store_references
+    (trees of up to 64 signals per pass, J + 2 launches per pass and filter)
+    after resetting the store.  FP32 builds the trees and their energies;
+    BF16x3 also packs the tensor-core operands.  value = stored samples / s;
+    the roofline counts the minimal bytes of the FP32 build (each signal read
+    once, its tree of 2 J N complex64 written once) over the call's time."""
+    import torch
+
+    from paper_cs_0607001_gb300 import sidwt as S
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n, Ns, Js = 256, 65536, 8
+    g = np.random.default_rng(17)
+    x = torch.from_numpy(((g.standard_normal(n * Ns) + 1j * g.standard_normal(n * Ns)) / np.sqrt(2))
+                         .astype(np.complex64)).to(dev)
+    offs = np.arange(n, dtype=np.int64) * Ns
+    stream = torch.cuda.current_stream()
+    res = {}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for prec in ("fp32", "bf16x3"):
+        with S.Ragged() as rg:
+            rg.set_precision(prec)
+
+            def step():
+                rg.reset_references()
+                rg.store_references(["cdf97"] * n, [Ns] * n, [Js] * n, x, offs)
+
+            for _ in range(max(3, args.warmup)):
+                step()
+            torch.cuda.synchronize()
+            ms, per = _timed_steps(step, max(3, args.steps), stream, torch)
+            rg.check()
+        res[prec] = {"ms_per_step": ms, "gsamples_s": n * Ns / (ms * 1e-3) / 1e9}
+    clk = clocks.stop()
+    nbytes = n * (Ns * 8 + 2 * Js * Ns * 8)
+    peak = measured_peaks().get("hbm_gbs", 6800.0)
+    ach = nbytes / (res["fp32"]["ms_per_step"] * 1e-3) / 1e9
+    return {
+        "metric": "stored-signal SIDWT trees, samples/s", "value": res["fp32"]["gsamples_s"], "unit": "GSamples/s",
+        "n_gpus": 1, "steps": max(3, args.steps), "warmup": max(3, args.warmup),
+        "ms_per_step": res["fp32"]["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"stored trees: {n} signals of N={Ns}, J={Js}, CDF 9/7 per step, 64 per pass",
+                   "l2": f"trees larger than L2 ({nbytes / 1e9:.2f} GB written per step)"},
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                     "traffic": None, "kernel": "tree_level_batch_kernel + tree_energy_batch_kernel",
+                     "what": "minimal bytes (signal read once, tree written once) over the whole store call"},
+        "per_precision": res, "clocks": clk,
+    }
+
+
 def other_configs(args) -> dict:
     """Short legs of the other configurations, run after the default line's
     timing so that one run records them all:
@@ -1296,7 +1351,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--pulses", type=int, default=4096)
     ap.add_argument("--items", type=int, default=10000)
-    ap.add_argument("--workload", default="two_ref", choices=["two_ref", "ragged", "single", "serve", "sweep", "c2f", "multitarget", "t97"])
+    ap.add_argument("--workload", default="two_ref", choices=["two_ref", "ragged", "single", "serve", "sweep", "c2f", "multitarget", "t97", "store"])
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000,100000,200000")
     ap.add_argument("--seconds", type=float, default=10.0)
     ap.add_argument("--max-requests", type=int, default=20000)
@@ -1312,7 +1367,7 @@ def main():
     fn = run_reference if args.impl == "reference" else {
         "ragged": run_ragged_workload, "single": run_single_workload, "serve": run_serve_workload,
         "sweep": run_sweep_workload, "c2f": run_c2f_workload, "multitarget": run_multitarget_workload,
-        "t97": run_t97_workload}.get(args.workload, run_ours)
+        "t97": run_t97_workload, "store": run_store_workload}.get(args.workload, run_ours)
     line = fn(args)
     if isinstance(line, dict):
         print(json.dumps(line))

@@ -281,11 +281,24 @@ __device__ __forceinline__ void window_pair(const TIn *__restrict__ v, int64_t K
                                             const LiftCoef &c, float2 &l, float2 &h) {
     using Sh = LiftShape<F, S>;
     float2 E[2 * WR + 1], O[2 * WR + 1];
+    // E[i] sits at base + 2 i and O[i] at base + 2 i -+ 1: a window that does
+    // not reach past either end of the row reads it directly, the others wrap
+    // (periodic extension, any number of times for rows shorter than it)
+    const int64_t base = 2 * (n - WR) - child;
+    if (base - 1 >= 0 && base + 4 * WR + 1 < K) {
+        const TIn *p = v + base;
 #pragma unroll
-    for (int i = 0; i <= 2 * WR; ++i) {
-        const int64_t m = n - WR + i;
-        E[i] = to_f2(v[wrapi(2 * m - child, K)]);
-        O[i] = to_f2(v[wrapi(Sh::d4 ? 2 * m - 1 - child : 2 * m + 1 - child, K)]);
+        for (int i = 0; i <= 2 * WR; ++i) {
+            E[i] = to_f2(p[2 * i]);
+            O[i] = to_f2(p[Sh::d4 ? 2 * i - 1 : 2 * i + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i <= 2 * WR; ++i) {
+            const int64_t m = n - WR + i;
+            E[i] = to_f2(v[wrapi(2 * m - child, K)]);
+            O[i] = to_f2(v[wrapi(Sh::d4 ? 2 * m - 1 - child : 2 * m + 1 - child, K)]);
+        }
     }
     lift_window<F, S, WR>(E, O, c);
     l = scale2(c.ce, E[WR]);

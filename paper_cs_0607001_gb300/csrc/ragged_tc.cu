@@ -499,21 +499,26 @@ struct StoreScales {
     int n;
 };
 
-// Element `local` of one scale's packed stored operand; the bands of the
-// scale's level start at tree[z.level_off] and are N elements apart.
-__device__ __forceinline__ __nv_bfloat16 stored_element(const float2 *__restrict__ tree, int64_t N,
-                                                        const StoreScale &z, int64_t local);
+// Chunk q (elements 8 q .. 8 q + 7, one 16-byte store) of one scale's packed
+// stored operand; the bands of the scale's level start at tree[z.level_off]
+// and are N elements apart.
+__device__ __forceinline__ uint4 stored_chunk(const float2 *__restrict__ tree, int64_t N, const StoreScale &z,
+                                              int64_t q);
 
 // Stored operand of one signal: element [b nv + v][h][row][blk][2 c + plane][e]
 // = hi (h = 0) or lo part of plane(w_{v,b}[(k0 + c + 8 s) mod K']), plane 0
-// Re, 1 Im, at polyphase sample s = row Lr + 8 blk + e.
-__global__ void pack_stored_kernel(const float2 *__restrict__ tree, int64_t N, StoreScales sc, int64_t total,
+// Re, 1 Im, at polyphase sample s = row Lr + 8 blk + e.  A thread writes the
+// 8 elements e of one (..., c, plane) chunk: every index but s is shared, so
+// the index arithmetic runs once per chunk.  Scale counts are multiples of
+// 128 elements and offsets multiples of 64, so chunks never straddle scales.
+__global__ void pack_stored_kernel(const float2 *__restrict__ tree, int64_t N, StoreScales sc, int64_t chunks,
                                    __nv_bfloat16 *__restrict__ out) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < chunks; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = 8 * q;
         int k = 0;
         while (k + 1 < sc.n && e >= sc.s[k + 1].first) ++k;
         const StoreScale &z = sc.s[k];
-        out[z.out_off + e - z.first] = stored_element(tree, N, z, e - z.first);
+        *reinterpret_cast<uint4 *>(out + z.out_off + e - z.first) = stored_chunk(tree, N, z, (e - z.first) >> 3);
     }
 }
 
@@ -531,8 +536,9 @@ struct PackBatch {
 };
 
 __global__ void pack_stored_batch_kernel(const float2 *__restrict__ tree, const __grid_constant__ PackBatch b,
-                                         int64_t total, __nv_bfloat16 *__restrict__ out) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+                                         int64_t chunks, __nv_bfloat16 *__restrict__ out) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < chunks; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = 8 * q;
         int lo = 0, hi = b.n - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -540,16 +546,15 @@ __global__ void pack_stored_batch_kernel(const float2 *__restrict__ tree, const 
             else hi = mid - 1;
         }
         const StoreScale &z = b.s[lo].z;
-        out[z.out_off + e - z.first] = stored_element(tree, b.s[lo].N, z, e - z.first);
+        *reinterpret_cast<uint4 *>(out + z.out_off + e - z.first) = stored_chunk(tree, b.s[lo].N, z, (e - z.first) >> 3);
     }
 }
 
-__device__ __forceinline__ __nv_bfloat16 stored_element(const float2 *__restrict__ tree, int64_t N,
-                                                    const StoreScale &z, int64_t local) {
-    const int ee = (int)(local & 7);
-    const int ch = (int)((local >> 3) & 15);
+__device__ __forceinline__ uint4 stored_chunk(const float2 *__restrict__ tree, int64_t N, const StoreScale &z,
+                                              int64_t q) {
+    const int ch = (int)(q & 15);
     const int nblk = z.Lr >> 3;
-    int64_t rest = local >> 7;
+    int64_t rest = q >> 4;
     const int blk = (int)(rest % nblk);
     rest /= nblk;
     const int64_t row = rest % z.Rs;
@@ -558,15 +563,26 @@ __device__ __forceinline__ __nv_bfloat16 stored_element(const float2 *__restrict
     const int vb = (int)(rest >> 1);
     const int b = vb / z.nv, v = vb - b * z.nv;
     const int c = ch >> 1, plane = ch & 1;
-    const int64_t s = row * z.Lr + 8 * blk + ee;
-    int64_t idx = ((int64_t)z.k0 + c + 8 * s) % z.Kp;
+    const int64_t s0 = row * z.Lr + 8 * blk;
+    int64_t idx = ((int64_t)z.k0 + c + 8 * s0) % z.Kp;
     if (idx < 0) idx += z.Kp;
-    const float2 x = tree[z.level_off + (int64_t)b * N + (int64_t)v * z.Kp + idx];
-    __nv_bfloat16 hi, lo;
-    split_bf16(plane ? x.y : x.x, hi, lo);
-    return h ? lo : hi;
+    const float2 *w = tree + z.level_off + (int64_t)b * N + (int64_t)v * z.Kp;
+    // sample s0 + e reads index idx + 8 e (mod K'); K' >= 64 > 8 e, so one wrap at most
+    uint32_t word[4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+        int64_t i0 = idx + 8 * e, i1 = i0 + 8;
+        if (i0 >= z.Kp) i0 -= z.Kp;
+        if (i1 >= z.Kp) i1 -= z.Kp;
+        const float2 x0 = w[i0], x1 = w[i1];
+        __nv_bfloat16 h0, l0, h1, l1;
+        split_bf16(plane ? x0.y : x0.x, h0, l0);
+        split_bf16(plane ? x1.y : x1.x, h1, l1);
+        const __nv_bfloat16 a0 = h ? l0 : h0, a1 = h ? l1 : h1;
+        word[e >> 1] = (uint32_t)__bfloat16_as_ushort(a0) | ((uint32_t)__bfloat16_as_ushort(a1) << 16);
+    }
+    return make_uint4(word[0], word[1], word[2], word[3]);
 }
-
 
 // ---------------------------------------------------------------------------
 // Host side
@@ -669,8 +685,9 @@ sidwt_status pack_stored(const float2 *tree, int64_t N, int J, const int64_t *a_
         total += sh.a_elems;
     }
     if (total == 0) return SIDWT_OK;
-    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
-    pack_stored_kernel<<<(unsigned)blocks, 256, 0, s>>>(tree, N, sc, total, static_cast<__nv_bfloat16 *>(abuf));
+    const int64_t chunks = total / 8;  // scale counts are multiples of 128 elements
+    const int64_t blocks = std::min<int64_t>((chunks + 255) / 256, 152 * 16);
+    pack_stored_kernel<<<(unsigned)blocks, 256, 0, s>>>(tree, N, sc, chunks, static_cast<__nv_bfloat16 *>(abuf));
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "stored tensor-core operand packing");
 }
@@ -683,8 +700,9 @@ sidwt_status pack_stored_batch(const float2 *tree, const PackItem *items, int n,
     int nl = 0;
     auto flush = [&]() -> sidwt_status {
         if (b.n == 0) return SIDWT_OK;
-        const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
-        pack_stored_batch_kernel<<<(unsigned)blocks, 256, 0, s>>>(tree, b, total,
+        const int64_t chunks = total / 8;
+        const int64_t blocks = std::min<int64_t>((chunks + 255) / 256, 152 * 16);
+        pack_stored_batch_kernel<<<(unsigned)blocks, 256, 0, s>>>(tree, b, chunks,
                                                                    static_cast<__nv_bfloat16 *>(abuf));
         cudaError_t e = cudaGetLastError();
         ++nl;
