@@ -172,6 +172,18 @@ sidwt_status sidwt_analyze(sidwt_plan *p, const void *y_dev, int64_t B, void *py
 sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const void *y_dev, int64_t B,
                              sidwt_precision prec, void *r_dev, sidwt_stream stream);
 
+/* sidwt_correlate without the received analysis: the pulses are those of
+ * the plan's last analysis (sidwt_analyze, sidwt_correlate or
+ * sidwt_correlate_c2f), whose pyramids and energies the plan still holds, so
+ * that one batch is correlated against several stored signals while each
+ * pulse is decomposed once (Sec. IV: the received signal's SIDWT feeds the
+ * products with every stored signal).  B must equal that analysis's batch;
+ * SIDWT_EINVAL otherwise, or when the plan's workspace was reallocated since
+ * (a larger batch, sidwt_plan_reserve).  Other arguments and results as for
+ * sidwt_correlate; calls on one plan must be ordered on one stream. */
+sidwt_status sidwt_correlate_again(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t B, sidwt_precision prec,
+                                   void *r_dev, sidwt_stream stream);
+
 /* Peaks of the last sidwt_correlate on this plan (B must match it), per
  * pulse b and scale j at [b][j]: lag_dev int32 (delay D of the stored signal
  * with the largest |r_j[D]|, smallest D on ties; -1 for an invalid pulse),

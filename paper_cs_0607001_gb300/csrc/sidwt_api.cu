@@ -75,6 +75,7 @@ static sidwt_status ensure_batch(sidwt_plan *p, int64_t B) {
     if (e != cudaSuccess) return cuda_fail(e, "synchronise before workspace growth");
     const int64_t cap = std::max<int64_t>(B, p->cap_batch);
     free_batch(p);
+    p->analyzed_B = -1;
     sidwt_status st = SIDWT_OK;
     const int64_t nk = cap * (p->J + 1);
     if ((st = dalloc(&p->pyr_f, (size_t)(cap * p->pyr_elems), "received pyramid")) ||
@@ -428,6 +429,7 @@ sidwt_status sidwt_analyze(sidwt_plan *p, const void *y_dev, int64_t B, void *py
     {
         StageTimer t(p, 2, s, B > 0 ? analyze_launch_count(p) : 0);
         if ((st = analyze_batch(p, y_dev, B, s))) return st;
+        p->analyzed_B = B;
     }
     cudaError_t e = cudaSuccess;
     if (pyr_dev && B > 0) {
@@ -441,11 +443,11 @@ sidwt_status sidwt_analyze(sidwt_plan *p, const void *y_dev, int64_t B, void *py
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "analysis copy-out");
 }
 
-sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const void *y_dev, int64_t B,
-                             sidwt_precision prec, void *r_dev, sidwt_stream stream) {
-    CHECK_PLAN(p);
-    sidwt_status st = check_pulses(p, y_dev, B);
-    if (st) return st;
+// The body of sidwt_correlate and sidwt_correlate_again: `again` correlates
+// the pulses of the plan's last analysis (no analysis launch, y_dev unused).
+static sidwt_status correlate_impl(sidwt_plan *p, const int32_t *ref_ids_dev, const void *y_dev, int64_t B,
+                                   sidwt_precision prec, void *r_dev, sidwt_stream stream, bool again) {
+    sidwt_status st = SIDWT_OK;
     if (B > 0 && !ref_ids_dev) {
         set_error("ref_ids_dev is NULL");
         return SIDWT_EINVAL;
@@ -458,6 +460,10 @@ sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const vo
     const bool tc32 = (prec == SIDWT_PREC_TF32X3);
     if (p->nrefs == 0 && B > 0) {
         set_error("no stored reference");
+        return SIDWT_EINVAL;
+    }
+    if (again && B != p->analyzed_B) {
+        set_error("B does not match the pulses of the plan's last analysis (sidwt_analyze or sidwt_correlate)");
         return SIDWT_EINVAL;
     }
     if ((st = ensure_batch(p, std::max<int64_t>(B, 1)))) return st;
@@ -479,9 +485,10 @@ sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const vo
         cudaError_t e = cudaMemsetAsync(p->keys, 0, p->cap_batch * (p->J + 1) * sizeof(unsigned long long), s);
         if (e != cudaSuccess) return cuda_fail(e, "memset");
     }
-    {
+    if (!again) {
         StageTimer t(p, 2, s, analyze_launch_count(p));
         if ((st = analyze_batch(p, y_dev, B, s))) return st;
+        p->analyzed_B = B;
     }
     p->keys_clean = false;
     {
@@ -502,6 +509,24 @@ sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const vo
     }
     p->keys_clean = true;
     return SIDWT_OK;
+}
+
+sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const void *y_dev, int64_t B,
+                             sidwt_precision prec, void *r_dev, sidwt_stream stream) {
+    CHECK_PLAN(p);
+    sidwt_status st = check_pulses(p, y_dev, B);
+    if (st) return st;
+    return correlate_impl(p, ref_ids_dev, y_dev, B, prec, r_dev, stream, false);
+}
+
+sidwt_status sidwt_correlate_again(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t B, sidwt_precision prec,
+                                   void *r_dev, sidwt_stream stream) {
+    CHECK_PLAN(p);
+    if (B < 0) {
+        set_error("negative batch");
+        return SIDWT_EINVAL;
+    }
+    return correlate_impl(p, ref_ids_dev, nullptr, B, prec, r_dev, stream, true);
 }
 
 sidwt_status sidwt_peaks(sidwt_plan *p, int64_t B, int32_t *lag_dev, float *mag_dev, double *norm_dev,

@@ -195,6 +195,7 @@ struct sidwt_plan {
     int32_t *err = nullptr;        // device error record
     sidwt::TileList tiles;
     int64_t last_B = -1;
+    int64_t analyzed_B = -1;  // pulses whose pyramid and energies the plan holds (sidwt_correlate_again)
 
     // sidwt_correlate_host: pinned host staging and device copies of the inputs
     void *h_stage = nullptr;

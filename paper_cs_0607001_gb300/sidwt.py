@@ -80,6 +80,7 @@ def lib():
     L.sidwt_reference_tree.argtypes = [_vp, _i32, _vp, _vp, _vp]
     L.sidwt_analyze.argtypes = [_vp, _vp, _i64, _vp, _vp, _vp]
     L.sidwt_correlate.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, _vp, _vp]
+    L.sidwt_correlate_again.argtypes = [_vp, _vp, _i64, ctypes.c_int, _vp, _vp]
     L.sidwt_peaks.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp]
     L.sidwt_correlate_host.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp, _vp]
     L.sidwt_correlate_host_async.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp, _vp]
@@ -126,7 +127,7 @@ def lib():
     L.sidwt_server_read_stats.argtypes = [_vp, ctypes.POINTER(ServerStats), ctypes.c_int]
     L.sidwt_server_destroy.argtypes = [_vp]
     for name in ("sidwt_plan_create", "sidwt_plan_destroy", "sidwt_plan_reserve", "sidwt_store_reference",
-                 "sidwt_reference_tree", "sidwt_analyze", "sidwt_correlate", "sidwt_peaks",
+                 "sidwt_reference_tree", "sidwt_analyze", "sidwt_correlate", "sidwt_correlate_again", "sidwt_peaks",
                  "sidwt_correlate_host", "sidwt_correlate_host_async", "sidwt_check", "sidwt_reset_references", "sidwt_set_timing",
                  "sidwt_read_timing", "sidwt_correlate_static", "sidwt_tc_selftest", "sidwt_debug_stall", "sidwt_ragged_create",
                  "sidwt_ragged_destroy", "sidwt_ragged_reserve", "sidwt_ragged_store_reference",
@@ -277,6 +278,20 @@ class Plan:
             r = torch.empty((B, self.J + 1, self.N), dtype=torch.complex64, device=y.device)
         _raise(lib().sidwt_correlate(self._h, _ptr(ref_ids), _ptr(y), B, _prec_id(precision), _ptr(r),
                                      _stream(stream)))
+        return r
+
+    def correlate_again(self, ref_ids: torch.Tensor, precision="fp32", want_r: bool = False,
+                        r_out: torch.Tensor | None = None, stream=None):
+        """The pulses of the plan's last analysis against other stored signals
+        (sidwt_correlate_again): no analysis is run."""
+        B = ref_ids.numel()
+        if ref_ids.dtype != torch.int32 or not ref_ids.is_cuda:
+            raise ValueError("ref_ids must be a CUDA int32 tensor with one id per pulse")
+        r = r_out
+        if want_r and r is None:
+            r = torch.empty((B, self.J + 1, self.N), dtype=torch.complex64, device=ref_ids.device)
+        _raise(lib().sidwt_correlate_again(self._h, _ptr(ref_ids), B, _prec_id(precision), _ptr(r),
+                                           _stream(stream)))
         return r
 
     def peaks(self, B: int, stream=None):
