@@ -499,26 +499,27 @@ struct StoreScales {
     int n;
 };
 
-// Chunk q (elements 8 q .. 8 q + 7, one 16-byte store) of one scale's packed
-// stored operand; the bands of the scale's level start at tree[z.level_off]
-// and are N elements apart.
-__device__ __forceinline__ uint4 stored_chunk(const float2 *__restrict__ tree, int64_t N, const StoreScale &z,
-                                              int64_t q);
+// Chunk pair q of one scale's packed stored operand: the hi and the lo chunk
+// (8 elements, one 16-byte store each) of the same (variant, row, block,
+// residue, plane), written at `o` (the scale's first element).  The bands of
+// the scale's level start at tree[z.level_off] and are N elements apart.
+__device__ __forceinline__ void stored_pair(const float2 *__restrict__ tree, int64_t N, const StoreScale &z,
+                                            int64_t q, __nv_bfloat16 *__restrict__ o);
 
 // Stored operand of one signal: element [b nv + v][h][row][blk][2 c + plane][e]
 // = hi (h = 0) or lo part of plane(w_{v,b}[(k0 + c + 8 s) mod K']), plane 0
 // Re, 1 Im, at polyphase sample s = row Lr + 8 blk + e.  A thread writes the
-// 8 elements e of one (..., c, plane) chunk: every index but s is shared, so
-// the index arithmetic runs once per chunk.  Scale counts are multiples of
-// 128 elements and offsets multiples of 64, so chunks never straddle scales.
-__global__ void pack_stored_kernel(const float2 *__restrict__ tree, int64_t N, StoreScales sc, int64_t chunks,
+// hi and lo chunks of one (..., c, plane): 8 samples e read once, split
+// once, and every index but s computed once.  Scale counts are multiples of
+// 128 elements (16 per chunk pair), so pairs never straddle scales.
+__global__ void pack_stored_kernel(const float2 *__restrict__ tree, int64_t N, StoreScales sc, int64_t pairs,
                                    __nv_bfloat16 *__restrict__ out) {
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < chunks; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = 8 * q;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < pairs; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = 16 * q;
         int k = 0;
         while (k + 1 < sc.n && e >= sc.s[k + 1].first) ++k;
         const StoreScale &z = sc.s[k];
-        *reinterpret_cast<uint4 *>(out + z.out_off + e - z.first) = stored_chunk(tree, N, z, (e - z.first) >> 3);
+        stored_pair(tree, N, z, (e - z.first) >> 4, out + z.out_off);
     }
 }
 
@@ -536,9 +537,9 @@ struct PackBatch {
 };
 
 __global__ void pack_stored_batch_kernel(const float2 *__restrict__ tree, const __grid_constant__ PackBatch b,
-                                         int64_t chunks, __nv_bfloat16 *__restrict__ out) {
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < chunks; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = 8 * q;
+                                         int64_t pairs, __nv_bfloat16 *__restrict__ out) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < pairs; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = 16 * q;
         int lo = 0, hi = b.n - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -546,42 +547,48 @@ __global__ void pack_stored_batch_kernel(const float2 *__restrict__ tree, const 
             else hi = mid - 1;
         }
         const StoreScale &z = b.s[lo].z;
-        *reinterpret_cast<uint4 *>(out + z.out_off + e - z.first) = stored_chunk(tree, b.s[lo].N, z, (e - z.first) >> 3);
+        stored_pair(tree, b.s[lo].N, z, (e - z.first) >> 4, out + z.out_off);
     }
 }
 
-__device__ __forceinline__ uint4 stored_chunk(const float2 *__restrict__ tree, int64_t N, const StoreScale &z,
-                                              int64_t q) {
+__device__ __forceinline__ void stored_pair(const float2 *__restrict__ tree, int64_t N, const StoreScale &z,
+                                            int64_t q64, __nv_bfloat16 *__restrict__ o) {
+    // 32-bit index arithmetic: a scale holds fewer than 2^31 chunks (checked
+    // when the launch is built), and its polyphase samples s and sequence
+    // indices stay below 2^31
+    const uint32_t q = (uint32_t)q64;
     const int ch = (int)(q & 15);
-    const int nblk = z.Lr >> 3;
-    int64_t rest = q >> 4;
+    const uint32_t nblk = (uint32_t)z.Lr >> 3;
+    uint32_t rest = q >> 4;
     const int blk = (int)(rest % nblk);
     rest /= nblk;
-    const int64_t row = rest % z.Rs;
-    rest /= z.Rs;
-    const int h = (int)(rest & 1);
-    const int vb = (int)(rest >> 1);
+    const int row = (int)(rest % (uint32_t)z.Rs);
+    const int vb = (int)(rest / (uint32_t)z.Rs);
     const int b = vb / z.nv, v = vb - b * z.nv;
     const int c = ch >> 1, plane = ch & 1;
-    const int64_t s0 = row * z.Lr + 8 * blk;
-    int64_t idx = ((int64_t)z.k0 + c + 8 * s0) % z.Kp;
+    const int s0 = row * z.Lr + 8 * blk;
+    int idx = (z.k0 + c + 8 * s0) % z.Kp;
     if (idx < 0) idx += z.Kp;
     const float2 *w = tree + z.level_off + (int64_t)b * N + (int64_t)v * z.Kp;
     // sample s0 + e reads index idx + 8 e (mod K'); K' >= 64 > 8 e, so one wrap at most
-    uint32_t word[4];
+    uint32_t hw[4], lw[4];
 #pragma unroll
     for (int e = 0; e < 8; e += 2) {
-        int64_t i0 = idx + 8 * e, i1 = i0 + 8;
+        int i0 = idx + 8 * e, i1 = i0 + 8;
         if (i0 >= z.Kp) i0 -= z.Kp;
         if (i1 >= z.Kp) i1 -= z.Kp;
         const float2 x0 = w[i0], x1 = w[i1];
         __nv_bfloat16 h0, l0, h1, l1;
         split_bf16(plane ? x0.y : x0.x, h0, l0);
         split_bf16(plane ? x1.y : x1.x, h1, l1);
-        const __nv_bfloat16 a0 = h ? l0 : h0, a1 = h ? l1 : h1;
-        word[e >> 1] = (uint32_t)__bfloat16_as_ushort(a0) | ((uint32_t)__bfloat16_as_ushort(a1) << 16);
+        hw[e >> 1] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        lw[e >> 1] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
     }
-    return make_uint4(word[0], word[1], word[2], word[3]);
+    // chunk (vb, h, row, blk, ch) starts at element 8 (((2 vb + h) Rs + row) nblk 16 + 16 blk + ch)
+    const int64_t per_h = (int64_t)z.Rs * nblk * 128;  // elements of one (vb, h) slab
+    const int64_t at = (int64_t)vb * 2 * per_h + ((int64_t)row * nblk + blk) * 128 + 8 * ch;
+    *reinterpret_cast<uint4 *>(o + at) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4 *>(o + at + per_h) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
 
 // ---------------------------------------------------------------------------
@@ -673,6 +680,10 @@ sidwt_status pack_stored(const float2 *tree, int64_t N, int J, const int64_t *a_
         Shape sh;
         if (a_off[j] < 0 || !shape_with(N, J, j, S_of[j], &sh)) continue;
         StoreScale &z = sc.s[sc.n++];
+        if (sh.a_elems / 8 >= (int64_t(1) << 31) || (int64_t)sh.Rs * sh.Lr * 8 + 64 >= (int64_t(1) << 31)) {
+            set_error("band too long for the stored-operand packing");
+            return SIDWT_EINVAL;
+        }
         z.out_off = a_off[j];
         z.first = total;
         z.count = sh.a_elems;
@@ -685,9 +696,9 @@ sidwt_status pack_stored(const float2 *tree, int64_t N, int J, const int64_t *a_
         total += sh.a_elems;
     }
     if (total == 0) return SIDWT_OK;
-    const int64_t chunks = total / 8;  // scale counts are multiples of 128 elements
-    const int64_t blocks = std::min<int64_t>((chunks + 255) / 256, 152 * 16);
-    pack_stored_kernel<<<(unsigned)blocks, 256, 0, s>>>(tree, N, sc, chunks, static_cast<__nv_bfloat16 *>(abuf));
+    const int64_t pairs = total / 16;  // scale counts are multiples of 128 elements
+    const int64_t blocks = std::min<int64_t>((pairs + 255) / 256, 152 * 16);
+    pack_stored_kernel<<<(unsigned)blocks, 256, 0, s>>>(tree, N, sc, pairs, static_cast<__nv_bfloat16 *>(abuf));
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SIDWT_OK : cuda_fail(e, "stored tensor-core operand packing");
 }
@@ -700,9 +711,9 @@ sidwt_status pack_stored_batch(const float2 *tree, const PackItem *items, int n,
     int nl = 0;
     auto flush = [&]() -> sidwt_status {
         if (b.n == 0) return SIDWT_OK;
-        const int64_t chunks = total / 8;
-        const int64_t blocks = std::min<int64_t>((chunks + 255) / 256, 152 * 16);
-        pack_stored_batch_kernel<<<(unsigned)blocks, 256, 0, s>>>(tree, b, chunks,
+        const int64_t pairs = total / 16;
+        const int64_t blocks = std::min<int64_t>((pairs + 255) / 256, 152 * 16);
+        pack_stored_batch_kernel<<<(unsigned)blocks, 256, 0, s>>>(tree, b, pairs,
                                                                    static_cast<__nv_bfloat16 *>(abuf));
         cudaError_t e = cudaGetLastError();
         ++nl;
@@ -718,6 +729,10 @@ sidwt_status pack_stored_batch(const float2 *tree, const PackItem *items, int n,
             if (b.n == kPackBatch) {
                 sidwt_status st = flush();
                 if (st) return st;
+            }
+            if (sh.a_elems / 8 >= (int64_t(1) << 31) || (int64_t)sh.Rs * sh.Lr * 8 + 64 >= (int64_t(1) << 31)) {
+                set_error("band too long for the stored-operand packing");
+                return SIDWT_EINVAL;
             }
             StoreScaleB &e = b.s[b.n++];
             e.N = it.N;
