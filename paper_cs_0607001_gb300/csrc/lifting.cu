@@ -340,11 +340,13 @@ __global__ void tree_level_batch_kernel(const float2 *__restrict__ x, float2 *__
         else hi_k = mid - 1;
     }
     const TreeItem it = b.it[lo_k];
-    const int64_t N = it.N, local = t - b.nprefix[lo_k];
-    const int64_t K = N >> j, H = K / 2;
-    const int nrows = 1 << j;
-    const int64_t orow = local / H, n = local - orow * H;
-    const int row = (int)(orow % nrows), child = (int)(orow / nrows);
+    // 32-bit index arithmetic (an item's outputs per level number N < 2^31);
+    // the 2^j rows of a child are a power of two
+    const int64_t N = it.N;
+    const int32_t local = (int32_t)(t - b.nprefix[lo_k]);
+    const int32_t K = (int32_t)(N >> j), H = K / 2;
+    const int32_t orow = local / H, n = local - orow * H;
+    const int row = orow & ((1 << j) - 1), child = orow >> j;
     const float2 *v = j == 0 ? x + it.x_off : tree + it.tree_off + 2 * N * (int64_t)(j - 1) + (int64_t)row * K;
     float2 l, h;
     window_pair<F, SIDE_X>(v, K, n, child, c, l, h);
