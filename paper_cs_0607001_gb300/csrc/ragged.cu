@@ -255,6 +255,8 @@ struct LatTable {
     int n;
 };
 constexpr int kLatMaxN = 8192;
+constexpr int kLatStageW = 4096;  // stored-band samples a CTA stages (both bands of a variant)
+constexpr int kLatChunk = 1024;   // received samples staged at a time
 
 __global__ void __launch_bounds__(256) corr_latency_kernel(const float2 *__restrict__ tree, int64_t tree_elems,
                                                            const float2 *__restrict__ pyr, int64_t pyr_elems,
@@ -263,6 +265,7 @@ __global__ void __launch_bounds__(256) corr_latency_kernel(const float2 *__restr
                                                            float2 *__restrict__ R, int32_t *__restrict__ saved,
                                                            int32_t *__restrict__ err) {
     __shared__ float2 part[8][33];
+    __shared__ float2 lat_sm[kLatStageW + kLatChunk];  // 40 KB
     pdl_wait();  // the analysis kernel's pyramid and energies
     pdl_release();
     const int b = blockIdx.y;
@@ -285,18 +288,48 @@ __global__ void __launch_bounds__(256) corr_latency_kernel(const float2 *__restr
     const int K = nb * Kp;
     const float2 *u0 = pyr + (int64_t)b * pyr_elems + 2 * N - 4 * (int64_t)Kp;
     const float2 *w0 = tree + (int64_t)ref * tree_elems + 2 * N * (int64_t)(z.lev - 1) + (int64_t)v * Kp;
-    const int per = (K + 7) / 8;
-    const int k0 = slice * per, k1 = min(K, k0 + per);
     const int qq = q < Kp ? q : 0;
     float ar = 0.f, ai = 0.f;
-    for (int kk = k0; kk < k1; ++kk) {
-        const int band = kk >= Kp ? 1 : 0;
-        int idx = kk - band * Kp - qq;
-        if (idx < 0) idx += Kp;
-        const float2 wv = w0[(int64_t)band * N + idx];
-        const float2 uv = u0[kk];
-        ar = fmaf(wv.x, uv.x, fmaf(wv.y, uv.y, ar));
-        ai = fmaf(wv.x, uv.y, fmaf(-wv.y, uv.x, ai));
+    if (nb * Kp <= kLatStageW) {
+        // the variant's band(s) and the received band, chunk by chunk, in
+        // shared memory (coalesced loads, one L2 round trip per chunk); slice
+        // s takes its eighth of each chunk, which for K <= kLatChunk is the
+        // same partition of k as the direct form below
+        float2 *ws = lat_sm, *us = lat_sm + kLatStageW;
+        for (int t = threadIdx.x; t < nb * Kp; t += blockDim.x) {
+            const int band = t >= Kp ? 1 : 0;
+            ws[t] = w0[(int64_t)band * N + (t - band * Kp)];
+        }
+        for (int c0 = 0; c0 < K; c0 += kLatChunk) {
+            const int cnt = min(kLatChunk, K - c0);
+            for (int t = threadIdx.x; t < cnt; t += blockDim.x) us[t] = u0[c0 + t];
+            __syncthreads();
+            const int per = (cnt + 7) / 8;
+            const int a0 = slice * per, a1 = min(cnt, a0 + per);
+            for (int i = a0; i < a1; ++i) {
+                const int kk = c0 + i;
+                const int band = kk >= Kp ? 1 : 0;
+                int idx = kk - band * Kp - qq;
+                if (idx < 0) idx += Kp;
+                const float2 wv = ws[band * Kp + idx];
+                const float2 uv = us[i];
+                ar = fmaf(wv.x, uv.x, fmaf(wv.y, uv.y, ar));
+                ai = fmaf(wv.x, uv.y, fmaf(-wv.y, uv.x, ai));
+            }
+            __syncthreads();  // the chunk's reads end before the next chunk overwrites it
+        }
+    } else {
+        const int per = (K + 7) / 8;
+        const int k0 = slice * per, k1 = min(K, k0 + per);
+        for (int kk = k0; kk < k1; ++kk) {
+            const int band = kk >= Kp ? 1 : 0;
+            int idx = kk - band * Kp - qq;
+            if (idx < 0) idx += Kp;
+            const float2 wv = w0[(int64_t)band * N + idx];
+            const float2 uv = u0[kk];
+            ar = fmaf(wv.x, uv.x, fmaf(wv.y, uv.y, ar));
+            ai = fmaf(wv.x, uv.y, fmaf(-wv.y, uv.x, ai));
+        }
     }
     part[slice][lane] = make_float2(ar, ai);
     __syncthreads();

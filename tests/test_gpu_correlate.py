@@ -41,8 +41,12 @@ class Rows:
 
 
 @pytest.mark.parametrize("fname,fid", list(U.FLOAT_FILTERS.items()))
+# batches of at most 16 pulses take the latency kernel: (2048, 3, 9) stages
+# its scale-0 bands in two chunks of the received band, (8192, 5, 3) reads
+# scale 0's bands (too long to stage) straight from memory
 @pytest.mark.parametrize("N,J,B,nrefs", [(1024, 4, 150, 3), (96, 5, 70, 2), (320, 6, 9, 1), (2048, 3, 65, 1),
-                                         (64, 6, 5, 4), (16, 1, 40, 2), (2, 1, 3, 1)])
+                                         (64, 6, 5, 4), (16, 1, 40, 2), (2, 1, 3, 1), (2048, 3, 9, 2),
+                                         (8192, 5, 3, 1)])
 def test_correlation_matches_oracle(oracle, fname, fid, N, J, B, nrefs):
     w = U.small_batch(nrefs, B, N, J, seed=N + B + fid)
     r, lag, mag, norm = run_plan(fname, N, J, w["refs"], w["y"], w["ref_ids"])
