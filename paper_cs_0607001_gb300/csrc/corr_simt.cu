@@ -244,24 +244,7 @@ __global__ void finalize_kernel(unsigned long long *__restrict__ keys, const int
     pdl_release();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B * (J + 1)) return;
-    const int64_t b = i / (J + 1);
-    const int j = (int)(i % (J + 1));
-    const int r = ids[b];
-    const unsigned long long k = keys[i];
-    keys[i] = 0ull;
-    if (r < 0 || r >= nrefs || k == 0ull || (fail && *fail)) {
-        lag[i] = -1;
-        mag[i] = 0.f;
-        norm[i] = 0.0;
-        return;
-    }
-    const uint32_t D = 0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFull);
-    const float m = sqrtf(__uint_as_float((uint32_t)(k >> 32)));
-    lag[i] = (int32_t)D;
-    mag[i] = m;
-    const double ex = xen[(int64_t)r * xen_len + ((1 << j) - 1) + (D & ((1u << j) - 1u))];
-    const double den = sqrt(ex * yen[i]);
-    norm[i] = den > 0.0 ? (double)m / den : 0.0;
+    finalize_entry(i, keys, ids, nrefs, xen, xen_len, yen, J, lag, mag, norm, fail);
 }
 
 }  // namespace

@@ -37,6 +37,33 @@ cudaError_t launch_dependent(void (*kernel)(K...), dim3 grid, dim3 block, size_t
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<A &&>(args)...);
 }
+
+// The peak record of entry i = b (J + 1) + j from its packed key (|r|^2 bits
+// high, ~D low): lag D, |r| and |r| over the FP64 energies (eq. 1); an
+// invalid id, a zero key or a set *fail gives lag -1.  The key is reset to
+// zero for the next call.
+__device__ __forceinline__ void finalize_entry(int64_t i, unsigned long long *keys, const int32_t *ids, int nrefs,
+                                               const double *xen, int64_t xen_len, const double *yen, int J,
+                                               int32_t *lag, float *mag, double *norm, const int32_t *fail) {
+    const int64_t b = i / (J + 1);
+    const int j = (int)(i % (J + 1));
+    const int r = ids[b];
+    const unsigned long long k = __ldcg(keys + i);
+    keys[i] = 0ull;
+    if (r < 0 || r >= nrefs || k == 0ull || (fail && *fail)) {
+        lag[i] = -1;
+        mag[i] = 0.f;
+        norm[i] = 0.0;
+        return;
+    }
+    const uint32_t D = 0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFull);
+    const float m = sqrtf(__uint_as_float((uint32_t)(k >> 32)));
+    lag[i] = (int32_t)D;
+    mag[i] = m;
+    const double ex = xen[(int64_t)r * xen_len + ((1 << j) - 1) + (D & ((1u << j) - 1u))];
+    const double den = sqrt(ex * yen[i]);
+    norm[i] = den > 0.0 ? (double)m / den : 0.0;
+}
 #endif
 
 enum Side { SIDE_X = 0, SIDE_Y = 1 };  // x: primal analysis P~(z^-1); y: dual P^T(z^-1)

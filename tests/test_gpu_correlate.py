@@ -227,3 +227,50 @@ def test_async_host_entry_point_pipeline(precision):
             np.testing.assert_array_equal(mag.numpy(), md.cpu().numpy())
             np.testing.assert_array_equal(norm.numpy(), nd.cpu().numpy())
             assert (lag.numpy()[:, 0] == ws[k]["delays"]).all()
+
+
+def test_latency_path_repeated_calls_and_graph_replays():
+    """Batches of at most 16 pulses: the latency kernel's last CTA forms the
+    peak records and resets its finished-CTA count, so calls one after the
+    other, and replays of a captured call, give the records of a fresh plan."""
+    from paper_cs_0607001_gb300 import sidwt
+    N, J, B = 512, 3, 5
+    w = inputs.random_batch(n_refs=2, B=2 * B, N=N, J=J, seed=41)
+    ids = [torch.from_numpy(w["ref_ids"][i * B:(i + 1) * B].copy()).to(U.dev()) for i in range(2)]
+    ys = [U.to_dev_c64(w["y"][i * B:(i + 1) * B]) for i in range(2)]
+
+    def fresh(i):
+        with sidwt.Plan("cdf97", N, J) as q:
+            for x in w["refs"]:
+                q.store_reference(U.to_dev_c64(x))
+            q.correlate(ids[i], ys[i])
+            return [t.cpu().numpy() for t in q.peaks(B)]
+
+    want = [fresh(0), fresh(1)]
+    with sidwt.Plan("cdf97", N, J) as p:
+        for x in w["refs"]:
+            p.store_reference(U.to_dev_c64(x))
+        for i in (0, 1, 0, 1):
+            p.correlate(ids[i], ys[i])
+            got = [t.cpu().numpy() for t in p.peaks(B)]
+            for a, b in zip(got, want[i]):
+                np.testing.assert_array_equal(a, b)
+        lag = torch.empty((B, J + 1), dtype=torch.int32, device=U.dev())
+        mag = torch.empty((B, J + 1), dtype=torch.float32, device=U.dev())
+        norm = torch.empty((B, J + 1), dtype=torch.float64, device=U.dev())
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            p.correlate(ids[1], ys[1])
+            p.peaks_into(B, lag, mag, norm)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            p.correlate(ids[1], ys[1])
+            p.peaks_into(B, lag, mag, norm)
+        for _ in range(3):
+            lag.fill_(-7)
+            g.replay()
+            torch.cuda.synchronize()
+            for a, b in zip((lag, mag, norm), want[1]):
+                np.testing.assert_array_equal(a.cpu().numpy(), b)
+        p.check()
