@@ -571,7 +571,8 @@ def run_ragged_workload(args):
             r.autotune()
             tune_s[precision] = time.perf_counter() - t0
         r.reserve(int((2 * Js * Ns).sum()), int((2 * Ns - 2 * (Ns >> Js)).sum()), slots)
-        return r, [r.store_reference(int(fs[i]), int(Ns[i]), int(Js[i]), refs[off[i]:off[i] + Ns[i]]) for i in range(n)]
+        # all stored signals in one call (their trees built together, 64 per pass)
+        return r, r.store_references([int(f) for f in fs], Ns, Js, refs, off)
 
     plain = None
     if prec != "fp32" and not args.no_plain:
