@@ -1392,12 +1392,12 @@ def other_configs(args) -> dict:
         d["wall_s"] = round(time.perf_counter() - t0, 1)
         out[name] = d
 
-    leg("c3_precision_sweep", run_sweep_workload, common + ("per_precision",),
+    leg("precision_sweep_64x16384_N4096", run_sweep_workload, common + ("per_precision",),
         no_plain=True, no_cpu=True, steps=3, warmup=3, pulses=4096)
-    leg("c4_ragged_batch", run_ragged_workload,
+    leg("ragged_batch_10000", run_ragged_workload,
         common + ("e2e", "stages_ms_direct_call", "gpu_launches", "peak_at_injected_delay_scale0"),
         no_plain=True, no_cpu=True, no_autotune=True, steps=3, warmup=3, items=10000)
-    leg("c5_serving", run_serve_workload,
+    leg("serving_1k_20k_req_s", run_serve_workload,
         ("metric", "value", "unit", "dtype", "config", "latency_ms", "saturated_latency_ms", "per_rate", "clocks"),
         no_cpu=True, rates="1000,20000", seconds=3.0, max_requests=6000, pool=2048, lanes=4)
     return out
