@@ -355,9 +355,76 @@ __global__ void tree_level_batch_kernel(const float2 *__restrict__ x, float2 *__
     A[N + orow * H + n] = h;
 }
 
+// Energies of a stored tree: row r of out (levels l = 0..J, variants
+// v < 2^l, r = 2^l - 1 + v) is ||c_l^v||^2 over K = N >> l samples (x itself
+// at l = 0).  Rows of K >= kEnBigRow samples are summed by a whole block, the
+// others by one warp each (eight a block), so that the many short rows of the
+// deep levels do not each hold a block.  Which form sums a row depends on K
+// alone, so a tree's energies come out the same from the single-signal and
+// the batched launches.
+constexpr int kEnBigRow = 4096;
+
+__host__ __device__ inline int energy_big_rows(int64_t N, int J) {
+    int n = 0;
+    for (int l = 0; l <= J && (N >> l) >= kEnBigRow; ++l) n += 1 << l;
+    return n;
+}
+__host__ __device__ inline int64_t energy_blocks(int64_t N, int J) {
+    const int rows = (2 << J) - 1, big = energy_big_rows(N, J);
+    return big + (rows - big + 7) / 8;
+}
+
+// One warp's sum of |X[k]|^2: lanes stride the row with four FP32-pair
+// accumulators each, then a fixed compensated tree; valid in lane 0.
+__device__ __forceinline__ double warp_row_energy(const float2 *__restrict__ X, int64_t K) {
+    const int lane = threadIdx.x & 31;
+    EnAcc a0, a1, a2, a3;
+    int64_t k = lane;
+    for (; k + 96 < K; k += 128) {
+        a0.add(sq2(X[k]));
+        a1.add(sq2(X[k + 32]));
+        a2.add(sq2(X[k + 64]));
+        a3.add(sq2(X[k + 96]));
+    }
+    for (; k < K; k += 32) a0.add(sq2(X[k]));
+    a0.add(a1);
+    a2.add(a3);
+    a0.add(a2);
+    for (int o = 16; o > 0; o >>= 1) {
+        EnAcc t;
+        t.hi = __shfl_down_sync(0xffffffffu, a0.hi, o);
+        t.lo = __shfl_down_sync(0xffffffffu, a0.lo, o);
+        a0.add(t);
+    }
+    return a0.total();
+}
+
+// Energy block bl of one tree (x: the signal, tr: its tree, out: its
+// 2^(J+1) - 1 energies); blockDim.x = 256.
+__device__ __forceinline__ void tree_energy_block(const float2 *__restrict__ x, const float2 *__restrict__ tr,
+                                                  int64_t N, int J, int bl, double *__restrict__ out, float2 *red) {
+    const int big = energy_big_rows(N, J), rows = (2 << J) - 1;
+    const bool whole = bl < big;  // uniform over the block
+    const int r = whole ? bl : big + (bl - big) * 8 + (int)(threadIdx.x >> 5);
+    if (!whole && r >= rows) return;
+    int l = 0;
+    while ((2 << l) - 1 <= r) ++l;
+    const int v = r - ((1 << l) - 1);
+    const int64_t K = N >> l;
+    const float2 *X = l == 0 ? x : tr + 2 * N * (int64_t)(l - 1) + (int64_t)v * K;
+    if (whole) {
+        EnAcc acc;
+        for (int64_t k = threadIdx.x; k < K; k += blockDim.x) acc.add(sq2(X[k]));
+        const double t = block_sum(acc, red);
+        if (threadIdx.x == 0) out[r] = t;
+    } else {
+        const double t = warp_row_energy(X, K);
+        if ((threadIdx.x & 31) == 0) out[r] = t;
+    }
+}
+
 // Energies of the batch's trees: block e -> item k (prefix sums of
-// 2^(J+1) - 1 blocks per item) and (level l, variant v) as in
-// ref_energy_kernel.
+// energy_blocks per item), then tree_energy_block.
 __global__ void tree_energy_batch_kernel(const float2 *__restrict__ x, const float2 *__restrict__ tree,
                                          double *__restrict__ xen, const __grid_constant__ TreeBatch b) {
     __shared__ float2 red[32];
@@ -369,16 +436,8 @@ __global__ void tree_energy_batch_kernel(const float2 *__restrict__ x, const flo
         else hi_k = mid - 1;
     }
     const TreeItem it = b.it[lo_k];
-    const int bl = (int)(e - b.eprefix[lo_k]);
-    int l = 0;
-    while ((2 << l) - 1 <= bl) ++l;
-    const int v = bl - ((1 << l) - 1);
-    const int64_t N = it.N, K = N >> l;
-    const float2 *X = l == 0 ? x + it.x_off : tree + it.tree_off + 2 * N * (int64_t)(l - 1) + (int64_t)v * K;
-    EnAcc acc;
-    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) acc.add(sq2(X[k]));
-    const double tot = block_sum(acc, red);
-    if (threadIdx.x == 0) xen[it.xen_off + bl] = tot;
+    tree_energy_block(x + it.x_off, tree + it.tree_off, it.N, it.J, (int)(e - b.eprefix[lo_k]), xen + it.xen_off,
+                      red);
 }
 
 template <int F, int S, typename TIn>
@@ -415,20 +474,11 @@ template <typename TIn, typename TTree>
 __global__ void ref_energy_kernel(const TIn *__restrict__ x, const TTree *__restrict__ tree, int64_t N,
                                   double *__restrict__ out);
 
-template <>
-__global__ void ref_energy_kernel<float2, float2>(const float2 *__restrict__ x, const float2 *__restrict__ tree,
-                                                  int64_t N, double *__restrict__ out) {
+// One float tree's energies: energy_blocks(N, J) blocks of 256 threads.
+__global__ void ref_energy_f_kernel(const float2 *__restrict__ x, const float2 *__restrict__ tree, int64_t N, int J,
+                                    double *__restrict__ out) {
     __shared__ float2 red[32];
-    const int b = blockIdx.x;
-    int l = 0;
-    while ((2 << l) - 1 <= b) ++l;
-    const int v = b - ((1 << l) - 1);
-    const int64_t K = N >> l;
-    const float2 *X = l == 0 ? x : tree + 2 * N * (int64_t)(l - 1) + (int64_t)v * K;
-    EnAcc acc;
-    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) acc.add(sq2(X[k]));
-    const double t = block_sum(acc, red);
-    if (threadIdx.x == 0) out[b] = t;
+    tree_energy_block(x, tree, N, J, blockIdx.x, out, red);
 }
 
 template <>
@@ -952,8 +1002,8 @@ sidwt_status build_reference_tree(sidwt_plan *p, const void *x_dev, int32_t ref,
             else
                 launch_level_any(p->filter, SIDE_X, tf + 2 * N * (int64_t)(j - 1), K, nv, 2, K, A, B, K / 2, c, s);
         }
-        ref_energy_kernel<float2, float2><<<(1 << (J + 1)) - 1, 256, 0, s>>>(
-            reinterpret_cast<const float2 *>(x_dev), tf, N, xe);
+        ref_energy_f_kernel<<<(unsigned)energy_blocks(N, J), 256, 0, s>>>(reinterpret_cast<const float2 *>(x_dev), tf,
+                                                                           N, J, xe);
     } else {
         int2 *ti = p->tree_i + (int64_t)ref * p->tree_elems;
         for (int j = 0; j < J; ++j) {
@@ -1002,7 +1052,7 @@ sidwt_status build_reference_trees(int filter, const float2 *x, float2 *tree, do
         std::stable_sort(b.it, b.it + b.n, [](const TreeItem &a, const TreeItem &c) { return a.J > c.J; });
         for (int k = 0; k < b.n; ++k) {
             b.nprefix[k + 1] = b.nprefix[k] + b.it[k].N;
-            b.eprefix[k + 1] = b.eprefix[k] + ((int64_t(2) << b.it[k].J) - 1);
+            b.eprefix[k + 1] = b.eprefix[k] + energy_blocks(b.it[k].N, b.it[k].J);
         }
         const int maxJ = b.it[0].J;
         if (b.eprefix[b.n] > 0x7fffffff || (b.nprefix[b.n] + 255) / 256 > 0x7fffffff) {
