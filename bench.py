@@ -1450,6 +1450,13 @@ def main():
         "ragged": run_ragged_workload, "single": run_single_workload, "serve": run_serve_workload,
         "sweep": run_sweep_workload, "c2f": run_c2f_workload, "multitarget": run_multitarget_workload,
         "t97": run_t97_workload, "store": run_store_workload}.get(args.workload, run_ours)
+    if args.impl != "reference" and args.workload not in ("two_ref", "ragged"):
+        # the other workloads run on one GPU: under a multi-rank launch rank 0
+        # alone runs them and the other ranks exit without work
+        from paper_cs_0607001_gb300 import multigpu as M
+        rank, world, _ = M.dist_env()
+        if rank != 0:
+            return 0
     line = fn(args)
     if isinstance(line, dict):
         print(json.dumps(line))
