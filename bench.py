@@ -615,10 +615,7 @@ def run_ragged_workload(args):
         # one batch split across the ranks, balanced by each pair's algorithmic
         # cost; this rank's pulses and stored signals repacked (even offsets)
         idx = M.shard_by_cost(M.pair_cost(w["N"], w["J"]), world)[rank]
-        seg = [np.arange(w["offsets"][i], w["offsets"][i] + w["N"][i]) for i in idx]
-        cat = np.concatenate(seg) if seg else np.zeros(0, np.int64)
-        w = dict(w, refs=w["refs"][cat], y=w["y"][cat], N=w["N"][idx], J=w["J"][idx], filter=w["filter"][idx],
-                 delays=w["delays"][idx], offsets=np.concatenate([[0], np.cumsum(w["N"][idx])[:-1]]).astype(np.int64))
+        w = M.subset_ragged(w, idx)
     Ns, Js, fs, off = w["N"], w["J"], w["filter"], w["offsets"]
     n = len(Ns)
     prec = args.precision

@@ -91,6 +91,22 @@ def shard_by_cost(costs, world: int) -> list[np.ndarray]:
     return [np.nonzero(owner == r)[0] for r in range(world)]
 
 
+def subset_ragged(batch: dict, idx) -> dict:
+    """The items `idx` of a packed ragged batch (keys refs and y: packed
+    complex samples; offsets, N, J, filter, delays: per item), repacked in
+    that order with offsets from 0 (even when every N is)."""
+    idx = np.asarray(idx, dtype=np.int64)
+    off, n = np.asarray(batch["offsets"]), np.asarray(batch["N"])
+    seg = [np.arange(off[i], off[i] + n[i]) for i in idx]
+    cat = np.concatenate(seg) if seg else np.zeros(0, np.int64)
+    out = dict(batch)
+    out["refs"], out["y"] = batch["refs"][cat], batch["y"][cat]
+    for k in ("N", "J", "filter", "delays"):
+        out[k] = np.asarray(batch[k])[idx]
+    out["offsets"] = np.concatenate([[0], np.cumsum(n[idx])[:-1]]).astype(np.int64)
+    return out
+
+
 def pair_cost(N, J) -> np.ndarray:
     """Algorithmic flops of the all-lag, all-scale correlation of one pair:
     8 N^2 (2 - 2^-J) (N lags at each of the J + 1 scales)."""

@@ -140,3 +140,25 @@ def test_gather_slots_rejects_overlap_and_gaps():
     with pytest.raises(ValueError, match="two ranks"):
         idx = np.array([0, 1, 1, 2, 3])
         M.gather_slots(idx, Js[idx] + 1, *_fake_records(idx, Js), 4, 1)
+
+
+def test_subset_ragged_repacks_each_rank_share():
+    """A rank's cost-balanced share of a ragged batch, repacked: every item's
+    pulse and stored signal are the original samples, offsets start at 0 and
+    stay even, and the shares together hold every item once."""
+    from paper_cs_0607001_gb300 import inputs
+    from paper_cs_0607001_gb300 import multigpu as M
+    w = inputs.ragged_batch(n=240)
+    parts = M.shard_by_cost(M.pair_cost(w["N"], w["J"]), 3)
+    assert sorted(np.concatenate(parts).tolist()) == list(range(len(w["N"])))
+    for idx in parts:
+        s = M.subset_ragged(w, idx)
+        assert s["offsets"][0] == 0 and (s["offsets"] % 2 == 0).all()
+        assert len(s["y"]) == int(w["N"][idx].sum()) == len(s["refs"])
+        for k, i in enumerate(idx):
+            a, b = s["offsets"][k], w["offsets"][i]
+            n = int(w["N"][i])
+            assert s["N"][k] == n and s["J"][k] == w["J"][i] and s["filter"][k] == w["filter"][i]
+            assert s["delays"][k] == w["delays"][i]
+            np.testing.assert_array_equal(s["y"][a:a + n], w["y"][b:b + n])
+            np.testing.assert_array_equal(s["refs"][a:a + n], w["refs"][b:b + n])
