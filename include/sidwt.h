@@ -177,9 +177,9 @@ sidwt_status sidwt_correlate(sidwt_plan *p, const int32_t *ref_ids_dev, const vo
  * sidwt_correlate_c2f), whose pyramids and energies the plan still holds, so
  * that one batch is correlated against several stored signals while each
  * pulse is decomposed once (Sec. IV: the received signal's SIDWT feeds the
- * products with every stored signal).  B must equal that analysis's batch;
- * SIDWT_EINVAL otherwise, or when the plan's workspace was reallocated since
- * (a larger batch, sidwt_plan_reserve).  Other arguments and results as for
+ * products with every stored signal).  B must equal that analysis's batch
+ * (B = 0 does nothing); SIDWT_EINVAL otherwise, or when the plan's workspace
+ * was reallocated since (a larger batch, sidwt_plan_reserve).  Other arguments and results as for
  * sidwt_correlate; calls on one plan must be ordered on one stream. */
 sidwt_status sidwt_correlate_again(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t B, sidwt_precision prec,
                                    void *r_dev, sidwt_stream stream);

@@ -462,7 +462,7 @@ static sidwt_status correlate_impl(sidwt_plan *p, const int32_t *ref_ids_dev, co
         set_error("no stored reference");
         return SIDWT_EINVAL;
     }
-    if (again && B != p->analyzed_B) {
+    if (again && B > 0 && B != p->analyzed_B) {
         set_error("B does not match the pulses of the plan's last analysis (sidwt_analyze or sidwt_correlate)");
         return SIDWT_EINVAL;
     }

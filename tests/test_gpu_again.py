@@ -75,6 +75,7 @@ def test_again_is_refused_without_a_matching_analysis(batch):
         p.correlate(ids, y)
         with pytest.raises(sidwt.SidwtError, match="EINVAL.*last analysis"):
             p.correlate_again(ids[:B - 1].contiguous())  # another batch size
+        p.correlate_again(ids[:0].contiguous())  # an empty batch does nothing
         p.reserve(3, 4 * B)  # the workspace is reallocated: the pyramids are gone
         with pytest.raises(sidwt.SidwtError, match="EINVAL.*last analysis"):
             p.correlate_again(ids)
