@@ -264,6 +264,7 @@ sidwt_status sidwt_correlate_c2f(sidwt_plan *p, const int32_t *ref_ids_dev, cons
     if ((st = group_pulses(p, ref_ids_dev, B, simt_tile_pulses(), s)) || (st = analyze_batch(p, y_dev, B, s)))
         return st;
     p->analyzed_B = B;
+    ++p->analysis_gen;
     p->keys_clean = false;  // scale J's keys are left set
     cudaError_t e = cudaMemsetAsync(p->keys, 0, B * (p->J + 1) * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "memset");

@@ -152,18 +152,23 @@ __global__ void __launch_bounds__(kThreads, 2)
 // Groups the batch by reference: perm lists pulse indices reference by
 // reference; every pulse tile holds up to tile_pulses pulses of one reference.
 // Pulses with an out-of-range id are left out and recorded in *err.
+constexpr int kGroupSmemRefs = 4096;  // references whose cursors the stable placement keeps in shared memory
+
 __global__ void __launch_bounds__(1024) group_kernel(const int32_t *__restrict__ ref_ids, int B, int nrefs, int TPp,
                                                      int32_t *__restrict__ cursor, int32_t *__restrict__ perm,
+                                                     const int32_t *__restrict__ perm_old,
                                                      int32_t *__restrict__ tile_ref, int32_t *__restrict__ tile_start,
                                                      int32_t *__restrict__ tile_count, int32_t *__restrict__ ntiles,
                                                      int32_t *__restrict__ saved, int32_t *__restrict__ err) {
     __shared__ int wsum_c[32], wsum_t[32];
-    __shared__ int carry_c, carry_t;
+    __shared__ int carry_c, carry_t, old_nvalid, changed;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     for (int r = tid; r < nrefs; r += blockDim.x) cursor[r] = 0;
     if (tid == 0) {
         carry_c = 0;
         carry_t = 0;
+        old_nvalid = ntiles[1];
+        changed = 0;
     }
     __syncthreads();
     for (int b = tid; b < B; b += blockDim.x) {
@@ -226,11 +231,42 @@ __global__ void __launch_bounds__(1024) group_kernel(const int32_t *__restrict__
         ntiles[0] = carry_t;
         ntiles[1] = carry_c;  // pulses with a valid reference id
     }
+    // stable grouping: a reference's pulses in increasing b.  Chunk by chunk
+    // and warp by warp in order, the lanes that share a reference take
+    // consecutive places from its cursor (the last of them advances it), the
+    // cursors in shared memory when the references fit.  The result is the
+    // same in every call with the same ids.
+    __shared__ int scur[kGroupSmemRefs];
+    int *cur = nrefs <= kGroupSmemRefs ? scur : cursor;
+    if (nrefs <= kGroupSmemRefs)
+        for (int r = tid; r < nrefs; r += blockDim.x) scur[r] = cursor[r];
     __syncthreads();
-    for (int b = tid; b < B; b += blockDim.x) {
-        const int r = ref_ids[b];
-        if (r >= 0 && r < nrefs) perm[atomicAdd(&cursor[r], 1)] = b;
+    const int nw = (int)(blockDim.x >> 5);
+    for (int base = 0; base < B; base += blockDim.x) {
+        const int b = base + tid;
+        const int r = b < B ? ref_ids[b] : -1;
+        const bool ok = r >= 0 && r < nrefs;
+        const unsigned peers = __match_any_sync(0xffffffffu, ok ? r : -1);
+        const int before = __popc(peers & ((1u << lane) - 1u));
+        for (int w = 0; w < nw; ++w) {
+            if (wid == w && ok) {
+                const int pos = cur[r] + before;
+                __syncwarp(peers);  // every lane of the group has read the cursor
+                perm[pos] = b;
+                if (before == __popc(peers) - 1) cur[r] = pos + 1;
+            }
+            __syncthreads();
+        }
     }
+    // ntiles[2]: whether the grouping (or the count of valid pulses) changed
+    // since the previous call (perm_old: its order; none: assume it did), so
+    // that an unchanged received operand need not be packed again
+    if (!perm_old) changed = 1;
+    else
+        for (int i = tid; i < carry_c; i += blockDim.x)
+            if (perm[i] != perm_old[i]) changed = 1;
+    __syncthreads();
+    if (tid == 0) ntiles[2] = (changed || old_nvalid != carry_c) ? 1 : 0;
 }
 
 // Reads each peak key once and resets it to zero, so that the next call on
@@ -250,7 +286,10 @@ __global__ void finalize_kernel(unsigned long long *__restrict__ keys, const int
 }  // namespace
 
 sidwt_status group_pulses(sidwt_plan *p, const int32_t *ref_ids_dev, int64_t B, int tile_pulses, cudaStream_t s) {
+    // the two order buffers swap: this call's order beside the previous one's
+    if (p->tiles.perm_prev) std::swap(p->tiles.perm, p->tiles.perm_prev);
     group_kernel<<<1, 1024, 0, s>>>(ref_ids_dev, (int)B, p->nrefs, tile_pulses, p->tiles.cursor, p->tiles.perm,
+                                    p->tiles.perm_prev,
                                     p->tiles.tile_ref, p->tiles.tile_start, p->tiles.tile_count, p->tiles.ntiles,
                                     p->ref_ids, p->err);
     cudaError_t e = cudaGetLastError();

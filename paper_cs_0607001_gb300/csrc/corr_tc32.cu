@@ -338,11 +338,15 @@ __global__ void pack_ref32_kernel(const float2 *__restrict__ tree, int64_t tree_
 // Received operand of one scale: row ((k / 16) * 2 + plane) of 16 TF32 values
 // u_plane[16 (k / 16) .. + 15] per pulse (grouped order) of the concatenated
 // bands (plane 0 Re, 1 Im), 64 bytes a pulse.  Block: 64 samples x 32 rows.
+// same_input: the buffers already hold this pyramid packed for this batch
+// size; the packing is skipped when the grouping is unchanged too (ntiles[2]).
 __global__ void __launch_bounds__(256) pack_rx32_kernel(const float2 *__restrict__ pyr, int64_t pyr_elems, int64_t off,
                                                         const int32_t *__restrict__ perm,
                                                         const int32_t *__restrict__ ntiles, int rows,
-                                                        uint32_t *__restrict__ bhi, uint32_t *__restrict__ blo) {
+                                                        uint32_t *__restrict__ bhi, uint32_t *__restrict__ blo,
+                                                        int same_input) {
     __shared__ float2 tile[32][65];
+    if (same_input && ntiles[2] == 0) return;  // uniform over the grid
     const int kb = blockIdx.x;  // 64 samples
     const int r0 = blockIdx.y * 32;
     const int nvalid = ntiles[1];
@@ -418,6 +422,7 @@ void free_tc32(sidwt_plan *p) {
     p->tc32_cap_refs = 0;
     p->tc32_cap_batch = 0;
     p->tc32_packed = 0;
+    p->tc32_rx_gen = -1;
 }
 
 static sidwt_status ensure_tc32(sidwt_plan *p) {
@@ -468,6 +473,10 @@ sidwt_status correlate_tc32(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_
         p->tc32_packed = p->nrefs;
     }
     const int64_t max_pt = (B + tc32::kTN - 1) / tc32::kTN + std::min<int64_t>(p->nrefs, B);
+    // as for BF16x3: an unchanged pyramid and grouping keep their packed operands
+    const bool same_input = p->tc32_rx_gen == p->analysis_gen && p->tc32_rx_B == B;
+    p->tc32_rx_gen = p->analysis_gen;
+    p->tc32_rx_B = B;
     for (int j = 0; j <= J; ++j) {
         if (!(mask & (1u << j))) continue;
         const int lev = j < J ? j + 1 : J;
@@ -479,7 +488,7 @@ sidwt_status correlate_tc32(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_
         {
             dim3 g((unsigned)(Kj / 64), (unsigned)((B + 31) / 32));
             tc32::pack_rx32_kernel<<<g, 256, 0, s>>>(p->pyr_f, p->pyr_elems, 2 * N - 4 * Kp, p->tiles.perm,
-                                                     p->tiles.ntiles, (int)B, bhi, blo);
+                                                     p->tiles.ntiles, (int)B, bhi, blo, same_input ? 1 : 0);
         }
         // TF32 data is moved as pairs of 16-bit units: a 64-byte row is 32 units
         CUtensorMap mA, mBh, mBl;

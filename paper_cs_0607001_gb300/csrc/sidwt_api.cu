@@ -58,7 +58,8 @@ static void free_batch(sidwt_plan *p) {
     dfree(p->mag);
     dfree(p->norm);
     dfree(p->ref_ids);
-    dfree(p->tiles.perm);
+    dfree(p->tiles.perm_base);
+    p->tiles.perm = p->tiles.perm_prev = nullptr;
     dfree(p->tiles.tile_ref);
     dfree(p->tiles.tile_start);
     dfree(p->tiles.tile_count);
@@ -83,13 +84,21 @@ static sidwt_status ensure_batch(sidwt_plan *p, int64_t B) {
         (st = dalloc(&p->yen, (size_t)nk, "received energies")) || (st = dalloc(&p->keys, (size_t)nk, "peak keys")) ||
         (st = dalloc(&p->lag, (size_t)nk, "peak lags")) || (st = dalloc(&p->mag, (size_t)nk, "peak magnitudes")) ||
         (st = dalloc(&p->norm, (size_t)nk, "peak norms")) || (st = dalloc(&p->ref_ids, (size_t)cap, "reference ids")) ||
-        (st = dalloc(&p->tiles.perm, (size_t)cap, "pulse order")) ||
+        (st = dalloc(&p->tiles.perm_base, (size_t)(2 * cap), "pulse order")) ||
         (st = dalloc(&p->tiles.tile_ref, (size_t)need_tiles, "tile list")) ||
         (st = dalloc(&p->tiles.tile_start, (size_t)need_tiles, "tile list")) ||
         (st = dalloc(&p->tiles.tile_count, (size_t)need_tiles, "tile list"))) {
         free_batch(p);
         return st;
     }
+    // both order buffers start out as "no pulse" (-1), so that the first
+    // grouping reads as changed
+    if (cudaMemset(p->tiles.perm_base, 0xFF, (size_t)(2 * cap) * sizeof(int32_t)) != cudaSuccess) {
+        free_batch(p);
+        return cuda_fail(cudaGetLastError(), "memset");
+    }
+    p->tiles.perm = p->tiles.perm_base;
+    p->tiles.perm_prev = p->tiles.perm_base + cap;
     p->cap_batch = cap;
     p->tiles.max_tiles = need_tiles;
     p->keys_clean = false;
@@ -273,8 +282,9 @@ sidwt_status sidwt_plan_create(sidwt_filter f, int64_t N, int J, sidwt_plan **ou
     p->xen_len = (int64_t(2) << J) - 1;
     p->pyr_elems = 2 * N - 2 * (N >> J);
     sidwt_status st = dalloc(&p->err, 1, "error record");
-    if (st == SIDWT_OK && (st = dalloc(&p->tiles.ntiles, 2, "tile count")) == SIDWT_OK) {
+    if (st == SIDWT_OK && (st = dalloc(&p->tiles.ntiles, 3, "tile count")) == SIDWT_OK) {
         cudaError_t e = cudaMemset(p->err, 0, sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMemset(p->tiles.ntiles, 0, 3 * sizeof(int32_t));
         if (e != cudaSuccess) st = cuda_fail(e, "memset");
     }
     if (st != SIDWT_OK) {
@@ -430,6 +440,7 @@ sidwt_status sidwt_analyze(sidwt_plan *p, const void *y_dev, int64_t B, void *py
         StageTimer t(p, 2, s, B > 0 ? analyze_launch_count(p) : 0);
         if ((st = analyze_batch(p, y_dev, B, s))) return st;
         p->analyzed_B = B;
+        ++p->analysis_gen;
     }
     cudaError_t e = cudaSuccess;
     if (pyr_dev && B > 0) {
@@ -489,6 +500,7 @@ static sidwt_status correlate_impl(sidwt_plan *p, const int32_t *ref_ids_dev, co
         StageTimer t(p, 2, s, analyze_launch_count(p));
         if ((st = analyze_batch(p, y_dev, B, s))) return st;
         p->analyzed_B = B;
+        ++p->analysis_gen;
     }
     p->keys_clean = false;
     {

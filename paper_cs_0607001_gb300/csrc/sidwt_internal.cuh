@@ -182,10 +182,12 @@ struct RaggedLiftGroups {
 // ---------------------------------------------------------------------------
 struct TileList {  // per correlate: pulse tiles grouped by reference
     int32_t *perm = nullptr;        // [B] pulse indices grouped by reference
+    int32_t *perm_prev = nullptr;   // the previous call's order (the two swap; null: not kept)
+    int32_t *perm_base = nullptr;   // the allocation holding both
     int32_t *tile_ref = nullptr;    // [max_tiles]
     int32_t *tile_start = nullptr;  // [max_tiles] offset into perm
     int32_t *tile_count = nullptr;  // [max_tiles]
-    int32_t *ntiles = nullptr;      // [2]: tiles, pulses with a valid id
+    int32_t *ntiles = nullptr;      // [3]: tiles, pulses with a valid id, grouping changed since the last call
     int32_t *cursor = nullptr;      // [cap_refs] scratch
     int64_t max_tiles = 0;
 };
@@ -223,6 +225,9 @@ struct sidwt_plan {
     sidwt::TileList tiles;
     int64_t last_B = -1;
     int64_t analyzed_B = -1;  // pulses whose pyramid and energies the plan holds (sidwt_correlate_again)
+    int64_t analysis_gen = 0;  // counts analyses: the packed received operands record the one they came from
+    int64_t tc_rx_gen = -1, tc_rx_B = -1;      // BF16x3 received operands: analysis and batch packed
+    int64_t tc32_rx_gen = -1, tc32_rx_B = -1;  // the same for 3xTF32
 
     // sidwt_correlate_host: pinned host staging and device copies of the inputs
     void *h_stage = nullptr;

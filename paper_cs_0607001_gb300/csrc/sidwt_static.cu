@@ -75,7 +75,7 @@ size_t layout(sidwt_plan &p, unsigned char *base, int64_t B, int32_t **ids_in) {
     p.tiles.tile_ref = c.take<int32_t>((size_t)p.tiles.max_tiles);
     p.tiles.tile_start = c.take<int32_t>((size_t)p.tiles.max_tiles);
     p.tiles.tile_count = c.take<int32_t>((size_t)p.tiles.max_tiles);
-    p.tiles.ntiles = c.take<int32_t>(2);
+    p.tiles.ntiles = c.take<int32_t>(3);
     p.tiles.cursor = c.take<int32_t>(1);
     p.err = c.take<int32_t>(1);
     return c.off;
