@@ -460,31 +460,47 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // Reference windows for one scale: row r = ((ref * nbands + band) * nv + v) * 48
 // + hilo * 24 + c * 3 + plane holds Lc elements W[t] = plane(w[(t + c) mod K'])
-// (plane 0: -Im, 1: Re, 2: Im), hi or lo part.
+// (plane 0: -Im, 1: Re, 2: Im), hi or lo part.  A block takes the hi and the
+// lo row of one (ref, band, v, c, plane); a thread 8 consecutive t (Lc and
+// K' are multiples of 64, so every chunk is one 16-byte store and its
+// indices wrap at most once).
 __global__ void pack_ref_kernel(const float2 *__restrict__ tree, int64_t tree_elems, int64_t N, int lev, int nbands,
                                 int ref0, int nrefs, int Lc, __nv_bfloat16 *__restrict__ out) {
     const int Kp = (int)(N >> lev), nv = 1 << lev;
-    const int rows_per_ref = nbands * nv * 48;
-    const int64_t r = (int64_t)blockIdx.x + (int64_t)ref0 * rows_per_ref;
-    const int ref = (int)(r / rows_per_ref);
+    const int pairs_per_ref = nbands * nv * 24;
+    const int64_t rp = (int64_t)blockIdx.x + (int64_t)ref0 * pairs_per_ref;
+    const int ref = (int)(rp / pairs_per_ref);
     if (ref >= ref0 + nrefs) return;
-    int rem = (int)(r % rows_per_ref);
+    int rem = (int)(rp % pairs_per_ref);
     const int plane = rem % 3;
     rem /= 3;
     const int c = rem % 8;
     rem /= 8;
-    const int hilo = rem % 2;
-    rem /= 2;
     const int vv = rem % nv;
     const int band = rem / nv;
     const float2 *w = tree + (int64_t)ref * tree_elems + 2 * N * (int64_t)(lev - 1) + (int64_t)band * N + (int64_t)vv * Kp;
-    __nv_bfloat16 *o = out + r * Lc;
-    for (int t = threadIdx.x; t < Lc; t += blockDim.x) {
-        const float2 x = w[(t + c) % Kp];
-        const float val = plane == 0 ? -x.y : (plane == 1 ? x.x : x.y);
-        __nv_bfloat16 hi, lo;
-        split_bf16(val, hi, lo);
-        o[t] = hilo ? lo : hi;
+    const int64_t row_hi = (((int64_t)ref * nbands + band) * nv + vv) * 48 + c * 3 + plane;
+    __nv_bfloat16 *oh = out + row_hi * Lc, *ol = out + (row_hi + 24) * Lc;
+    for (int q = threadIdx.x; q < Lc / 8; q += blockDim.x) {
+        const int t0 = 8 * q;
+        int idx = (t0 + c) % Kp;
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            const float2 x0 = w[idx];
+            if (++idx == Kp) idx = 0;
+            const float2 x1 = w[idx];
+            if (++idx == Kp) idx = 0;
+            const float v0 = plane == 0 ? -x0.y : (plane == 1 ? x0.x : x0.y);
+            const float v1 = plane == 0 ? -x1.y : (plane == 1 ? x1.x : x1.y);
+            __nv_bfloat16 h0, l0, h1, l1;
+            split_bf16(v0, h0, l0);
+            split_bf16(v1, h1, l1);
+            hw[e >> 1] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            lw[e >> 1] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        }
+        *reinterpret_cast<uint4 *>(oh + t0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(ol + t0) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
     }
 }
 
@@ -678,7 +694,8 @@ sidwt_status correlate_tc(sidwt_plan *p, int64_t B, float2 *r_dev, cudaStream_t 
             if (!(mask & (1u << j))) continue;
             const int lev = j < J ? j + 1 : J;
             const int nb = j < J ? 2 : 1;
-            const int64_t rows = (int64_t)(p->nrefs - p->tc_packed) * tc_rows_per_ref(p, j);
+            // one block per (hi, lo) row pair
+            const int64_t rows = (int64_t)(p->nrefs - p->tc_packed) * tc_rows_per_ref(p, j) / 2;
             tc::pack_ref_kernel<<<(unsigned)rows, 256, 0, s>>>(p->tree_f, p->tree_elems, N, lev, nb, p->tc_packed,
                                                   p->nrefs - p->tc_packed, tc_lc(N >> lev),
                                                   reinterpret_cast<__nv_bfloat16 *>(p->tc_ref[j]));
