@@ -79,3 +79,32 @@ def test_again_is_refused_without_a_matching_analysis(batch):
         p.reserve(3, 4 * B)  # the workspace is reallocated: the pyramids are gone
         with pytest.raises(sidwt.SidwtError, match="EINVAL.*last analysis"):
             p.correlate_again(ids)
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3"])
+def test_again_with_the_same_grouping_reuses_the_packed_operands(batch, precision):
+    """The same ids again: the pulses' packed operands are kept (the grouping
+    is stable and unchanged), and the result is the first call's, bit for
+    bit; then other ids (the grouping changes, so they are packed again) and
+    the first ids once more (packed again) give a fresh call's results."""
+    w = batch
+    y = U.to_dev_c64(w["y"])
+    g = np.random.default_rng(8)
+    ids_a = torch.from_numpy(g.integers(0, 3, B).astype(np.int32)).to(U.dev())
+    ids_b = torch.from_numpy(g.integers(0, 3, B).astype(np.int32)).to(U.dev())
+
+    def fresh(ids):
+        with plan_with_refs(w) as q:
+            r = q.correlate(ids, y, precision=precision, want_r=True)
+            return r.cpu().numpy(), [t.cpu().numpy() for t in q.peaks(B)]
+
+    want_a, want_b = fresh(ids_a), fresh(ids_b)
+    with plan_with_refs(w) as p:
+        p.correlate(ids_a, y, precision=precision)
+        for ids, want in ((ids_a, want_a), (ids_a, want_a), (ids_b, want_b), (ids_a, want_a)):
+            r = p.correlate_again(ids, precision=precision, want_r=True)
+            got = [t.cpu().numpy() for t in p.peaks(B)]
+            np.testing.assert_array_equal(r.cpu().numpy(), want[0])
+            for a, b in zip(got, want[1]):
+                np.testing.assert_array_equal(a, b)
+        p.check()
