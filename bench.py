@@ -14,7 +14,13 @@ Workload (one "step" = one pass of the whole path over one batch):
 `python bench.py --gpus N --steps K --warmup W` prints one JSON line.  With N
 ranks the batch is split: every rank stores both references and correlates a
 contiguous 1/N of the pulses, and the peak records are gathered in batch order
-after timing (total work fixed: "scaling": "strong").
+after timing (total work fixed: "scaling": "strong").  At N = 1 the line
+also carries short legs of the precision sweep, the 10000-pulse ragged batch
+and the serving loop (`other_configs`; `--no-extra` skips them), and its
+`e2e` runs the whole step from pinned host memory.
+`--workload {ragged,single,serve,sweep,store,c2f,multitarget,t97}` runs one of
+the other workloads on its own (ragged splits across ranks by pair cost; the
+rest run on rank 0).
 `--impl reference` times the FP64 CPU oracle on a bounded sample instead.
 """
 from __future__ import annotations
