@@ -518,8 +518,11 @@ def run_ours(args):
             stream_e2e.synchronize()
             return M.max_over_ranks((time.perf_counter() - t0) / k_e2e)
 
+        e2e_clocks = ClockSampler(local)
+        e2e_clocks.start()
         el_seq = timed(e2e_seq)
         el = timed(e2e_pipe)
+        e2e_clk = e2e_clocks.stop()
         lag_back = hout2[(max(1, args.steps) - 1) & 1]["cdf97"][0].numpy()[:, 0]
         # bytes per step over all ranks
         h2d = int(M.sum_over_ranks(2 * (y_pin.numel() * 8 + ids_pin.numel() * 4) + refs_pin.numel() * 8
@@ -533,6 +536,7 @@ def run_ours(args):
                        "pulses copied in on a copy stream beside the correlations, analysed, their energies "
                        "copied back",
                "peak_at_injected_delay_scale0": float(np.mean(lag_back == w["delays"])),
+               "clocks": e2e_clk,
                "sequential": {"value": total_pairs * N / el_seq / 1e9, "ms_per_step": el_seq * 1e3,
                               "path": "the same step with sidwt_correlate_host (blocking) per filter, one "
                                       "after the other"}}
